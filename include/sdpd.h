@@ -1,0 +1,201 @@
+/*
+ * sdpd.h -- C ABI of the GB300 library for one time step of Smoothed
+ * Dissipative Particle Dynamics (SDPD) integrated by Velocity Verlet and a
+ * Shardlow-like pairwise fluctuation/dissipation sweep with the Metropolis
+ * corrections of Faure & Stoltz, "Stable and accurate schemes for Smoothed
+ * Dissipative Particle Dynamics".
+ *
+ * Conventions shared by every call:
+ *  - Units are the caller's; kB is a parameter (1 in reduced units).
+ *  - Arrays cross the boundary in particle-id order: particle k of the array
+ *    given to sdpd_set_state has id k.  Positions and momenta are [N][3]
+ *    row-major float64, internal energies [N] float64.
+ *  - "on_device" = 1: the pointer is CUDA device memory of the current
+ *    device; 0: host memory (pinned or pageable).
+ *  - The caller owns every pointer it passes; the library copies from it and
+ *    keeps nothing.  Device memory of the library is one workspace that the
+ *    caller allocates (sdpd_workspace_bytes) and binds (sdpd_bind_workspace);
+ *    the library calls no allocator.
+ *  - Every call returns an int status (SDPD_OK = 0 or an SDPD_ERR_* code);
+ *    errors found by device code are sticky and are returned by the next
+ *    call that synchronises (sdpd_observables, sdpd_get_state, sdpd_sync).
+ *  - Work is enqueued on the CUDA stream given to sdpd_create.  Only the
+ *    calls documented as synchronising wait for it.
+ */
+#ifndef SDPD_H
+#define SDPD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define SDPD_OK 0
+#define SDPD_ERR_INVALID_ARG 1        /* a parameter is out of its domain */
+#define SDPD_ERR_BOX_TOO_SMALL 2      /* fewer than 4 cells (even) of side >= h on an axis */
+#define SDPD_ERR_NONPOSITIVE_ENERGY 3 /* sdpd_set_state got eps_i <= 0 or a non-finite value */
+#define SDPD_ERR_NEGATIVE_ENERGY 4    /* the SSA scheme produced eps_i <= 0 (no rejection in SSA) */
+#define SDPD_ERR_NAN 5                /* a non-finite momentum or energy was found */
+#define SDPD_ERR_CUDA 6               /* a CUDA runtime call failed */
+#define SDPD_ERR_TIMEOUT 7            /* a bounded device wait ran out */
+#define SDPD_ERR_NO_WORKSPACE 8       /* no (or too small a) workspace is bound */
+#define SDPD_ERR_CAPACITY 9           /* a 2x2x2 cell block exceeded its particle/pair capacity */
+#define SDPD_ERR_NO_STATE 10          /* sdpd_step/get_state before sdpd_set_state */
+
+/* smoothing kernels */
+#define SDPD_KERNEL_CUBIC 0 /* cubic spline, Eq. (sdpd-cubic-w) */
+#define SDPD_KERNEL_LUCY 1  /* Lucy: W = 105/(16 pi h^3)(1+3x)(1-x)^3, x = r/h */
+
+/* fluctuation/dissipation schemes */
+#define SDPD_SCHEME_SSA 0  /* Shardlow-like splitting, Section 3.2: every move accepted */
+#define SDPD_SCHEME_AMS 1  /* approximate Metropolis, Section 3.3.3: energy bound only */
+#define SDPD_SCHEME_EMS 2  /* exact Metropolis, Section 3.3.2: bound + ratio of Eq. (metropolis-ratio) */
+#define SDPD_SCHEME_NONE 3 /* Velocity Verlet only (the paper's "Verlet" timing reference) */
+
+/* arithmetic of the device path */
+#define SDPD_FP64 0  /* every operation in float64 */
+#define SDPD_MIXED 1 /* pair arithmetic in float32; eps, its updates and energy sums in float64 */
+
+typedef struct sdpd_handle sdpd_t;
+
+typedef struct {
+  double kB;     /* Boltzmann constant */
+  double eta;    /* shear viscosity eta > 0 (Section 2.2.2) */
+  double zeta;   /* bulk viscosity, 0 <= zeta < 5 eta / 3 so both kappa are > 0 */
+  double c_rho;  /* density coefficient of the ideal-gas entropy
+                    S = C_K ln eps - c_rho ln rho (Eq. pg-eos); < 0 selects (K-1)/2 */
+  int kernel;    /* SDPD_KERNEL_* */
+  int scheme;    /* SDPD_SCHEME_* */
+  int precision; /* SDPD_FP64 or SDPD_MIXED */
+  int fd_only;   /* 1: skip Velocity Verlet, run the fluctuation/dissipation sweep
+                    only (Section 4.1) */
+  int theta;     /* multiple time step ratio (Section 4.2): one sweep with time
+                    step theta*dt after every theta Verlet steps; 1 = single step */
+  int debug;     /* 1: reserve workspace for per-pair records (sdpd_debug_get) */
+} sdpd_params;
+
+/* Observables of the current state (Section 2.2: E and the total momentum
+ * are the invariants of the dynamics).  All sums in float64. */
+typedef struct {
+  double E;          /* total energy sum_i eps_i + |p_i|^2 / (2m) */
+  double E_int;      /* sum_i eps_i */
+  double E_kin;      /* sum_i |p_i|^2 / (2m) */
+  double P[3];       /* total momentum */
+  double T_kin;      /* sum_i |p_i|^2 / (3 (N-1) m kB) */
+  double T_int;      /* mean internal temperature (1/N) sum_i T(eps_i) */
+  double eps_min;    /* smallest internal energy */
+  int64_t n_pairs;   /* pair updates since the last counter reset */
+  int64_t n_accept;
+  int64_t n_reject_bound;      /* rejected by the energy bound, Eq. (energy-bound) */
+  int64_t n_reject_metropolis; /* rejected by U > A of Eq. (metropolis-ratio) */
+  int64_t fd_step;   /* fluctuation/dissipation sweeps done (the random-number step) */
+  int64_t vv_step;   /* Velocity Verlet steps done */
+  int status;        /* sticky device status (SDPD_OK or an error code) */
+} sdpd_obs;
+
+/* Create a handle for N particles in the periodic box [0,box[0]) x ... of the
+ * paper's problem statement (Section 2.1: N particles of mass m, smoothing
+ * length h; Section 4: ideal gas of particle size K, heat capacity
+ * C_K = 3/2 (K-1) kB).  Host only: validates the parameters (K > 4/3 so that
+ * d_ij < 1 in Eq. (sdpd-gamma-sigma); every box side gives an even number
+ * >= 4 of cells of side >= h), chooses the cell grid and the workspace size.
+ * stream: a cudaStream_t (NULL = the legacy default stream).
+ * Errors: SDPD_ERR_INVALID_ARG, SDPD_ERR_BOX_TOO_SMALL.  *out is NULL on error. */
+int sdpd_create(int64_t N, const double box[3], double m, double h, double K,
+                const sdpd_params* params, void* stream, sdpd_t** out);
+
+/* Bytes of device workspace the handle needs (256-byte aligned start). */
+size_t sdpd_workspace_bytes(const sdpd_t* s);
+
+/* Bind caller-allocated device memory of at least sdpd_workspace_bytes bytes
+ * on the current device.  The library never frees it.  Uploads the cell
+ * tables (asynchronous on the handle's stream).
+ * Errors: SDPD_ERR_NO_WORKSPACE (NULL, too small or misaligned), SDPD_ERR_CUDA. */
+int sdpd_bind_workspace(sdpd_t* s, void* device_ptr, size_t bytes);
+
+/* Load a state (q[N][3], p[N][3], eps[N], float64, id order) and prepare it:
+ * cell binning and sorting, then the densities of Eq. (sdpd-rho-v) and the
+ * pressures of Section 2.1.2.  Positions outside [0, L) are wrapped.  Resets
+ * the sweep counter (random-number step) to 0 and the pair counters.
+ * Host pointers are copied before the call returns; device pointers are read
+ * on the stream.  Errors: SDPD_ERR_NO_WORKSPACE, SDPD_ERR_NONPOSITIVE_ENERGY
+ * (eps_i <= 0 or non-finite, checked on the host when on_device = 0, else
+ * reported at the next synchronising call), SDPD_ERR_CUDA. */
+int sdpd_set_state(sdpd_t* s, const double* q, const double* p, const double* eps, int on_device);
+
+/* Copy the state back in id order (positions wrapped into [0, L)).
+ * Synchronises the stream; returns the sticky device status. */
+int sdpd_get_state(sdpd_t* s, double* q, double* p, double* eps, int on_device);
+
+/* Advance nsteps Velocity Verlet steps of size dt (Eq. sdpd-verlet, entropies
+ * fixed during the step, Section 3.1), each followed -- every theta steps --
+ * by one fluctuation/dissipation sweep over all pairs r_ij < h with step
+ * theta*dt (Sections 3.2-3.3).  The sweep visits the pairs in the colour
+ * order of the library (8 cell-parity colours; within a colour the 2x2x2
+ * cell blocks are independent; within a block pairs go by (min id, max id))
+ * and draws the pair's random numbers from Philox4x64-10 keyed by seed with
+ * counter (sweep number, min id, max id, 0).  Asynchronous on the handle's
+ * stream.  Errors: SDPD_ERR_INVALID_ARG (dt <= 0, nsteps < 0),
+ * SDPD_ERR_NO_STATE, SDPD_ERR_CUDA; device errors are sticky. */
+int sdpd_step(sdpd_t* s, double dt, int64_t nsteps, uint64_t seed);
+
+/* Reduce the observables of the current state (float64) and copy them to
+ * *out.  Synchronises the stream; returns out->status. */
+int sdpd_observables(sdpd_t* s, sdpd_obs* out);
+
+/* Wait for the stream; return the sticky device status. */
+int sdpd_sync(sdpd_t* s);
+
+/* Set / read the sweep counter (the random-number step), e.g. to resume a
+ * run from a saved state: 20 steps equal 10 steps, sdpd_get_state,
+ * sdpd_set_state, sdpd_set_fd_step(10), 10 steps. */
+int sdpd_set_fd_step(sdpd_t* s, int64_t fd_step);
+int64_t sdpd_get_fd_step(const sdpd_t* s);
+
+/* Reset the pair counters of sdpd_obs. */
+int sdpd_reset_counters(sdpd_t* s);
+
+/* Debug read-outs (synchronising).  what:
+ *  SDPD_DEBUG_ORDER   int64[N]   ids in storage order (Morton order of cells, then id)
+ *  SDPD_DEBUG_CELLS   int32[N][3] cell of each particle, id order
+ *  SDPD_DEBUG_RHO     double[N]  density rho_i, id order
+ *  SDPD_DEBUG_FORCE   double[N][3] conservative force of Eq. (cons-forces) at the
+ *                     current state, id order (computed on demand)
+ *  SDPD_DEBUG_NCOUNT  int32[N]   number of neighbours j != i with r_ij < h, id order
+ *  SDPD_DEBUG_PAIRS   sdpd_pair_rec[] of the last sweep (needs params.debug = 1),
+ *                     one per pair in an order of the library's choosing
+ * dst: host memory, cap = capacity in elements; *count receives the number
+ * of elements written.  Errors: SDPD_ERR_INVALID_ARG (unknown what or too
+ * small cap), SDPD_ERR_NO_STATE. */
+#define SDPD_DEBUG_ORDER 0
+#define SDPD_DEBUG_CELLS 1
+#define SDPD_DEBUG_RHO 2
+#define SDPD_DEBUG_FORCE 3
+#define SDPD_DEBUG_NCOUNT 4
+#define SDPD_DEBUG_PAIRS 5
+
+typedef struct {
+  int64_t id_i, id_j; /* id_i < id_j */
+  int32_t colour;     /* 0..7 */
+  int32_t owner;      /* owner cell ox + nx (oy + ny oz) */
+  int32_t decision;   /* 0 accept, 1 energy-bound reject, 2 Metropolis reject */
+  int32_t level;      /* position of the pair in its block's dependency schedule */
+  double margin;      /* EMS: a - ln U; otherwise the smaller new internal energy */
+} sdpd_pair_rec;
+
+int sdpd_debug_get(sdpd_t* s, int what, void* dst, int64_t cap, int64_t* count);
+
+/* Free the handle (not the workspace). */
+void sdpd_destroy(sdpd_t* s);
+
+/* Static text for a status code. */
+const char* sdpd_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SDPD_H */

@@ -31,8 +31,10 @@
  *      fixed, then one fluctuation/dissipation sweep; the first kick of every
  *      step is recomputed with the current (post-sweep) pressures.
  *  R12 sweep order: colour 0..7, owner cells of that colour by linear index,
- *      then pairs by (min id, max id).  Colour and owner are defined in
- *      orc_pair_owner below.
+ *      then, inside the owner's 2x2x2 block of cells, pairs by
+ *      (rank(j) - rank(i), rank(i)), where rank(x) is the position of x's id
+ *      among the ids of all particles in the block's 8 cells and i is the
+ *      lower id.  Colour and owner are defined in orc_pair_owner below.
  *  R13 the energy bound of Eq. (energy-bound) rejects iff the smaller new
  *      internal energy is <= 0; the Metropolis step rejects iff U > exp(a).
  *      The internal-energy change is -1/2 of the change of the pair's kinetic
@@ -537,15 +539,67 @@ int orc_pair_owner(const orc_params* P, const int32_t ca[3], const int32_t cb[3]
 typedef struct {
   int64_t i, j;
   int32_t colour, owner;
+  int32_t rank_i, rank_j; /* ranks of the ids inside the owner's block */
 } orc_pair;
 
 static int cmp_pair(const void* a, const void* b) {
   const orc_pair* x = (const orc_pair*)a; const orc_pair* y = (const orc_pair*)b;
   if (x->colour != y->colour) return x->colour < y->colour ? -1 : 1;
   if (x->owner != y->owner) return x->owner < y->owner ? -1 : 1;
-  if (x->i != y->i) return x->i < y->i ? -1 : 1;
-  if (x->j != y->j) return x->j < y->j ? -1 : 1;
+  int32_t dx = x->rank_j - x->rank_i, dy = y->rank_j - y->rank_i;
+  if (dx != dy) return dx < dy ? -1 : 1;
+  if (x->rank_i != y->rank_i) return x->rank_i < y->rank_i ? -1 : 1;
   return 0;
+}
+
+/* Cells of all particles as linear indices, and per cell its member ids in
+ * ascending order (cell_off[c] .. cell_off[c+1] in cell_mem). */
+typedef struct {
+  int64_t* cell_off;
+  int64_t* cell_mem;
+} orc_cell_lists;
+
+static int build_cell_lists(const orc_params* P, const double* q, orc_cell_lists* cl) {
+  int64_t ncell = (int64_t)P->n_c[0] * P->n_c[1] * P->n_c[2];
+  cl->cell_off = (int64_t*)calloc((size_t)(ncell + 1), sizeof(int64_t));
+  cl->cell_mem = (int64_t*)malloc(sizeof(int64_t) * (size_t)(P->N ? P->N : 1));
+  int64_t* lin = (int64_t*)malloc(sizeof(int64_t) * (size_t)(P->N ? P->N : 1));
+  if (!cl->cell_off || !cl->cell_mem || !lin) return ORC_ERR_ALLOC;
+  for (int64_t k = 0; k < P->N; ++k) {
+    int c[3];
+    for (int a = 0; a < 3; ++a) c[a] = orc_cell_1d(P, a, q[3 * k + a]);
+    lin[k] = c[0] + (int64_t)P->n_c[0] * (c[1] + (int64_t)P->n_c[1] * c[2]);
+    cl->cell_off[lin[k] + 1]++;
+  }
+  for (int64_t c = 0; c < ncell; ++c) cl->cell_off[c + 1] += cl->cell_off[c];
+  int64_t* fill = (int64_t*)calloc((size_t)(ncell ? ncell : 1), sizeof(int64_t));
+  for (int64_t k = 0; k < P->N; ++k) /* ids ascending -> each list sorted */
+    cl->cell_mem[cl->cell_off[lin[k]] + fill[lin[k]]++] = k;
+  free(fill);
+  free(lin);
+  return ORC_OK;
+}
+
+/* rank of id among the particles of the 2x2x2 block of cells starting at the
+ * owner cell: the number of particles in those 8 cells with a smaller id. */
+static int32_t block_rank(const orc_params* P, const orc_cell_lists* cl, int64_t owner, int64_t id) {
+  int o[3] = {(int)(owner % P->n_c[0]), (int)((owner / P->n_c[0]) % P->n_c[1]),
+              (int)(owner / ((int64_t)P->n_c[0] * P->n_c[1]))};
+  int32_t r = 0;
+  for (int d = 0; d < 8; ++d) {
+    int c[3] = {(o[0] + (d & 1)) % P->n_c[0], (o[1] + ((d >> 1) & 1)) % P->n_c[1],
+                (o[2] + ((d >> 2) & 1)) % P->n_c[2]};
+    int64_t lc = c[0] + (int64_t)P->n_c[0] * (c[1] + (int64_t)P->n_c[1] * c[2]);
+    /* members of cell lc with an id below id: binary search of the sorted list */
+    int64_t lo = cl->cell_off[lc], hi = cl->cell_off[lc + 1];
+    while (lo < hi) {
+      int64_t mid = lo + (hi - lo) / 2;
+      if (cl->cell_mem[mid] < id) lo = mid + 1;
+      else hi = mid;
+    }
+    r += (int32_t)(lo - cl->cell_off[lc]);
+  }
+  return r;
 }
 
 /* All pairs i < j with r_ij < h, in sweep order.  Caller frees *out. */
@@ -595,6 +649,16 @@ int orc_enumerate_pairs(const orc_params* P, const double* q, orc_pair** out, in
     }
   }
   free(cnt);
+  /* ranks of the two ids inside the owner's block */
+  orc_cell_lists cl;
+  if (build_cell_lists(P, q, &cl) != ORC_OK) { free(pr); return ORC_ERR_ALLOC; }
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t k = 0; k < np; ++k) {
+    pr[k].rank_i = block_rank(P, &cl, pr[k].owner, pr[k].i);
+    pr[k].rank_j = block_rank(P, &cl, pr[k].owner, pr[k].j);
+  }
+  free(cl.cell_off);
+  free(cl.cell_mem);
   qsort(pr, (size_t)np, sizeof(orc_pair), cmp_pair);
   *out = pr;
   *npairs = np;

@@ -1,0 +1,296 @@
+// sdpd_internal.cuh -- device building blocks and the handle layout shared by
+// the translation units of the SDPD library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sdpd.h"
+
+namespace sdpd {
+
+// ---------------------------------------------------------------------------
+// Capacities of one 2x2x2 block of cells (the unit of the pair colouring).
+// ---------------------------------------------------------------------------
+constexpr int kMaxBlock = 256;   // particles in a block (8-bit local index)
+constexpr int kMaxPairs = 2048;  // owned pairs of a block
+constexpr int kMaxLevels = 255;  // dependency levels of a block's pair schedule
+
+// Sticky device status bits, mapped to SDPD_ERR_* on the host.
+enum : int {
+  kStNegative = 1,    // SSA produced eps <= 0
+  kStNaN = 2,         // non-finite momentum / energy
+  kStCapacity = 4,    // block capacity exceeded
+  kStBadEnergy = 8,   // set_state got eps <= 0
+};
+
+// Per-run constants; every kernel gets a copy by value.
+struct Consts {
+  int64_t N;
+  int nc[3];
+  int ncell;
+  double L[3], halfL[3], cs[3];
+  double scale[3];      // mixed precision: box side / 2^32 (fixed-point unit)
+  double inv_scale[3];  // 2^32 / box side
+  double h, h2, m, kB;
+  double C_K, c_rho;
+  double kpar_m2, kperp_m2;  // (10/3 eta + 4 zeta) m^2 and (5/3 eta - zeta) m^2
+  double cW, cF, W0;         // kernel constants and W(0)
+  int kernel, scheme;
+};
+
+// ---------------------------------------------------------------------------
+// Smoothing kernels of Section 2.1.1 as functions of x = r/h in [0, 1).
+// W: cubic spline of Eq. (sdpd-cubic-w) (cW = 8/(pi h^3)) or Lucy's kernel
+// (cW = 105/(16 pi h^3)).  F with grad W = -F(r) r: cubic cF = 48/(pi h^5),
+// outer branch (h/r)(1-x)^2; Lucy cF = 315/(4 pi h^5), F = cF (1-x)^2.
+// ---------------------------------------------------------------------------
+template <int KIND, class R>
+__device__ __forceinline__ R kernel_W(R x, R cW) {
+  R y = R(1) - x;
+  if (KIND == SDPD_KERNEL_LUCY) return cW * (R(1) + R(3) * x) * (y * y * y);
+  if (x <= R(0.5)) return cW * (R(1) - R(6) * x * x + R(6) * x * x * x);
+  return R(2) * cW * (y * y * y);
+}
+
+template <int KIND, class R>
+__device__ __forceinline__ R kernel_F(R x, R cF) {
+  R y = R(1) - x;
+  if (KIND == SDPD_KERNEL_LUCY) return cF * (y * y);
+  if (x <= R(0.5)) return cF * (R(2) - R(3) * x);
+  return cF * (y * y) / x;
+}
+
+// ---------------------------------------------------------------------------
+// Philox4x64-10 counter-based generator (Salmon, Moraes, Dror, Shaw, SC'11):
+// ten rounds of (multiply words 0 and 2 by the round constants; swap the
+// halves, xoring the high halves with words 1, 3 and the key), the key
+// advanced by the Weyl increments between rounds.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void philox4x64_10(uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3,
+                                              uint64_t k0, uint64_t k1, uint64_t out[4]) {
+  const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+  const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    uint64_t hi0 = __umul64hi(M0, c0), lo0 = M0 * c0;
+    uint64_t hi1 = __umul64hi(M1, c2), lo1 = M1 * c2;
+    uint64_t y0 = hi1 ^ c1 ^ k0, y2 = hi0 ^ c3 ^ k1;
+    c0 = y0; c1 = lo1; c2 = y2; c3 = lo0;
+    k0 += W0; k1 += W1;
+  }
+  out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+// Random numbers of one pair at one sweep: G ~ N(0, I3) and U ~ U(0,1).
+// Key (seed, 0), counter (sweep, id_min, id_max, 0).  Words 0 and 1 give G0,
+// G1 by Box-Muller on two uniforms; word 2 gives G2 by Box-Muller on its two
+// 32-bit halves; word 3 gives U.  float64: 53-bit uniforms (32-bit for G2);
+// float32: 23-bit uniforms from the top bits of the same words.
+__device__ __forceinline__ void pair_randoms(uint64_t seed, uint64_t sweep, uint64_t idi, uint64_t idj,
+                                             double G[3], double* U) {
+  uint64_t w[4];
+  philox4x64_10(sweep, idi, idj, 0ull, seed, 0ull, w);
+  const double two53 = 1.0 / 9007199254740992.0, two32 = 1.0 / 4294967296.0;
+  double u0 = ((double)(w[0] >> 11) + 0.5) * two53;
+  double u1 = ((double)(w[1] >> 11) + 0.5) * two53;
+  double R = sqrt(-2.0 * log(u0));
+  double s, c;
+  sincospi(2.0 * u1, &s, &c);
+  G[0] = R * c;
+  G[1] = R * s;
+  double u2 = ((double)(uint32_t)(w[2] >> 32) + 0.5) * two32;
+  double u3 = ((double)(uint32_t)(w[2] & 0xffffffffull) + 0.5) * two32;
+  G[2] = sqrt(-2.0 * log(u2)) * cospi(2.0 * u3);
+  *U = ((double)(w[3] >> 11) + 0.5) * two53;
+}
+
+__device__ __forceinline__ void pair_randoms(uint64_t seed, uint64_t sweep, uint64_t idi, uint64_t idj,
+                                             float G[3], float* U) {
+  uint64_t w[4];
+  philox4x64_10(sweep, idi, idj, 0ull, seed, 0ull, w);
+  const float two23 = 1.0f / 8388608.0f;
+  float u0 = ((float)(uint32_t)(w[0] >> 41) + 0.5f) * two23;
+  float u1 = ((float)(uint32_t)(w[1] >> 41) + 0.5f) * two23;
+  float R = sqrtf(-2.0f * logf(u0));
+  float s, c;
+  sincospif(2.0f * u1, &s, &c);
+  G[0] = R * c;
+  G[1] = R * s;
+  float u2 = ((float)(uint32_t)(w[2] >> 41) + 0.5f) * two23;
+  float u3 = ((float)((uint32_t)(w[2] & 0xffffffffull) >> 9) + 0.5f) * two23;
+  G[2] = sqrtf(-2.0f * logf(u2)) * cospif(2.0f * u3);
+  *U = ((float)(uint32_t)(w[3] >> 41) + 0.5f) * two23;
+}
+
+// ---------------------------------------------------------------------------
+// Precision policies.
+//   Fp64: positions float64 absolute in [0, L); all arithmetic float64.
+//   Mixed: positions 32-bit fixed point (x = u * L / 2^32, so the periodic
+//   wrap and the minimum image are integer wrap-around); pair arithmetic in
+//   float32 on cell-relative coordinates; eps in float64.
+// ---------------------------------------------------------------------------
+struct alignas(32) D4 { double x, y, z, w; };
+struct alignas(16) F4 { float x, y, z, w; };
+
+struct Fp64 {
+  using R = double;   // pair arithmetic, momenta, densities
+  using V4 = D4;      // (x, y, z, w) records
+  using Q = double;   // stored position component
+  static constexpr bool mixed = false;
+};
+struct Mixed {
+  using R = float;
+  using V4 = F4;
+  using Q = uint32_t;
+  static constexpr bool mixed = true;
+};
+
+// Packed cell coordinates (10 bits per axis).
+__host__ __device__ __forceinline__ uint32_t pack_cell(int cx, int cy, int cz) {
+  return (uint32_t)cx | ((uint32_t)cy << 10) | ((uint32_t)cz << 20);
+}
+__host__ __device__ __forceinline__ void unpack_cell(uint32_t c, int& cx, int& cy, int& cz) {
+  cx = (int)(c & 1023u); cy = (int)((c >> 10) & 1023u); cz = (int)(c >> 20);
+}
+
+__device__ __forceinline__ D4 ld4(const D4* p) {
+  const double2* q = reinterpret_cast<const double2*>(p);
+  double2 a = __ldg(q), b = __ldg(q + 1);
+  return D4{a.x, a.y, b.x, b.y};
+}
+__device__ __forceinline__ F4 ld4(const F4* p) {
+  float4 a = __ldg(reinterpret_cast<const float4*>(p));
+  return F4{a.x, a.y, a.z, a.w};
+}
+__device__ __forceinline__ void st4(D4* p, const D4& v) {
+  double2* q = reinterpret_cast<double2*>(p);
+  q[0] = make_double2(v.x, v.y);
+  q[1] = make_double2(v.z, v.w);
+}
+__device__ __forceinline__ void st4(F4* p, const F4& v) {
+  *reinterpret_cast<float4*>(p) = make_float4(v.x, v.y, v.z, v.w);
+}
+__device__ __forceinline__ double cellbits_to_w(uint32_t c, D4*) { return (double)c; }
+__device__ __forceinline__ float cellbits_to_w(uint32_t c, F4*) { return __uint_as_float(c); }
+__device__ __forceinline__ uint32_t w_to_cellbits(double w) { return (uint32_t)w; }
+__device__ __forceinline__ uint32_t w_to_cellbits(float w) { return __float_as_uint(w); }
+
+// Periodic minimum image of a float64 displacement (compare and subtract).
+__device__ __forceinline__ double min_image(double d, double L, double halfL) {
+  if (d > halfL) return __dsub_rn(d, L);
+  if (d < -halfL) return __dadd_rn(d, L);
+  return d;
+}
+// r^2 with the fused multiply-adds written out (fixed rounding sequence).
+__device__ __forceinline__ double r2_of(double dx, double dy, double dz) {
+  return __fma_rn(dz, dz, __fma_rn(dy, dy, __dmul_rn(dx, dx)));
+}
+__device__ __forceinline__ float r2_of(float dx, float dy, float dz) {
+  return __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+}
+
+// ---------------------------------------------------------------------------
+// Device state of one handle.
+// ---------------------------------------------------------------------------
+template <class P>
+struct Arrays {
+  using R = typename P::R;
+  using V4 = typename P::V4;
+  using Q = typename P::Q;
+  V4* q4;      // sorted: (x, y, z, cell bits); mixed: cell-relative float coordinates
+  Q* qx;       // sorted positions (float64 absolute or 32-bit fixed point)
+  Q* qy;
+  Q* qz;
+  R* px;
+  R* py;
+  R* pz;
+  double* eps;
+  R* rho;
+  int32_t* id;
+};
+
+struct Workspace {
+  // two copies of the sorted state (A = current, B = sort target); typed
+  // views are made per precision from these raw pointers
+  void* q4[2];
+  void* qx[2];
+  void* qy[2];
+  void* qz[2];
+  void* px[2];
+  void* py[2];
+  void* pz[2];
+  double* eps[2];
+  void* rho[2];
+  int32_t* id[2];
+  void* qp4;            // sorted (x, y, z, pi): positions and p/rho^2 for force passes
+  // binning and sorting scratch
+  int32_t* key;         // cell rank per particle (old order)
+  int32_t* slot;        // arrival slot in the cell (old order)
+  int32_t* tmp;         // bucketed old indices
+  void* qdx;            // drifted positions, old order
+  void* qdy;
+  void* qdz;
+  int32_t* cell_count;  // [ncell] (kept zero between uses)
+  int32_t* cell_start;  // [ncell + 1]
+  int32_t* mrank;       // linear cell -> Morton rank
+  uint32_t* rcoord;     // Morton rank -> packed cell coordinates
+  uint32_t* xmin[3];    // mixed: fixed-point lower edge of each cell, per axis
+  // pair schedule of the fluctuation/dissipation sweep (per owner cell)
+  uint32_t* sched_hdr;    // npairs | nlevels << 16
+  uint16_t* sched_lvl;    // [ncell][kMaxLevels + 1] level offsets
+  uint16_t* sched_pair;   // [ncell][kMaxPairs] (local min-id | local max-id << 8)
+  // host <-> device staging in id order (float64)
+  double* io_q;
+  double* io_p;
+  double* io_e;
+  // reductions and status
+  double* obs_partial;        // [kObsBlocks][8]
+  double* obs;                // [8]
+  unsigned long long* counters;  // [4]: pairs, accept, reject bound, reject metropolis
+  int* status;
+  sdpd_pair_rec* pair_recs;   // debug
+  unsigned long long* pair_rec_count;
+  int64_t pair_rec_cap;
+};
+
+constexpr int kObsBlocks = 304;
+
+template <class P>
+Arrays<P> view(const Workspace& w, int k) {
+  Arrays<P> a;
+  a.q4 = (typename P::V4*)w.q4[k];
+  a.qx = (typename P::Q*)w.qx[k];
+  a.qy = (typename P::Q*)w.qy[k];
+  a.qz = (typename P::Q*)w.qz[k];
+  a.px = (typename P::R*)w.px[k];
+  a.py = (typename P::R*)w.py[k];
+  a.pz = (typename P::R*)w.pz[k];
+  a.eps = w.eps[k];
+  a.rho = (typename P::R*)w.rho[k];
+  a.id = w.id[k];
+  return a;
+}
+
+// ---------------------------------------------------------------------------
+// Launchers (host side), one per pipeline stage; P in {Fp64, Mixed}.
+// ---------------------------------------------------------------------------
+template <class P>
+void launch_load(const Consts& c, const Workspace& w, cudaStream_t s);
+template <class P>
+void launch_sort(const Consts& c, const Workspace& w, int from, cudaStream_t s);
+template <class P>
+void launch_unload(const Consts& c, const Workspace& w, int cur, cudaStream_t s);
+template <class P>
+void launch_density(const Consts& c, const Workspace& w, int cur, int update_eos, int32_t* ncount_by_id,
+                    cudaStream_t s);
+template <class P>
+void launch_force(const Consts& c, const Workspace& w, int cur, double half_dt, double dt_drift,
+                  double* force_by_id, cudaStream_t s);
+template <class P>
+void launch_fd(const Consts& c, const Workspace& w, int cur, double dt, uint64_t seed, uint64_t sweep,
+               int record, cudaStream_t s);
+template <class P>
+void launch_observables(const Consts& c, const Workspace& w, int cur, cudaStream_t s);
+
+}  // namespace sdpd

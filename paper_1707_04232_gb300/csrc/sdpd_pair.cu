@@ -1,0 +1,274 @@
+// sdpd_pair.cu -- the two pair passes of Velocity Verlet: the density sum of
+// Eq. (sdpd-rho-v) with the equation-of-state update of Section 3.1, and the
+// conservative force of Eq. (cons-forces) with the half kick (and, for the
+// first kick of a step, the drift and the cell binning of the new position).
+//
+// One thread per particle in storage order; the neighbour search walks the
+// 27 cells around the particle's cell (cell side >= h) with the predicate
+// r^2 < h^2 after the periodic minimum image.
+#include "sdpd_internal.cuh"
+
+namespace sdpd {
+
+// Geometry of one home particle: displacement to a neighbour j.
+// Float64: absolute coordinates and the minimum image.
+// Mixed: coordinates relative to the own cell's lower corner; per axis and
+// neighbour offset o in {-1, 0, +1} the home coordinate shifted by the
+// (exact, fixed-point) distance between the two cells' corners.
+template <class P>
+struct Home;
+
+template <>
+struct Home<Fp64> {
+  double x, y, z, L[3], halfL[3];
+  __device__ void init(const Consts& c, const D4& q, int, int, int, const uint32_t*, const uint32_t*,
+                       const uint32_t*) {
+    x = q.x; y = q.y; z = q.z;
+    for (int d = 0; d < 3; ++d) { L[d] = c.L[d]; halfL[d] = c.halfL[d]; }
+  }
+  __device__ __forceinline__ void disp(int, int, int, const D4& qj, double& dx, double& dy,
+                                       double& dz) const {
+    dx = min_image(__dsub_rn(x, qj.x), L[0], halfL[0]);
+    dy = min_image(__dsub_rn(y, qj.y), L[1], halfL[1]);
+    dz = min_image(__dsub_rn(z, qj.z), L[2], halfL[2]);
+  }
+};
+
+template <>
+struct Home<Mixed> {
+  float hx[3], hy[3], hz[3];
+  __device__ void init(const Consts& c, const F4& q, int cx, int cy, int cz, const uint32_t* xmx,
+                       const uint32_t* xmy, const uint32_t* xmz) {
+    const float sx = (float)c.scale[0], sy = (float)c.scale[1], sz = (float)c.scale[2];
+    for (int o = -1; o <= 1; ++o) {
+      int nx = cx + o, ny = cy + o, nz = cz + o;
+      nx += nx < 0 ? c.nc[0] : (nx >= c.nc[0] ? -c.nc[0] : 0);
+      ny += ny < 0 ? c.nc[1] : (ny >= c.nc[1] ? -c.nc[1] : 0);
+      nz += nz < 0 ? c.nc[2] : (nz >= c.nc[2] ? -c.nc[2] : 0);
+      hx[o + 1] = q.x + (float)(int32_t)(xmx[cx] - xmx[nx]) * sx;
+      hy[o + 1] = q.y + (float)(int32_t)(xmy[cy] - xmy[ny]) * sy;
+      hz[o + 1] = q.z + (float)(int32_t)(xmz[cz] - xmz[nz]) * sz;
+    }
+  }
+  __device__ __forceinline__ void disp(int ox, int oy, int oz, const F4& qj, float& dx, float& dy,
+                                       float& dz) const {
+    dx = hx[ox + 1] - qj.x;
+    dy = hy[oy + 1] - qj.y;
+    dz = hz[oz + 1] - qj.z;
+  }
+};
+
+__device__ __forceinline__ int wrapc(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+
+// ---------------------------------------------------------------------------
+// Density, Eq. (sdpd-rho-v): rho_i = m W(0) + sum_{j != i, r_ij < h} m W(r_ij);
+// then the energies at fixed entropy (Section 3.1): S_i = S(eps_i, rho_old),
+// eps_i = E(S_i, rho_i), and pi_i = P_i / rho_i^2 from Eq. (pg-eos):
+// P = c_rho rho eps / (C_K m).
+// ---------------------------------------------------------------------------
+template <class P, int KIND>
+__global__ void __launch_bounds__(128) k_density(Consts c, Arrays<P> a, typename P::V4* __restrict__ qp4,
+                                                 const int32_t* __restrict__ cell_start,
+                                                 const int32_t* __restrict__ mrank,
+                                                 const uint32_t* __restrict__ xmx,
+                                                 const uint32_t* __restrict__ xmy,
+                                                 const uint32_t* __restrict__ xmz, int update_eos,
+                                                 int32_t* __restrict__ ncount_by_id) {
+  using R = typename P::R;
+  using V4 = typename P::V4;
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= c.N) return;
+  const V4 qi = ld4(&a.q4[i]);
+  int cx, cy, cz;
+  unpack_cell(w_to_cellbits(qi.w), cx, cy, cz);
+  Home<P> home;
+  home.init(c, qi, cx, cy, cz, xmx, xmy, xmz);
+  const R h2 = (R)c.h2, inv_h = R(1) / (R)c.h, cW = (R)c.cW;
+  R acc = R(0);
+  int cnt = 0;
+  for (int oz = -1; oz <= 1; ++oz) {
+    const int nz = wrapc(cz + oz, c.nc[2]);
+    for (int oy = -1; oy <= 1; ++oy) {
+      const int ny = wrapc(cy + oy, c.nc[1]);
+      for (int ox = -1; ox <= 1; ++ox) {
+        const int nx = wrapc(cx + ox, c.nc[0]);
+        const int r = __ldg(&mrank[nx + c.nc[0] * (ny + c.nc[1] * nz)]);
+        const int beg = __ldg(&cell_start[r]), end = __ldg(&cell_start[r + 1]);
+        for (int j = beg; j < end; ++j) {
+          if (j == i) continue;
+          const V4 qj = ld4(&a.q4[j]);
+          R dx, dy, dz;
+          home.disp(ox, oy, oz, qj, dx, dy, dz);
+          const R r2 = r2_of(dx, dy, dz);
+          if (r2 < h2) {
+            acc += kernel_W<KIND>(sqrt(r2) * inv_h, cW);
+            ++cnt;
+          }
+        }
+      }
+    }
+  }
+  if (ncount_by_id) ncount_by_id[a.id[i]] = cnt;
+  const R rho_new = (R)c.m * ((R)c.W0 + acc);
+  double e = a.eps[i];
+  if (update_eos) {
+    if constexpr (P::mixed) {
+      // eps * (rho_new / rho_old)^(c_rho / C_K), the factor minus one formed
+      // from log1p / expm1 of small arguments so float32 keeps it accurate
+      const float ro = a.rho[i];
+      const float g = expm1f((float)(c.c_rho / c.C_K) * log1pf((rho_new - ro) / ro));
+      e = fma(e, (double)g, e);
+    } else {
+      const double S = c.C_K * log(e) - c.c_rho * log((double)a.rho[i]);
+      e = exp((S + c.c_rho * log((double)rho_new)) / c.C_K);
+    }
+    a.eps[i] = e;
+  }
+  a.rho[i] = rho_new;
+  R pi;
+  if constexpr (P::mixed) pi = (float)e * (float)(c.c_rho / (c.C_K * c.m)) / rho_new;
+  else pi = c.c_rho * e / (c.C_K * c.m * rho_new);
+  V4 o = qi;
+  o.w = pi;
+  st4(&qp4[i], o);
+}
+
+// ---------------------------------------------------------------------------
+// Conservative force, Eq. (cons-forces): F_i = sum_{j != i, r_ij < h}
+// m^2 (pi_i + pi_j) F(r_ij) r_ij, and the kick p_i += F_i dt/2 of Eq.
+// (sdpd-verlet).  With drift: q_i += p_i dt/m (wrapped), new cell counted
+// for the sort.
+// ---------------------------------------------------------------------------
+template <class P, int KIND>
+__global__ void __launch_bounds__(128) k_force(Consts c, Arrays<P> a, const typename P::V4* __restrict__ qp4,
+                                               const int32_t* __restrict__ cell_start,
+                                               const int32_t* __restrict__ mrank,
+                                               const uint32_t* __restrict__ xmx,
+                                               const uint32_t* __restrict__ xmy,
+                                               const uint32_t* __restrict__ xmz, double half_dt,
+                                               double dt_drift, typename P::Q* __restrict__ qdx,
+                                               typename P::Q* __restrict__ qdy,
+                                               typename P::Q* __restrict__ qdz, int32_t* __restrict__ key,
+                                               int32_t* __restrict__ slot, int32_t* __restrict__ cell_count,
+                                               double* __restrict__ force_by_id) {
+  using R = typename P::R;
+  using V4 = typename P::V4;
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= c.N) return;
+  const V4 qi = ld4(&a.q4[i]);
+  const R pi_i = ld4(&qp4[i]).w;
+  int cx, cy, cz;
+  unpack_cell(w_to_cellbits(qi.w), cx, cy, cz);
+  Home<P> home;
+  home.init(c, qi, cx, cy, cz, xmx, xmy, xmz);
+  const R h2 = (R)c.h2, inv_h = R(1) / (R)c.h, cF = (R)c.cF;
+  R fx = R(0), fy = R(0), fz = R(0);
+  for (int oz = -1; oz <= 1; ++oz) {
+    const int nz = wrapc(cz + oz, c.nc[2]);
+    for (int oy = -1; oy <= 1; ++oy) {
+      const int ny = wrapc(cy + oy, c.nc[1]);
+      for (int ox = -1; ox <= 1; ++ox) {
+        const int nx = wrapc(cx + ox, c.nc[0]);
+        const int r = __ldg(&mrank[nx + c.nc[0] * (ny + c.nc[1] * nz)]);
+        const int beg = __ldg(&cell_start[r]), end = __ldg(&cell_start[r + 1]);
+        for (int j = beg; j < end; ++j) {
+          if (j == i) continue;
+          const V4 qj = ld4(&qp4[j]);
+          R dx, dy, dz;
+          home.disp(ox, oy, oz, qj, dx, dy, dz);
+          const R r2 = r2_of(dx, dy, dz);
+          if (r2 < h2) {
+            const R s = (pi_i + qj.w) * kernel_F<KIND>(sqrt(r2) * inv_h, cF);
+            fx += s * dx;
+            fy += s * dy;
+            fz += s * dz;
+          }
+        }
+      }
+    }
+  }
+  const R m2 = (R)(c.m * c.m);
+  fx *= m2; fy *= m2; fz *= m2;
+  if (force_by_id) {
+    const int64_t k = a.id[i];
+    force_by_id[3 * k] = fx;
+    force_by_id[3 * k + 1] = fy;
+    force_by_id[3 * k + 2] = fz;
+  }
+  const R hdt = (R)half_dt;
+  R px = a.px[i] + fx * hdt, py = a.py[i] + fy * hdt, pz = a.pz[i] + fz * hdt;
+  a.px[i] = px; a.py[i] = py; a.pz[i] = pz;
+  if (dt_drift != 0.0) {
+    int nc3[3];
+    if constexpr (P::mixed) {
+      // fixed point: the displacement in units of L / 2^32, wrap-around = periodic
+      const float k = (float)(dt_drift / c.m);
+      uint32_t ux = a.qx[i] + (uint32_t)__float2int_rn(px * k * (float)c.inv_scale[0]);
+      uint32_t uy = a.qy[i] + (uint32_t)__float2int_rn(py * k * (float)c.inv_scale[1]);
+      uint32_t uz = a.qz[i] + (uint32_t)__float2int_rn(pz * k * (float)c.inv_scale[2]);
+      qdx[i] = ux; qdy[i] = uy; qdz[i] = uz;
+      nc3[0] = (int)__umulhi(ux, (uint32_t)c.nc[0]);
+      nc3[1] = (int)__umulhi(uy, (uint32_t)c.nc[1]);
+      nc3[2] = (int)__umulhi(uz, (uint32_t)c.nc[2]);
+    } else {
+      double pp[3] = {px, py, pz}, qq[3] = {a.qx[i], a.qy[i], a.qz[i]};
+      for (int d = 0; d < 3; ++d) {
+        double x = __dadd_rn(qq[d], __ddiv_rn(__dmul_rn(pp[d], dt_drift), c.m));
+        if (x >= c.L[d]) x = __dsub_rn(x, c.L[d]);
+        else if (x < 0.0) x = __dadd_rn(x, c.L[d]);
+        if (x >= c.L[d]) x = 0.0;
+        qq[d] = x;
+        int cc = (int)floor(__ddiv_rn(x, c.cs[d]));
+        nc3[d] = cc >= c.nc[d] ? c.nc[d] - 1 : (cc < 0 ? 0 : cc);
+      }
+      qdx[i] = qq[0]; qdy[i] = qq[1]; qdz[i] = qq[2];
+    }
+    const int r = mrank[nc3[0] + c.nc[0] * (nc3[1] + c.nc[1] * nc3[2])];
+    key[i] = r;
+    slot[i] = atomicAdd(&cell_count[r], 1);
+  }
+}
+
+static inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+template <class P>
+void launch_density(const Consts& c, const Workspace& w, int cur, int update_eos, int32_t* ncount_by_id,
+                    cudaStream_t s) {
+  if (c.N == 0) return;
+  Arrays<P> a = view<P>(w, cur);
+  auto qp4 = (typename P::V4*)w.qp4;
+  if (c.kernel == SDPD_KERNEL_LUCY)
+    k_density<P, SDPD_KERNEL_LUCY><<<blocks_for(c.N, 128), 128, 0, s>>>(
+        c, a, qp4, w.cell_start, w.mrank, w.xmin[0], w.xmin[1], w.xmin[2], update_eos, ncount_by_id);
+  else
+    k_density<P, SDPD_KERNEL_CUBIC><<<blocks_for(c.N, 128), 128, 0, s>>>(
+        c, a, qp4, w.cell_start, w.mrank, w.xmin[0], w.xmin[1], w.xmin[2], update_eos, ncount_by_id);
+}
+
+template <class P>
+void launch_force(const Consts& c, const Workspace& w, int cur, double half_dt, double dt_drift,
+                  double* force_by_id, cudaStream_t s) {
+  if (c.N == 0) return;
+  Arrays<P> a = view<P>(w, cur);
+  auto qp4 = (const typename P::V4*)w.qp4;
+  auto qdx = (typename P::Q*)w.qdx;
+  auto qdy = (typename P::Q*)w.qdy;
+  auto qdz = (typename P::Q*)w.qdz;
+  if (c.kernel == SDPD_KERNEL_LUCY)
+    k_force<P, SDPD_KERNEL_LUCY><<<blocks_for(c.N, 128), 128, 0, s>>>(
+        c, a, qp4, w.cell_start, w.mrank, w.xmin[0], w.xmin[1], w.xmin[2], half_dt, dt_drift, qdx, qdy,
+        qdz, w.key, w.slot, w.cell_count, force_by_id);
+  else
+    k_force<P, SDPD_KERNEL_CUBIC><<<blocks_for(c.N, 128), 128, 0, s>>>(
+        c, a, qp4, w.cell_start, w.mrank, w.xmin[0], w.xmin[1], w.xmin[2], half_dt, dt_drift, qdx, qdy,
+        qdz, w.key, w.slot, w.cell_count, force_by_id);
+}
+
+template void launch_density<Fp64>(const Consts&, const Workspace&, int, int, int32_t*, cudaStream_t);
+template void launch_density<Mixed>(const Consts&, const Workspace&, int, int, int32_t*, cudaStream_t);
+template void launch_force<Fp64>(const Consts&, const Workspace&, int, double, double, double*,
+                                 cudaStream_t);
+template void launch_force<Mixed>(const Consts&, const Workspace&, int, double, double, double*,
+                                  cudaStream_t);
+
+}  // namespace sdpd

@@ -359,8 +359,18 @@ def test_colouring_is_conflict_free():
             off = (cells[pid] - o) % n_c
             assert ((off == 0) | (off == 1)).all()
         assert rec["colour"] == (o[0] & 1) | ((o[1] & 1) << 1) | ((o[2] & 1) << 2)
-    # sweep order: colour, owner, ids ascending
-    key = np.stack([recs["colour"], recs["owner"], recs["id_i"], recs["id_j"]])
+    # sweep order: colour, owner, then inside the owner's block by
+    # (rank difference, lower rank), ranks of ids among the block's particles
+    rank_i = np.empty(len(recs), dtype=np.int64)
+    rank_j = np.empty(len(recs), dtype=np.int64)
+    for own in np.unique(recs["owner"]):
+        sel = np.nonzero(recs["owner"] == own)[0]
+        o = np.array([own % n_c[0], (own // n_c[0]) % n_c[1], own // (n_c[0] * n_c[1])])
+        members = np.nonzero((((cells - o) % n_c) <= 1).all(axis=1))[0]
+        rank_i[sel] = np.searchsorted(members, recs["id_i"][sel])
+        rank_j[sel] = np.searchsorted(members, recs["id_j"][sel])
+    assert (rank_i < rank_j).all()
+    key = np.stack([recs["colour"], recs["owner"], rank_j - rank_i, rank_i])
     assert (np.lexsort(key[::-1]) == np.arange(len(recs))).all()
     # within one colour, different owners touch disjoint particles
     for c in range(8):

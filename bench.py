@@ -1,0 +1,360 @@
+"""Throughput of the SDPD time step (Velocity Verlet + Metropolised
+Shardlow-like sweep) on GB300.
+
+Workload (default): a single large fluid of N = 128^3 = 2,097,152 particles on
+a jittered simple-cubic lattice (spacing a = 1, jitter +-0.05a, L = 128),
+Lucy kernel h = 2.5a, kT = 1, K = 50, eta = 1, dt = 0.005, EMS, mixed
+precision (float32 pair arithmetic, float64 internal energies).  One bench
+step = one full time step of every stage on the device.
+
+Prints one JSON line (see the keys below).  With torchrun (N > 1 ranks) every
+rank runs an independent replica (different seed) on its own GPU; ``value`` is
+the particle-steps of all ranks divided by the slowest rank's time.
+
+``--impl reference`` times the FP64 CPU oracle on the host cores instead (a
+bounded sample of the same workload, see ``cpu_sample``).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1707_04232_gb300.inputs import Workload, lattice_state  # noqa: E402
+
+METRIC = "particle-steps/s (SDPD+Metropolis SSA) at N=2M; % HBM roofline; vs FP64 form"
+UNIT = "particle-steps/s"
+SMS = 152
+FP32_LANES_PER_SM = 128
+NOMINAL_SM_MHZ = 2070.0
+FALLBACK_HBM_GBS = 6800.0
+# algorithmic traffic of one particle-step: state read + written once
+BYTES_PER_PARTICLE_STEP = {"mixed": 64.0, "fp64": 112.0}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--n", type=int, default=128, help="lattice sites per axis")
+    ap.add_argument("--scheme", default="ems", choices=["ssa", "ams", "ems", "none"])
+    ap.add_argument("--K", type=float, default=50.0)
+    ap.add_argument("--dt", type=float, default=0.005)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-n", type=int, default=32, help="lattice sites per axis of the CPU sample")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            with open(path) as f:
+                d = json.load(f)
+            return d, "measured"
+        except Exception:
+            pass
+    return {}, "fallback"
+
+
+def hbm_peak():
+    d, src = measured_peaks()
+    for k in ("hbm_gbs", "hbm_GBs", "hbm"):
+        if k in d:
+            v = d[k]
+            if isinstance(v, dict):
+                v = v.get("value", v.get("gbs"))
+            try:
+                return float(v), "of measured"
+            except Exception:
+                pass
+    return FALLBACK_HBM_GBS, "of fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        if not self.rows:
+            return None
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in self.rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(self.rows)}
+
+
+def cpu_sample(args, steps: int):
+    """Time the FP64 oracle on a bounded sample of the workload: an
+    args.cpu_n^3 sub-lattice with the same density, temperature, K, dt and
+    scheme.  Returns (particle-steps/s, threads, description)."""
+    import oracle as O
+
+    w = Workload(n=args.cpu_n, K=args.K, kT=1.0)
+    q, p, e = lattice_state(w)
+    scheme = {"ssa": O.SCHEME_SSA, "ams": O.SCHEME_AMS, "ems": O.SCHEME_EMS, "none": O.SCHEME_NONE}[args.scheme]
+    P = O.Config(N=w.N, L=w.L, K=w.K, scheme=scheme).params()
+    O.lib()
+    t0 = time.perf_counter()
+    st, q, p, e, stats, _ = O.run(P, q, p, e, args.dt, steps, seed=1)
+    dt = time.perf_counter() - t0
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    desc = ("O(N^2) brute-force FP64 oracle, %d^3 = %d-particle sub-lattice of the same fluid, %d step(s), "
+            "%.1f s" % (args.cpu_n, w.N, steps, dt))
+    return w.N * steps / dt, threads, desc
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    steps, warm = args.steps, args.warmup
+    # warm-up steps of the oracle are not timed; each timed step is a bounded
+    # sample (a cpu_n^3 sub-lattice) of the workload
+    if warm > 0:
+        cpu_sample(args, 1)
+    ps, threads, desc = cpu_sample(args, steps)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": ps, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": steps, "warmup": warm, "ms_per_step": 1e3 * (args.cpu_n ** 3) / ps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": workload_config(args),
+        "cpu_baseline": {"value": ps, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc},
+        "e2e": {"value": ps, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def workload_config(args):
+    N = args.n ** 3
+    return {"workload": "single large fluid: %d^3 = %d particles, jittered sc lattice, L=%d, Lucy h=2.5a, "
+                        "kT=1, K=%g, dt=%g, %s, %s" % (args.n, N, args.n, args.K, args.dt,
+                                                      args.scheme.upper(), args.precision),
+            "N": N, "K": args.K, "kT": 1.0, "dt": args.dt, "h": 2.5, "kernel": "lucy",
+            "scheme": args.scheme, "precision": args.precision,
+            "l2": "inputs larger than L2 (per-step working set > 129 MB)"}
+
+
+# algorithmic float operations of the two pair passes, per neighbour pair
+# (r < h) visit, and of one pair update of the sweep; see the design doc
+FLOPS_PER_VISIT = {"density_eos": 18.0, "kick1_drift_bin": 24.0, "kick2": 24.0}
+FLOPS_PER_PAIR_UPDATE = {"ems": 260.0, "ams": 150.0, "ssa": 140.0}
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_1707_04232_gb300 import sdpd
+
+    torch.cuda.set_device(local_rank)
+    dev_index = torch.cuda.current_device()
+    w = Workload(n=args.n, K=args.K, kT=1.0, seed=rank)
+    q, p, e = lattice_state(w)
+    scheme = {"ssa": sdpd.SCHEME_SSA, "ams": sdpd.SCHEME_AMS, "ems": sdpd.SCHEME_EMS, "none": sdpd.SCHEME_NONE}[args.scheme]
+    prec = sdpd.MIXED if args.precision == "mixed" else sdpd.FP64
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        s = sdpd.SDPD(w.N, w.L, m=w.m, h=w.h, K=w.K, precision=prec, scheme=scheme, stream=stream)
+        s.set_state(q, p, e)
+        for _ in range(args.warmup):
+            s.step(args.dt, 1, seed=1234 + rank)
+        s.sync()
+        o0 = s.observables()
+        s.reset_counters()
+        launches0 = s.kernel_launches
+        s.enable_stage_timing(True)
+        clocks = ClockSampler(dev_index)
+        clocks.start()
+        barrier(world)
+        start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        start.record(stream)
+        s.step(args.dt, args.steps, seed=1234 + rank)
+        end.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        clk = clocks.stop()
+        ms = start.elapsed_time(end)
+        stages = s.stage_times()
+        launches = s.kernel_launches - launches0
+        o1 = s.observables()
+    ms_max = allreduce_max(ms, world)
+    total_ps = w.N * args.steps * world
+    value = total_ps / (ms_max * 1e-3)
+    # ---- roofline of the dominant stage ----
+    top = max(stages, key=lambda k: stages[k][0])
+    top_ms, top_launches = stages[top]
+    per_launch_s = top_ms * 1e-3 / max(1, top_launches)
+    sm_max = (clk or {}).get("sm_max_mhz") or NOMINAL_SM_MHZ
+    alu_peak = SMS * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12  # FP32 TFLOP/s
+    if top == "fd_colours":
+        units = o1["n_pairs"] / max(1, top_launches)  # pair updates per colour launch
+        flops = FLOPS_PER_PAIR_UPDATE[args.scheme] * units
+    elif top in FLOPS_PER_VISIT:
+        nvisits = w.N * 80.0  # neighbour visits per launch (lattice: 80 per particle)
+        flops = FLOPS_PER_VISIT[top] * nvisits
+    else:
+        flops = None
+    roof = None
+    if flops is not None:
+        ach = flops / per_launch_s / 1e12
+        roof = {"kernel": top, "bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": ach / alu_peak, "traffic": None,
+                "peak_note": "FP32 FMA peak = 152 SMs x 128 lanes x 2 x %.0f MHz (recipe unit counts, "
+                             "sampled max clock)" % sm_max,
+                "per_launch_ms": per_launch_s * 1e3}
+    hbm, hbm_note = hbm_peak()
+    bpp = BYTES_PER_PARTICLE_STEP[args.precision]
+    hbm_frac = value / world * bpp / (hbm * 1e9)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.precision == "mixed" else "f64",
+        "data": "synthetic", "config": workload_config(args),
+        "hbm_roofline": {"bytes_per_particle_step": bpp, "peak_gbs": hbm, "frac": hbm_frac,
+                         "note": hbm_note},
+        "roofline": roof,
+        "stages_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
+        "gpu_launches": launches,
+        "clocks": clk,
+        "physics": {"E0": o0["E"], "E1": o1["E"], "T_kin": o1["T_kin"], "T_int": o1["T_int"],
+                    "eps_min": o1["eps_min"], "n_pairs": o1["n_pairs"],
+                    "reject_rate": (o1["n_reject_bound"] + o1["n_reject_metropolis"]) / max(1, o1["n_pairs"]),
+                    "status": o1["status"]},
+    }
+    # ---- end to end through the public API with host buffers ----
+    if not args.no_e2e:
+        e2e = run_e2e(args, s, q, p, e, stream, world, w.N)
+        line["e2e"] = e2e
+    del s
+    if rank == 0 and not args.no_cpu and world == 1:
+        ps, threads, desc = cpu_sample(args, 2)
+        line["cpu_baseline"] = {"value": ps, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc}
+    if rank == 0:
+        print(json.dumps(line))
+
+
+def run_e2e(args, s, q, p, e, stream, world, N):
+    """Each e2e step: host->device copy of the state from pinned memory
+    (sdpd_set_state), one time step, device->host copy of the new state
+    (sdpd_get_state)."""
+    import torch
+
+    qh = torch.from_numpy(q).pin_memory()
+    ph = torch.from_numpy(p).pin_memory()
+    eh = torch.from_numpy(e).pin_memory()
+    qo = torch.empty_like(qh).pin_memory()
+    po = torch.empty_like(ph).pin_memory()
+    eo = torch.empty_like(eh).pin_memory()
+    from paper_1707_04232_gb300 import sdpd
+
+    def one(k):
+        sdpd._check(sdpd.sdpd_set_state(s.h, qh.data_ptr(), ph.data_ptr(), eh.data_ptr(), 0), "set_state")
+        s.fd_step = k
+        s.step(args.dt, 1, seed=99)
+        sdpd._check(sdpd.sdpd_get_state(s.h, qo.data_ptr(), po.data_ptr(), eo.data_ptr(), 0), "get_state")
+
+    nsteps = max(1, min(args.steps, 10))
+    for k in range(2):
+        one(k)
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(nsteps):
+        one(k)
+    torch.cuda.synchronize()
+    dt = allreduce_max(time.perf_counter() - t0, world)
+    return {"value": N * nsteps * world / dt, "unit": UNIT, "h2d_bytes_per_step": 56 * N,
+            "d2h_bytes_per_step": 56 * N, "steps": nsteps,
+            "note": "per step: set_state from pinned host (q,p,eps f64), 1 time step, get_state to pinned host"}
+
+
+_dist = None
+
+
+def barrier(world):
+    if world > 1:
+        _dist.barrier()
+
+
+def allreduce_max(x, world):
+    if world == 1:
+        return x
+    import torch
+    t = torch.tensor([float(x)], device="cuda")
+    _dist.all_reduce(t, op=_dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def main():
+    global _dist
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+        _dist = dist
+    run_ours(args, rank, world, local_rank)
+    if world > 1:
+        _dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -135,7 +135,8 @@ int sdpd_get_state(sdpd_t* s, double* q, double* p, double* eps, int on_device);
  * by one fluctuation/dissipation sweep over all pairs r_ij < h with step
  * theta*dt (Sections 3.2-3.3).  The sweep visits the pairs in the colour
  * order of the library (8 cell-parity colours; within a colour the 2x2x2
- * cell blocks are independent; within a block pairs go by (min id, max id))
+ * cell blocks are independent; within a block pairs go by (rank difference,
+ * lower rank), rank = position of the id among the block's particles)
  * and draws the pair's random numbers from Philox4x64-10 keyed by seed with
  * counter (sweep number, min id, max id, 0).  Asynchronous on the handle's
  * stream.  Errors: SDPD_ERR_INVALID_ARG (dt <= 0, nsteps < 0),
@@ -157,6 +158,20 @@ int64_t sdpd_get_fd_step(const sdpd_t* s);
 
 /* Reset the pair counters of sdpd_obs. */
 int sdpd_reset_counters(sdpd_t* s);
+
+/* Number of CUDA kernels the handle has launched so far (a VV step launches
+ * 6, a sweep 10, sdpd_set_state 5, sdpd_observables 2). */
+int64_t sdpd_kernel_launches(const sdpd_t* s);
+
+/* Per-stage timing with CUDA events recorded on the handle's stream around
+ * every stage that sdpd_step launches.  Stages: 0 first kick + drift +
+ * binning, 1 sort, 2 density + EOS, 3 second kick, 4 sweep schedule,
+ * 5 sweep colours (8 launches per sweep).  sdpd_stage_times synchronises and
+ * returns, per stage, the summed milliseconds and the number of kernel
+ * launches since timing was enabled (arrays of n entries, n <= 6). */
+#define SDPD_NSTAGES 6
+int sdpd_enable_stage_timing(sdpd_t* s, int on);
+int sdpd_stage_times(sdpd_t* s, double* ms, int64_t* launches, int n);
 
 /* Debug read-outs (synchronising).  what:
  *  SDPD_DEBUG_ORDER   int64[N]   ids in storage order (Morton order of cells, then id)

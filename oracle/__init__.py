@@ -107,6 +107,8 @@ def lib():
             "orc_density": (None, [P, _dp, _dp]),
             "orc_neighbour_counts": (None, [P, _dp, _i32p]),
             "orc_forces": (None, [P, _dp, _dp, _dp, _dp]),
+            "orc_density_at": (None, [P, _dp, _i64p, C.c_int64, _dp]),
+            "orc_forces_at": (None, [P, _dp, _dp, _i64p, C.c_int64, _dp]),
             "orc_hamiltonian": (C.c_double, [P, _dp, _dp, _dp]),
             "orc_verlet": (None, [P, _dp, _dp, _dp, C.c_double]),
             "orc_philox4x64_10": (None, [_u64p, _u64p, _u64p]),
@@ -210,6 +212,22 @@ def forces(P: Params, q, rho, eps) -> np.ndarray:
     f = np.empty((P.N, 3))
     lib().orc_forces(C.byref(P), _d(q), _d(rho), _d(eps), _d(f))
     return f
+
+
+def density_at(P: Params, q, idx) -> np.ndarray:
+    q = _f64(q)
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    out = np.empty(len(idx))
+    lib().orc_density_at(C.byref(P), _d(q), idx.ctypes.data_as(_i64p), len(idx), _d(out))
+    return out
+
+
+def forces_at(P: Params, q, eps, idx) -> np.ndarray:
+    q, eps = _f64(q), _f64(eps)
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    out = np.empty((len(idx), 3))
+    lib().orc_forces_at(C.byref(P), _d(q), _d(eps), idx.ctypes.data_as(_i64p), len(idx), _d(out))
+    return out
 
 
 def cells(P: Params, q) -> np.ndarray:

@@ -302,6 +302,66 @@ void orc_forces(const orc_params* P, const double* q, const double* rho, const d
   free(pi);
 }
 
+/* Density of selected particles only (the same sum as orc_density, one
+ * particle at a time): rho[k] = rho_{idx[k]}. */
+void orc_density_at(const orc_params* P, const double* q, const int64_t* idx, int64_t n, double* rho) {
+  const double h2 = P->h * P->h;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t k = 0; k < n; ++k) {
+    int64_t i = idx[k];
+    double s = 0.0;
+    for (int64_t j = 0; j < P->N; ++j) {
+      double d[3];
+      displacement(P, q, i, j, d);
+      double r2 = orc_r2(d[0], d[1], d[2]);
+      if (r2 < h2) s += P->m * orc_W(P->kernel, sqrt(r2), P->h);
+    }
+    rho[k] = s;
+  }
+}
+
+/* Conservative force on selected particles (Eq. cons-forces), with the
+ * densities of the particle and of each of its neighbours recomputed by the
+ * full sum: force[3k..3k+2] = F_{idx[k]}. */
+void orc_forces_at(const orc_params* P, const double* q, const double* eps, const int64_t* idx, int64_t n,
+                   double* force) {
+  const double h2 = P->h * P->h;
+  const double m2 = P->m * P->m;
+  for (int64_t k = 0; k < n; ++k) {
+    int64_t i = idx[k];
+    double rho_i;
+    orc_density_at(P, q, &i, 1, &rho_i);
+    double pi_i = orc_P(P, eps[i], rho_i) / (rho_i * rho_i);
+    double f[3] = {0.0, 0.0, 0.0};
+#pragma omp parallel
+    {
+      double fl[3] = {0.0, 0.0, 0.0};
+#pragma omp for schedule(dynamic, 4096)
+      for (int64_t j = 0; j < P->N; ++j) {
+        if (j == i) continue;
+        double d[3];
+        displacement(P, q, i, j, d);
+        double r2 = orc_r2(d[0], d[1], d[2]);
+        if (r2 < h2) {
+          double rho_j = 0.0;
+          for (int64_t l = 0; l < P->N; ++l) {
+            double e[3];
+            displacement(P, q, j, l, e);
+            double s2 = orc_r2(e[0], e[1], e[2]);
+            if (s2 < h2) rho_j += P->m * orc_W(P->kernel, sqrt(s2), P->h);
+          }
+          double pi_j = orc_P(P, eps[j], rho_j) / (rho_j * rho_j);
+          double c = m2 * (pi_i + pi_j) * orc_F(P->kernel, sqrt(r2), P->h);
+          for (int a = 0; a < 3; ++a) fl[a] += c * d[a];
+        }
+      }
+#pragma omp critical
+      for (int a = 0; a < 3; ++a) f[a] += fl[a];
+    }
+    for (int a = 0; a < 3; ++a) force[3 * k + a] = f[a];
+  }
+}
+
 /* Hamiltonian of Section 3.1 at fixed entropies:
  * H = sum |p_i|^2/(2m) + sum E(S_i, rho_i(q)). */
 double orc_hamiltonian(const orc_params* P, const double* q, const double* p, const double* S) {

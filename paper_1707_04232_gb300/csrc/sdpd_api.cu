@@ -1,0 +1,727 @@
+// sdpd_api.cu -- the C ABI of include/sdpd.h: parameter checks, workspace
+// layout, cell tables, the time-step driver and the float64 observables.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "sdpd_internal.cuh"
+
+using namespace sdpd;
+
+struct sdpd_handle {
+  Consts c;
+  sdpd_params prm;
+  double K;
+  cudaStream_t stream;
+  size_t ws_bytes;
+  char* ws;
+  Workspace w;
+  int cur;
+  bool has_state;
+  int64_t fd_step, vv_step;
+  int64_t launches;
+  std::vector<int32_t> mrank_h;
+  std::vector<uint32_t> rcoord_h;
+  std::vector<uint32_t> xmin_h[3];
+  int64_t pair_rec_cap;
+  int device;  // device of the bound workspace; selected on entry to every call
+  // stage timing: event pairs recorded on the stream, reduced at sync points
+  bool timing;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pending;
+  double stage_ms[SDPD_NSTAGES];
+  int64_t stage_launches[SDPD_NSTAGES];
+};
+
+namespace {
+
+constexpr size_t kAlign = 256;
+
+struct Layout {
+  size_t off = 0;
+  size_t take(size_t bytes) {
+    size_t o = off;
+    off += (bytes + kAlign - 1) / kAlign * kAlign;
+    return o;
+  }
+};
+
+// Interleave the bits of (x, y, z), x lowest: the Morton code of a cell.
+uint64_t morton3(uint32_t x, uint32_t y, uint32_t z) {
+  uint64_t code = 0;
+  for (int b = 0; b < 21; ++b) {
+    code |= (uint64_t)((x >> b) & 1u) << (3 * b);
+    code |= (uint64_t)((y >> b) & 1u) << (3 * b + 1);
+    code |= (uint64_t)((z >> b) & 1u) << (3 * b + 2);
+  }
+  return code;
+}
+
+int map_status(int bits) {
+  if (bits & kStNaN) return SDPD_ERR_NAN;
+  if (bits & kStNegative) return SDPD_ERR_NEGATIVE_ENERGY;
+  if (bits & kStCapacity) return SDPD_ERR_CAPACITY;
+  if (bits & kStBadEnergy) return SDPD_ERR_NONPOSITIVE_ENERGY;
+  return SDPD_OK;
+}
+
+// Observables: per-block float64 partial sums, then one block in fixed order.
+// slots: 0 sum eps, 1 kinetic energy, 2..4 momentum, 5 sum T, 6 min eps,
+// 7 non-finite flag.
+template <class P>
+__global__ void k_obs_partial(Consts c, Arrays<P> a, double* partial) {
+  double s[6] = {0, 0, 0, 0, 0, 0};
+  double emin = INFINITY, bad = 0.0;
+  const double inv2m = 0.5 / c.m, invCK = 1.0 / c.C_K;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < c.N; i += (int64_t)gridDim.x * blockDim.x) {
+    const double e = a.eps[i];
+    const double px = a.px[i], py = a.py[i], pz = a.pz[i];
+    s[0] += e;
+    s[1] += (px * px + py * py + pz * pz) * inv2m;
+    s[2] += px; s[3] += py; s[4] += pz;
+    s[5] += e * invCK;
+    emin = fmin(emin, e);
+    if (!isfinite(e) || !isfinite(px) || !isfinite(py) || !isfinite(pz)) bad = 1.0;
+  }
+  __shared__ double red[8][32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  double v[8] = {s[0], s[1], s[2], s[3], s[4], s[5], emin, bad};
+  for (int k = 0; k < 8; ++k) {
+    double x = v[k];
+    for (int o = 16; o > 0; o >>= 1) {
+      double y = __shfl_xor_sync(0xffffffffu, x, o);
+      x = (k == 6) ? fmin(x, y) : (k == 7 ? fmax(x, y) : x + y);
+    }
+    if (lane == 0) red[k][wid] = x;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = blockDim.x >> 5;
+    for (int k = 0; k < 8; ++k) {
+      double x = lane < nw ? red[k][lane] : (k == 6 ? INFINITY : 0.0);
+      for (int o = 16; o > 0; o >>= 1) {
+        double y = __shfl_xor_sync(0xffffffffu, x, o);
+        x = (k == 6) ? fmin(x, y) : (k == 7 ? fmax(x, y) : x + y);
+      }
+      if (lane == 0) partial[blockIdx.x * 8 + k] = x;
+    }
+  }
+}
+
+__global__ void k_obs_final(const double* partial, int nb, double* out, int* status) {
+  const int lane = threadIdx.x;
+  for (int k = 0; k < 8; ++k) {
+    double x = (k == 6) ? INFINITY : 0.0;
+    for (int b = lane; b < nb; b += 32) {
+      const double y = partial[b * 8 + k];
+      x = (k == 6) ? fmin(x, y) : (k == 7 ? fmax(x, y) : x + y);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const double y = __shfl_xor_sync(0xffffffffu, x, o);
+      x = (k == 6) ? fmin(x, y) : (k == 7 ? fmax(x, y) : x + y);
+    }
+    if (lane == 0) out[k] = x;
+  }
+  if (lane == 0 && out[7] != 0.0) atomicOr(status, kStNaN);
+}
+
+template <class P>
+size_t layout(sdpd_handle* s, Workspace* w, char* base) {
+  const Consts& c = s->c;
+  using R = typename P::R;
+  using Q = typename P::Q;
+  using V4 = typename P::V4;
+  const size_t N = (size_t)(c.N > 0 ? c.N : 1);
+  const size_t nc = (size_t)c.ncell;
+  Layout L;
+  auto at = [&](size_t bytes) -> void* { return base ? base + L.take(bytes) : (L.take(bytes), nullptr); };
+  for (int k = 0; k < 2; ++k) {
+    w->q4[k] = at(N * sizeof(V4));
+    w->qx[k] = at(N * sizeof(Q));
+    w->qy[k] = at(N * sizeof(Q));
+    w->qz[k] = at(N * sizeof(Q));
+    w->px[k] = at(N * sizeof(R));
+    w->py[k] = at(N * sizeof(R));
+    w->pz[k] = at(N * sizeof(R));
+    w->eps[k] = (double*)at(N * sizeof(double));
+    w->rho[k] = at(N * sizeof(R));
+    w->id[k] = (int32_t*)at(N * sizeof(int32_t));
+  }
+  w->qp4 = at(N * sizeof(V4));
+  w->key = (int32_t*)at(N * 4);
+  w->slot = (int32_t*)at(N * 4);
+  w->tmp = (int32_t*)at(2 * N * 4);
+  w->qdx = at(N * sizeof(Q));
+  w->qdy = at(N * sizeof(Q));
+  w->qdz = at(N * sizeof(Q));
+  w->cell_count = (int32_t*)at(nc * 4);
+  w->cell_start = (int32_t*)at((nc + 1) * 4);
+  w->mrank = (int32_t*)at(nc * 4);
+  w->rcoord = (uint32_t*)at(nc * 4);
+  for (int d = 0; d < 3; ++d) w->xmin[d] = (uint32_t*)at((size_t)c.nc[d] * 4);
+  w->sched_hdr = (uint32_t*)at(nc * 4);
+  w->sched_lvl = (uint16_t*)at(nc * (kMaxLevels + 1) * 2);
+  w->sched_pair = (uint16_t*)at(2 * nc * kMaxPairs * 2);
+  w->io_q = (double*)at(3 * N * 8);
+  w->io_p = (double*)at(3 * N * 8);
+  w->io_e = (double*)at(N * 8);
+  w->obs_partial = (double*)at(kObsBlocks * 8 * 8);
+  w->obs = (double*)at(16 * 8);
+  w->counters = (unsigned long long*)at(4 * 8);
+  w->status = (int*)at(8);
+  w->pair_rec_count = (unsigned long long*)at(8);
+  w->pair_rec_cap = s->pair_rec_cap;
+  w->pair_recs = s->pair_rec_cap > 0 ? (sdpd_pair_rec*)at((size_t)s->pair_rec_cap * sizeof(sdpd_pair_rec)) : nullptr;
+  return L.off;
+}
+
+size_t layout_any(sdpd_handle* s, Workspace* w, char* base) {
+  return s->prm.precision == SDPD_MIXED ? layout<Mixed>(s, w, base) : layout<Fp64>(s, w, base);
+}
+
+int cuda_ok(cudaError_t e) { return e == cudaSuccess ? SDPD_OK : SDPD_ERR_CUDA; }
+
+// Make the workspace's device current for this runtime on the calling thread.
+int use_device(sdpd_handle* s) {
+  if (s->device < 0) return SDPD_OK;
+  int cur = -1;
+  if (cudaGetDevice(&cur) == cudaSuccess && cur == s->device) return SDPD_OK;
+  return cuda_ok(cudaSetDevice(s->device));
+}
+
+int launch_status() {
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? SDPD_OK : SDPD_ERR_CUDA;
+}
+
+template <class P>
+void do_load(sdpd_handle* s) {
+  launch_load<P>(s->c, s->w, s->stream);
+  launch_sort<P>(s->c, s->w, 0, s->stream);
+  s->cur = 1;
+  launch_density<P>(s->c, s->w, s->cur, 0, nullptr, s->stream);
+  s->launches += 5;
+}
+
+cudaEvent_t take_event(sdpd_handle* s) {
+  if (!s->ev_pool.empty()) {
+    cudaEvent_t e = s->ev_pool.back();
+    s->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Reduce the recorded event pairs (the stream must be synchronised).
+void drain_events(sdpd_handle* s) {
+  for (auto& it : s->ev_pending) {
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, it.second.first, it.second.second) == cudaSuccess) s->stage_ms[it.first] += ms;
+    s->ev_pool.push_back(it.second.first);
+    s->ev_pool.push_back(it.second.second);
+  }
+  s->ev_pending.clear();
+}
+
+// Brackets one stage with events when timing is on.
+struct StageTimer {
+  sdpd_handle* s;
+  int stage;
+  int launches;
+  cudaEvent_t a = nullptr;
+  StageTimer(sdpd_handle* s_, int st, int nl) : s(s_), stage(st), launches(nl) {
+    if (s->timing) {
+      a = take_event(s);
+      cudaEventRecord(a, s->stream);
+    }
+  }
+  ~StageTimer() {
+    if (s->timing) {
+      cudaEvent_t b = take_event(s);
+      cudaEventRecord(b, s->stream);
+      s->ev_pending.push_back({stage, {a, b}});
+      s->stage_launches[stage] += launches;
+      if (s->ev_pending.size() > 4096) {  // bound the pool: wait for the oldest
+        cudaStreamSynchronize(s->stream);
+        drain_events(s);
+      }
+    }
+  }
+};
+
+template <class P>
+void do_steps(sdpd_handle* s, double dt, int64_t nsteps, uint64_t seed) {
+  const Consts& c = s->c;
+  const int theta = s->prm.theta < 1 ? 1 : s->prm.theta;
+  const bool fd = s->prm.scheme != SDPD_SCHEME_NONE;
+  for (int64_t n = 0; n < nsteps; ++n) {
+    if (!s->prm.fd_only) {
+      {  // p^{n+1/2} = p^n + F^n dt/2, q^{n+1} = q^n + p^{n+1/2} dt/m
+        StageTimer t(s, 0, 1);
+        launch_force<P>(c, s->w, s->cur, 0.5 * dt, dt, nullptr, s->stream);
+      }
+      {
+        StageTimer t(s, 1, 3);
+        launch_sort<P>(c, s->w, s->cur, s->stream);
+      }
+      s->cur = 1 - s->cur;
+      {  // rho^{n+1}, eps^{n+1} = E(S, rho^{n+1})
+        StageTimer t(s, 2, 1);
+        launch_density<P>(c, s->w, s->cur, 1, nullptr, s->stream);
+      }
+      {  // p^{n+1} = p^{n+1/2} + F^{n+1} dt/2
+        StageTimer t(s, 3, 1);
+        launch_force<P>(c, s->w, s->cur, 0.5 * dt, 0.0, nullptr, s->stream);
+      }
+      s->launches += 6;
+      s->vv_step++;
+    }
+    if (fd && (s->prm.fd_only || (n + 1) % theta == 0)) {
+      const double dt_fd = s->prm.fd_only ? dt : theta * dt;
+      const int rec = s->w.pair_recs != nullptr;
+      if (rec) cudaMemsetAsync(s->w.pair_rec_count, 0, 8, s->stream);
+      {
+        StageTimer t(s, 4, 2);
+        launch_fd_schedule<P>(c, s->w, s->cur, s->stream);
+      }
+      {
+        StageTimer t(s, 5, 8);
+        launch_fd_colours<P>(c, s->w, s->cur, dt_fd, seed, (uint64_t)s->fd_step, rec, s->stream);
+      }
+      s->launches += 10;
+      s->fd_step++;
+    }
+  }
+}
+
+template <class P>
+void do_observables(sdpd_handle* s) {
+  launch_observables<P>(s->c, s->w, s->cur, s->stream);
+  s->launches += 2;
+}
+
+}  // namespace
+
+namespace sdpd {
+template <class P>
+void launch_observables(const Consts& c, const Workspace& w, int cur, cudaStream_t s) {
+  k_obs_partial<P><<<kObsBlocks, 256, 0, s>>>(c, view<P>(w, cur), w.obs_partial);
+  k_obs_final<<<1, 32, 0, s>>>(w.obs_partial, kObsBlocks, w.obs, w.status);
+}
+template void launch_observables<Fp64>(const Consts&, const Workspace&, int, cudaStream_t);
+template void launch_observables<Mixed>(const Consts&, const Workspace&, int, cudaStream_t);
+}  // namespace sdpd
+
+extern "C" {
+
+const char* sdpd_strerror(int st) {
+  switch (st) {
+    case SDPD_OK: return "ok";
+    case SDPD_ERR_INVALID_ARG: return "invalid argument";
+    case SDPD_ERR_BOX_TOO_SMALL: return "box too small: need an even number >= 4 of cells of side >= h per axis";
+    case SDPD_ERR_NONPOSITIVE_ENERGY: return "internal energy <= 0 or not finite in the given state";
+    case SDPD_ERR_NEGATIVE_ENERGY: return "SSA produced a non-positive internal energy";
+    case SDPD_ERR_NAN: return "non-finite momentum or energy";
+    case SDPD_ERR_CUDA: return "CUDA runtime error";
+    case SDPD_ERR_TIMEOUT: return "bounded device wait ran out";
+    case SDPD_ERR_NO_WORKSPACE: return "no or too small workspace bound";
+    case SDPD_ERR_CAPACITY: return "a 2x2x2 cell block exceeded its particle or pair capacity";
+    case SDPD_ERR_NO_STATE: return "no state loaded";
+    default: return "unknown status";
+  }
+}
+
+int sdpd_create(int64_t N, const double box[3], double m, double h, double K, const sdpd_params* prm,
+                void* stream, sdpd_t** out) {
+  if (!out) return SDPD_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!box || !prm) return SDPD_ERR_INVALID_ARG;
+  if (N < 0 || N >= (int64_t)INT32_MAX) return SDPD_ERR_INVALID_ARG;
+  if (!(m > 0) || !isfinite(m) || !(h > 0) || !isfinite(h)) return SDPD_ERR_INVALID_ARG;
+  if (!(K > 4.0 / 3.0) || !isfinite(K)) return SDPD_ERR_INVALID_ARG;
+  if (!(prm->kB > 0) || !isfinite(prm->kB)) return SDPD_ERR_INVALID_ARG;
+  if (!(prm->eta > 0) || !isfinite(prm->eta)) return SDPD_ERR_INVALID_ARG;
+  if (!(prm->zeta >= 0) || !(prm->zeta < 5.0 * prm->eta / 3.0)) return SDPD_ERR_INVALID_ARG;
+  if (prm->kernel != SDPD_KERNEL_CUBIC && prm->kernel != SDPD_KERNEL_LUCY) return SDPD_ERR_INVALID_ARG;
+  if (prm->scheme < SDPD_SCHEME_SSA || prm->scheme > SDPD_SCHEME_NONE) return SDPD_ERR_INVALID_ARG;
+  if (prm->precision != SDPD_FP64 && prm->precision != SDPD_MIXED) return SDPD_ERR_INVALID_ARG;
+  if (prm->theta < 1 || prm->theta > 1000000) return SDPD_ERR_INVALID_ARG;
+  if (prm->fd_only && prm->scheme == SDPD_SCHEME_NONE) return SDPD_ERR_INVALID_ARG;
+  sdpd_handle* s = new (std::nothrow) sdpd_handle();
+  if (!s) return SDPD_ERR_INVALID_ARG;
+  Consts& c = s->c;
+  c.N = N;
+  int64_t ncell = 1;
+  for (int d = 0; d < 3; ++d) {
+    if (!(box[d] > 0) || !isfinite(box[d])) { delete s; return SDPD_ERR_INVALID_ARG; }
+    double ratio = floor(box[d] / h);
+    int64_t n = ratio > 1024.0 ? 1024 : (int64_t)ratio;
+    n -= n % 2;
+    if (n < 4) { delete s; return SDPD_ERR_BOX_TOO_SMALL; }
+    c.nc[d] = (int)n;
+    c.L[d] = box[d];
+    c.halfL[d] = 0.5 * box[d];
+    c.cs[d] = box[d] / (double)n;
+    c.scale[d] = box[d] / 4294967296.0;
+    c.inv_scale[d] = 4294967296.0 / box[d];
+    ncell *= n;
+  }
+  c.ncell = (int)ncell;
+  c.h = h;
+  c.h2 = h * h;
+  c.m = m;
+  c.kB = prm->kB;
+  c.C_K = 1.5 * (K - 1.0) * prm->kB;
+  c.c_rho = prm->c_rho < 0 ? 0.5 * (K - 1.0) : prm->c_rho;
+  c.kpar_m2 = (10.0 / 3.0 * prm->eta + 4.0 * prm->zeta) * m * m;
+  c.kperp_m2 = (5.0 / 3.0 * prm->eta - prm->zeta) * m * m;
+  const double h3 = h * h * h, h5 = h3 * h * h;
+  if (prm->kernel == SDPD_KERNEL_LUCY) {
+    c.cW = 105.0 / (16.0 * M_PI * h3);
+    c.cF = 315.0 / (4.0 * M_PI * h5);
+  } else {
+    c.cW = 8.0 / (M_PI * h3);
+    c.cF = 48.0 / (M_PI * h5);
+  }
+  c.W0 = c.cW;
+  c.kernel = prm->kernel;
+  c.scheme = prm->scheme;
+  s->prm = *prm;
+  s->K = K;
+  s->stream = (cudaStream_t)stream;
+  s->ws = nullptr;
+  s->cur = 0;
+  s->has_state = false;
+  s->fd_step = s->vv_step = 0;
+  s->launches = 0;
+  s->pair_rec_cap = prm->debug ? std::max<int64_t>(1, N) * 64 : 0;
+  s->timing = false;
+  s->device = -1;
+  for (int k = 0; k < SDPD_NSTAGES; ++k) { s->stage_ms[k] = 0.0; s->stage_launches[k] = 0; }
+  // Morton order of the cells: rank of every cell, and the cell of every rank
+  s->mrank_h.resize((size_t)ncell);
+  s->rcoord_h.resize((size_t)ncell);
+  std::vector<std::pair<uint64_t, int64_t>> codes((size_t)ncell);
+  for (int z = 0; z < c.nc[2]; ++z)
+    for (int y = 0; y < c.nc[1]; ++y)
+      for (int x = 0; x < c.nc[0]; ++x) {
+        int64_t lin = x + (int64_t)c.nc[0] * (y + (int64_t)c.nc[1] * z);
+        codes[(size_t)lin] = {morton3(x, y, z), lin};
+      }
+  std::sort(codes.begin(), codes.end());
+  for (int64_t r = 0; r < ncell; ++r) {
+    int64_t lin = codes[(size_t)r].second;
+    int x = (int)(lin % c.nc[0]), y = (int)((lin / c.nc[0]) % c.nc[1]), z = (int)(lin / ((int64_t)c.nc[0] * c.nc[1]));
+    s->mrank_h[(size_t)lin] = (int32_t)r;
+    s->rcoord_h[(size_t)r] = pack_cell(x, y, z);
+  }
+  // fixed-point lower edge of each cell: ceil(c 2^32 / n_c)
+  for (int d = 0; d < 3; ++d) {
+    s->xmin_h[d].resize((size_t)c.nc[d]);
+    for (int k = 0; k < c.nc[d]; ++k) {
+      uint64_t num = ((uint64_t)k << 32) + (uint64_t)c.nc[d] - 1;
+      s->xmin_h[d][(size_t)k] = (uint32_t)(num / (uint64_t)c.nc[d]);
+    }
+  }
+  s->ws_bytes = layout_any(s, &s->w, nullptr);
+  *out = s;
+  return SDPD_OK;
+}
+
+size_t sdpd_workspace_bytes(const sdpd_t* s) { return s ? s->ws_bytes : 0; }
+
+int sdpd_bind_workspace(sdpd_t* s, void* ptr, size_t bytes) {
+  if (!s) return SDPD_ERR_INVALID_ARG;
+  if (!ptr || bytes < s->ws_bytes || ((uintptr_t)ptr % kAlign) != 0) return SDPD_ERR_NO_WORKSPACE;
+  cudaPointerAttributes attr;
+  if (cudaPointerGetAttributes(&attr, ptr) != cudaSuccess || attr.type != cudaMemoryTypeDevice) {
+    cudaGetLastError();
+    return SDPD_ERR_NO_WORKSPACE;
+  }
+  s->device = attr.device;
+  if (use_device(s) != SDPD_OK) return SDPD_ERR_CUDA;
+  s->ws = (char*)ptr;
+  layout_any(s, &s->w, s->ws);
+  const Consts& c = s->c;
+  cudaStream_t st = s->stream;
+  int e = SDPD_OK;
+  e |= cuda_ok(cudaMemcpyAsync(s->w.mrank, s->mrank_h.data(), (size_t)c.ncell * 4, cudaMemcpyHostToDevice, st));
+  e |= cuda_ok(cudaMemcpyAsync(s->w.rcoord, s->rcoord_h.data(), (size_t)c.ncell * 4, cudaMemcpyHostToDevice, st));
+  for (int d = 0; d < 3; ++d)
+    e |= cuda_ok(cudaMemcpyAsync(s->w.xmin[d], s->xmin_h[d].data(), (size_t)c.nc[d] * 4, cudaMemcpyHostToDevice, st));
+  e |= cuda_ok(cudaMemsetAsync(s->w.cell_count, 0, (size_t)c.ncell * 4, st));
+  e |= cuda_ok(cudaMemsetAsync(s->w.counters, 0, 4 * 8, st));
+  e |= cuda_ok(cudaMemsetAsync(s->w.status, 0, 8, st));
+  e |= cuda_ok(cudaMemsetAsync(s->w.sched_hdr, 0, (size_t)c.ncell * 4, st));
+  e |= cuda_ok(cudaStreamSynchronize(st));
+  s->has_state = false;
+  return e ? SDPD_ERR_CUDA : SDPD_OK;
+}
+
+int sdpd_set_state(sdpd_t* s, const double* q, const double* p, const double* eps, int on_device) {
+  if (!s) return SDPD_ERR_INVALID_ARG;
+  if (!s->ws) return SDPD_ERR_NO_WORKSPACE;
+  if (use_device(s) != SDPD_OK) return SDPD_ERR_CUDA;
+  const int64_t N = s->c.N;
+  if (N > 0 && (!q || !p || !eps)) return SDPD_ERR_INVALID_ARG;
+  if (!on_device) {
+    for (int64_t i = 0; i < N; ++i)
+      if (!(eps[i] > 0.0) || !isfinite(eps[i])) return SDPD_ERR_NONPOSITIVE_ENERGY;
+  }
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  int e = SDPD_OK;
+  cudaStream_t st = s->stream;
+  if (N > 0) {
+    e |= cuda_ok(cudaMemcpyAsync(s->w.io_q, q, (size_t)N * 3 * 8, kind, st));
+    e |= cuda_ok(cudaMemcpyAsync(s->w.io_p, p, (size_t)N * 3 * 8, kind, st));
+    e |= cuda_ok(cudaMemcpyAsync(s->w.io_e, eps, (size_t)N * 8, kind, st));
+  }
+  e |= cuda_ok(cudaMemsetAsync(s->w.counters, 0, 4 * 8, st));
+  e |= cuda_ok(cudaMemsetAsync(s->w.status, 0, 8, st));
+  if (e) return SDPD_ERR_CUDA;
+  if (s->prm.precision == SDPD_MIXED) do_load<Mixed>(s);
+  else do_load<Fp64>(s);
+  if (!on_device && N > 0) {
+    // host buffers may be reused by the caller as soon as we return
+    if (cudaStreamSynchronize(st) != cudaSuccess) return SDPD_ERR_CUDA;
+  }
+  s->fd_step = 0;
+  s->vv_step = 0;
+  s->has_state = true;
+  return launch_status();
+}
+
+int sdpd_get_state(sdpd_t* s, double* q, double* p, double* eps, int on_device) {
+  if (!s) return SDPD_ERR_INVALID_ARG;
+  if (!s->ws) return SDPD_ERR_NO_WORKSPACE;
+  if (use_device(s) != SDPD_OK) return SDPD_ERR_CUDA;
+  if (!s->has_state) return SDPD_ERR_NO_STATE;
+  const int64_t N = s->c.N;
+  cudaStream_t st = s->stream;
+  if (s->prm.precision == SDPD_MIXED) launch_unload<Mixed>(s->c, s->w, s->cur, st);
+  else launch_unload<Fp64>(s->c, s->w, s->cur, st);
+  s->launches += 1;
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  int e = SDPD_OK;
+  if (N > 0) {
+    if (q) e |= cuda_ok(cudaMemcpyAsync(q, s->w.io_q, (size_t)N * 3 * 8, kind, st));
+    if (p) e |= cuda_ok(cudaMemcpyAsync(p, s->w.io_p, (size_t)N * 3 * 8, kind, st));
+    if (eps) e |= cuda_ok(cudaMemcpyAsync(eps, s->w.io_e, (size_t)N * 8, kind, st));
+  }
+  if (e) return SDPD_ERR_CUDA;
+  return sdpd_sync(s);
+}
+
+int sdpd_step(sdpd_t* s, double dt, int64_t nsteps, uint64_t seed) {
+  if (!s) return SDPD_ERR_INVALID_ARG;
+  if (!(dt > 0) || !isfinite(dt) || nsteps < 0) return SDPD_ERR_INVALID_ARG;
+  if (!s->ws) return SDPD_ERR_NO_WORKSPACE;
+  if (use_device(s) != SDPD_OK) return SDPD_ERR_CUDA;
+  if (!s->has_state) return SDPD_ERR_NO_STATE;
+  if (s->prm.precision == SDPD_MIXED) do_steps<Mixed>(s, dt, nsteps, seed);
+  else do_steps<Fp64>(s, dt, nsteps, seed);
+  return launch_status();
+}
+
+int sdpd_sync(sdpd_t* s) {
+  if (!s) return SDPD_ERR_INVALID_ARG;
+  if (!s->ws) return SDPD_ERR_NO_WORKSPACE;
+  if (use_device(s) != SDPD_OK) return SDPD_ERR_CUDA;
+  int bits = 0;
+  if (cudaMemcpyAsync(&bits, s->w.status, sizeof(int), cudaMemcpyDeviceToHost, s->stream) != cudaSuccess)
+    return SDPD_ERR_CUDA;
+  if (cudaStreamSynchronize(s->stream) != cudaSuccess) return SDPD_ERR_CUDA;
+  if (cudaGetLastError() != cudaSuccess) return SDPD_ERR_CUDA;
+  return map_status(bits);
+}
+
+int sdpd_observables(sdpd_t* s, sdpd_obs* out) {
+  if (!s || !out) return SDPD_ERR_INVALID_ARG;
+  if (!s->ws) return SDPD_ERR_NO_WORKSPACE;
+  if (use_device(s) != SDPD_OK) return SDPD_ERR_CUDA;
+  if (!s->has_state) return SDPD_ERR_NO_STATE;
+  memset(out, 0, sizeof(*out));
+  if (s->prm.precision == SDPD_MIXED) do_observables<Mixed>(s);
+  else do_observables<Fp64>(s);
+  double o[8];
+  unsigned long long cnt[4];
+  if (cudaMemcpyAsync(o, s->w.obs, sizeof(o), cudaMemcpyDeviceToHost, s->stream) != cudaSuccess ||
+      cudaMemcpyAsync(cnt, s->w.counters, sizeof(cnt), cudaMemcpyDeviceToHost, s->stream) != cudaSuccess)
+    return SDPD_ERR_CUDA;
+  int st = sdpd_sync(s);
+  const int64_t N = s->c.N;
+  out->E_int = o[0];
+  out->E_kin = o[1];
+  out->E = o[0] + o[1];
+  out->P[0] = o[2]; out->P[1] = o[3]; out->P[2] = o[4];
+  out->T_kin = N > 1 ? 2.0 * o[1] / (3.0 * (double)(N - 1) * s->c.kB) : 0.0;
+  out->T_int = N > 0 ? o[5] / (double)N : 0.0;
+  out->eps_min = N > 0 ? o[6] : 0.0;
+  out->n_pairs = (int64_t)cnt[0];
+  out->n_accept = (int64_t)cnt[1];
+  out->n_reject_bound = (int64_t)cnt[2];
+  out->n_reject_metropolis = (int64_t)cnt[3];
+  out->fd_step = s->fd_step;
+  out->vv_step = s->vv_step;
+  out->status = st;
+  return st;
+}
+
+int sdpd_set_fd_step(sdpd_t* s, int64_t v) {
+  if (!s || v < 0) return SDPD_ERR_INVALID_ARG;
+  s->fd_step = v;
+  return SDPD_OK;
+}
+
+int64_t sdpd_get_fd_step(const sdpd_t* s) { return s ? s->fd_step : -1; }
+
+int sdpd_reset_counters(sdpd_t* s) {
+  if (!s) return SDPD_ERR_INVALID_ARG;
+  if (!s->ws) return SDPD_ERR_NO_WORKSPACE;
+  if (use_device(s) != SDPD_OK) return SDPD_ERR_CUDA;
+  return cuda_ok(cudaMemsetAsync(s->w.counters, 0, 4 * 8, s->stream));
+}
+
+int64_t sdpd_kernel_launches(const sdpd_t* s) { return s ? s->launches : -1; }
+
+int sdpd_enable_stage_timing(sdpd_t* s, int on) {
+  if (!s) return SDPD_ERR_INVALID_ARG;
+  if (cudaStreamSynchronize(s->stream) != cudaSuccess) return SDPD_ERR_CUDA;
+  drain_events(s);
+  s->timing = on != 0;
+  for (int k = 0; k < SDPD_NSTAGES; ++k) { s->stage_ms[k] = 0.0; s->stage_launches[k] = 0; }
+  return SDPD_OK;
+}
+
+int sdpd_stage_times(sdpd_t* s, double* ms, int64_t* launches, int n) {
+  if (!s || n < 0 || n > SDPD_NSTAGES) return SDPD_ERR_INVALID_ARG;
+  if (cudaStreamSynchronize(s->stream) != cudaSuccess) return SDPD_ERR_CUDA;
+  drain_events(s);
+  for (int k = 0; k < n; ++k) {
+    if (ms) ms[k] = s->stage_ms[k];
+    if (launches) launches[k] = s->stage_launches[k];
+  }
+  return SDPD_OK;
+}
+
+int sdpd_debug_get(sdpd_t* s, int what, void* dst, int64_t cap, int64_t* count) {
+  if (!s || !dst) return SDPD_ERR_INVALID_ARG;
+  if (!s->ws) return SDPD_ERR_NO_WORKSPACE;
+  if (use_device(s) != SDPD_OK) return SDPD_ERR_CUDA;
+  if (!s->has_state) return SDPD_ERR_NO_STATE;
+  const int64_t N = s->c.N;
+  const bool mixed = s->prm.precision == SDPD_MIXED;
+  cudaStream_t st = s->stream;
+  const int cur = s->cur;
+  if (count) *count = 0;
+  std::vector<int32_t> ids((size_t)N);
+  if (N > 0 && cudaMemcpyAsync(ids.data(), s->w.id[cur], (size_t)N * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return SDPD_ERR_CUDA;
+  switch (what) {
+    case SDPD_DEBUG_ORDER: {
+      if (cap < N) return SDPD_ERR_INVALID_ARG;
+      if (cudaStreamSynchronize(st) != cudaSuccess) return SDPD_ERR_CUDA;
+      int64_t* o = (int64_t*)dst;
+      for (int64_t t = 0; t < N; ++t) o[t] = ids[(size_t)t];
+      if (count) *count = N;
+      return sdpd_sync(s);
+    }
+    case SDPD_DEBUG_CELLS: {
+      if (cap < N) return SDPD_ERR_INVALID_ARG;
+      const size_t rec = mixed ? 16 : 32;
+      std::vector<unsigned char> q4((size_t)N * rec);
+      if (N > 0 && cudaMemcpyAsync(q4.data(), s->w.q4[cur], (size_t)N * rec, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return SDPD_ERR_CUDA;
+      if (cudaStreamSynchronize(st) != cudaSuccess) return SDPD_ERR_CUDA;
+      int32_t* o = (int32_t*)dst;
+      for (int64_t t = 0; t < N; ++t) {
+        uint32_t cb;
+        if (mixed) {
+          memcpy(&cb, &q4[(size_t)t * rec + 12], 4);
+        } else {
+          double w;
+          memcpy(&w, &q4[(size_t)t * rec + 24], 8);
+          cb = (uint32_t)w;
+        }
+        int cx, cy, cz;
+        unpack_cell(cb, cx, cy, cz);
+        const int64_t k = ids[(size_t)t];
+        o[3 * k] = cx; o[3 * k + 1] = cy; o[3 * k + 2] = cz;
+      }
+      if (count) *count = N;
+      return sdpd_sync(s);
+    }
+    case SDPD_DEBUG_RHO: {
+      if (cap < N) return SDPD_ERR_INVALID_ARG;
+      double* o = (double*)dst;
+      if (mixed) {
+        std::vector<float> r((size_t)N);
+        if (N > 0 && cudaMemcpyAsync(r.data(), s->w.rho[cur], (size_t)N * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+          return SDPD_ERR_CUDA;
+        if (cudaStreamSynchronize(st) != cudaSuccess) return SDPD_ERR_CUDA;
+        for (int64_t t = 0; t < N; ++t) o[ids[(size_t)t]] = r[(size_t)t];
+      } else {
+        std::vector<double> r((size_t)N);
+        if (N > 0 && cudaMemcpyAsync(r.data(), s->w.rho[cur], (size_t)N * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+          return SDPD_ERR_CUDA;
+        if (cudaStreamSynchronize(st) != cudaSuccess) return SDPD_ERR_CUDA;
+        for (int64_t t = 0; t < N; ++t) o[ids[(size_t)t]] = r[(size_t)t];
+      }
+      if (count) *count = N;
+      return sdpd_sync(s);
+    }
+    case SDPD_DEBUG_FORCE: {
+      if (cap < 3 * N) return SDPD_ERR_INVALID_ARG;
+      if (mixed) launch_force<Mixed>(s->c, s->w, cur, 0.0, 0.0, s->w.io_p, st);
+      else launch_force<Fp64>(s->c, s->w, cur, 0.0, 0.0, s->w.io_p, st);
+      s->launches += 1;
+      if (N > 0 && cudaMemcpyAsync(dst, s->w.io_p, (size_t)N * 24, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return SDPD_ERR_CUDA;
+      if (count) *count = 3 * N;
+      return sdpd_sync(s);
+    }
+    case SDPD_DEBUG_NCOUNT: {
+      if (cap < N) return SDPD_ERR_INVALID_ARG;
+      if (mixed) launch_density<Mixed>(s->c, s->w, cur, 0, (int32_t*)s->w.io_q, st);
+      else launch_density<Fp64>(s->c, s->w, cur, 0, (int32_t*)s->w.io_q, st);
+      s->launches += 1;
+      if (N > 0 && cudaMemcpyAsync(dst, s->w.io_q, (size_t)N * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return SDPD_ERR_CUDA;
+      if (count) *count = N;
+      return sdpd_sync(s);
+    }
+    case SDPD_DEBUG_PAIRS: {
+      if (!s->w.pair_recs) return SDPD_ERR_INVALID_ARG;
+      unsigned long long n = 0;
+      if (cudaMemcpyAsync(&n, s->w.pair_rec_count, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess) return SDPD_ERR_CUDA;
+      if (cudaStreamSynchronize(st) != cudaSuccess) return SDPD_ERR_CUDA;
+      int64_t m = std::min<int64_t>((int64_t)n, s->w.pair_rec_cap);
+      if (cap < m) return SDPD_ERR_INVALID_ARG;
+      if (m > 0 && cudaMemcpyAsync(dst, s->w.pair_recs, (size_t)m * sizeof(sdpd_pair_rec), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return SDPD_ERR_CUDA;
+      if (count) *count = m;
+      int r = sdpd_sync(s);
+      if (r == SDPD_OK && (int64_t)n > s->w.pair_rec_cap) return SDPD_ERR_CAPACITY;
+      return r;
+    }
+    default:
+      return SDPD_ERR_INVALID_ARG;
+  }
+}
+
+void sdpd_destroy(sdpd_t* s) {
+  if (!s) return;
+  if (!s->ev_pending.empty()) {
+    cudaStreamSynchronize(s->stream);
+    drain_events(s);
+  }
+  for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
+  delete s;
+}
+
+}  // extern "C"

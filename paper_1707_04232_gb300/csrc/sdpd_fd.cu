@@ -1,0 +1,622 @@
+// sdpd_fd.cu -- the pairwise fluctuation/dissipation sweep (Sections 3.2-3.3)
+// made data-parallel by a conflict-free pair colouring.
+//
+// Colouring.  A pair whose particles sit in cells a and b (equal or adjacent
+// along each axis, since the cell side is >= h) is owned by the cell o that is
+// the lower of a and b along each axis (periodically); both cells then lie in
+// the 2x2x2 block o + {0,1}^3.  With local cell codes delta in 0..7 (bit k =
+// offset along axis k) a pair of cells (dA, dB) of the block is owned by o iff
+// dA & dB == 0.  The colour of o is its parity pattern; blocks of one colour
+// are disjoint when every cell count is even, so the 8 colours are swept one
+// after the other and the blocks of a colour in parallel.
+//
+// Order inside a block.  Pairs go by (rank(j) - rank(i), rank(i)), rank = the
+// position of the id among the block's particles, i the lower id.  Any
+// schedule that keeps, for every particle, its pairs in that order gives the
+// same result as the sequential sweep; the schedule used here runs the pairs
+// in dependency levels (level = length of the longest chain of earlier pairs
+// sharing a particle), so the pairs of a level touch disjoint particles.
+//
+// Three kernels per sweep prepare the schedule of every block (positions are
+// fixed during the sweep): k_sched_enum (one warp per block: owned pairs,
+// canonical order), k_sched_levels (one thread per block: dependency levels,
+// pairs bucketed by level); then k_fd_colour runs once per colour (one warp
+// per block: the pair updates level by level in shared memory).
+#include "sdpd_internal.cuh"
+
+namespace sdpd {
+
+constexpr int kRowWords = kMaxBlock / 32;  // words of one bitmap row
+
+// Cells of the block of owner (ox, oy, oz): start / count in storage order,
+// and the local offset of each cell in the block's concatenation.
+struct BlockCells {
+  int start[8], cnt[8], base[9];
+};
+
+__device__ __forceinline__ void block_cells(const Consts& c, int ox, int oy, int oz,
+                                            const int32_t* __restrict__ mrank,
+                                            const int32_t* __restrict__ cell_start, BlockCells& b) {
+  b.base[0] = 0;
+#pragma unroll
+  for (int d = 0; d < 8; ++d) {
+    int cx = ox + (d & 1), cy = oy + ((d >> 1) & 1), cz = oz + ((d >> 2) & 1);
+    if (cx >= c.nc[0]) cx -= c.nc[0];
+    if (cy >= c.nc[1]) cy -= c.nc[1];
+    if (cz >= c.nc[2]) cz -= c.nc[2];
+    int r = __ldg(&mrank[cx + c.nc[0] * (cy + c.nc[1] * cz)]);
+    b.start[d] = __ldg(&cell_start[r]);
+    b.cnt[d] = __ldg(&cell_start[r + 1]) - b.start[d];
+    b.base[d + 1] = b.base[d] + b.cnt[d];
+  }
+}
+
+__device__ __forceinline__ int cell_code_of(const BlockCells& b, int k) {
+  int d = 0;
+#pragma unroll
+  for (int t = 1; t < 8; ++t) d += (k >= b.base[t]);
+  return d;
+}
+
+// Block-local coordinates of a particle.  Float64: absolute (the minimum
+// image is taken per pair, as in the neighbour search).  Mixed: relative to
+// the block's lower corner, from the cell-relative coordinates and the exact
+// fixed-point distance between cell corners.
+template <class P>
+struct BlockGeom;
+
+template <>
+struct BlockGeom<Fp64> {
+  double L[3], halfL[3];
+  __device__ void init(const Consts& c, int, int, int, const uint32_t*, const uint32_t*, const uint32_t*) {
+    for (int d = 0; d < 3; ++d) { L[d] = c.L[d]; halfL[d] = c.halfL[d]; }
+  }
+  __device__ __forceinline__ void local(const D4& q, int, double& x, double& y, double& z) const {
+    x = q.x; y = q.y; z = q.z;
+  }
+  __device__ __forceinline__ void disp(double xa, double ya, double za, double xb, double yb, double zb,
+                                       double& dx, double& dy, double& dz) const {
+    dx = min_image(__dsub_rn(xa, xb), L[0], halfL[0]);
+    dy = min_image(__dsub_rn(ya, yb), L[1], halfL[1]);
+    dz = min_image(__dsub_rn(za, zb), L[2], halfL[2]);
+  }
+};
+
+template <>
+struct BlockGeom<Mixed> {
+  float off[3];  // corner of the upper cell relative to the lower one, per axis
+  __device__ void init(const Consts& c, int ox, int oy, int oz, const uint32_t* xmx, const uint32_t* xmy,
+                       const uint32_t* xmz) {
+    int o[3] = {ox, oy, oz};
+    const uint32_t* xm[3] = {xmx, xmy, xmz};
+    for (int d = 0; d < 3; ++d) {
+      int up = o[d] + 1 >= c.nc[d] ? 0 : o[d] + 1;
+      off[d] = (float)(int32_t)(xm[d][up] - xm[d][o[d]]) * (float)c.scale[d];
+    }
+  }
+  __device__ __forceinline__ void local(const F4& q, int code, float& x, float& y, float& z) const {
+    x = q.x + ((code & 1) ? off[0] : 0.0f);
+    y = q.y + ((code & 2) ? off[1] : 0.0f);
+    z = q.z + ((code & 4) ? off[2] : 0.0f);
+  }
+  __device__ __forceinline__ void disp(float xa, float ya, float za, float xb, float yb, float zb, float& dx,
+                                       float& dy, float& dz) const {
+    dx = xa - xb; dy = ya - yb; dz = za - zb;
+  }
+};
+
+__device__ __forceinline__ void owner_coords(const Consts& c, int64_t o, int& ox, int& oy, int& oz) {
+  ox = (int)(o % c.nc[0]);
+  oy = (int)((o / c.nc[0]) % c.nc[1]);
+  oz = (int)(o / ((int64_t)c.nc[0] * c.nc[1]));
+}
+
+// ---------------------------------------------------------------------------
+// Schedule, step 1: owned pairs of every block in canonical order.
+// ---------------------------------------------------------------------------
+constexpr int kSchedWarps = 2;
+
+template <class P>
+struct SchedSmem {
+  using R = typename P::R;
+  int32_t id[kMaxBlock];
+  R x[kMaxBlock], y[kMaxBlock], z[kMaxBlock];
+  uint8_t rank[kMaxBlock];
+  uint8_t perm[kMaxBlock];
+  uint32_t bits[kMaxBlock][kRowWords];  // row = rank difference, bit = lower rank
+  int32_t rowoff[kMaxBlock + 1];
+};
+
+template <class P>
+__global__ void __launch_bounds__(kSchedWarps * 32)
+    k_sched_enum(Consts c, Arrays<P> a, const int32_t* __restrict__ cell_start, const int32_t* __restrict__ mrank,
+                 const uint32_t* __restrict__ xmx, const uint32_t* __restrict__ xmy,
+                 const uint32_t* __restrict__ xmz, uint32_t* __restrict__ hdr, uint16_t* __restrict__ canon,
+                 int* status) {
+  using R = typename P::R;
+  __shared__ SchedSmem<P> sm_all[kSchedWarps];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t o = (int64_t)blockIdx.x * kSchedWarps + warp;
+  if (o >= c.ncell) return;
+  SchedSmem<P>& sm = sm_all[warp];
+  int ox, oy, oz;
+  owner_coords(c, o, ox, oy, oz);
+  BlockCells b;
+  block_cells(c, ox, oy, oz, mrank, cell_start, b);
+  const int nb = b.base[8];
+  if (nb > kMaxBlock) {
+    if (lane == 0) { atomicOr(status, kStCapacity); hdr[o] = 0; }
+    return;
+  }
+  BlockGeom<P> geo;
+  geo.init(c, ox, oy, oz, xmx, xmy, xmz);
+  for (int t = lane; t < kMaxBlock * kRowWords; t += 32) (&sm.bits[0][0])[t] = 0u;
+  for (int k = lane; k < nb; k += 32) {
+    const int d = cell_code_of(b, k);
+    const int g = b.start[d] + (k - b.base[d]);
+    sm.id[k] = a.id[g];
+    R x, y, z;
+    geo.local(ld4(&a.q4[g]), d, x, y, z);
+    sm.x[k] = x; sm.y[k] = y; sm.z[k] = z;
+  }
+  __syncwarp();
+  // rank of each id among the block's ids: every cell's ids are ascending
+  for (int k = lane; k < nb; k += 32) {
+    const int32_t myid = sm.id[k];
+    int r = 0;
+    for (int d = 0; d < 8; ++d) {
+      int lo = b.base[d], hi = b.base[d + 1];
+      while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (sm.id[mid] < myid) lo = mid + 1;
+        else hi = mid;
+      }
+      r += lo - b.base[d];
+    }
+    sm.rank[k] = (uint8_t)r;
+    sm.perm[r] = (uint8_t)k;
+  }
+  __syncwarp();
+  // owned cell pairs (dA & dB) == 0, candidates r^2 < h^2 (r > 0)
+  const R h2 = (R)c.h2;
+  for (int dA = 0; dA < 8; ++dA) {
+    for (int dB = dA; dB < 8; ++dB) {
+      if (dA & dB) continue;
+      const int nA = b.cnt[dA], nB = b.cnt[dB];
+      const int total = nA * nB;
+      if (total == 0) continue;
+      const float inv_nB = 1.0f / (float)nB;
+      for (int t = lane; t < total; t += 32) {
+        const int ia = (int)(((float)t + 0.5f) * inv_nB);  // exact floor(t / nB) for t < 2^16
+        const int ib = t - ia * nB;
+        if (dA == dB && ia >= ib) continue;
+        const int ka = b.base[dA] + ia, kb = b.base[dB] + ib;
+        R dx, dy, dz;
+        geo.disp(sm.x[ka], sm.y[ka], sm.z[ka], sm.x[kb], sm.y[kb], sm.z[kb], dx, dy, dz);
+        const R r2 = r2_of(dx, dy, dz);
+        if (r2 < h2 && r2 > R(0)) {
+          const int ra = sm.rank[ka], rb = sm.rank[kb];
+          const int lo = min(ra, rb), df = max(ra, rb) - lo;
+          atomicOr(&sm.bits[df][lo >> 5], 1u << (lo & 31));
+        }
+      }
+    }
+  }
+  __syncwarp();
+  // exclusive scan of the row populations (8 rows per lane)
+  int cnt8[8], sum = 0;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int row = lane * 8 + q;
+    int n = 0;
+#pragma unroll
+    for (int w = 0; w < kRowWords; ++w) n += __popc(sm.bits[row][w]);
+    cnt8[q] = n;
+    sum += n;
+  }
+  int incl = sum;
+  for (int s = 1; s < 32; s <<= 1) {
+    int t = __shfl_up_sync(0xffffffffu, incl, s);
+    if (lane >= s) incl += t;
+  }
+  const int npairs = __shfl_sync(0xffffffffu, incl, 31);
+  int run = incl - sum;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    sm.rowoff[lane * 8 + q] = run;
+    run += cnt8[q];
+  }
+  if (npairs > kMaxPairs) {
+    if (lane == 0) { atomicOr(status, kStCapacity); hdr[o] = 0; }
+    return;
+  }
+  __syncwarp();
+  // write the pairs row by row (difference ascending), lower rank ascending
+  uint16_t* out = canon + o * kMaxPairs;
+  for (int row = lane; row < kMaxBlock; row += 32) {
+    int pos = sm.rowoff[row];
+    for (int w = 0; w < kRowWords; ++w) {
+      uint32_t bits = sm.bits[row][w];
+      while (bits) {
+        const int bit = __ffs(bits) - 1;
+        bits &= bits - 1;
+        const int lo = w * 32 + bit;
+        out[pos++] = (uint16_t)(sm.perm[lo] | (sm.perm[lo + row] << 8));
+      }
+    }
+  }
+  if (lane == 0) hdr[o] = (uint32_t)npairs;
+}
+
+// ---------------------------------------------------------------------------
+// Schedule, step 2: dependency levels of the canonical order and the pairs
+// bucketed by level (one thread per block).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) k_sched_levels(int64_t ncell, uint32_t* __restrict__ hdr,
+                                                      const uint16_t* __restrict__ canon,
+                                                      uint16_t* __restrict__ lvl, uint16_t* __restrict__ pairs,
+                                                      int* status) {
+  const int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (o >= ncell) return;
+  const int np = (int)(hdr[o] & 0xffffu);
+  uint16_t* off = lvl + o * (kMaxLevels + 1);
+  const uint16_t* in = canon + o * kMaxPairs;
+  uint16_t* out = pairs + o * kMaxPairs;
+  uint8_t last[kMaxBlock];
+  uint16_t cnt[kMaxLevels + 1];
+  for (int k = 0; k < kMaxBlock; ++k) last[k] = 0;
+  for (int k = 0; k <= kMaxLevels; ++k) cnt[k] = 0;
+  int nlev = 0;
+  bool overflow = false;
+  for (int k = 0; k < np; ++k) {
+    const uint16_t pr = in[k];
+    const int u = pr & 255, v = pr >> 8;
+    const int L = max(last[u], last[v]);
+    if (L >= kMaxLevels) { overflow = true; break; }
+    last[u] = last[v] = (uint8_t)(L + 1);
+    cnt[L]++;
+    nlev = max(nlev, L + 1);
+  }
+  if (overflow) {
+    atomicOr(status, kStCapacity);
+    hdr[o] = 0;
+    off[0] = 0;
+    return;
+  }
+  int run = 0;
+  for (int L = 0; L < nlev; ++L) {
+    const int n = cnt[L];
+    off[L] = (uint16_t)run;
+    cnt[L] = (uint16_t)run;
+    run += n;
+  }
+  off[nlev] = (uint16_t)run;
+  for (int k = 0; k < kMaxBlock; ++k) last[k] = 0;
+  for (int k = 0; k < np; ++k) {
+    const uint16_t pr = in[k];
+    const int u = pr & 255, v = pr >> 8;
+    const int L = max(last[u], last[v]);
+    last[u] = last[v] = (uint8_t)(L + 1);
+    out[cnt[L]++] = pr;
+  }
+  hdr[o] = (uint32_t)np | ((uint32_t)nlev << 16);
+}
+
+// ---------------------------------------------------------------------------
+// One pair update.
+// ---------------------------------------------------------------------------
+template <class R>
+struct FDConst {
+  R m, inv_m, half_m, inv_h, cF;
+  R kpar_m2, kperp_m2;  // (10/3 eta + 4 zeta) m^2, (5/3 eta - zeta) m^2
+  R inv_C_K, kB, two_over_CK, dt_over_m;
+  R CKm1;               // C_K / kB - 1
+  R four_kB_over_m;
+  int scheme;
+};
+
+// alpha = exp(-2 gamma dt / m) and zt = (2/m) zeta of Section 3.2 for both
+// directions at energies (ei, ej), with gamma = kappa (1 - d) and
+// sigma = 2 sqrt(kappa kB Ti Tj / (Ti + Tj)) of Eq. (sdpd-gamma-sigma):
+// zt^2 = sigma^2 (1 - alpha^2) / (m gamma) = 4 kB Ti Tj / ((Ti+Tj) m (1-d)) (1 - alpha^2)
+// (kappa cancels).  Ideal gas: T = eps / C_K and C = C_K, so
+// d = kB Ti Tj / (Ti + Tj)^2 * 2 / C_K.
+template <class R>
+__device__ __forceinline__ void pair_coeffs(const FDConst<R>& k, R kpar, R kperp, R ei, R ej, R& apar,
+                                            R& aperp, R& zpar, R& zperp) {
+  const R Ti = ei * k.inv_C_K, Tj = ej * k.inv_C_K;
+  const R sT = Ti + Tj, pT = Ti * Tj;
+  const R hT = pT / sT;
+  const R d = k.kB * hT / sT * k.two_over_CK;
+  const R omd = R(1) - d;
+  const R xpar = R(-2) * kpar * omd * k.dt_over_m, xperp = R(-2) * kperp * omd * k.dt_over_m;
+  apar = exp(xpar);
+  aperp = exp(xperp);
+  const R s = k.four_kB_over_m * hT / omd;
+  zpar = sqrt(s * -expm1(R(2) * xpar));
+  zperp = sqrt(s * -expm1(R(2) * xperp));
+}
+
+// Returns 0 accept, 1 energy-bound reject, 2 Metropolis reject.
+template <class P, int KIND>
+__device__ __forceinline__ int fd_pair(const FDConst<typename P::R>& k, typename P::R rx, typename P::R ry,
+                                       typename P::R rz, typename P::R rho_i, typename P::R rho_j,
+                                       typename P::R* pi, typename P::R* pj, double& ei, double& ej,
+                                       const typename P::R G[3], typename P::R U, double& margin,
+                                       bool& negative) {
+  using R = typename P::R;
+  const R r = sqrt(r2_of(rx, ry, rz));
+  const R inv_r = R(1) / r;
+  const R ex = rx * inv_r, ey = ry * inv_r, ez = rz * inv_r;
+  const R base = kernel_F<KIND>(r * k.inv_h, k.cF) / (rho_i * rho_j);
+  const R kpar = k.kpar_m2 * base, kperp = k.kperp_m2 * base;
+  margin = 0.0;
+  if (!(kperp > R(0)) || !(kpar > R(0))) return 0;  // at r = h the pair does nothing
+  const R vx = (pi[0] - pj[0]) * k.inv_m, vy = (pi[1] - pj[1]) * k.inv_m, vz = (pi[2] - pj[2]) * k.inv_m;
+  const R eir = (R)ei, ejr = (R)ej;
+  R apar, aperp, zpar, zperp;
+  pair_coeffs(k, kpar, kperp, eir, ejr, apar, aperp, zpar, zperp);
+  // proposal, Eq. (proposal): v' = sum_theta P^theta (alpha^theta v + zt^theta G)
+  const R vpar = ex * vx + ey * vy + ez * vz;
+  const R gpar = ex * G[0] + ey * G[1] + ez * G[2];
+  const R cpar = (apar - aperp) * vpar + (zpar - zperp) * gpar;
+  const R wx = aperp * vx + zperp * G[0] + cpar * ex;
+  const R wy = aperp * vy + zperp * G[1] + cpar * ey;
+  const R wz = aperp * vz + zperp * G[2] + cpar * ez;
+  // momenta of Eq. (proposal-update), energy shared equally (Section 3.2)
+  const R dpx = k.half_m * (wx - vx), dpy = k.half_m * (wy - vy), dpz = k.half_m * (wz - vz);
+  const R nix = pi[0] + dpx, niy = pi[1] + dpy, niz = pi[2] + dpz;
+  const R njx = pj[0] - dpx, njy = pj[1] - dpy, njz = pj[2] - dpz;
+  double deps;
+  R depsr;
+  if constexpr (P::mixed) {
+    // -1/2 of the kinetic-energy change of the stored momenta, as a sum of
+    // (new - old)(new + old) products so float32 carries no cancellation
+    const float dk = (nix - pi[0]) * (nix + pi[0]) + (niy - pi[1]) * (niy + pi[1]) +
+                     (niz - pi[2]) * (niz + pi[2]) + (njx - pj[0]) * (njx + pj[0]) +
+                     (njy - pj[1]) * (njy + pj[1]) + (njz - pj[2]) * (njz + pj[2]);
+    depsr = -0.25f * k.inv_m * dk;
+    deps = (double)depsr;
+  } else {
+    const double ko = pi[0] * pi[0] + pj[0] * pj[0] + pi[1] * pi[1] + pj[1] * pj[1] + pi[2] * pi[2] +
+                      pj[2] * pj[2];
+    const double kn = nix * nix + njx * njx + niy * niy + njy * njy + niz * niz + njz * njz;
+    deps = -0.5 * (kn - ko) * (0.5 * k.inv_m);
+    depsr = deps;
+  }
+  const double ein = ei + deps, ejn = ej + deps;
+  const double emin = fmin(ein, ejn);
+  int decision = 0;
+  margin = emin;
+  if (k.scheme == SDPD_SCHEME_SSA) {
+    if (!(emin > 0.0)) negative = true;
+  } else if (!(emin > 0.0)) {
+    decision = 1;  // energy bound, Eq. (energy-bound)
+  } else if (k.scheme == SDPD_SCHEME_EMS) {
+    // Metropolis ratio, Eq. (metropolis-ratio): the reverse move from v'
+    // with the coefficients at the proposed energies
+    R bpar, bperp, ypar, yperp;
+    pair_coeffs(k, kpar, kperp, eir + depsr, ejr + depsr, bpar, bperp, ypar, yperp);
+    const R wpar = ex * wx + ey * wy + ez * wz;
+    const R cb = (bpar - bperp) * wpar;
+    const R bx = vx - (bperp * wx + cb * ex), by = vy - (bperp * wy + cb * ey), bz = vz - (bperp * wz + cb * ez);
+    const R spar = ex * bx + ey * by + ez * bz;
+    const R ip = R(1) / yperp;
+    const R cq = (R(1) / ypar - ip) * spar;
+    const R qx = bx * ip + cq * ex, qy = by * ip + cq * ey, qz = bz * ip + cq * ez;
+    const R quad = qx * qx + qy * qy + qz * qz;
+    const R g2 = G[0] * G[0] + G[1] * G[1] + G[2] * G[2];
+    // log|B(v)| - log|B(v')| with |B| = zt_par zt_perp^2
+    const R ldet = log(zpar / ypar) + R(2) * log(zperp / yperp);
+    // (S(eps') - S(eps))/kB - (log T(eps') - log T(eps)) = (C_K/kB - 1) log(eps'/eps) per particle
+    const R ent = k.CKm1 * (log1p(depsr / eir) + log1p(depsr / ejr));
+    const R a = R(0.5) * (g2 - quad) + ldet + ent;
+    const R mg = a - log(U);
+    margin = (double)mg;
+    if (mg < R(0)) decision = 2;  // U > exp(a)
+  }
+  if (decision == 0) {
+    pi[0] = nix; pi[1] = niy; pi[2] = niz;
+    pj[0] = njx; pj[1] = njy; pj[2] = njz;
+    ei = ein;
+    ej = ejn;
+  }
+  return decision;
+}
+
+// ---------------------------------------------------------------------------
+// One colour of the sweep: one warp per block of that colour.
+// ---------------------------------------------------------------------------
+template <class P>
+struct FdSmem {
+  using R = typename P::R;
+  R px[kMaxBlock], py[kMaxBlock], pz[kMaxBlock];
+  double e[kMaxBlock];
+  R rho[kMaxBlock];
+  R x[kMaxBlock], y[kMaxBlock], z[kMaxBlock];
+  int32_t id[kMaxBlock];
+  int32_t g[kMaxBlock];
+};
+
+template <class P>
+constexpr int fd_warps() { return P::mixed ? 4 : 2; }
+
+template <class P, int KIND>
+__global__ void __launch_bounds__(fd_warps<P>() * 32)
+    k_fd_colour(Consts c, FDConst<typename P::R> k, Arrays<P> a, typename P::V4* __restrict__ qp4,
+                const int32_t* __restrict__ cell_start, const int32_t* __restrict__ mrank,
+                const uint32_t* __restrict__ xmx, const uint32_t* __restrict__ xmy,
+                const uint32_t* __restrict__ xmz, const uint32_t* __restrict__ hdr,
+                const uint16_t* __restrict__ lvl, const uint16_t* __restrict__ pairs, int colour, uint64_t seed,
+                uint64_t sweep, unsigned long long* counters, int* status, sdpd_pair_rec* recs,
+                unsigned long long* rec_count, int64_t rec_cap) {
+  using R = typename P::R;
+  constexpr int W = fd_warps<P>();
+  __shared__ FdSmem<P> sm_all[W];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int hx = c.nc[0] >> 1, hy = c.nc[1] >> 1, hz = c.nc[2] >> 1;
+  const int64_t w = (int64_t)blockIdx.x * W + warp;
+  if (w >= (int64_t)hx * hy * hz) return;
+  FdSmem<P>& sm = sm_all[warp];
+  const int ox = 2 * (int)(w % hx) + (colour & 1);
+  const int oy = 2 * (int)((w / hx) % hy) + ((colour >> 1) & 1);
+  const int oz = 2 * (int)(w / ((int64_t)hx * hy)) + ((colour >> 2) & 1);
+  const int64_t o = ox + (int64_t)c.nc[0] * (oy + (int64_t)c.nc[1] * oz);
+  const uint32_t hd = hdr[o];
+  const int np = (int)(hd & 0xffffu), nlev = (int)(hd >> 16);
+  if (np == 0) return;
+  BlockCells b;
+  block_cells(c, ox, oy, oz, mrank, cell_start, b);
+  const int nb = b.base[8];
+  BlockGeom<P> geo;
+  geo.init(c, ox, oy, oz, xmx, xmy, xmz);
+  for (int q = lane; q < nb; q += 32) {
+    const int d = cell_code_of(b, q);
+    const int g = b.start[d] + (q - b.base[d]);
+    sm.g[q] = g;
+    sm.px[q] = a.px[g]; sm.py[q] = a.py[g]; sm.pz[q] = a.pz[g];
+    sm.e[q] = a.eps[g];
+    sm.rho[q] = a.rho[g];
+    sm.id[q] = a.id[g];
+    R x, y, z;
+    geo.local(ld4(&a.q4[g]), d, x, y, z);
+    sm.x[q] = x; sm.y[q] = y; sm.z[q] = z;
+  }
+  __syncwarp();
+  const uint16_t* off = lvl + o * (kMaxLevels + 1);
+  const uint16_t* pl = pairs + o * kMaxPairs;
+  unsigned long long n_acc = 0, n_rb = 0, n_rm = 0, n_tot = 0;
+  bool negative = false, bad = false;
+  for (int L = 0; L < nlev; ++L) {
+    const int beg = off[L], end = off[L + 1];
+    for (int t = beg + lane; t < end; t += 32) {
+      const uint16_t pr = pl[t];
+      const int ia = pr & 255, ib = pr >> 8;  // ia holds the lower id
+      R rx, ry, rz;
+      geo.disp(sm.x[ia], sm.y[ia], sm.z[ia], sm.x[ib], sm.y[ib], sm.z[ib], rx, ry, rz);
+      R G[3], U;
+      pair_randoms(seed, sweep, (uint64_t)sm.id[ia], (uint64_t)sm.id[ib], G, &U);
+      R pa[3] = {sm.px[ia], sm.py[ia], sm.pz[ia]};
+      R pb[3] = {sm.px[ib], sm.py[ib], sm.pz[ib]};
+      double ea = sm.e[ia], eb = sm.e[ib], margin;
+      const int dcs = fd_pair<P, KIND>(k, rx, ry, rz, sm.rho[ia], sm.rho[ib], pa, pb, ea, eb, G, U, margin,
+                                       negative);
+      if (dcs == 0) {
+        sm.px[ia] = pa[0]; sm.py[ia] = pa[1]; sm.pz[ia] = pa[2];
+        sm.px[ib] = pb[0]; sm.py[ib] = pb[1]; sm.pz[ib] = pb[2];
+        sm.e[ia] = ea;
+        sm.e[ib] = eb;
+        bad |= !isfinite(ea) || !isfinite(eb);
+      }
+      ++n_tot;
+      n_acc += dcs == 0;
+      n_rb += dcs == 1;
+      n_rm += dcs == 2;
+      if (recs) {
+        const unsigned long long s = atomicAdd(rec_count, 1ull);
+        if ((int64_t)s < rec_cap) {
+          sdpd_pair_rec rc;
+          rc.id_i = sm.id[ia];
+          rc.id_j = sm.id[ib];
+          rc.colour = colour;
+          rc.owner = (int32_t)o;
+          rc.decision = dcs;
+          rc.level = L;
+          rc.margin = margin;
+          recs[s] = rc;
+        }
+      }
+    }
+    __syncwarp();
+  }
+  const R pi_coef = (R)(c.c_rho / (c.C_K * c.m));
+  for (int q = lane; q < nb; q += 32) {
+    const int g = sm.g[q];
+    a.px[g] = sm.px[q]; a.py[g] = sm.py[q]; a.pz[g] = sm.pz[q];
+    const double e = sm.e[q];
+    a.eps[g] = e;
+    // pressure over rho^2 of the new energy, Eq. (pg-eos): pi = c_rho eps / (C_K m rho)
+    qp4[g].w = (R)e * pi_coef / sm.rho[q];
+  }
+  // counters
+  for (int s = 16; s > 0; s >>= 1) {
+    n_tot += __shfl_xor_sync(0xffffffffu, n_tot, s);
+    n_acc += __shfl_xor_sync(0xffffffffu, n_acc, s);
+    n_rb += __shfl_xor_sync(0xffffffffu, n_rb, s);
+    n_rm += __shfl_xor_sync(0xffffffffu, n_rm, s);
+  }
+  const unsigned any_neg = __any_sync(0xffffffffu, negative), any_bad = __any_sync(0xffffffffu, bad);
+  if (lane == 0) {
+    atomicAdd(&counters[0], n_tot);
+    atomicAdd(&counters[1], n_acc);
+    atomicAdd(&counters[2], n_rb);
+    atomicAdd(&counters[3], n_rm);
+    if (any_neg) atomicOr(status, kStNegative);
+    if (any_bad) atomicOr(status, kStNaN);
+  }
+}
+
+template <class R>
+static FDConst<R> fd_const(const Consts& c, double dt) {
+  FDConst<R> k;
+  k.m = (R)c.m;
+  k.inv_m = (R)(1.0 / c.m);
+  k.half_m = (R)(0.5 * c.m);
+  k.inv_h = (R)(1.0 / c.h);
+  k.cF = (R)c.cF;
+  k.kpar_m2 = (R)c.kpar_m2;
+  k.kperp_m2 = (R)c.kperp_m2;
+  k.inv_C_K = (R)(1.0 / c.C_K);
+  k.kB = (R)c.kB;
+  k.two_over_CK = (R)(2.0 / c.C_K);
+  k.dt_over_m = (R)(dt / c.m);
+  k.CKm1 = (R)(c.C_K / c.kB - 1.0);
+  k.four_kB_over_m = (R)(4.0 * c.kB / c.m);
+  k.scheme = c.scheme;
+  return k;
+}
+
+template <class P>
+void launch_fd_schedule(const Consts& c, const Workspace& w, int cur, cudaStream_t s) {
+  if (c.N == 0) return;
+  Arrays<P> a = view<P>(w, cur);
+  uint16_t* canon = w.sched_pair + (size_t)c.ncell * kMaxPairs;
+  const unsigned gs = (unsigned)((c.ncell + kSchedWarps - 1) / kSchedWarps);
+  k_sched_enum<P><<<gs, kSchedWarps * 32, 0, s>>>(c, a, w.cell_start, w.mrank, w.xmin[0], w.xmin[1],
+                                                   w.xmin[2], w.sched_hdr, canon, w.status);
+  k_sched_levels<<<(unsigned)((c.ncell + 127) / 128), 128, 0, s>>>(c.ncell, w.sched_hdr, canon, w.sched_lvl,
+                                                                   w.sched_pair, w.status);
+}
+
+template <class P>
+void launch_fd_colours(const Consts& c, const Workspace& w, int cur, double dt, uint64_t seed, uint64_t sweep,
+                       int record, cudaStream_t s) {
+  if (c.N == 0) return;
+  using R = typename P::R;
+  Arrays<P> a = view<P>(w, cur);
+  const FDConst<R> k = fd_const<R>(c, dt);
+  constexpr int W = fd_warps<P>();
+  const int64_t nown = (int64_t)(c.nc[0] / 2) * (c.nc[1] / 2) * (c.nc[2] / 2);
+  const unsigned gf = (unsigned)((nown + W - 1) / W);
+  auto qp4 = (typename P::V4*)w.qp4;
+  sdpd_pair_rec* recs = record ? w.pair_recs : nullptr;
+  for (int col = 0; col < 8; ++col) {
+    if (c.kernel == SDPD_KERNEL_LUCY)
+      k_fd_colour<P, SDPD_KERNEL_LUCY><<<gf, W * 32, 0, s>>>(
+          c, k, a, qp4, w.cell_start, w.mrank, w.xmin[0], w.xmin[1], w.xmin[2], w.sched_hdr, w.sched_lvl,
+          w.sched_pair, col, seed, sweep, w.counters, w.status, recs, w.pair_rec_count, w.pair_rec_cap);
+    else
+      k_fd_colour<P, SDPD_KERNEL_CUBIC><<<gf, W * 32, 0, s>>>(
+          c, k, a, qp4, w.cell_start, w.mrank, w.xmin[0], w.xmin[1], w.xmin[2], w.sched_hdr, w.sched_lvl,
+          w.sched_pair, col, seed, sweep, w.counters, w.status, recs, w.pair_rec_count, w.pair_rec_cap);
+  }
+}
+
+template void launch_fd_schedule<Fp64>(const Consts&, const Workspace&, int, cudaStream_t);
+template void launch_fd_schedule<Mixed>(const Consts&, const Workspace&, int, cudaStream_t);
+template void launch_fd_colours<Fp64>(const Consts&, const Workspace&, int, double, uint64_t, uint64_t, int,
+                                      cudaStream_t);
+template void launch_fd_colours<Mixed>(const Consts&, const Workspace&, int, double, uint64_t, uint64_t, int,
+                                       cudaStream_t);
+
+}  // namespace sdpd

@@ -288,8 +288,10 @@ template <class P>
 void launch_force(const Consts& c, const Workspace& w, int cur, double half_dt, double dt_drift,
                   double* force_by_id, cudaStream_t s);
 template <class P>
-void launch_fd(const Consts& c, const Workspace& w, int cur, double dt, uint64_t seed, uint64_t sweep,
-               int record, cudaStream_t s);
+void launch_fd_schedule(const Consts& c, const Workspace& w, int cur, cudaStream_t s);
+template <class P>
+void launch_fd_colours(const Consts& c, const Workspace& w, int cur, double dt, uint64_t seed, uint64_t sweep,
+                       int record, cudaStream_t s);
 template <class P>
 void launch_observables(const Consts& c, const Workspace& w, int cur, cudaStream_t s);
 

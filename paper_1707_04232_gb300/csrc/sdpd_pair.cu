@@ -86,10 +86,13 @@ __global__ void __launch_bounds__(128) k_density(Consts c, Arrays<P> a, typename
   const R h2 = (R)c.h2, inv_h = R(1) / (R)c.h, cW = (R)c.cW;
   R acc = R(0);
   int cnt = 0;
+#pragma unroll
   for (int oz = -1; oz <= 1; ++oz) {
     const int nz = wrapc(cz + oz, c.nc[2]);
+#pragma unroll
     for (int oy = -1; oy <= 1; ++oy) {
       const int ny = wrapc(cy + oy, c.nc[1]);
+#pragma unroll
       for (int ox = -1; ox <= 1; ++ox) {
         const int nx = wrapc(cx + ox, c.nc[0]);
         const int r = __ldg(&mrank[nx + c.nc[0] * (ny + c.nc[1] * nz)]);
@@ -127,7 +130,7 @@ __global__ void __launch_bounds__(128) k_density(Consts c, Arrays<P> a, typename
   a.rho[i] = rho_new;
   R pi;
   if constexpr (P::mixed) pi = (float)e * (float)(c.c_rho / (c.C_K * c.m)) / rho_new;
-  else pi = c.c_rho * e / (c.C_K * c.m * rho_new);
+  else pi = e * (c.c_rho / (c.C_K * c.m)) / rho_new;
   V4 o = qi;
   o.w = pi;
   st4(&qp4[i], o);
@@ -163,10 +166,13 @@ __global__ void __launch_bounds__(128) k_force(Consts c, Arrays<P> a, const type
   home.init(c, qi, cx, cy, cz, xmx, xmy, xmz);
   const R h2 = (R)c.h2, inv_h = R(1) / (R)c.h, cF = (R)c.cF;
   R fx = R(0), fy = R(0), fz = R(0);
+#pragma unroll
   for (int oz = -1; oz <= 1; ++oz) {
     const int nz = wrapc(cz + oz, c.nc[2]);
+#pragma unroll
     for (int oy = -1; oy <= 1; ++oy) {
       const int ny = wrapc(cy + oy, c.nc[1]);
+#pragma unroll
       for (int ox = -1; ox <= 1; ++ox) {
         const int nx = wrapc(cx + ox, c.nc[0]);
         const int r = __ldg(&mrank[nx + c.nc[0] * (ny + c.nc[1] * nz)]);

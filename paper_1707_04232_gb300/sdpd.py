@@ -1,0 +1,333 @@
+"""ctypes binding of the SDPD C ABI (include/sdpd.h).
+
+Argument marshalling only: every step of the path runs in the CUDA library.
+PyTorch provides the device workspace and the stream.  There is no CPU
+fallback: if the CUDA library cannot be loaded, importing this module fails.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+OK = 0
+ERR_INVALID_ARG, ERR_BOX_TOO_SMALL, ERR_NONPOSITIVE_ENERGY, ERR_NEGATIVE_ENERGY = 1, 2, 3, 4
+ERR_NAN, ERR_CUDA, ERR_TIMEOUT, ERR_NO_WORKSPACE, ERR_CAPACITY, ERR_NO_STATE = 5, 6, 7, 8, 9, 10
+KERNEL_CUBIC, KERNEL_LUCY = 0, 1
+SCHEME_SSA, SCHEME_AMS, SCHEME_EMS, SCHEME_NONE = 0, 1, 2, 3
+FP64, MIXED = 0, 1
+DEBUG_ORDER, DEBUG_CELLS, DEBUG_RHO, DEBUG_FORCE, DEBUG_NCOUNT, DEBUG_PAIRS = range(6)
+
+
+class sdpd_params(C.Structure):
+    _fields_ = [
+        ("kB", C.c_double), ("eta", C.c_double), ("zeta", C.c_double), ("c_rho", C.c_double),
+        ("kernel", C.c_int), ("scheme", C.c_int), ("precision", C.c_int), ("fd_only", C.c_int),
+        ("theta", C.c_int), ("debug", C.c_int),
+    ]
+
+
+class sdpd_obs(C.Structure):
+    _fields_ = [
+        ("E", C.c_double), ("E_int", C.c_double), ("E_kin", C.c_double), ("P", C.c_double * 3),
+        ("T_kin", C.c_double), ("T_int", C.c_double), ("eps_min", C.c_double),
+        ("n_pairs", C.c_int64), ("n_accept", C.c_int64), ("n_reject_bound", C.c_int64),
+        ("n_reject_metropolis", C.c_int64), ("fd_step", C.c_int64), ("vv_step", C.c_int64),
+        ("status", C.c_int),
+    ]
+
+
+PAIR_REC_DTYPE = np.dtype([
+    ("id_i", np.int64), ("id_j", np.int64), ("colour", np.int32), ("owner", np.int32),
+    ("decision", np.int32), ("level", np.int32), ("margin", np.float64),
+])
+
+# Every symbol include/sdpd.h declares: (name, restype, argtypes).
+_H = C.c_void_p
+_dp = C.POINTER(C.c_double)
+SIGNATURES = [
+    ("sdpd_create", C.c_int, [C.c_int64, _dp, C.c_double, C.c_double, C.c_double,
+                              C.POINTER(sdpd_params), C.c_void_p, C.POINTER(_H)]),
+    ("sdpd_workspace_bytes", C.c_size_t, [_H]),
+    ("sdpd_bind_workspace", C.c_int, [_H, C.c_void_p, C.c_size_t]),
+    ("sdpd_set_state", C.c_int, [_H, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+    ("sdpd_get_state", C.c_int, [_H, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+    ("sdpd_step", C.c_int, [_H, C.c_double, C.c_int64, C.c_uint64]),
+    ("sdpd_observables", C.c_int, [_H, C.POINTER(sdpd_obs)]),
+    ("sdpd_sync", C.c_int, [_H]),
+    ("sdpd_set_fd_step", C.c_int, [_H, C.c_int64]),
+    ("sdpd_get_fd_step", C.c_int64, [_H]),
+    ("sdpd_reset_counters", C.c_int, [_H]),
+    ("sdpd_kernel_launches", C.c_int64, [_H]),
+    ("sdpd_enable_stage_timing", C.c_int, [_H, C.c_int]),
+    ("sdpd_stage_times", C.c_int, [_H, _dp, C.POINTER(C.c_int64), C.c_int]),
+    ("sdpd_debug_get", C.c_int, [_H, C.c_int, C.c_void_p, C.c_int64, C.POINTER(C.c_int64)]),
+    ("sdpd_destroy", None, [_H]),
+    ("sdpd_strerror", C.c_char_p, [C.c_int]),
+]
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None):
+    """Load (building first if needed) the CUDA library; raises if impossible."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if path is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            _build.build()
+    lib = C.CDLL(path)
+    for name, res, args in SIGNATURES:
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+class SDPDError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        msg = load().sdpd_strerror(status).decode()
+        super().__init__("%s: %s (status %d)" % (where, msg, status))
+        self.status = status
+
+
+def _check(status: int, where: str):
+    if status != OK:
+        raise SDPDError(status, where)
+
+
+# --- thin wrappers with the C names ------------------------------------------------
+
+def sdpd_create(N, box, m, h, K, params: sdpd_params, stream: int = 0):
+    b = (C.c_double * 3)(*[float(x) for x in box])
+    out = _H()
+    st = load().sdpd_create(int(N), b, float(m), float(h), float(K), C.byref(params),
+                            C.c_void_p(stream), C.byref(out))
+    return st, out
+
+
+def sdpd_workspace_bytes(h) -> int:
+    return load().sdpd_workspace_bytes(h)
+
+
+def sdpd_bind_workspace(h, ptr: int, nbytes: int) -> int:
+    return load().sdpd_bind_workspace(h, C.c_void_p(ptr), nbytes)
+
+
+def sdpd_set_state(h, q, p, eps, on_device: int) -> int:
+    return load().sdpd_set_state(h, q, p, eps, on_device)
+
+
+def sdpd_get_state(h, q, p, eps, on_device: int) -> int:
+    return load().sdpd_get_state(h, q, p, eps, on_device)
+
+
+def sdpd_step(h, dt, nsteps, seed) -> int:
+    return load().sdpd_step(h, float(dt), int(nsteps), int(seed))
+
+
+def sdpd_observables(h, out: sdpd_obs) -> int:
+    return load().sdpd_observables(h, C.byref(out))
+
+
+def sdpd_sync(h) -> int:
+    return load().sdpd_sync(h)
+
+
+def sdpd_set_fd_step(h, v) -> int:
+    return load().sdpd_set_fd_step(h, int(v))
+
+
+def sdpd_get_fd_step(h) -> int:
+    return load().sdpd_get_fd_step(h)
+
+
+def sdpd_reset_counters(h) -> int:
+    return load().sdpd_reset_counters(h)
+
+
+def sdpd_kernel_launches(h) -> int:
+    return load().sdpd_kernel_launches(h)
+
+
+NSTAGES = 6
+STAGE_NAMES = ["kick1_drift_bin", "sort", "density_eos", "kick2", "fd_schedule", "fd_colours"]
+
+
+def sdpd_enable_stage_timing(h, on) -> int:
+    return load().sdpd_enable_stage_timing(h, int(bool(on)))
+
+
+def sdpd_stage_times(h):
+    ms = (C.c_double * NSTAGES)()
+    nl = (C.c_int64 * NSTAGES)()
+    st = load().sdpd_stage_times(h, ms, nl, NSTAGES)
+    return st, list(ms), list(nl)
+
+
+def sdpd_debug_get(h, what, dst_ptr, cap):
+    cnt = C.c_int64(0)
+    st = load().sdpd_debug_get(h, int(what), C.c_void_p(dst_ptr), int(cap), C.byref(cnt))
+    return st, cnt.value
+
+
+def sdpd_destroy(h):
+    load().sdpd_destroy(h)
+
+
+def sdpd_strerror(st) -> str:
+    return load().sdpd_strerror(int(st)).decode()
+
+
+# --- convenience object ------------------------------------------------------------
+
+def _ptr(a) -> int:
+    """Data pointer of a numpy array or a torch tensor."""
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return a.data_ptr()
+
+
+class SDPD:
+    """One SDPD system on the current CUDA device.
+
+    The workspace is a torch uint8 tensor owned by this object; all work runs
+    on ``stream`` (default: torch's current stream)."""
+
+    def __init__(self, N, box, m=1.0, h=2.5, K=100.0, *, kB=1.0, eta=1.0, zeta=0.0, c_rho=-1.0,
+                 kernel=KERNEL_LUCY, scheme=SCHEME_EMS, precision=FP64, fd_only=False, theta=1,
+                 debug=False, stream=None):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("SDPD needs a CUDA device")
+        self.torch = torch
+        self.N = int(N)
+        prm = sdpd_params(kB=kB, eta=eta, zeta=zeta, c_rho=c_rho, kernel=kernel, scheme=scheme,
+                          precision=precision, fd_only=int(bool(fd_only)), theta=int(theta),
+                          debug=int(bool(debug)))
+        self.params = prm
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        st, self.h = sdpd_create(N, box if np.ndim(box) else (box,) * 3, m, h, K, prm,
+                                 self.stream.cuda_stream)
+        _check(st, "sdpd_create")
+        nbytes = sdpd_workspace_bytes(self.h)
+        self.workspace = torch.empty(max(nbytes, 1), dtype=torch.uint8, device="cuda")
+        _check(sdpd_bind_workspace(self.h, self.workspace.data_ptr(), nbytes), "sdpd_bind_workspace")
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h:
+            try:
+                sdpd_sync(h)
+            finally:
+                sdpd_destroy(h)
+            self.h = None
+
+    def set_state(self, q, p, eps):
+        if isinstance(q, np.ndarray):
+            q = np.ascontiguousarray(q, dtype=np.float64)
+            p = np.ascontiguousarray(p, dtype=np.float64)
+            eps = np.ascontiguousarray(eps, dtype=np.float64)
+            _check(sdpd_set_state(self.h, _ptr(q), _ptr(p), _ptr(eps), 0), "sdpd_set_state")
+        else:
+            q, p, eps = (t.contiguous().double() for t in (q, p, eps))
+            _check(sdpd_set_state(self.h, _ptr(q), _ptr(p), _ptr(eps), 1), "sdpd_set_state")
+            self._keep = (q, p, eps)
+
+    def get_state(self):
+        q = np.empty((self.N, 3))
+        p = np.empty((self.N, 3))
+        e = np.empty(self.N)
+        _check(sdpd_get_state(self.h, _ptr(q), _ptr(p), _ptr(e), 0), "sdpd_get_state")
+        return q, p, e
+
+    def get_state_device(self, q, p, eps):
+        """Copy the state into float64 CUDA tensors (id order); synchronises."""
+        _check(sdpd_get_state(self.h, _ptr(q), _ptr(p), _ptr(eps), 1), "sdpd_get_state")
+
+    def step(self, dt, nsteps=1, seed=0):
+        _check(sdpd_step(self.h, dt, nsteps, seed), "sdpd_step")
+
+    def sync(self):
+        return sdpd_sync(self.h)
+
+    def observables(self, check=True) -> dict:
+        o = sdpd_obs()
+        st = sdpd_observables(self.h, o)
+        if check:
+            _check(st, "sdpd_observables")
+        return {"E": o.E, "E_int": o.E_int, "E_kin": o.E_kin, "P": np.array(o.P[:]),
+                "T_kin": o.T_kin, "T_int": o.T_int, "eps_min": o.eps_min, "n_pairs": o.n_pairs,
+                "n_accept": o.n_accept, "n_reject_bound": o.n_reject_bound,
+                "n_reject_metropolis": o.n_reject_metropolis, "fd_step": o.fd_step,
+                "vv_step": o.vv_step, "status": o.status}
+
+    @property
+    def fd_step(self) -> int:
+        return sdpd_get_fd_step(self.h)
+
+    @fd_step.setter
+    def fd_step(self, v):
+        _check(sdpd_set_fd_step(self.h, v), "sdpd_set_fd_step")
+
+    def reset_counters(self):
+        _check(sdpd_reset_counters(self.h), "sdpd_reset_counters")
+
+    @property
+    def kernel_launches(self) -> int:
+        return sdpd_kernel_launches(self.h)
+
+    def enable_stage_timing(self, on=True):
+        _check(sdpd_enable_stage_timing(self.h, on), "sdpd_enable_stage_timing")
+
+    def stage_times(self) -> dict:
+        st, ms, nl = sdpd_stage_times(self.h)
+        _check(st, "sdpd_stage_times")
+        return {name: (m, n) for name, m, n in zip(STAGE_NAMES, ms, nl)}
+
+    def _debug(self, what, arr, cap):
+        st, n = sdpd_debug_get(self.h, what, _ptr(arr), cap)
+        _check(st, "sdpd_debug_get")
+        return n
+
+    def order(self) -> np.ndarray:
+        out = np.empty(self.N, dtype=np.int64)
+        self._debug(DEBUG_ORDER, out, self.N)
+        return out
+
+    def cells(self) -> np.ndarray:
+        out = np.empty((self.N, 3), dtype=np.int32)
+        self._debug(DEBUG_CELLS, out, self.N)
+        return out
+
+    def density(self) -> np.ndarray:
+        out = np.empty(self.N)
+        self._debug(DEBUG_RHO, out, self.N)
+        return out
+
+    def forces(self) -> np.ndarray:
+        out = np.empty((self.N, 3))
+        self._debug(DEBUG_FORCE, out, 3 * self.N)
+        return out
+
+    def neighbour_counts(self) -> np.ndarray:
+        out = np.empty(self.N, dtype=np.int32)
+        self._debug(DEBUG_NCOUNT, out, self.N)
+        return out
+
+    def pair_records(self) -> np.ndarray:
+        cap = max(1, self.N) * 64
+        out = np.empty(cap, dtype=PAIR_REC_DTYPE)
+        n = self._debug(DEBUG_PAIRS, out, cap)
+        return out[:n].copy()

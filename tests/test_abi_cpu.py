@@ -1,0 +1,74 @@
+"""The C-ABI library loads without a GPU and exports every symbol that
+include/sdpd.h declares; host-side argument checks need no device."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+from paper_1707_04232_gb300 import build as B
+from paper_1707_04232_gb300 import sdpd
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "sdpd.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(sdpd_[a-z_]+)\s*\(", text)))
+
+
+def test_library_builds_and_exports_every_declared_symbol():
+    path = B.build()
+    lib = C.CDLL(path)
+    names = declared_functions()
+    assert len(names) >= 14
+    for n in names:
+        assert hasattr(lib, n), n
+    bound = {name for name, _, _ in sdpd.SIGNATURES}
+    assert set(names) == bound
+
+
+def _params(**kw):
+    p = sdpd.sdpd_params(kB=1.0, eta=1.0, zeta=0.0, c_rho=-1.0, kernel=1, scheme=2, precision=0,
+                         fd_only=0, theta=1, debug=0)
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+@pytest.mark.parametrize("kw,box,K,expect", [
+    ({}, (10.0, 10.0, 10.0), 100.0, sdpd.OK),
+    ({}, (9.0, 10.0, 10.0), 100.0, sdpd.ERR_BOX_TOO_SMALL),
+    ({}, (10.0, 10.0, 10.0), 1.2, sdpd.ERR_INVALID_ARG),   # K <= 4/3
+    ({"eta": 0.0}, (10.0, 10.0, 10.0), 100.0, sdpd.ERR_INVALID_ARG),
+    ({"zeta": 2.0}, (10.0, 10.0, 10.0), 100.0, sdpd.ERR_INVALID_ARG),  # zeta >= 5 eta / 3
+    ({"kernel": 7}, (10.0, 10.0, 10.0), 100.0, sdpd.ERR_INVALID_ARG),
+    ({"theta": 0}, (10.0, 10.0, 10.0), 100.0, sdpd.ERR_INVALID_ARG),
+])
+def test_create_validates_on_host(kw, box, K, expect):
+    st, h = sdpd.sdpd_create(1000, box, 1.0, 2.5, K, _params(**kw), 0)
+    assert st == expect
+    if st == sdpd.OK:
+        assert sdpd.sdpd_workspace_bytes(h) > 0
+        # no workspace bound: every device call is refused without touching a GPU
+        assert sdpd.sdpd_step(h, 0.005, 1, 0) == sdpd.ERR_NO_WORKSPACE
+        assert sdpd.sdpd_bind_workspace(h, 0, 0) == sdpd.ERR_NO_WORKSPACE
+        assert sdpd.sdpd_step(h, -1.0, 1, 0) == sdpd.ERR_INVALID_ARG
+        sdpd.sdpd_destroy(h)
+    else:
+        assert not h
+
+
+def test_workspace_scales_with_precision():
+    st, h64 = sdpd.sdpd_create(32768, (32.0,) * 3, 1.0, 2.5, 100.0, _params(precision=0), 0)
+    st2, hm = sdpd.sdpd_create(32768, (32.0,) * 3, 1.0, 2.5, 100.0, _params(precision=1), 0)
+    assert st == st2 == sdpd.OK
+    assert sdpd.sdpd_workspace_bytes(hm) < sdpd.sdpd_workspace_bytes(h64)
+    sdpd.sdpd_destroy(h64)
+    sdpd.sdpd_destroy(hm)
+
+
+def test_strerror_covers_codes():
+    for code in range(11):
+        assert sdpd.sdpd_strerror(code) != "unknown status"

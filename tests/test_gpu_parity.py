@@ -1,0 +1,323 @@
+"""GPU path versus the FP64 oracle, element by element, on seeded inputs.
+
+Tolerances (from the accuracy targets of the library):
+  * cell indices, storage order, neighbour sets, pair colours and owners:
+    bit-exact (float64 path; the predicate r^2 < h^2 is a fixed sequence of
+    correctly rounded operations on both sides);
+  * float64 path: rho within 1e-12 relative, F within 1e-12 of max|F|;
+    accept/reject decisions equal, a flip allowed only where the oracle's
+    margin |a - ln U| (or the energy bound margin) is below 1e-9;
+  * mixed path (float32 pair arithmetic): rho within 1e-5 of max rho, F within
+    1e-5 of max|F|;
+  * trajectories: positions within 1e-6 a after 10 steps.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1707_04232_gb300.inputs import Workload, lattice_state, random_box_state
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - collected on CPU-only hosts
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_1707_04232_gb300 import sdpd  # noqa: E402
+
+DT = 0.005
+
+
+def system(kind: str):
+    """(q, p, eps, L, K) of a named test system."""
+    if kind == "lattice1000":
+        w = Workload(n=10, K=100.0)
+        q, p, e = lattice_state(w)
+        return q, p, e, (w.L,) * 3, w.K
+    if kind == "lattice_cold_K5":
+        w = Workload(n=10, K=5.0, kT=0.1, jitter=0.05, seed=4)
+        q, p, e = lattice_state(w)
+        return q, p, e, (w.L,) * 3, w.K
+    if kind == "random_rect":  # ragged N, rectangular box, disordered fluid
+        L = (12.5, 15.0, 17.3)
+        N = int(round(L[0] * L[1] * L[2]))
+        C_K = 1.5 * (20.0 - 1.0)
+        q, p, e = random_box_state(N, 1.0, 1.0, 1.0, C_K, seed=9)
+        q = q * np.array(L)
+        q = np.where(q >= np.array(L), 0.0, q)
+        e = e * (0.5 + np.random.default_rng(3).random(N))
+        return q, p, e, L, 20.0
+    if kind == "lattice32k":
+        w = Workload(n=32, K=100.0, seed=1)
+        q, p, e = lattice_state(w)
+        return q, p, e, (w.L,) * 3, w.K
+    raise KeyError(kind)
+
+
+def oparams(N, L, K, kernel=O.KERNEL_LUCY, scheme=O.SCHEME_EMS):
+    return O.Config(N=N, L=tuple(L), K=K, kernel=kernel, scheme=scheme).params()
+
+
+def gpu(N, L, K, precision=sdpd.FP64, kernel=sdpd.KERNEL_LUCY, scheme=sdpd.SCHEME_EMS, **kw):
+    return sdpd.SDPD(N, L, m=1.0, h=2.5, K=K, precision=precision, kernel=kernel, scheme=scheme, **kw)
+
+
+def min_image_err(a, b, L):
+    L = np.asarray(L)
+    d = (a - b + 0.5 * L) % L - 0.5 * L
+    return np.abs(d).max()
+
+
+# --------------------------------------------------------------------------
+# Binning, order, neighbour sets
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("kind", ["lattice1000", "random_rect", "lattice32k"])
+def test_cells_order_and_neighbours_bit_exact(kind):
+    q, p, e, L, K = system(kind)
+    N = len(e)
+    s = gpu(N, L, K)
+    s.set_state(q, p, e)
+    P = oparams(N, L, K)
+    assert (s.cells() == O.cells(P, q)).all()
+    assert (s.order() == O.sorted_order(P, q)).all()
+    assert (s.neighbour_counts() == O.neighbour_counts(P, q)).all()
+
+
+# --------------------------------------------------------------------------
+# Density (Eq. sdpd-rho-v) and conservative force (Eq. cons-forces)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("kernel", [sdpd.KERNEL_LUCY, sdpd.KERNEL_CUBIC])
+@pytest.mark.parametrize("kind", ["lattice1000", "random_rect", "lattice32k"])
+def test_density_and_force_fp64(kind, kernel):
+    q, p, e, L, K = system(kind)
+    N = len(e)
+    s = gpu(N, L, K, kernel=kernel)
+    s.set_state(q, p, e)
+    P = oparams(N, L, K, kernel=kernel)
+    rho = O.density(P, q)
+    assert np.abs(s.density() - rho).max() <= 1e-12 * rho.max()
+    f = O.forces(P, q, rho, e)
+    assert np.abs(s.forces() - f).max() <= 1e-12 * np.abs(f).max()
+
+
+@pytest.mark.parametrize("kernel", [sdpd.KERNEL_LUCY, sdpd.KERNEL_CUBIC])
+@pytest.mark.parametrize("kind", ["lattice1000", "random_rect", "lattice32k"])
+def test_density_and_force_mixed(kind, kernel):
+    q, p, e, L, K = system(kind)
+    N = len(e)
+    s = gpu(N, L, K, precision=sdpd.MIXED, kernel=kernel)
+    s.set_state(q, p, e)
+    P = oparams(N, L, K, kernel=kernel)
+    rho = O.density(P, q)
+    assert np.abs(s.density() - rho).max() <= 1e-5 * rho.max()
+    f = O.forces(P, q, rho, e)
+    assert np.abs(s.forces() - f).max() <= 1e-5 * np.abs(f).max()
+
+
+# --------------------------------------------------------------------------
+# One fluctuation/dissipation sweep (Sections 3.2-3.3)
+# --------------------------------------------------------------------------
+
+def check_sweep_against_oracle(recs_g, recs_o, tol_flip=1e-9):
+    key = lambda r: (int(r["id_i"]), int(r["id_j"]))
+    go = {key(r): r for r in recs_g}
+    oo = {key(r): (k, r) for k, r in enumerate(recs_o)}
+    assert set(go) == set(oo), "pair sets differ"
+    flips = []
+    for k, (pos, ro) in oo.items():
+        rg = go[k]
+        assert rg["colour"] == ro["colour"] and rg["owner"] == ro["owner"]
+        if rg["decision"] != ro["decision"]:
+            flips.append((k, ro["margin"], rg["margin"]))
+    for k, mo, mg in flips:
+        assert abs(mo) < tol_flip, "decision flip with margin %g at %s" % (mo, k)
+    # the GPU schedule keeps every particle's pairs in the oracle's order
+    pos_of = {k: pos for k, (pos, _) in oo.items()}
+    per_particle = {}
+    for r in recs_g:
+        for pid in (int(r["id_i"]), int(r["id_j"])):
+            per_particle.setdefault(pid, []).append((int(r["colour"]), int(r["level"]), pos_of[key(r)]))
+    for pid, lst in per_particle.items():
+        lst.sort()
+        seq = [t[2] for t in lst]
+        assert seq == sorted(seq), "particle %d: schedule breaks the sweep order" % pid
+    return flips
+
+
+@pytest.mark.parametrize("scheme", [sdpd.SCHEME_EMS, sdpd.SCHEME_AMS, sdpd.SCHEME_SSA])
+@pytest.mark.parametrize("kind", ["lattice1000", "random_rect", "lattice_cold_K5"])
+def test_fd_sweep_fp64_matches_oracle(kind, scheme):
+    q, p, e, L, K = system(kind)
+    N = len(e)
+    dt = 0.05 if kind == "lattice_cold_K5" else DT
+    s = gpu(N, L, K, scheme=scheme, fd_only=True, debug=True)
+    s.set_state(q, p, e)
+    s.step(dt, 1, seed=77)
+    qg, pg, eg = s.get_state()
+    recs = s.pair_records()
+    P = oparams(N, L, K, scheme=scheme)
+    st, po, eo, stats, recs_o = O.fd_sweep(P, q, p, e, dt, 77, 0, records=True)
+    flips = check_sweep_against_oracle(recs, recs_o)
+    obs = s.observables(check=False)
+    assert obs["n_pairs"] == stats.n_pairs
+    if not flips:
+        assert obs["n_accept"] == stats.n_accept
+        assert np.abs(pg - po).max() <= 1e-10 * max(1.0, np.abs(po).max())
+        assert np.abs(eg - eo).max() <= 1e-10 * eo.max()
+    assert (qg == q).all()  # the sweep never moves particles
+
+
+def test_fd_sweep_mixed_statistics():
+    """Mixed precision: same pair set and colouring, same decisions except
+    near ties, energy conserved by every sweep to float32 accuracy of the
+    kinetic-energy changes."""
+    q, p, e, L, K = system("lattice_cold_K5")
+    N = len(e)
+    s = gpu(N, L, K, precision=sdpd.MIXED, fd_only=True, debug=True)
+    s.set_state(q, p, e)
+    E0 = s.observables()["E"]
+    s.step(0.05, 1, seed=5)
+    recs = s.pair_records()
+    P = oparams(N, L, K)
+    st, po, eo, stats, recs_o = O.fd_sweep(P, q, p, e, 0.05, 5, 0, records=True)
+    assert {(int(r["id_i"]), int(r["id_j"])) for r in recs} == {(int(r["id_i"]), int(r["id_j"])) for r in recs_o}
+    agree = np.mean([a == b for a, b in zip(sorted(recs, key=lambda r: (r["id_i"], r["id_j"]))["decision"],
+                                              sorted(recs_o, key=lambda r: (r["id_i"], r["id_j"]))["decision"])])
+    assert agree > 0.999
+    E1 = s.observables()["E"]
+    assert abs(E1 - E0) < 1e-6 * abs(E0)
+
+
+# --------------------------------------------------------------------------
+# Full steps
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("kind,scheme,theta", [("lattice1000", sdpd.SCHEME_EMS, 1),
+                                               ("lattice1000", sdpd.SCHEME_AMS, 1),
+                                               ("random_rect", sdpd.SCHEME_EMS, 1),
+                                               ("lattice1000", sdpd.SCHEME_EMS, 5),
+                                               ("lattice1000", sdpd.SCHEME_NONE, 1)])
+def test_trajectory_fp64_10_steps(kind, scheme, theta):
+    q, p, e, L, K = system(kind)
+    N = len(e)
+    s = gpu(N, L, K, scheme=scheme, theta=theta)
+    s.set_state(q, p, e)
+    s.step(DT, 10, seed=3)
+    qg, pg, eg = s.get_state()
+    P = oparams(N, L, K, scheme=scheme)
+    st, qo, po, eo, stats, nfd = O.run(P, q, p, e, DT, 10, seed=3, theta=theta)
+    assert st == O.OK
+    assert min_image_err(qg, qo, L) < 1e-6
+    assert np.abs(pg - po).max() < 1e-6 * max(1.0, np.abs(po).max())
+    assert np.abs(eg - eo).max() < 1e-6 * eo.max()
+    obs = s.observables()
+    assert obs["fd_step"] == nfd
+
+
+@pytest.mark.parametrize("kind", ["lattice1000", "random_rect"])
+def test_trajectory_mixed_10_steps(kind):
+    q, p, e, L, K = system(kind)
+    N = len(e)
+    s = gpu(N, L, K, precision=sdpd.MIXED)
+    s.set_state(q, p, e)
+    s.step(DT, 10, seed=3)
+    qg, pg, eg = s.get_state()
+    P = oparams(N, L, K)
+    st, qo, po, eo, stats, _ = O.run(P, q, p, e, DT, 10, seed=3)
+    assert min_image_err(qg, qo, L) < 1e-5
+    o_g = s.observables()
+    o_o = O.observables(P, po, eo)
+    assert abs(o_g["E"] - o_o["E"]) < 1e-6 * abs(o_o["E"])
+    assert abs(o_g["T_kin"] - o_o["T_kin"]) < 1e-3 * o_o["T_kin"]
+
+
+# --------------------------------------------------------------------------
+# Invariants, restart, edge cases
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("precision", [sdpd.FP64, sdpd.MIXED])
+def test_fd_only_conserves_energy_and_momentum(precision):
+    q, p, e, L, K = system("lattice_cold_K5")
+    N = len(e)
+    s = gpu(N, L, K, precision=precision, fd_only=True)
+    s.set_state(q, p, e)
+    o0 = s.observables()
+    s.step(0.1, 20, seed=1)
+    o1 = s.observables()
+    tol = 1e-12 if precision == sdpd.FP64 else 1e-6
+    assert abs(o1["E"] - o0["E"]) < tol * abs(o0["E"])
+    assert np.abs(o1["P"] - o0["P"]).max() < (1e-11 if precision == sdpd.FP64 else 1e-3)
+    assert o1["eps_min"] > 0.0
+    assert o1["n_pairs"] > 0 and o1["n_accept"] <= o1["n_pairs"]
+
+
+@pytest.mark.parametrize("precision", [sdpd.FP64, sdpd.MIXED])
+def test_checkpoint_resume_is_bitwise(precision):
+    q, p, e, L, K = system("random_rect")
+    N = len(e)
+    a = gpu(N, L, K, precision=precision)
+    a.set_state(q, p, e)
+    a.step(DT, 8, seed=11)
+    qa, pa, ea = a.get_state()
+    b = gpu(N, L, K, precision=precision)
+    b.set_state(q, p, e)
+    b.step(DT, 4, seed=11)
+    qb, pb, eb = b.get_state()
+    b.set_state(qb, pb, eb)
+    b.fd_step = 4
+    b.step(DT, 4, seed=11)
+    qb, pb, eb = b.get_state()
+    assert (qa == qb).all() and (pa == pb).all() and (ea == eb).all()
+
+
+def test_ssa_negative_energy_is_reported_not_fatal():
+    w = Workload(n=10, K=1.5, kT=1.0)
+    q, p, e = lattice_state(w)
+    s = gpu(w.N, (w.L,) * 3, w.K, scheme=sdpd.SCHEME_SSA, fd_only=True)
+    s.set_state(q, p, e)
+    s.step(2.0, 5, seed=2)
+    obs = s.observables(check=False)
+    assert obs["status"] in (sdpd.ERR_NEGATIVE_ENERGY, sdpd.ERR_NAN)
+    # AMS and EMS on the same stress case keep every energy positive
+    for scheme in (sdpd.SCHEME_AMS, sdpd.SCHEME_EMS):
+        s = gpu(w.N, (w.L,) * 3, w.K, scheme=scheme, fd_only=True)
+        s.set_state(q, p, e)
+        s.step(2.0, 5, seed=2)
+        obs = s.observables()
+        assert obs["status"] == 0 and obs["eps_min"] > 0 and obs["n_reject_bound"] > 0
+
+
+def test_bad_state_and_empty_system():
+    q, p, e, L, K = system("lattice1000")
+    s = gpu(len(e), L, K)
+    bad = e.copy()
+    bad[17] = -1.0
+    with pytest.raises(sdpd.SDPDError) as ex:
+        s.set_state(q, p, bad)
+    assert ex.value.status == sdpd.ERR_NONPOSITIVE_ENERGY
+    with pytest.raises(sdpd.SDPDError):
+        s.step(DT, 1)  # no state loaded
+    z = gpu(0, L, K)
+    z.set_state(np.zeros((0, 3)), np.zeros((0, 3)), np.zeros(0))
+    z.step(DT, 3, seed=1)
+    o = z.observables()
+    assert o["E"] == 0.0 and o["status"] == 0
+
+
+def test_device_state_io_matches_host_io():
+    q, p, e, L, K = system("random_rect")
+    N = len(e)
+    a = gpu(N, L, K)
+    a.set_state(q, p, e)
+    b = gpu(N, L, K)
+    b.set_state(torch.from_numpy(q).cuda(), torch.from_numpy(p).cuda(), torch.from_numpy(e).cuda())
+    a.step(DT, 3, seed=4)
+    b.step(DT, 3, seed=4)
+    qd = torch.empty((N, 3), dtype=torch.float64, device="cuda")
+    pd = torch.empty_like(qd)
+    ed = torch.empty(N, dtype=torch.float64, device="cuda")
+    b.get_state_device(qd, pd, ed)
+    qa, pa, ea = a.get_state()
+    assert (qd.cpu().numpy() == qa).all() and (pd.cpu().numpy() == pa).all() and (ed.cpu().numpy() == ea).all()

@@ -76,6 +76,20 @@ def test_perfect_lattice_density_and_neighbours():
         assert np.abs(f).max() < 1e-12
 
 
+def test_sampled_density_and_force_equal_full_sums():
+    """The per-particle entry points used for sampled checks at full size
+    compute the same sums as the all-particle ones."""
+    w = Workload(n=10, jitter=0.3, seed=13)
+    q, p, eps = lattice_state(w)
+    eps = eps * (1 + 0.2 * np.random.default_rng(2).random(w.N))
+    P = small_cfg().params()
+    rho = O.density(P, q)
+    f = O.forces(P, q, rho, eps)
+    idx = np.array([0, 7, 123, 999])
+    assert np.abs(O.density_at(P, q, idx) - rho[idx]).max() <= 1e-14 * rho.max()
+    assert np.abs(O.forces_at(P, q, eps, idx) - f[idx]).max() <= 1e-12 * np.abs(f).max()
+
+
 def test_min_image_and_wrap():
     L = 10.0
     assert O.lib().orc_min_image(6.0, L) == -4.0

@@ -252,29 +252,34 @@ __global__ void __launch_bounds__(kSchedWarps * 32)
 // Schedule, step 2: dependency levels of the canonical order and the pairs
 // bucketed by level (one thread per block).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) k_sched_levels(int64_t ncell, uint32_t* __restrict__ hdr,
-                                                      const uint16_t* __restrict__ canon,
-                                                      uint16_t* __restrict__ lvl, uint16_t* __restrict__ pairs,
-                                                      int* status) {
-  const int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+constexpr int kLevelThreads = 32;
+
+__global__ void __launch_bounds__(kLevelThreads) k_sched_levels(int64_t ncell, uint32_t* __restrict__ hdr,
+                                                              const uint16_t* __restrict__ canon,
+                                                              uint16_t* __restrict__ lvl,
+                                                              uint16_t* __restrict__ pairs, int* status) {
+  // per-thread scratch in shared memory, interleaved by thread:
+  // last level of each particle, and the pair count (then offset) per level
+  __shared__ uint8_t last_s[kMaxBlock][kLevelThreads];
+  __shared__ uint16_t cnt_s[kMaxLevels + 1][kLevelThreads];
+  const int t = threadIdx.x;
+  const int64_t o = blockIdx.x * (int64_t)blockDim.x + t;
   if (o >= ncell) return;
   const int np = (int)(hdr[o] & 0xffffu);
   uint16_t* off = lvl + o * (kMaxLevels + 1);
   const uint16_t* in = canon + o * kMaxPairs;
   uint16_t* out = pairs + o * kMaxPairs;
-  uint8_t last[kMaxBlock];
-  uint16_t cnt[kMaxLevels + 1];
-  for (int k = 0; k < kMaxBlock; ++k) last[k] = 0;
-  for (int k = 0; k <= kMaxLevels; ++k) cnt[k] = 0;
+  for (int k = 0; k < kMaxBlock; ++k) last_s[k][t] = 0;
+  for (int k = 0; k <= kMaxLevels; ++k) cnt_s[k][t] = 0;
   int nlev = 0;
   bool overflow = false;
   for (int k = 0; k < np; ++k) {
     const uint16_t pr = in[k];
     const int u = pr & 255, v = pr >> 8;
-    const int L = max(last[u], last[v]);
+    const int L = max(last_s[u][t], last_s[v][t]);
     if (L >= kMaxLevels) { overflow = true; break; }
-    last[u] = last[v] = (uint8_t)(L + 1);
-    cnt[L]++;
+    last_s[u][t] = last_s[v][t] = (uint8_t)(L + 1);
+    cnt_s[L][t]++;
     nlev = max(nlev, L + 1);
   }
   if (overflow) {
@@ -285,19 +290,19 @@ __global__ void __launch_bounds__(128) k_sched_levels(int64_t ncell, uint32_t* _
   }
   int run = 0;
   for (int L = 0; L < nlev; ++L) {
-    const int n = cnt[L];
+    const int n = cnt_s[L][t];
     off[L] = (uint16_t)run;
-    cnt[L] = (uint16_t)run;
+    cnt_s[L][t] = (uint16_t)run;
     run += n;
   }
   off[nlev] = (uint16_t)run;
-  for (int k = 0; k < kMaxBlock; ++k) last[k] = 0;
+  for (int k = 0; k < kMaxBlock; ++k) last_s[k][t] = 0;
   for (int k = 0; k < np; ++k) {
     const uint16_t pr = in[k];
     const int u = pr & 255, v = pr >> 8;
-    const int L = max(last[u], last[v]);
-    last[u] = last[v] = (uint8_t)(L + 1);
-    out[cnt[L]++] = pr;
+    const int L = max(last_s[u][t], last_s[v][t]);
+    last_s[u][t] = last_s[v][t] = (uint8_t)(L + 1);
+    out[cnt_s[L][t]++] = pr;
   }
   hdr[o] = (uint32_t)np | ((uint32_t)nlev << 16);
 }
@@ -315,6 +320,58 @@ struct FDConst {
   int scheme;
 };
 
+// Elementary functions of the sweep.  float64: the correctly rounded /
+// accurate library versions.  float32 (mixed path): hardware approximations
+// (relative error ~1e-7) for the proposal coefficients and Box-Muller -- the
+// Metropolis step stays exact for any deterministic proposal coefficients
+// because the forward and reverse moves use the same functions -- and the
+// accurate log1p for the entropy term of the target measure.
+namespace fm {
+__device__ __forceinline__ double div(double a, double b) { return a / b; }
+__device__ __forceinline__ float div(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double exp(double x) { return ::exp(x); }
+__device__ __forceinline__ float exp(float x) { return __expf(x); }
+__device__ __forceinline__ double log(double x) { return ::log(x); }
+__device__ __forceinline__ float log(float x) { return __logf(x); }
+__device__ __forceinline__ double sqrt(double x) { return ::sqrt(x); }
+__device__ __forceinline__ float sqrt(float x) { return x * rsqrtf(x); }
+__device__ __forceinline__ double rsqrt(double x) { return 1.0 / ::sqrt(x); }
+__device__ __forceinline__ float rsqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double expm1(double x) { return ::expm1(x); }
+// exp(x) - 1 for x <= 0: Taylor polynomial for small |x| (relative error
+// < 1e-8 below 1/8), the hardware exponential above
+__device__ __forceinline__ float expm1(float x) {
+  if (x > -0.125f) return x * (1.0f + x * (0.5f + x * (1.0f / 6.0f + x * (1.0f / 24.0f + x * (1.0f / 120.0f + x * (1.0f / 720.0f))))));
+  return __expf(x) - 1.0f;
+}
+__device__ __forceinline__ double log1p(double x) { return ::log1p(x); }
+__device__ __forceinline__ float log1p(float x) { return log1pf(x); }
+}  // namespace fm
+
+// Box-Muller normals and the uniform of one pair at one sweep (see
+// pair_randoms); the float32 path uses the hardware log and sin/cos.
+__device__ __forceinline__ void pair_randoms_fast(uint64_t seed, uint64_t sweep, uint64_t idi, uint64_t idj,
+                                                  float G[3], float* U) {
+  uint64_t w[4];
+  philox4x64_10(sweep, idi, idj, 0ull, seed, 0ull, w);
+  const float two23 = 1.0f / 8388608.0f, twopi = 6.28318530717958647692f;
+  const float u0 = ((float)(uint32_t)(w[0] >> 41) + 0.5f) * two23;
+  const float u1 = ((float)(uint32_t)(w[1] >> 41) + 0.5f) * two23;
+  const float R = fm::sqrt(-2.0f * __logf(u0));
+  float sn, cs;
+  __sincosf(twopi * u1, &sn, &cs);
+  G[0] = R * cs;
+  G[1] = R * sn;
+  const float u2 = ((float)(uint32_t)(w[2] >> 41) + 0.5f) * two23;
+  const float u3 = ((float)((uint32_t)(w[2] & 0xffffffffull) >> 9) + 0.5f) * two23;
+  G[2] = fm::sqrt(-2.0f * __logf(u2)) * __cosf(twopi * u3);
+  *U = ((float)(uint32_t)(w[3] >> 41) + 0.5f) * two23;
+}
+__device__ __forceinline__ void pair_randoms_fast(uint64_t seed, uint64_t sweep, uint64_t idi, uint64_t idj,
+                                                  double G[3], double* U) {
+  pair_randoms(seed, sweep, idi, idj, G, U);
+}
+
 // alpha = exp(-2 gamma dt / m) and zt = (2/m) zeta of Section 3.2 for both
 // directions at energies (ei, ej), with gamma = kappa (1 - d) and
 // sigma = 2 sqrt(kappa kB Ti Tj / (Ti + Tj)) of Eq. (sdpd-gamma-sigma):
@@ -325,37 +382,39 @@ template <class R>
 __device__ __forceinline__ void pair_coeffs(const FDConst<R>& k, R kpar, R kperp, R ei, R ej, R& apar,
                                             R& aperp, R& zpar, R& zperp) {
   const R Ti = ei * k.inv_C_K, Tj = ej * k.inv_C_K;
-  const R sT = Ti + Tj, pT = Ti * Tj;
-  const R hT = pT / sT;
-  const R d = k.kB * hT / sT * k.two_over_CK;
-  const R omd = R(1) - d;
+  const R sT = Ti + Tj;
+  const R hT = fm::div(Ti * Tj, sT);
+  const R omd = R(1) - fm::div(k.kB * hT * k.two_over_CK, sT);
   const R xpar = R(-2) * kpar * omd * k.dt_over_m, xperp = R(-2) * kperp * omd * k.dt_over_m;
-  apar = exp(xpar);
-  aperp = exp(xperp);
-  const R s = k.four_kB_over_m * hT / omd;
-  zpar = sqrt(s * -expm1(R(2) * xpar));
-  zperp = sqrt(s * -expm1(R(2) * xperp));
+  apar = fm::exp(xpar);
+  aperp = fm::exp(xperp);
+  const R s = fm::div(k.four_kB_over_m * hT, omd);
+  zpar = fm::sqrt(s * -fm::expm1(R(2) * xpar));
+  zperp = fm::sqrt(s * -fm::expm1(R(2) * xperp));
 }
 
-// Returns 0 accept, 1 energy-bound reject, 2 Metropolis reject.
-template <class P, int KIND>
-__device__ __forceinline__ int fd_pair(const FDConst<typename P::R>& k, typename P::R rx, typename P::R ry,
-                                       typename P::R rz, typename P::R rho_i, typename P::R rho_j,
-                                       typename P::R* pi, typename P::R* pj, double& ei, double& ej,
-                                       const typename P::R G[3], typename P::R U, double& margin,
-                                       bool& negative) {
+// State-dependent part of one pair update on (p_i, p_j) with internal
+// energies (ei, ej) in the arithmetic type R, given the pair's unit vector
+// e = r_ij / r_ij, base = F(r_ij) / (rho_i rho_j) and its random numbers.
+// Returns 0 accept, 1 energy-bound reject, 2 Metropolis reject; deps receives
+// the energy change shared by the two particles (applied by the caller on
+// acceptance).  exact_bound: float64 re-check of the energy bound for the
+// mixed path when its float32 margin is not decisive; it returns the smaller
+// new internal energy in float64.
+template <class P, class ExactBound>
+__device__ __forceinline__ int fd_pair(const FDConst<typename P::R>& k, typename P::R ex, typename P::R ey,
+                                       typename P::R ez, typename P::R base, const typename P::R G[3],
+                                       typename P::R U, typename P::R* pi, typename P::R* pj,
+                                       typename P::R ei, typename P::R ej, typename P::R& deps,
+                                       typename P::R& margin, bool& negative, ExactBound exact_bound) {
   using R = typename P::R;
-  const R r = sqrt(r2_of(rx, ry, rz));
-  const R inv_r = R(1) / r;
-  const R ex = rx * inv_r, ey = ry * inv_r, ez = rz * inv_r;
-  const R base = kernel_F<KIND>(r * k.inv_h, k.cF) / (rho_i * rho_j);
   const R kpar = k.kpar_m2 * base, kperp = k.kperp_m2 * base;
-  margin = 0.0;
+  margin = R(0);
+  deps = R(0);
   if (!(kperp > R(0)) || !(kpar > R(0))) return 0;  // at r = h the pair does nothing
   const R vx = (pi[0] - pj[0]) * k.inv_m, vy = (pi[1] - pj[1]) * k.inv_m, vz = (pi[2] - pj[2]) * k.inv_m;
-  const R eir = (R)ei, ejr = (R)ej;
   R apar, aperp, zpar, zperp;
-  pair_coeffs(k, kpar, kperp, eir, ejr, apar, aperp, zpar, zperp);
+  pair_coeffs(k, kpar, kperp, ei, ej, apar, aperp, zpar, zperp);
   // proposal, Eq. (proposal): v' = sum_theta P^theta (alpha^theta v + zt^theta G)
   const R vpar = ex * vx + ey * vy + ez * vz;
   const R gpar = ex * G[0] + ey * G[1] + ez * G[2];
@@ -367,75 +426,86 @@ __device__ __forceinline__ int fd_pair(const FDConst<typename P::R>& k, typename
   const R dpx = k.half_m * (wx - vx), dpy = k.half_m * (wy - vy), dpz = k.half_m * (wz - vz);
   const R nix = pi[0] + dpx, niy = pi[1] + dpy, niz = pi[2] + dpz;
   const R njx = pj[0] - dpx, njy = pj[1] - dpy, njz = pj[2] - dpz;
-  double deps;
-  R depsr;
   if constexpr (P::mixed) {
     // -1/2 of the kinetic-energy change of the stored momenta, as a sum of
     // (new - old)(new + old) products so float32 carries no cancellation
     const float dk = (nix - pi[0]) * (nix + pi[0]) + (niy - pi[1]) * (niy + pi[1]) +
                      (niz - pi[2]) * (niz + pi[2]) + (njx - pj[0]) * (njx + pj[0]) +
                      (njy - pj[1]) * (njy + pj[1]) + (njz - pj[2]) * (njz + pj[2]);
-    depsr = -0.25f * k.inv_m * dk;
-    deps = (double)depsr;
+    deps = -0.25f * k.inv_m * dk;
   } else {
     const double ko = pi[0] * pi[0] + pj[0] * pj[0] + pi[1] * pi[1] + pj[1] * pj[1] + pi[2] * pi[2] +
                       pj[2] * pj[2];
     const double kn = nix * nix + njx * njx + niy * niy + njy * njy + niz * niz + njz * njz;
     deps = -0.5 * (kn - ko) * (0.5 * k.inv_m);
-    depsr = deps;
   }
-  const double ein = ei + deps, ejn = ej + deps;
-  const double emin = fmin(ein, ejn);
-  int decision = 0;
+  // energy bound, Eq. (energy-bound): both new internal energies > 0
+  const R emin_old = ei < ej ? ei : ej;
+  R emin = emin_old + deps;
+  if constexpr (P::mixed) {
+    // float32 decides unless the margin is within a few ulps of zero
+    if (fabsf(emin) <= 8.0f * 1.1920929e-7f * emin_old) emin = exact_bound(deps) > 0.0 ? 1.0f : -1.0f;
+  }
   margin = emin;
+  int decision = 0;
   if (k.scheme == SDPD_SCHEME_SSA) {
-    if (!(emin > 0.0)) negative = true;
-  } else if (!(emin > 0.0)) {
-    decision = 1;  // energy bound, Eq. (energy-bound)
+    if (!(emin > R(0))) negative = true;
+  } else if (!(emin > R(0))) {
+    decision = 1;
   } else if (k.scheme == SDPD_SCHEME_EMS) {
     // Metropolis ratio, Eq. (metropolis-ratio): the reverse move from v'
     // with the coefficients at the proposed energies
     R bpar, bperp, ypar, yperp;
-    pair_coeffs(k, kpar, kperp, eir + depsr, ejr + depsr, bpar, bperp, ypar, yperp);
+    pair_coeffs(k, kpar, kperp, ei + deps, ej + deps, bpar, bperp, ypar, yperp);
     const R wpar = ex * wx + ey * wy + ez * wz;
     const R cb = (bpar - bperp) * wpar;
     const R bx = vx - (bperp * wx + cb * ex), by = vy - (bperp * wy + cb * ey), bz = vz - (bperp * wz + cb * ez);
     const R spar = ex * bx + ey * by + ez * bz;
-    const R ip = R(1) / yperp;
-    const R cq = (R(1) / ypar - ip) * spar;
+    const R ip = fm::div(R(1), yperp);
+    const R cq = (fm::div(R(1), ypar) - ip) * spar;
     const R qx = bx * ip + cq * ex, qy = by * ip + cq * ey, qz = bz * ip + cq * ez;
     const R quad = qx * qx + qy * qy + qz * qz;
     const R g2 = G[0] * G[0] + G[1] * G[1] + G[2] * G[2];
     // log|B(v)| - log|B(v')| with |B| = zt_par zt_perp^2
-    const R ldet = log(zpar / ypar) + R(2) * log(zperp / yperp);
-    // (S(eps') - S(eps))/kB - (log T(eps') - log T(eps)) = (C_K/kB - 1) log(eps'/eps) per particle
-    const R ent = k.CKm1 * (log1p(depsr / eir) + log1p(depsr / ejr));
+    const R ldet = fm::log(fm::div(zpar * zperp * zperp, ypar * yperp * yperp));
+    // (S(eps') - S(eps))/kB - (log T(eps') - log T(eps)) = (C_K/kB - 1) log(eps'/eps)
+    // summed over the two particles: log1p(x) + log1p(y) = log1p(x + y + x y)
+    const R xi = fm::div(deps, ei), xj = fm::div(deps, ej);
+    const R ent = k.CKm1 * fm::log1p(xi + xj + xi * xj);
     const R a = R(0.5) * (g2 - quad) + ldet + ent;
-    const R mg = a - log(U);
-    margin = (double)mg;
+    const R mg = a - fm::log(U);
+    margin = mg;
     if (mg < R(0)) decision = 2;  // U > exp(a)
   }
   if (decision == 0) {
     pi[0] = nix; pi[1] = niy; pi[2] = niz;
     pj[0] = njx; pj[1] = njy; pj[2] = njz;
-    ei = ein;
-    ej = ejn;
   }
   return decision;
 }
 
 // ---------------------------------------------------------------------------
 // One colour of the sweep: one warp per block of that colour.
+//
+// The block's particles (momenta and energies) live in shared memory; the
+// pairs run level by level.  Everything of a pair that does not depend on the
+// momenta and energies (unit vector, F(r)/(rho_i rho_j), random numbers) is
+// computed ahead for a chunk of consecutive levels by all 32 lanes and staged
+// in shared memory, so only the state-dependent part runs at the width of a
+// level.
 // ---------------------------------------------------------------------------
-template <class P>
+constexpr int kChunk = 128;  // pairs staged per chunk (a level has <= kMaxBlock/2 pairs)
+
+template <class R>
 struct FdSmem {
-  using R = typename P::R;
   R px[kMaxBlock], py[kMaxBlock], pz[kMaxBlock];
-  double e[kMaxBlock];
-  R rho[kMaxBlock];
-  R x[kMaxBlock], y[kMaxBlock], z[kMaxBlock];
-  int32_t id[kMaxBlock];
+  R e[kMaxBlock];    // energy at hand (float64 path: the energy itself)
+  R acc[kMaxBlock];  // mixed path: float32 sum of this visit's energy changes
   int32_t g[kMaxBlock];
+  // staged pair data of the current chunk
+  R G0[kChunk], G1[kChunk], G2[kChunk], U[kChunk];
+  R ex[kChunk], ey[kChunk], ez[kChunk], base[kChunk];
+  uint16_t pr[kChunk];
 };
 
 template <class P>
@@ -452,12 +522,12 @@ __global__ void __launch_bounds__(fd_warps<P>() * 32)
                 unsigned long long* rec_count, int64_t rec_cap) {
   using R = typename P::R;
   constexpr int W = fd_warps<P>();
-  __shared__ FdSmem<P> sm_all[W];
+  __shared__ FdSmem<R> sm_all[W];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int hx = c.nc[0] >> 1, hy = c.nc[1] >> 1, hz = c.nc[2] >> 1;
   const int64_t w = (int64_t)blockIdx.x * W + warp;
   if (w >= (int64_t)hx * hy * hz) return;
-  FdSmem<P>& sm = sm_all[warp];
+  FdSmem<R>& sm = sm_all[warp];
   const int ox = 2 * (int)(w % hx) + (colour & 1);
   const int oy = 2 * (int)((w / hx) % hy) + ((colour >> 1) & 1);
   const int oz = 2 * (int)(w / ((int64_t)hx * hy)) + ((colour >> 2) & 1);
@@ -475,68 +545,114 @@ __global__ void __launch_bounds__(fd_warps<P>() * 32)
     const int g = b.start[d] + (q - b.base[d]);
     sm.g[q] = g;
     sm.px[q] = a.px[g]; sm.py[q] = a.py[g]; sm.pz[q] = a.pz[g];
-    sm.e[q] = a.eps[g];
-    sm.rho[q] = a.rho[g];
-    sm.id[q] = a.id[g];
-    R x, y, z;
-    geo.local(ld4(&a.q4[g]), d, x, y, z);
-    sm.x[q] = x; sm.y[q] = y; sm.z[q] = z;
+    sm.e[q] = (R)a.eps[g];
+    sm.acc[q] = R(0);
   }
   __syncwarp();
   const uint16_t* off = lvl + o * (kMaxLevels + 1);
   const uint16_t* pl = pairs + o * kMaxPairs;
+  const R inv_h = k.inv_h, cF = k.cF;
   unsigned long long n_acc = 0, n_rb = 0, n_rm = 0, n_tot = 0;
   bool negative = false, bad = false;
-  for (int L = 0; L < nlev; ++L) {
-    const int beg = off[L], end = off[L + 1];
-    for (int t = beg + lane; t < end; t += 32) {
+  int L0 = 0;
+  while (L0 < nlev) {
+    // chunk = levels [L0, L1) holding at most kChunk pairs
+    const int cbeg = off[L0];
+    int L1 = L0 + 1;
+    for (int base_l = L0 + 1; base_l <= nlev; base_l += 32) {
+      const int Lq = base_l + lane;
+      const bool fits = Lq <= nlev && (int)off[Lq] - cbeg <= kChunk;
+      const unsigned m = __ballot_sync(0xffffffffu, fits);
+      if (m == 0u) break;
+      L1 = base_l + 31 - __clz(m);
+      if (m != 0xffffffffu) break;
+    }
+    const int cend = off[L1];
+    // stage the chunk: geometry, kernel factor and random numbers
+    for (int t = cbeg + lane; t < cend; t += 32) {
       const uint16_t pr = pl[t];
       const int ia = pr & 255, ib = pr >> 8;  // ia holds the lower id
-      R rx, ry, rz;
-      geo.disp(sm.x[ia], sm.y[ia], sm.z[ia], sm.x[ib], sm.y[ib], sm.z[ib], rx, ry, rz);
+      const int ga = sm.g[ia], gb = sm.g[ib];
+      R xa, ya, za, xb, yb, zb, rx, ry, rz;
+      geo.local(ld4(&a.q4[ga]), cell_code_of(b, ia), xa, ya, za);
+      geo.local(ld4(&a.q4[gb]), cell_code_of(b, ib), xb, yb, zb);
+      geo.disp(xa, ya, za, xb, yb, zb, rx, ry, rz);
+      const R r2 = r2_of(rx, ry, rz);
+      const R inv_r = fm::rsqrt(r2);
+      const int slot = t - cbeg;
+      sm.pr[slot] = pr;
+      sm.ex[slot] = rx * inv_r;
+      sm.ey[slot] = ry * inv_r;
+      sm.ez[slot] = rz * inv_r;
+      sm.base[slot] = fm::div(kernel_F<KIND>(r2 * inv_r * inv_h, cF), a.rho[ga] * a.rho[gb]);
       R G[3], U;
-      pair_randoms(seed, sweep, (uint64_t)sm.id[ia], (uint64_t)sm.id[ib], G, &U);
-      R pa[3] = {sm.px[ia], sm.py[ia], sm.pz[ia]};
-      R pb[3] = {sm.px[ib], sm.py[ib], sm.pz[ib]};
-      double ea = sm.e[ia], eb = sm.e[ib], margin;
-      const int dcs = fd_pair<P, KIND>(k, rx, ry, rz, sm.rho[ia], sm.rho[ib], pa, pb, ea, eb, G, U, margin,
-                                       negative);
-      if (dcs == 0) {
-        sm.px[ia] = pa[0]; sm.py[ia] = pa[1]; sm.pz[ia] = pa[2];
-        sm.px[ib] = pb[0]; sm.py[ib] = pb[1]; sm.pz[ib] = pb[2];
-        sm.e[ia] = ea;
-        sm.e[ib] = eb;
-        bad |= !isfinite(ea) || !isfinite(eb);
-      }
-      ++n_tot;
-      n_acc += dcs == 0;
-      n_rb += dcs == 1;
-      n_rm += dcs == 2;
-      if (recs) {
-        const unsigned long long s = atomicAdd(rec_count, 1ull);
-        if ((int64_t)s < rec_cap) {
-          sdpd_pair_rec rc;
-          rc.id_i = sm.id[ia];
-          rc.id_j = sm.id[ib];
-          rc.colour = colour;
-          rc.owner = (int32_t)o;
-          rc.decision = dcs;
-          rc.level = L;
-          rc.margin = margin;
-          recs[s] = rc;
-        }
-      }
+      pair_randoms_fast(seed, sweep, (uint64_t)a.id[ga], (uint64_t)a.id[gb], G, &U);
+      sm.G0[slot] = G[0]; sm.G1[slot] = G[1]; sm.G2[slot] = G[2]; sm.U[slot] = U;
     }
     __syncwarp();
+    for (int L = L0; L < L1; ++L) {
+      const int beg = off[L], end = off[L + 1];
+      for (int t = beg + lane; t < end; t += 32) {
+        const int slot = t - cbeg;
+        const uint16_t pr = sm.pr[slot];
+        const int ia = pr & 255, ib = pr >> 8;
+        R pa[3] = {sm.px[ia], sm.py[ia], sm.pz[ia]};
+        R pb[3] = {sm.px[ib], sm.py[ib], sm.pz[ib]};
+        const R ea = sm.e[ia], eb = sm.e[ib];
+        const R G[3] = {sm.G0[slot], sm.G1[slot], sm.G2[slot]};
+        R deps, margin;
+        // float64 bound for the mixed path: energies at load plus this visit's sums
+        auto exact = [&](R dv) -> double {
+          const double da = a.eps[sm.g[ia]] + (double)sm.acc[ia];
+          const double db = a.eps[sm.g[ib]] + (double)sm.acc[ib];
+          return fmin(da, db) + (double)dv;
+        };
+        const int dcs = fd_pair<P>(k, sm.ex[slot], sm.ey[slot], sm.ez[slot], sm.base[slot], G, sm.U[slot], pa,
+                                   pb, ea, eb, deps, margin, negative, exact);
+        if (dcs == 0) {
+          sm.px[ia] = pa[0]; sm.py[ia] = pa[1]; sm.pz[ia] = pa[2];
+          sm.px[ib] = pb[0]; sm.py[ib] = pb[1]; sm.pz[ib] = pb[2];
+          sm.e[ia] = ea + deps;
+          sm.e[ib] = eb + deps;
+          if constexpr (P::mixed) {
+            sm.acc[ia] += deps;
+            sm.acc[ib] += deps;
+          }
+          bad |= !isfinite(sm.e[ia]) || !isfinite(sm.e[ib]);
+        }
+        ++n_tot;
+        n_acc += dcs == 0;
+        n_rb += dcs == 1;
+        n_rm += dcs == 2;
+        if (recs) {
+          const unsigned long long s = atomicAdd(rec_count, 1ull);
+          if ((int64_t)s < rec_cap) {
+            sdpd_pair_rec rc;
+            rc.id_i = a.id[sm.g[ia]];
+            rc.id_j = a.id[sm.g[ib]];
+            rc.colour = colour;
+            rc.owner = (int32_t)o;
+            rc.decision = dcs;
+            rc.level = L;
+            rc.margin = (double)margin;
+            recs[s] = rc;
+          }
+        }
+      }
+      __syncwarp();
+    }
+    L0 = L1;
   }
   const R pi_coef = (R)(c.c_rho / (c.C_K * c.m));
   for (int q = lane; q < nb; q += 32) {
     const int g = sm.g[q];
     a.px[g] = sm.px[q]; a.py[g] = sm.py[q]; a.pz[g] = sm.pz[q];
-    const double e = sm.e[q];
+    double e;
+    if constexpr (P::mixed) e = a.eps[g] + (double)sm.acc[q];  // one float64 update per visit
+    else e = sm.e[q];
     a.eps[g] = e;
     // pressure over rho^2 of the new energy, Eq. (pg-eos): pi = c_rho eps / (C_K m rho)
-    qp4[g].w = (R)e * pi_coef / sm.rho[q];
+    qp4[g].w = (R)e * pi_coef / a.rho[g];
   }
   // counters
   for (int s = 16; s > 0; s >>= 1) {
@@ -584,8 +700,8 @@ void launch_fd_schedule(const Consts& c, const Workspace& w, int cur, cudaStream
   const unsigned gs = (unsigned)((c.ncell + kSchedWarps - 1) / kSchedWarps);
   k_sched_enum<P><<<gs, kSchedWarps * 32, 0, s>>>(c, a, w.cell_start, w.mrank, w.xmin[0], w.xmin[1],
                                                    w.xmin[2], w.sched_hdr, canon, w.status);
-  k_sched_levels<<<(unsigned)((c.ncell + 127) / 128), 128, 0, s>>>(c.ncell, w.sched_hdr, canon, w.sched_lvl,
-                                                                   w.sched_pair, w.status);
+  k_sched_levels<<<(unsigned)((c.ncell + kLevelThreads - 1) / kLevelThreads), kLevelThreads, 0, s>>>(
+      c.ncell, w.sched_hdr, canon, w.sched_lvl, w.sched_pair, w.status);
 }
 
 template <class P>

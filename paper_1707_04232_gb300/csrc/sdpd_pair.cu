@@ -26,8 +26,8 @@ struct Home<Fp64> {
     x = q.x; y = q.y; z = q.z;
     for (int d = 0; d < 3; ++d) { L[d] = c.L[d]; halfL[d] = c.halfL[d]; }
   }
-  __device__ __forceinline__ void disp(int, int, int, const D4& qj, double& dx, double& dy,
-                                       double& dz) const {
+  __device__ __forceinline__ void frame(int, int, int) {}
+  __device__ __forceinline__ void disp(const D4& qj, double& dx, double& dy, double& dz) const {
     dx = min_image(__dsub_rn(x, qj.x), L[0], halfL[0]);
     dy = min_image(__dsub_rn(y, qj.y), L[1], halfL[1]);
     dz = min_image(__dsub_rn(z, qj.z), L[2], halfL[2]);
@@ -36,25 +36,28 @@ struct Home<Fp64> {
 
 template <>
 struct Home<Mixed> {
-  float hx[3], hy[3], hz[3];
-  __device__ void init(const Consts& c, const F4& q, int cx, int cy, int cz, const uint32_t* xmx,
-                       const uint32_t* xmy, const uint32_t* xmz) {
-    const float sx = (float)c.scale[0], sy = (float)c.scale[1], sz = (float)c.scale[2];
-    for (int o = -1; o <= 1; ++o) {
-      int nx = cx + o, ny = cy + o, nz = cz + o;
-      nx += nx < 0 ? c.nc[0] : (nx >= c.nc[0] ? -c.nc[0] : 0);
-      ny += ny < 0 ? c.nc[1] : (ny >= c.nc[1] ? -c.nc[1] : 0);
-      nz += nz < 0 ? c.nc[2] : (nz >= c.nc[2] ? -c.nc[2] : 0);
-      hx[o + 1] = q.x + (float)(int32_t)(xmx[cx] - xmx[nx]) * sx;
-      hy[o + 1] = q.y + (float)(int32_t)(xmy[cy] - xmy[ny]) * sy;
-      hz[o + 1] = q.z + (float)(int32_t)(xmz[cz] - xmz[nz]) * sz;
-    }
+  float x, y, z, sx, sy, sz;
+  int cx, cy, cz;
+  const uint32_t *xmx, *xmy, *xmz;
+  float hx, hy, hz;  // home coordinates in the frame of the current neighbour cell
+  __device__ void init(const Consts& c, const F4& q, int cx_, int cy_, int cz_, const uint32_t* xmx_,
+                       const uint32_t* xmy_, const uint32_t* xmz_) {
+    x = q.x; y = q.y; z = q.z;
+    sx = (float)c.scale[0]; sy = (float)c.scale[1]; sz = (float)c.scale[2];
+    cx = cx_; cy = cy_; cz = cz_;
+    xmx = xmx_; xmy = xmy_; xmz = xmz_;
   }
-  __device__ __forceinline__ void disp(int ox, int oy, int oz, const F4& qj, float& dx, float& dy,
-                                       float& dz) const {
-    dx = hx[ox + 1] - qj.x;
-    dy = hy[oy + 1] - qj.y;
-    dz = hz[oz + 1] - qj.z;
+  // shift into the frame of neighbour cell (nx, ny, nz): exact fixed-point
+  // distance between the two cells' lower corners
+  __device__ __forceinline__ void frame(int nx, int ny, int nz) {
+    hx = x + (float)(int32_t)(__ldg(&xmx[cx]) - __ldg(&xmx[nx])) * sx;
+    hy = y + (float)(int32_t)(__ldg(&xmy[cy]) - __ldg(&xmy[ny])) * sy;
+    hz = z + (float)(int32_t)(__ldg(&xmz[cz]) - __ldg(&xmz[nz])) * sz;
+  }
+  __device__ __forceinline__ void disp(const F4& qj, float& dx, float& dy, float& dz) const {
+    dx = hx - qj.x;
+    dy = hy - qj.y;
+    dz = hz - qj.z;
   }
 };
 
@@ -86,22 +89,24 @@ __global__ void __launch_bounds__(128) k_density(Consts c, Arrays<P> a, typename
   const R h2 = (R)c.h2, inv_h = R(1) / (R)c.h, cW = (R)c.cW;
   R acc = R(0);
   int cnt = 0;
-#pragma unroll
+#pragma unroll 1
   for (int oz = -1; oz <= 1; ++oz) {
     const int nz = wrapc(cz + oz, c.nc[2]);
-#pragma unroll
+#pragma unroll 1
     for (int oy = -1; oy <= 1; ++oy) {
       const int ny = wrapc(cy + oy, c.nc[1]);
-#pragma unroll
+#pragma unroll 1
       for (int ox = -1; ox <= 1; ++ox) {
         const int nx = wrapc(cx + ox, c.nc[0]);
         const int r = __ldg(&mrank[nx + c.nc[0] * (ny + c.nc[1] * nz)]);
         const int beg = __ldg(&cell_start[r]), end = __ldg(&cell_start[r + 1]);
+        home.frame(nx, ny, nz);
+#pragma unroll 4
         for (int j = beg; j < end; ++j) {
           if (j == i) continue;
           const V4 qj = ld4(&a.q4[j]);
           R dx, dy, dz;
-          home.disp(ox, oy, oz, qj, dx, dy, dz);
+          home.disp(qj, dx, dy, dz);
           const R r2 = r2_of(dx, dy, dz);
           if (r2 < h2) {
             acc += kernel_W<KIND>(sqrt(r2) * inv_h, cW);
@@ -166,22 +171,24 @@ __global__ void __launch_bounds__(128) k_force(Consts c, Arrays<P> a, const type
   home.init(c, qi, cx, cy, cz, xmx, xmy, xmz);
   const R h2 = (R)c.h2, inv_h = R(1) / (R)c.h, cF = (R)c.cF;
   R fx = R(0), fy = R(0), fz = R(0);
-#pragma unroll
+#pragma unroll 1
   for (int oz = -1; oz <= 1; ++oz) {
     const int nz = wrapc(cz + oz, c.nc[2]);
-#pragma unroll
+#pragma unroll 1
     for (int oy = -1; oy <= 1; ++oy) {
       const int ny = wrapc(cy + oy, c.nc[1]);
-#pragma unroll
+#pragma unroll 1
       for (int ox = -1; ox <= 1; ++ox) {
         const int nx = wrapc(cx + ox, c.nc[0]);
         const int r = __ldg(&mrank[nx + c.nc[0] * (ny + c.nc[1] * nz)]);
         const int beg = __ldg(&cell_start[r]), end = __ldg(&cell_start[r + 1]);
+        home.frame(nx, ny, nz);
+#pragma unroll 4
         for (int j = beg; j < end; ++j) {
           if (j == i) continue;
           const V4 qj = ld4(&qp4[j]);
           R dx, dy, dz;
-          home.disp(ox, oy, oz, qj, dx, dy, dz);
+          home.disp(qj, dx, dy, dz);
           const R r2 = r2_of(dx, dy, dz);
           if (r2 < h2) {
             const R s = (pi_i + qj.w) * kernel_F<KIND>(sqrt(r2) * inv_h, cF);

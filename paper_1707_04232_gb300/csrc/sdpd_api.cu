@@ -159,6 +159,7 @@ size_t layout(sdpd_handle* s, Workspace* w, char* base) {
   w->qdz = at(N * sizeof(Q));
   w->cell_count = (int32_t*)at(nc * 4);
   w->cell_start = (int32_t*)at((nc + 1) * 4);
+  w->tile_sum = (int32_t*)at((nc / 2048 + 2) * 4);
   w->mrank = (int32_t*)at(nc * 4);
   w->rcoord = (uint32_t*)at(nc * 4);
   for (int d = 0; d < 3; ++d) w->xmin[d] = (uint32_t*)at((size_t)c.nc[d] * 4);
@@ -203,7 +204,7 @@ void do_load(sdpd_handle* s) {
   launch_sort<P>(s->c, s->w, 0, s->stream);
   s->cur = 1;
   launch_density<P>(s->c, s->w, s->cur, 0, nullptr, s->stream);
-  s->launches += 5;
+  s->launches += 7;
 }
 
 cudaEvent_t take_event(sdpd_handle* s) {
@@ -266,7 +267,7 @@ void do_steps(sdpd_handle* s, double dt, int64_t nsteps, uint64_t seed) {
         launch_force<P>(c, s->w, s->cur, 0.5 * dt, dt, nullptr, s->stream);
       }
       {
-        StageTimer t(s, 1, 3);
+        StageTimer t(s, 1, 5);
         launch_sort<P>(c, s->w, s->cur, s->stream);
       }
       s->cur = 1 - s->cur;
@@ -278,7 +279,7 @@ void do_steps(sdpd_handle* s, double dt, int64_t nsteps, uint64_t seed) {
         StageTimer t(s, 3, 1);
         launch_force<P>(c, s->w, s->cur, 0.5 * dt, 0.0, nullptr, s->stream);
       }
-      s->launches += 6;
+      s->launches += 8;
       s->vv_step++;
     }
     if (fd && (s->prm.fd_only || (n + 1) % theta == 0)) {

@@ -150,7 +150,11 @@ __global__ void __launch_bounds__(kSchedWarps * 32)
   }
   BlockGeom<P> geo;
   geo.init(c, ox, oy, oz, xmx, xmy, xmz);
-  for (int t = lane; t < kMaxBlock * kRowWords; t += 32) (&sm.bits[0][0])[t] = 0u;
+  const int nw = (nb + 31) >> 5;  // bitmap words in use per row
+  for (int t = lane; t < nb * kRowWords; t += 32) {
+    const int row = t / kRowWords, wd = t - row * kRowWords;
+    if (wd < nw) sm.bits[row][wd] = 0u;
+  }
   for (int k = lane; k < nb; k += 32) {
     const int d = cell_code_of(b, k);
     const int g = b.start[d] + (k - b.base[d]);
@@ -161,18 +165,30 @@ __global__ void __launch_bounds__(kSchedWarps * 32)
   }
   __syncwarp();
   // rank of each id among the block's ids: every cell's ids are ascending
+  int maxcnt = 0;
+#pragma unroll
+  for (int d = 0; d < 8; ++d) maxcnt = max(maxcnt, b.cnt[d]);
+  int steps = 0;
+  while ((1 << steps) <= maxcnt) ++steps;
   for (int k = lane; k < nb; k += 32) {
     const int32_t myid = sm.id[k];
-    int r = 0;
-    for (int d = 0; d < 8; ++d) {
-      int lo = b.base[d], hi = b.base[d + 1];
-      while (lo < hi) {
-        int mid = (lo + hi) >> 1;
-        if (sm.id[mid] < myid) lo = mid + 1;
-        else hi = mid;
+    // per cell: number of ids below myid (branch-free lower bound with a
+    // fixed number of halvings, the 8 searches independent of each other)
+    int pos[8], len[8];
+#pragma unroll
+    for (int d = 0; d < 8; ++d) { pos[d] = b.base[d]; len[d] = b.cnt[d]; }
+    for (int it = 0; it < steps; ++it) {
+#pragma unroll
+      for (int d = 0; d < 8; ++d) {
+        const int half = len[d] >> 1;
+        const bool below = len[d] > 0 && sm.id[pos[d] + half] < myid;
+        pos[d] = below ? pos[d] + half + 1 : pos[d];
+        len[d] = below ? len[d] - half - 1 : half;
       }
-      r += lo - b.base[d];
     }
+    int r = 0;
+#pragma unroll
+    for (int d = 0; d < 8; ++d) r += pos[d] - b.base[d];
     sm.rank[k] = (uint8_t)r;
     sm.perm[r] = (uint8_t)k;
   }
@@ -209,8 +225,8 @@ __global__ void __launch_bounds__(kSchedWarps * 32)
   for (int q = 0; q < 8; ++q) {
     const int row = lane * 8 + q;
     int n = 0;
-#pragma unroll
-    for (int w = 0; w < kRowWords; ++w) n += __popc(sm.bits[row][w]);
+    if (row >= 1 && row < nb)
+      for (int w = 0; w < nw; ++w) n += __popc(sm.bits[row][w]);
     cnt8[q] = n;
     sum += n;
   }
@@ -233,9 +249,9 @@ __global__ void __launch_bounds__(kSchedWarps * 32)
   __syncwarp();
   // write the pairs row by row (difference ascending), lower rank ascending
   uint16_t* out = canon + o * kMaxPairs;
-  for (int row = lane; row < kMaxBlock; row += 32) {
+  for (int row = 1 + lane; row < nb; row += 32) {
     int pos = sm.rowoff[row];
-    for (int w = 0; w < kRowWords; ++w) {
+    for (int w = 0; w < nw; ++w) {
       uint32_t bits = sm.bits[row][w];
       while (bits) {
         const int bit = __ffs(bits) - 1;
@@ -252,59 +268,86 @@ __global__ void __launch_bounds__(kSchedWarps * 32)
 // Schedule, step 2: dependency levels of the canonical order and the pairs
 // bucketed by level (one thread per block).
 // ---------------------------------------------------------------------------
+// One thread per block walks that block's canonical list; a warp handles 32
+// consecutive blocks and stages their lists through shared memory 32 entries
+// at a time with coalesced loads.
 constexpr int kLevelThreads = 32;
+constexpr int kTile = 32;
 
 __global__ void __launch_bounds__(kLevelThreads) k_sched_levels(int64_t ncell, uint32_t* __restrict__ hdr,
                                                               const uint16_t* __restrict__ canon,
                                                               uint16_t* __restrict__ lvl,
                                                               uint16_t* __restrict__ pairs, int* status) {
-  // per-thread scratch in shared memory, interleaved by thread:
-  // last level of each particle, and the pair count (then offset) per level
-  __shared__ uint8_t last_s[kMaxBlock][kLevelThreads];
-  __shared__ uint16_t cnt_s[kMaxLevels + 1][kLevelThreads];
+  __shared__ uint8_t last_s[kMaxBlock][kLevelThreads];      // level after which a particle is free
+  __shared__ uint16_t cnt_s[kMaxLevels + 1][kLevelThreads];  // pairs per level, then running offset
+  __shared__ uint16_t tile[kLevelThreads][kTile + 1];
   const int t = threadIdx.x;
-  const int64_t o = blockIdx.x * (int64_t)blockDim.x + t;
-  if (o >= ncell) return;
-  const int np = (int)(hdr[o] & 0xffffu);
-  uint16_t* off = lvl + o * (kMaxLevels + 1);
-  const uint16_t* in = canon + o * kMaxPairs;
-  uint16_t* out = pairs + o * kMaxPairs;
+  const int64_t o0 = (int64_t)blockIdx.x * kLevelThreads;
+  const int64_t o = o0 + t;
+  const bool live = o < ncell;
+  const int np = live ? (int)(hdr[o] & 0xffffu) : 0;
+  int npmax = np;
+  for (int s = 16; s > 0; s >>= 1) npmax = max(npmax, __shfl_xor_sync(0xffffffffu, npmax, s));
   for (int k = 0; k < kMaxBlock; ++k) last_s[k][t] = 0;
   for (int k = 0; k <= kMaxLevels; ++k) cnt_s[k][t] = 0;
   int nlev = 0;
   bool overflow = false;
-  for (int k = 0; k < np; ++k) {
-    const uint16_t pr = in[k];
-    const int u = pr & 255, v = pr >> 8;
-    const int L = max(last_s[u][t], last_s[v][t]);
-    if (L >= kMaxLevels) { overflow = true; break; }
-    last_s[u][t] = last_s[v][t] = (uint8_t)(L + 1);
-    cnt_s[L][t]++;
-    nlev = max(nlev, L + 1);
+  // pass 1: level of every pair, pairs per level
+  for (int k0 = 0; k0 < npmax; k0 += kTile) {
+    __syncwarp();
+    for (int j = 0; j < kLevelThreads; ++j) {
+      const int64_t oj = o0 + j;
+      if (oj < ncell) tile[j][t] = canon[oj * kMaxPairs + k0 + t];
+    }
+    __syncwarp();
+    const int kn = min(kTile, np - k0);
+    for (int k = 0; k < kn; ++k) {
+      const uint16_t pr = tile[t][k];
+      const int u = pr & 255, v = pr >> 8;
+      const int L = max(last_s[u][t], last_s[v][t]);
+      if (L >= kMaxLevels) { overflow = true; continue; }
+      last_s[u][t] = last_s[v][t] = (uint8_t)(L + 1);
+      cnt_s[L][t]++;
+      nlev = max(nlev, L + 1);
+    }
   }
-  if (overflow) {
+  if (live && overflow) {
     atomicOr(status, kStCapacity);
     hdr[o] = 0;
-    off[0] = 0;
-    return;
+    lvl[o * (kMaxLevels + 1)] = 0;
   }
-  int run = 0;
-  for (int L = 0; L < nlev; ++L) {
-    const int n = cnt_s[L][t];
-    off[L] = (uint16_t)run;
-    cnt_s[L][t] = (uint16_t)run;
-    run += n;
+  uint16_t* off = lvl + o * (kMaxLevels + 1);
+  if (live && !overflow) {
+    int run = 0;
+    for (int L = 0; L < nlev; ++L) {
+      const int n = cnt_s[L][t];
+      off[L] = (uint16_t)run;
+      cnt_s[L][t] = (uint16_t)run;
+      run += n;
+    }
+    off[nlev] = (uint16_t)run;
   }
-  off[nlev] = (uint16_t)run;
   for (int k = 0; k < kMaxBlock; ++k) last_s[k][t] = 0;
-  for (int k = 0; k < np; ++k) {
-    const uint16_t pr = in[k];
-    const int u = pr & 255, v = pr >> 8;
-    const int L = max(last_s[u][t], last_s[v][t]);
-    last_s[u][t] = last_s[v][t] = (uint8_t)(L + 1);
-    out[cnt_s[L][t]++] = pr;
+  // pass 2: the pairs bucketed by level
+  uint16_t* out = pairs + o * kMaxPairs;
+  for (int k0 = 0; k0 < npmax; k0 += kTile) {
+    __syncwarp();
+    for (int j = 0; j < kLevelThreads; ++j) {
+      const int64_t oj = o0 + j;
+      if (oj < ncell) tile[j][t] = canon[oj * kMaxPairs + k0 + t];
+    }
+    __syncwarp();
+    if (!live || overflow) continue;
+    const int kn = min(kTile, np - k0);
+    for (int k = 0; k < kn; ++k) {
+      const uint16_t pr = tile[t][k];
+      const int u = pr & 255, v = pr >> 8;
+      const int L = max(last_s[u][t], last_s[v][t]);
+      last_s[u][t] = last_s[v][t] = (uint8_t)(L + 1);
+      out[cnt_s[L][t]++] = pr;
+    }
   }
-  hdr[o] = (uint32_t)np | ((uint32_t)nlev << 16);
+  if (live && !overflow) hdr[o] = (uint32_t)np | ((uint32_t)nlev << 16);
 }
 
 // ---------------------------------------------------------------------------

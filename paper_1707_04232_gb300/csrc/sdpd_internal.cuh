@@ -233,6 +233,7 @@ struct Workspace {
   void* qdz;
   int32_t* cell_count;  // [ncell] (kept zero between uses)
   int32_t* cell_start;  // [ncell + 1]
+  int32_t* tile_sum;    // scan scratch: one entry per 2048 cells
   int32_t* mrank;       // linear cell -> Morton rank
   uint32_t* rcoord;     // Morton rank -> packed cell coordinates
   uint32_t* xmin[3];    // mixed: fixed-point lower edge of each cell, per axis

@@ -67,44 +67,90 @@ __global__ void k_load(Consts c, const double* __restrict__ io_q, const double* 
   slot[k] = atomicAdd(&cell_count[r], 1);
 }
 
-// Exclusive scan of the cell counts (one block); leaves the counts at zero.
-__global__ void k_scan(int ncell, int32_t* cell_count, int32_t* cell_start) {
+// Exclusive scan of the cell counts in three passes (tile sums, scan of the
+// tile sums in one block, tile scans); leaves the counts at zero.
+constexpr int kScanTile = 2048;  // cells per tile: 256 threads x 8
+
+__global__ void __launch_bounds__(256) k_scan_tiles(int ncell, const int32_t* __restrict__ cell_count,
+                                                    int32_t* __restrict__ tile_sum) {
+  __shared__ int32_t red[8];
+  const int base = blockIdx.x * kScanTile + threadIdx.x * 8;
+  int32_t s = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) s += base + k < ncell ? cell_count[base + k] : 0;
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int32_t t = 0;
+    for (int k = 0; k < 8; ++k) t += red[k];
+    tile_sum[blockIdx.x] = t;
+  }
+}
+
+// exclusive scan of up to 1024 * 32 tile sums by one block of 1024 threads
+__global__ void __launch_bounds__(1024) k_scan_sums(int ntiles, int32_t* __restrict__ tile_sum, int32_t* total) {
   __shared__ int32_t warp_tot[32];
-  __shared__ int32_t carry_s;
-  const int nt = blockDim.x;
-  const int per = (ncell + nt - 1) / nt;
-  const int beg = threadIdx.x * per;
-  const int end = min(ncell, beg + per);
+  const int per = (ntiles + 1023) / 1024;
+  const int beg = threadIdx.x * per, end = min(ntiles, beg + per);
   int32_t local = 0;
-  for (int i = beg; i < end; ++i) local += cell_count[i];
-  // block-wide exclusive scan of the per-thread totals
-  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int i = beg; i < end; ++i) local += tile_sum[i];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   int32_t v = local;
   for (int o = 1; o < 32; o <<= 1) {
-    int32_t t = __shfl_up_sync(0xffffffffu, v, o);
+    const int32_t t = __shfl_up_sync(0xffffffffu, v, o);
     if (lane >= o) v += t;
   }
   if (lane == 31) warp_tot[wid] = v;
   __syncthreads();
   if (wid == 0) {
-    int nw = (nt + 31) >> 5;
-    int32_t t = lane < nw ? warp_tot[lane] : 0;
+    int32_t t = warp_tot[lane];
     for (int o = 1; o < 32; o <<= 1) {
-      int32_t u = __shfl_up_sync(0xffffffffu, t, o);
+      const int32_t u = __shfl_up_sync(0xffffffffu, t, o);
       if (lane >= o) t += u;
     }
-    if (lane < nw) warp_tot[lane] = t;  // inclusive
-    if (lane == nw - 1) carry_s = t;
+    warp_tot[lane] = t;
   }
   __syncthreads();
   int32_t run = v - local + (wid > 0 ? warp_tot[wid - 1] : 0);
   for (int i = beg; i < end; ++i) {
-    int32_t n = cell_count[i];
-    cell_start[i] = run;
-    cell_count[i] = 0;
+    const int32_t n = tile_sum[i];
+    tile_sum[i] = run;
     run += n;
   }
-  if (threadIdx.x == 0) cell_start[ncell] = carry_s;
+  if (threadIdx.x == 1023) *total = warp_tot[31];
+}
+
+__global__ void __launch_bounds__(256) k_scan_apply(int ncell, int32_t* __restrict__ cell_count,
+                                                    int32_t* __restrict__ cell_start,
+                                                    const int32_t* __restrict__ tile_sum) {
+  __shared__ int32_t warp_tot[8];
+  const int base = blockIdx.x * kScanTile + threadIdx.x * 8;
+  int32_t v[8], s = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    v[k] = base + k < ncell ? cell_count[base + k] : 0;
+    s += v[k];
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int32_t incl = s;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) warp_tot[wid] = incl;
+  __syncthreads();
+  int32_t wbase = 0;
+  for (int k = 0; k < wid; ++k) wbase += warp_tot[k];
+  int32_t run = tile_sum[blockIdx.x] + wbase + incl - s;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    if (base + k < ncell) {
+      cell_start[base + k] = run;
+      cell_count[base + k] = 0;
+    }
+    run += v[k];
+  }
 }
 
 __global__ void k_scatter(int64_t N, const int32_t* __restrict__ key, const int32_t* __restrict__ slot,
@@ -192,7 +238,10 @@ void launch_load(const Consts& c, const Workspace& w, cudaStream_t s) {
 
 template <class P>
 void launch_sort(const Consts& c, const Workspace& w, int from, cudaStream_t s) {
-  k_scan<<<1, 1024, 0, s>>>(c.ncell, w.cell_count, w.cell_start);
+  const int ntiles = (c.ncell + kScanTile - 1) / kScanTile;
+  k_scan_tiles<<<ntiles, 256, 0, s>>>(c.ncell, w.cell_count, w.tile_sum);
+  k_scan_sums<<<1, 1024, 0, s>>>(ntiles, w.tile_sum, w.cell_start + c.ncell);
+  k_scan_apply<<<ntiles, 256, 0, s>>>(c.ncell, w.cell_count, w.cell_start, w.tile_sum);
   if (c.N == 0) return;
   Arrays<P> src = view<P>(w, from), dst = view<P>(w, 1 - from);
   // w.tmp holds 2N entries: bucketed old indices, then their ids

@@ -188,7 +188,7 @@ def workload_config(args):
 # algorithmic float operations of the two pair passes, per neighbour pair
 # (r < h) visit, and of one pair update of the sweep; see the design doc
 FLOPS_PER_VISIT = {"density_eos": 18.0, "kick1_drift_bin": 24.0, "kick2": 24.0}
-FLOPS_PER_PAIR_UPDATE = {"ems": 260.0, "ams": 150.0, "ssa": 140.0}
+FLOPS_PER_PAIR_UPDATE = {"ems": 210.0, "ams": 150.0, "ssa": 140.0}
 
 
 def run_ours(args, rank, world, local_rank):

@@ -63,7 +63,7 @@ uint64_t morton3(uint32_t x, uint32_t y, uint32_t z) {
 int map_status(int bits) {
   if (bits & kStNaN) return SDPD_ERR_NAN;
   if (bits & kStNegative) return SDPD_ERR_NEGATIVE_ENERGY;
-  if (bits & kStCapacity) return SDPD_ERR_CAPACITY;
+  if (bits & (kStCapacity | kStNbrCap)) return SDPD_ERR_CAPACITY;
   if (bits & kStBadEnergy) return SDPD_ERR_NONPOSITIVE_ENERGY;
   return SDPD_OK;
 }
@@ -151,6 +151,8 @@ size_t layout(sdpd_handle* s, Workspace* w, char* base) {
     w->id[k] = (int32_t*)at(N * sizeof(int32_t));
   }
   w->qp4 = at(N * sizeof(V4));
+  w->nlist = (uint32_t*)at(N * (size_t)c.nbr_cap * 4);
+  w->nn = (int32_t*)at(N * 4);
   w->key = (int32_t*)at(N * 4);
   w->slot = (int32_t*)at(N * 4);
   w->tmp = (int32_t*)at(2 * N * 4);
@@ -390,6 +392,7 @@ int sdpd_create(int64_t N, const double box[3], double m, double h, double K, co
     c.cF = 48.0 / (M_PI * h5);
   }
   c.W0 = c.cW;
+  c.nbr_cap = 160;
   c.kernel = prm->kernel;
   c.scheme = prm->scheme;
   s->prm = *prm;

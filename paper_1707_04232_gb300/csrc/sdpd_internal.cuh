@@ -22,6 +22,7 @@ enum : int {
   kStNaN = 2,         // non-finite momentum / energy
   kStCapacity = 4,    // block capacity exceeded
   kStBadEnergy = 8,   // set_state got eps <= 0
+  kStNbrCap = 16,     // a particle has more neighbours than its list holds
 };
 
 // Per-run constants; every kernel gets a copy by value.
@@ -37,7 +38,14 @@ struct Consts {
   double kpar_m2, kperp_m2;  // (10/3 eta + 4 zeta) m^2 and (5/3 eta - zeta) m^2
   double cW, cF, W0;         // kernel constants and W(0)
   int kernel, scheme;
+  int nbr_cap;               // neighbour-list entries per particle
 };
+
+// Neighbour-list entry: neighbour index << 6 | stencil offset code, the code
+// holding (o + 1) per axis in 2 bits (x lowest) for o in {-1, 0, +1}.
+__host__ __device__ __forceinline__ uint32_t nbr_entry(int j, int ox, int oy, int oz) {
+  return ((uint32_t)j << 6) | (uint32_t)((ox + 1) | ((oy + 1) << 2) | ((oz + 1) << 4));
+}
 
 // ---------------------------------------------------------------------------
 // Smoothing kernels of Section 2.1.1 as functions of x = r/h in [0, 1).
@@ -224,6 +232,8 @@ struct Workspace {
   void* rho[2];
   int32_t* id[2];
   void* qp4;            // sorted (x, y, z, pi): positions and p/rho^2 for force passes
+  uint32_t* nlist;      // neighbour lists, entry k of particle i at nlist[i * nbr_cap + k]
+  int32_t* nn;          // neighbour count per particle
   // binning and sorting scratch
   int32_t* key;         // cell rank per particle (old order)
   int32_t* slot;        // arrival slot in the cell (old order)

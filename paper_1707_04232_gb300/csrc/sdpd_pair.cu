@@ -27,6 +27,10 @@ struct Home<Fp64> {
     for (int d = 0; d < 3; ++d) { L[d] = c.L[d]; halfL[d] = c.halfL[d]; }
   }
   __device__ __forceinline__ void frame(int, int, int) {}
+  __device__ __forceinline__ void frames_all(const Consts&) {}
+  __device__ __forceinline__ void disp_code(uint32_t, const D4& qj, double& dx, double& dy, double& dz) const {
+    disp(qj, dx, dy, dz);
+  }
   __device__ __forceinline__ void disp(const D4& qj, double& dx, double& dy, double& dz) const {
     dx = min_image(__dsub_rn(x, qj.x), L[0], halfL[0]);
     dy = min_image(__dsub_rn(y, qj.y), L[1], halfL[1]);
@@ -59,6 +63,27 @@ struct Home<Mixed> {
     dy = hy - qj.y;
     dz = hz - qj.z;
   }
+  // all nine shifted home coordinates, for walking a neighbour list
+  float fx[3], fy[3], fz[3];
+  __device__ __forceinline__ void frames_all(const Consts& c) {
+#pragma unroll
+    for (int o = 0; o < 3; ++o) {
+      int nx = cx + o - 1, ny = cy + o - 1, nz = cz + o - 1;
+      nx += nx < 0 ? c.nc[0] : (nx >= c.nc[0] ? -c.nc[0] : 0);
+      ny += ny < 0 ? c.nc[1] : (ny >= c.nc[1] ? -c.nc[1] : 0);
+      nz += nz < 0 ? c.nc[2] : (nz >= c.nc[2] ? -c.nc[2] : 0);
+      frame(nx, ny, nz);
+      fx[o] = hx; fy[o] = hy; fz[o] = hz;
+    }
+  }
+  __device__ __forceinline__ static float pick(const float* v, uint32_t k) {
+    return k == 0 ? v[0] : (k == 1 ? v[1] : v[2]);
+  }
+  __device__ __forceinline__ void disp_code(uint32_t code, const F4& qj, float& dx, float& dy, float& dz) const {
+    dx = pick(fx, code & 3u) - qj.x;
+    dy = pick(fy, (code >> 2) & 3u) - qj.y;
+    dz = pick(fz, (code >> 4) & 3u) - qj.z;
+  }
 };
 
 __device__ __forceinline__ int wrapc(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
@@ -76,7 +101,9 @@ __global__ void __launch_bounds__(128) k_density(Consts c, Arrays<P> a, typename
                                                  const uint32_t* __restrict__ xmx,
                                                  const uint32_t* __restrict__ xmy,
                                                  const uint32_t* __restrict__ xmz, int update_eos,
-                                                 int32_t* __restrict__ ncount_by_id) {
+                                                 int32_t* __restrict__ ncount_by_id,
+                                                 uint32_t* __restrict__ nlist, int32_t* __restrict__ nn,
+                                                 int* __restrict__ status) {
   using R = typename P::R;
   using V4 = typename P::V4;
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -110,6 +137,7 @@ __global__ void __launch_bounds__(128) k_density(Consts c, Arrays<P> a, typename
           const R r2 = r2_of(dx, dy, dz);
           if (r2 < h2) {
             acc += kernel_W<KIND>(sqrt(r2) * inv_h, cW);
+            if (cnt < c.nbr_cap) nlist[i * c.nbr_cap + cnt] = nbr_entry(j, ox, oy, oz);
             ++cnt;
           }
         }
@@ -117,6 +145,8 @@ __global__ void __launch_bounds__(128) k_density(Consts c, Arrays<P> a, typename
     }
   }
   if (ncount_by_id) ncount_by_id[a.id[i]] = cnt;
+  nn[i] = min(cnt, c.nbr_cap);
+  if (cnt > c.nbr_cap) atomicOr(status, kStNbrCap);
   const R rho_new = (R)c.m * ((R)c.W0 + acc);
   double e = a.eps[i];
   if (update_eos) {
@@ -158,7 +188,8 @@ __global__ void __launch_bounds__(128) k_force(Consts c, Arrays<P> a, const type
                                                typename P::Q* __restrict__ qdy,
                                                typename P::Q* __restrict__ qdz, int32_t* __restrict__ key,
                                                int32_t* __restrict__ slot, int32_t* __restrict__ cell_count,
-                                               double* __restrict__ force_by_id) {
+                                               double* __restrict__ force_by_id,
+                                               const uint32_t* __restrict__ nlist, const int32_t* __restrict__ nn) {
   using R = typename P::R;
   using V4 = typename P::V4;
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -169,36 +200,20 @@ __global__ void __launch_bounds__(128) k_force(Consts c, Arrays<P> a, const type
   unpack_cell(w_to_cellbits(qi.w), cx, cy, cz);
   Home<P> home;
   home.init(c, qi, cx, cy, cz, xmx, xmy, xmz);
-  const R h2 = (R)c.h2, inv_h = R(1) / (R)c.h, cF = (R)c.cF;
+  const R inv_h = R(1) / (R)c.h, cF = (R)c.cF;
   R fx = R(0), fy = R(0), fz = R(0);
-#pragma unroll 1
-  for (int oz = -1; oz <= 1; ++oz) {
-    const int nz = wrapc(cz + oz, c.nc[2]);
-#pragma unroll 1
-    for (int oy = -1; oy <= 1; ++oy) {
-      const int ny = wrapc(cy + oy, c.nc[1]);
-#pragma unroll 1
-      for (int ox = -1; ox <= 1; ++ox) {
-        const int nx = wrapc(cx + ox, c.nc[0]);
-        const int r = __ldg(&mrank[nx + c.nc[0] * (ny + c.nc[1] * nz)]);
-        const int beg = __ldg(&cell_start[r]), end = __ldg(&cell_start[r + 1]);
-        home.frame(nx, ny, nz);
-#pragma unroll 4
-        for (int j = beg; j < end; ++j) {
-          if (j == i) continue;
-          const V4 qj = ld4(&qp4[j]);
-          R dx, dy, dz;
-          home.disp(qj, dx, dy, dz);
-          const R r2 = r2_of(dx, dy, dz);
-          if (r2 < h2) {
-            const R s = (pi_i + qj.w) * kernel_F<KIND>(sqrt(r2) * inv_h, cF);
-            fx += s * dx;
-            fy += s * dy;
-            fz += s * dz;
-          }
-        }
-      }
-    }
+  home.frames_all(c);
+  const int n = nn[i];
+  for (int k = 0; k < n; ++k) {
+    const uint32_t e = __ldg(&nlist[i * c.nbr_cap + k]);
+    const V4 qj = ld4(&qp4[e >> 6]);
+    R dx, dy, dz;
+    home.disp_code(e & 63u, qj, dx, dy, dz);
+    const R r2 = r2_of(dx, dy, dz);
+    const R s = (pi_i + qj.w) * kernel_F<KIND>(sqrt(r2) * inv_h, cF);
+    fx += s * dx;
+    fy += s * dy;
+    fz += s * dz;
   }
   const R m2 = (R)(c.m * c.m);
   fx *= m2; fy *= m2; fz *= m2;
@@ -252,10 +267,12 @@ void launch_density(const Consts& c, const Workspace& w, int cur, int update_eos
   auto qp4 = (typename P::V4*)w.qp4;
   if (c.kernel == SDPD_KERNEL_LUCY)
     k_density<P, SDPD_KERNEL_LUCY><<<blocks_for(c.N, 128), 128, 0, s>>>(
-        c, a, qp4, w.cell_start, w.mrank, w.xmin[0], w.xmin[1], w.xmin[2], update_eos, ncount_by_id);
+        c, a, qp4, w.cell_start, w.mrank, w.xmin[0], w.xmin[1], w.xmin[2], update_eos, ncount_by_id, w.nlist,
+        w.nn, w.status);
   else
     k_density<P, SDPD_KERNEL_CUBIC><<<blocks_for(c.N, 128), 128, 0, s>>>(
-        c, a, qp4, w.cell_start, w.mrank, w.xmin[0], w.xmin[1], w.xmin[2], update_eos, ncount_by_id);
+        c, a, qp4, w.cell_start, w.mrank, w.xmin[0], w.xmin[1], w.xmin[2], update_eos, ncount_by_id, w.nlist,
+        w.nn, w.status);
 }
 
 template <class P>
@@ -270,11 +287,11 @@ void launch_force(const Consts& c, const Workspace& w, int cur, double half_dt, 
   if (c.kernel == SDPD_KERNEL_LUCY)
     k_force<P, SDPD_KERNEL_LUCY><<<blocks_for(c.N, 128), 128, 0, s>>>(
         c, a, qp4, w.cell_start, w.mrank, w.xmin[0], w.xmin[1], w.xmin[2], half_dt, dt_drift, qdx, qdy,
-        qdz, w.key, w.slot, w.cell_count, force_by_id);
+        qdz, w.key, w.slot, w.cell_count, force_by_id, w.nlist, w.nn);
   else
     k_force<P, SDPD_KERNEL_CUBIC><<<blocks_for(c.N, 128), 128, 0, s>>>(
         c, a, qp4, w.cell_start, w.mrank, w.xmin[0], w.xmin[1], w.xmin[2], half_dt, dt_drift, qdx, qdy,
-        qdz, w.key, w.slot, w.cell_count, force_by_id);
+        qdz, w.key, w.slot, w.cell_count, force_by_id, w.nlist, w.nn);
 }
 
 template void launch_density<Fp64>(const Consts&, const Workspace&, int, int, int32_t*, cudaStream_t);

@@ -160,7 +160,7 @@ int64_t sdpd_get_fd_step(const sdpd_t* s);
 int sdpd_reset_counters(sdpd_t* s);
 
 /* Number of CUDA kernels the handle has launched so far (a VV step launches
- * 8, a sweep 10, sdpd_set_state 7, sdpd_observables 2). */
+ * 8, a sweep 11, sdpd_set_state 7, sdpd_observables 2). */
 int64_t sdpd_kernel_launches(const sdpd_t* s);
 
 /* Per-stage timing with CUDA events recorded on the handle's stream around

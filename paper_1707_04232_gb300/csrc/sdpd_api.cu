@@ -168,6 +168,7 @@ size_t layout(sdpd_handle* s, Workspace* w, char* base) {
   w->sched_hdr = (uint32_t*)at(nc * 4);
   w->sched_lvl = (uint16_t*)at(nc * (kMaxLevels + 1) * 2);
   w->sched_pair = (uint16_t*)at(2 * nc * kMaxPairs * 2);
+  w->level_of = (uint8_t*)at(nc * kMaxPairs);
   w->io_q = (double*)at(3 * N * 8);
   w->io_p = (double*)at(3 * N * 8);
   w->io_e = (double*)at(N * 8);
@@ -289,14 +290,14 @@ void do_steps(sdpd_handle* s, double dt, int64_t nsteps, uint64_t seed) {
       const int rec = s->w.pair_recs != nullptr;
       if (rec) cudaMemsetAsync(s->w.pair_rec_count, 0, 8, s->stream);
       {
-        StageTimer t(s, 4, 2);
+        StageTimer t(s, 4, 3);
         launch_fd_schedule<P>(c, s->w, s->cur, s->stream);
       }
       {
         StageTimer t(s, 5, 8);
         launch_fd_colours<P>(c, s->w, s->cur, dt_fd, seed, (uint64_t)s->fd_step, rec, s->stream);
       }
-      s->launches += 10;
+      s->launches += 11;
       s->fd_step++;
     }
   }

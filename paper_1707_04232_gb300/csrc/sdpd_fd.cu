@@ -268,19 +268,20 @@ __global__ void __launch_bounds__(kSchedWarps * 32)
 // Schedule, step 2: dependency levels of the canonical order and the pairs
 // bucketed by level (one thread per block).
 // ---------------------------------------------------------------------------
-// One thread per block walks that block's canonical list; a warp handles 32
-// consecutive blocks and stages their lists through shared memory 32 entries
-// at a time with coalesced loads.
+// Levels, step 1: one thread per block walks that block's canonical list and
+// records the level of every pair (the longest chain of earlier pairs sharing
+// a particle).  A warp handles 32 consecutive blocks and moves their lists
+// and levels through shared memory 32 entries at a time, so every global
+// access is coalesced.
 constexpr int kLevelThreads = 32;
 constexpr int kTile = 32;
 
-__global__ void __launch_bounds__(kLevelThreads) k_sched_levels(int64_t ncell, uint32_t* __restrict__ hdr,
-                                                              const uint16_t* __restrict__ canon,
-                                                              uint16_t* __restrict__ lvl,
-                                                              uint16_t* __restrict__ pairs, int* status) {
-  __shared__ uint8_t last_s[kMaxBlock][kLevelThreads];      // level after which a particle is free
-  __shared__ uint16_t cnt_s[kMaxLevels + 1][kLevelThreads];  // pairs per level, then running offset
+__global__ void __launch_bounds__(kLevelThreads) k_sched_walk(int64_t ncell, uint32_t* __restrict__ hdr,
+                                                            const uint16_t* __restrict__ canon,
+                                                            uint8_t* __restrict__ level_of, int* status) {
+  __shared__ uint8_t last_s[kMaxBlock][kLevelThreads];  // level after which a particle is free
   __shared__ uint16_t tile[kLevelThreads][kTile + 1];
+  __shared__ uint8_t ltile[kLevelThreads][kTile + 4];
   const int t = threadIdx.x;
   const int64_t o0 = (int64_t)blockIdx.x * kLevelThreads;
   const int64_t o = o0 + t;
@@ -289,10 +290,8 @@ __global__ void __launch_bounds__(kLevelThreads) k_sched_levels(int64_t ncell, u
   int npmax = np;
   for (int s = 16; s > 0; s >>= 1) npmax = max(npmax, __shfl_xor_sync(0xffffffffu, npmax, s));
   for (int k = 0; k < kMaxBlock; ++k) last_s[k][t] = 0;
-  for (int k = 0; k <= kMaxLevels; ++k) cnt_s[k][t] = 0;
   int nlev = 0;
   bool overflow = false;
-  // pass 1: level of every pair, pairs per level
   for (int k0 = 0; k0 < npmax; k0 += kTile) {
     __syncwarp();
     for (int j = 0; j < kLevelThreads; ++j) {
@@ -305,49 +304,78 @@ __global__ void __launch_bounds__(kLevelThreads) k_sched_levels(int64_t ncell, u
       const uint16_t pr = tile[t][k];
       const int u = pr & 255, v = pr >> 8;
       const int L = max(last_s[u][t], last_s[v][t]);
-      if (L >= kMaxLevels) { overflow = true; continue; }
+      if (L >= kMaxLevels) { overflow = true; ltile[t][k] = 0; continue; }
       last_s[u][t] = last_s[v][t] = (uint8_t)(L + 1);
-      cnt_s[L][t]++;
+      ltile[t][k] = (uint8_t)L;
       nlev = max(nlev, L + 1);
     }
-  }
-  if (live && overflow) {
-    atomicOr(status, kStCapacity);
-    hdr[o] = 0;
-    lvl[o * (kMaxLevels + 1)] = 0;
-  }
-  uint16_t* off = lvl + o * (kMaxLevels + 1);
-  if (live && !overflow) {
-    int run = 0;
-    for (int L = 0; L < nlev; ++L) {
-      const int n = cnt_s[L][t];
-      off[L] = (uint16_t)run;
-      cnt_s[L][t] = (uint16_t)run;
-      run += n;
-    }
-    off[nlev] = (uint16_t)run;
-  }
-  for (int k = 0; k < kMaxBlock; ++k) last_s[k][t] = 0;
-  // pass 2: the pairs bucketed by level
-  uint16_t* out = pairs + o * kMaxPairs;
-  for (int k0 = 0; k0 < npmax; k0 += kTile) {
     __syncwarp();
     for (int j = 0; j < kLevelThreads; ++j) {
       const int64_t oj = o0 + j;
-      if (oj < ncell) tile[j][t] = canon[oj * kMaxPairs + k0 + t];
-    }
-    __syncwarp();
-    if (!live || overflow) continue;
-    const int kn = min(kTile, np - k0);
-    for (int k = 0; k < kn; ++k) {
-      const uint16_t pr = tile[t][k];
-      const int u = pr & 255, v = pr >> 8;
-      const int L = max(last_s[u][t], last_s[v][t]);
-      last_s[u][t] = last_s[v][t] = (uint8_t)(L + 1);
-      out[cnt_s[L][t]++] = pr;
+      if (oj < ncell) level_of[oj * kMaxPairs + k0 + t] = ltile[j][t];
     }
   }
-  if (live && !overflow) hdr[o] = (uint32_t)np | ((uint32_t)nlev << 16);
+  if (live) {
+    if (overflow) {
+      atomicOr(status, kStCapacity);
+      hdr[o] = 0;
+    } else {
+      hdr[o] = (uint32_t)np | ((uint32_t)nlev << 16);
+    }
+  }
+}
+
+// Levels, step 2: one warp per block buckets the canonical list by level
+// (order inside a level is free: its pairs touch disjoint particles) and
+// writes the level offsets.
+constexpr int kBucketWarps = 4;
+
+__global__ void __launch_bounds__(kBucketWarps * 32) k_sched_bucket(int64_t ncell, const uint32_t* __restrict__ hdr,
+                                                                  const uint16_t* __restrict__ canon,
+                                                                  const uint8_t* __restrict__ level_of,
+                                                                  uint16_t* __restrict__ lvl,
+                                                                  uint16_t* __restrict__ pairs) {
+  __shared__ int32_t cnt_s[kBucketWarps][kMaxLevels + 1];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t o = (int64_t)blockIdx.x * kBucketWarps + warp;
+  if (o >= ncell) return;
+  const uint32_t hd = hdr[o];
+  const int np = (int)(hd & 0xffffu), nlev = (int)(hd >> 16);
+  int32_t* cnt = cnt_s[warp];
+  for (int L = lane; L <= kMaxLevels; L += 32) cnt[L] = 0;
+  __syncwarp();
+  const uint16_t* in = canon + o * kMaxPairs;
+  const uint8_t* lv = level_of + o * kMaxPairs;
+  for (int k = lane; k < np; k += 32) atomicAdd(&cnt[lv[k]], 1);
+  __syncwarp();
+  // exclusive scan over nlev (<= 255) levels: 8 per lane
+  int v[8], sum = 0;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int L = lane * 8 + q;
+    v[q] = L < nlev ? cnt[L] : 0;
+    sum += v[q];
+  }
+  int incl = sum;
+  for (int s = 1; s < 32; s <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, incl, s);
+    if (lane >= s) incl += t;
+  }
+  int run = incl - sum;
+  uint16_t* off = lvl + o * (kMaxLevels + 1);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int L = lane * 8 + q;
+    if (L < nlev) {
+      off[L] = (uint16_t)run;
+      cnt[L] = run;
+    }
+    run += v[q];
+  }
+  if (lane == 31) off[nlev] = (uint16_t)run;
+  __syncwarp();
+  uint16_t* out = pairs + o * kMaxPairs;
+  for (int k = lane; k < np; k += 32) out[atomicAdd(&cnt[lv[k]], 1)] = in[k];
 }
 
 // ---------------------------------------------------------------------------
@@ -528,16 +556,30 @@ __device__ __forceinline__ int fd_pair(const FDConst<typename P::R>& k, typename
 }
 
 // ---------------------------------------------------------------------------
-// One colour of the sweep: one warp per block of that colour.
+// One colour of the sweep.  A warp runs kOwnersPerWarp blocks of the colour
+// side by side, each on its own group of lanes, in lockstep over the blocks'
+// dependency levels.
 //
-// The block's particles (momenta and energies) live in shared memory; the
-// pairs run level by level.  Everything of a pair that does not depend on the
-// momenta and energies (unit vector, F(r)/(rho_i rho_j), random numbers) is
-// computed ahead for a chunk of consecutive levels by all 32 lanes and staged
-// in shared memory, so only the state-dependent part runs at the width of a
-// level.
+// A block's particles (momenta and energies) live in shared memory.  The
+// block's pairs are consumed in chunks of kChunk consecutive pairs of its
+// level-ordered list: first every lane of the group stages the chunk's
+// state-independent data (unit vector, F(r)/(rho_i rho_j), random numbers),
+// then the chunk's levels (or parts of a level: pairs of one level are
+// independent) run one after the other, the lanes of the group sharing a
+// level's pairs.
 // ---------------------------------------------------------------------------
-constexpr int kChunk = 128;  // pairs staged per chunk (a level has <= kMaxBlock/2 pairs)
+constexpr int kOwnersPerWarp = 2;
+constexpr int kGroupLanes = 32 / kOwnersPerWarp;
+constexpr int kChunk = 32;
+
+// Cell code inside the block of owner (ox, oy, oz) of a particle whose cell
+// bits are w: bit k set iff the particle sits in the upper cell along axis k.
+template <class T>
+__device__ __forceinline__ int block_code(T w, int ox, int oy, int oz) {
+  int cx, cy, cz;
+  unpack_cell(w_to_cellbits(w), cx, cy, cz);
+  return (cx != ox) | ((cy != oy) << 1) | ((cz != oz) << 2);
+}
 
 template <class R>
 struct FdSmem {
@@ -552,10 +594,10 @@ struct FdSmem {
 };
 
 template <class P>
-constexpr int fd_warps() { return P::mixed ? 4 : 2; }
+constexpr int fd_warps() { return P::mixed ? 2 : 1; }
 
 template <class P, int KIND>
-__global__ void __launch_bounds__(fd_warps<P>() * 32)
+__global__ void __launch_bounds__(fd_warps<P>() * 32, P::mixed ? 8 : 4)
     k_fd_colour(Consts c, FDConst<typename P::R> k, Arrays<P> a, typename P::V4* __restrict__ qp4,
                 const int32_t* __restrict__ cell_start, const int32_t* __restrict__ mrank,
                 const uint32_t* __restrict__ xmx, const uint32_t* __restrict__ xmy,
@@ -565,25 +607,32 @@ __global__ void __launch_bounds__(fd_warps<P>() * 32)
                 unsigned long long* rec_count, int64_t rec_cap) {
   using R = typename P::R;
   constexpr int W = fd_warps<P>();
-  __shared__ FdSmem<R> sm_all[W];
+  __shared__ FdSmem<R> sm_all[W][kOwnersPerWarp];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int grp = lane / kGroupLanes, gl = lane % kGroupLanes;
   const int hx = c.nc[0] >> 1, hy = c.nc[1] >> 1, hz = c.nc[2] >> 1;
-  const int64_t w = (int64_t)blockIdx.x * W + warp;
-  if (w >= (int64_t)hx * hy * hz) return;
-  FdSmem<R>& sm = sm_all[warp];
-  const int ox = 2 * (int)(w % hx) + (colour & 1);
-  const int oy = 2 * (int)((w / hx) % hy) + ((colour >> 1) & 1);
-  const int oz = 2 * (int)(w / ((int64_t)hx * hy)) + ((colour >> 2) & 1);
-  const int64_t o = ox + (int64_t)c.nc[0] * (oy + (int64_t)c.nc[1] * oz);
-  const uint32_t hd = hdr[o];
-  const int np = (int)(hd & 0xffffu), nlev = (int)(hd >> 16);
-  if (np == 0) return;
+  const int64_t nown = (int64_t)hx * hy * hz;
+  const int64_t w = ((int64_t)blockIdx.x * W + warp) * kOwnersPerWarp + grp;
+  FdSmem<R>& sm = sm_all[warp][grp];
+  int np = 0, nlev = 0;
+  int64_t o = 0;
+  int ox = 0, oy = 0, oz = 0;
+  if (w < nown) {
+    ox = 2 * (int)(w % hx) + (colour & 1);
+    oy = 2 * (int)((w / hx) % hy) + ((colour >> 1) & 1);
+    oz = 2 * (int)(w / ((int64_t)hx * hy)) + ((colour >> 2) & 1);
+    o = ox + (int64_t)c.nc[0] * (oy + (int64_t)c.nc[1] * oz);
+    const uint32_t hd = hdr[o];
+    np = (int)(hd & 0xffffu);
+    nlev = (int)(hd >> 16);
+  }
   BlockCells b;
-  block_cells(c, ox, oy, oz, mrank, cell_start, b);
-  const int nb = b.base[8];
+  b.base[8] = 0;
+  if (np > 0) block_cells(c, ox, oy, oz, mrank, cell_start, b);
+  const int nb = np > 0 ? b.base[8] : 0;
   BlockGeom<P> geo;
   geo.init(c, ox, oy, oz, xmx, xmy, xmz);
-  for (int q = lane; q < nb; q += 32) {
+  for (int q = gl; q < nb; q += kGroupLanes) {
     const int d = cell_code_of(b, q);
     const int g = b.start[d] + (q - b.base[d]);
     sm.g[q] = g;
@@ -597,28 +646,18 @@ __global__ void __launch_bounds__(fd_warps<P>() * 32)
   const R inv_h = k.inv_h, cF = k.cF;
   unsigned long long n_acc = 0, n_rb = 0, n_rm = 0, n_tot = 0;
   bool negative = false, bad = false;
-  int L0 = 0;
-  while (L0 < nlev) {
-    // chunk = levels [L0, L1) holding at most kChunk pairs
-    const int cbeg = off[L0];
-    int L1 = L0 + 1;
-    for (int base_l = L0 + 1; base_l <= nlev; base_l += 32) {
-      const int Lq = base_l + lane;
-      const bool fits = Lq <= nlev && (int)off[Lq] - cbeg <= kChunk;
-      const unsigned m = __ballot_sync(0xffffffffu, fits);
-      if (m == 0u) break;
-      L1 = base_l + 31 - __clz(m);
-      if (m != 0xffffffffu) break;
-    }
-    const int cend = off[L1];
-    // stage the chunk: geometry, kernel factor and random numbers
-    for (int t = cbeg + lane; t < cend; t += 32) {
+  int L = 0, pos = 0;
+  while (__any_sync(0xffffffffu, pos < np)) {
+    // stage pairs [cbeg, cend) of the level-ordered list
+    const int cbeg = pos, cend = min(pos + kChunk, np);
+    for (int t = cbeg + gl; t < cend; t += kGroupLanes) {
       const uint16_t pr = pl[t];
       const int ia = pr & 255, ib = pr >> 8;  // ia holds the lower id
       const int ga = sm.g[ia], gb = sm.g[ib];
       R xa, ya, za, xb, yb, zb, rx, ry, rz;
-      geo.local(ld4(&a.q4[ga]), cell_code_of(b, ia), xa, ya, za);
-      geo.local(ld4(&a.q4[gb]), cell_code_of(b, ib), xb, yb, zb);
+      const typename P::V4 qa = ld4(&a.q4[ga]), qb = ld4(&a.q4[gb]);
+      geo.local(qa, block_code(qa.w, ox, oy, oz), xa, ya, za);
+      geo.local(qb, block_code(qb.w, ox, oy, oz), xb, yb, zb);
       geo.disp(xa, ya, za, xb, yb, zb, rx, ry, rz);
       const R r2 = r2_of(rx, ry, rz);
       const R inv_r = fm::rsqrt(r2);
@@ -633,9 +672,15 @@ __global__ void __launch_bounds__(fd_warps<P>() * 32)
       sm.G0[slot] = G[0]; sm.G1[slot] = G[1]; sm.G2[slot] = G[2]; sm.U[slot] = U;
     }
     __syncwarp();
-    for (int L = L0; L < L1; ++L) {
-      const int beg = off[L], end = off[L + 1];
-      for (int t = beg + lane; t < end; t += 32) {
+    // the chunk's levels, or parts of them
+    bool more = cbeg < cend;
+    while (__any_sync(0xffffffffu, more)) {
+      int lb = 0, le = 0;
+      if (more) {
+        lb = max((int)off[L], cbeg);
+        le = min((int)off[L + 1], cend);
+      }
+      for (int t = lb + gl; t < le; t += kGroupLanes) {
         const int slot = t - cbeg;
         const uint16_t pr = sm.pr[slot];
         const int ia = pr & 255, ib = pr >> 8;
@@ -683,11 +728,20 @@ __global__ void __launch_bounds__(fd_warps<P>() * 32)
         }
       }
       __syncwarp();
+      if (more) {
+        if ((int)off[L + 1] <= cend) {  // level L done
+          ++L;
+          more = L < nlev && (int)off[L] < cend;
+        } else {
+          more = false;  // level L continues in the next chunk
+        }
+      }
     }
-    L0 = L1;
+    pos = cend;
+    __syncwarp();
   }
   const R pi_coef = (R)(c.c_rho / (c.C_K * c.m));
-  for (int q = lane; q < nb; q += 32) {
+  for (int q = gl; q < nb; q += kGroupLanes) {
     const int g = sm.g[q];
     a.px[g] = sm.px[q]; a.py[g] = sm.py[q]; a.pz[g] = sm.pz[q];
     double e;
@@ -706,10 +760,12 @@ __global__ void __launch_bounds__(fd_warps<P>() * 32)
   }
   const unsigned any_neg = __any_sync(0xffffffffu, negative), any_bad = __any_sync(0xffffffffu, bad);
   if (lane == 0) {
-    atomicAdd(&counters[0], n_tot);
-    atomicAdd(&counters[1], n_acc);
-    atomicAdd(&counters[2], n_rb);
-    atomicAdd(&counters[3], n_rm);
+    if (n_tot) {
+      atomicAdd(&counters[0], n_tot);
+      atomicAdd(&counters[1], n_acc);
+      atomicAdd(&counters[2], n_rb);
+      atomicAdd(&counters[3], n_rm);
+    }
     if (any_neg) atomicOr(status, kStNegative);
     if (any_bad) atomicOr(status, kStNaN);
   }
@@ -743,8 +799,10 @@ void launch_fd_schedule(const Consts& c, const Workspace& w, int cur, cudaStream
   const unsigned gs = (unsigned)((c.ncell + kSchedWarps - 1) / kSchedWarps);
   k_sched_enum<P><<<gs, kSchedWarps * 32, 0, s>>>(c, a, w.cell_start, w.mrank, w.xmin[0], w.xmin[1],
                                                    w.xmin[2], w.sched_hdr, canon, w.status);
-  k_sched_levels<<<(unsigned)((c.ncell + kLevelThreads - 1) / kLevelThreads), kLevelThreads, 0, s>>>(
-      c.ncell, w.sched_hdr, canon, w.sched_lvl, w.sched_pair, w.status);
+  k_sched_walk<<<(unsigned)((c.ncell + kLevelThreads - 1) / kLevelThreads), kLevelThreads, 0, s>>>(
+      c.ncell, w.sched_hdr, canon, w.level_of, w.status);
+  k_sched_bucket<<<(unsigned)((c.ncell + kBucketWarps - 1) / kBucketWarps), kBucketWarps * 32, 0, s>>>(
+      c.ncell, w.sched_hdr, canon, w.level_of, w.sched_lvl, w.sched_pair);
 }
 
 template <class P>
@@ -756,7 +814,8 @@ void launch_fd_colours(const Consts& c, const Workspace& w, int cur, double dt, 
   const FDConst<R> k = fd_const<R>(c, dt);
   constexpr int W = fd_warps<P>();
   const int64_t nown = (int64_t)(c.nc[0] / 2) * (c.nc[1] / 2) * (c.nc[2] / 2);
-  const unsigned gf = (unsigned)((nown + W - 1) / W);
+  const int64_t per_block = (int64_t)W * kOwnersPerWarp;
+  const unsigned gf = (unsigned)((nown + per_block - 1) / per_block);
   auto qp4 = (typename P::V4*)w.qp4;
   sdpd_pair_rec* recs = record ? w.pair_recs : nullptr;
   for (int col = 0; col < 8; ++col) {

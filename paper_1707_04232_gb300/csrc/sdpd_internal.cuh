@@ -251,6 +251,7 @@ struct Workspace {
   uint32_t* sched_hdr;    // npairs | nlevels << 16
   uint16_t* sched_lvl;    // [ncell][kMaxLevels + 1] level offsets
   uint16_t* sched_pair;   // [ncell][kMaxPairs] (local min-id | local max-id << 8)
+  uint8_t* level_of;      // [ncell][kMaxPairs] level of each pair in canonical order
   // host <-> device staging in id order (float64)
   double* io_q;
   double* io_p;

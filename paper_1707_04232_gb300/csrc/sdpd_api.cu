@@ -153,6 +153,7 @@ size_t layout(sdpd_handle* s, Workspace* w, char* base) {
   w->qp4 = at(N * sizeof(V4));
   w->nlist = (uint32_t*)at(N * (size_t)c.nbr_cap * 4);
   w->nn = (int32_t*)at(N * 4);
+  w->nbr_off = (uint8_t*)at(N * 28);
   w->key = (int32_t*)at(N * 4);
   w->slot = (int32_t*)at(N * 4);
   w->tmp = (int32_t*)at(2 * N * 4);

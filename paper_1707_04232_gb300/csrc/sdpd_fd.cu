@@ -116,29 +116,29 @@ __device__ __forceinline__ void owner_coords(const Consts& c, int64_t o, int& ox
 // ---------------------------------------------------------------------------
 constexpr int kSchedWarps = 2;
 
-template <class P>
 struct SchedSmem {
-  using R = typename P::R;
   int32_t id[kMaxBlock];
-  R x[kMaxBlock], y[kMaxBlock], z[kMaxBlock];
   uint8_t rank[kMaxBlock];
   uint8_t perm[kMaxBlock];
   uint32_t bits[kMaxBlock][kRowWords];  // row = rank difference, bit = lower rank
   int32_t rowoff[kMaxBlock + 1];
 };
 
+// The owned pairs are read from the neighbour lists of the density pass: a
+// particle in block cell dA pairs with owned partners only in the cells
+// dB with dA & dB == 0, whose entries sit in known stencil groups of its
+// list row.  Each owned pair is met from both of its particles and kept from
+// the one with the lower rank.
 template <class P>
 __global__ void __launch_bounds__(kSchedWarps * 32)
     k_sched_enum(Consts c, Arrays<P> a, const int32_t* __restrict__ cell_start, const int32_t* __restrict__ mrank,
-                 const uint32_t* __restrict__ xmx, const uint32_t* __restrict__ xmy,
-                 const uint32_t* __restrict__ xmz, uint32_t* __restrict__ hdr, uint16_t* __restrict__ canon,
-                 int* status) {
-  using R = typename P::R;
-  __shared__ SchedSmem<P> sm_all[kSchedWarps];
+                 const uint32_t* __restrict__ nlist, const uint8_t* __restrict__ nbr_off,
+                 uint32_t* __restrict__ hdr, uint16_t* __restrict__ canon, int* status) {
+  __shared__ SchedSmem sm_all[kSchedWarps];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t o = (int64_t)blockIdx.x * kSchedWarps + warp;
   if (o >= c.ncell) return;
-  SchedSmem<P>& sm = sm_all[warp];
+  SchedSmem& sm = sm_all[warp];
   int ox, oy, oz;
   owner_coords(c, o, ox, oy, oz);
   BlockCells b;
@@ -148,8 +148,6 @@ __global__ void __launch_bounds__(kSchedWarps * 32)
     if (lane == 0) { atomicOr(status, kStCapacity); hdr[o] = 0; }
     return;
   }
-  BlockGeom<P> geo;
-  geo.init(c, ox, oy, oz, xmx, xmy, xmz);
   const int nw = (nb + 31) >> 5;  // bitmap words in use per row
   for (int t = lane; t < nb * kRowWords; t += 32) {
     const int row = t / kRowWords, wd = t - row * kRowWords;
@@ -157,11 +155,7 @@ __global__ void __launch_bounds__(kSchedWarps * 32)
   }
   for (int k = lane; k < nb; k += 32) {
     const int d = cell_code_of(b, k);
-    const int g = b.start[d] + (k - b.base[d]);
-    sm.id[k] = a.id[g];
-    R x, y, z;
-    geo.local(ld4(&a.q4[g]), d, x, y, z);
-    sm.x[k] = x; sm.y[k] = y; sm.z[k] = z;
+    sm.id[k] = a.id[b.start[d] + (k - b.base[d])];
   }
   __syncwarp();
   // rank of each id among the block's ids: every cell's ids are ascending
@@ -193,29 +187,28 @@ __global__ void __launch_bounds__(kSchedWarps * 32)
     sm.perm[r] = (uint8_t)k;
   }
   __syncwarp();
-  // owned cell pairs (dA & dB) == 0, candidates r^2 < h^2 (r > 0)
-  const R h2 = (R)c.h2;
-  for (int dA = 0; dA < 8; ++dA) {
-    for (int dB = dA; dB < 8; ++dB) {
-      if (dA & dB) continue;
-      const int nA = b.cnt[dA], nB = b.cnt[dB];
-      const int total = nA * nB;
-      if (total == 0) continue;
-      const float inv_nB = 1.0f / (float)nB;
-      for (int t = lane; t < total; t += 32) {
-        const int ia = (int)(((float)t + 0.5f) * inv_nB);  // exact floor(t / nB) for t < 2^16
-        const int ib = t - ia * nB;
-        if (dA == dB && ia >= ib) continue;
-        const int ka = b.base[dA] + ia, kb = b.base[dB] + ib;
-        R dx, dy, dz;
-        geo.disp(sm.x[ka], sm.y[ka], sm.z[ka], sm.x[kb], sm.y[kb], sm.z[kb], dx, dy, dz);
-        const R r2 = r2_of(dx, dy, dz);
-        if (r2 < h2 && r2 > R(0)) {
-          const int ra = sm.rank[ka], rb = sm.rank[kb];
-          const int lo = min(ra, rb), df = max(ra, rb) - lo;
-          atomicOr(&sm.bits[df][lo >> 5], 1u << (lo & 31));
-        }
+  for (int k = lane; k < nb; k += 32) {
+    const int dA = cell_code_of(b, k);
+    const int g = b.start[dA] + (k - b.base[dA]);
+    const int rk = sm.rank[k];
+    const uint8_t* off = nbr_off + (int64_t)g * 28;
+    const uint32_t* row = nlist + (int64_t)g * c.nbr_cap;
+    // partner cells dB: subsets of the complement of dA
+    const int free = 7 & ~dA;
+    int dB = free;
+    while (true) {
+      const int sx = ((dB & 1) - (dA & 1)) + 1, sy = (((dB >> 1) & 1) - ((dA >> 1) & 1)) + 1,
+                sz = (((dB >> 2) & 1) - ((dA >> 2) & 1)) + 1;
+      const int st = sx + 3 * sy + 9 * sz;
+      const int e0 = off[st], e1 = off[st + 1];
+      const int sB = b.start[dB], bB = b.base[dB];
+      for (int q = e0; q < e1; ++q) {
+        const int j = (int)(__ldg(&row[q]) >> 6);
+        const int rj = sm.rank[bB + (j - sB)];
+        if (rk < rj) atomicOr(&sm.bits[rj - rk][rk >> 5], 1u << (rk & 31));
       }
+      if (dB == 0) break;
+      dB = (dB - 1) & free;
     }
   }
   __syncwarp();
@@ -223,10 +216,10 @@ __global__ void __launch_bounds__(kSchedWarps * 32)
   int cnt8[8], sum = 0;
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
-    const int row = lane * 8 + q;
+    const int rr = lane * 8 + q;
     int n = 0;
-    if (row >= 1 && row < nb)
-      for (int w = 0; w < nw; ++w) n += __popc(sm.bits[row][w]);
+    if (rr >= 1 && rr < nb)
+      for (int w = 0; w < nw; ++w) n += __popc(sm.bits[rr][w]);
     cnt8[q] = n;
     sum += n;
   }
@@ -249,25 +242,21 @@ __global__ void __launch_bounds__(kSchedWarps * 32)
   __syncwarp();
   // write the pairs row by row (difference ascending), lower rank ascending
   uint16_t* out = canon + o * kMaxPairs;
-  for (int row = 1 + lane; row < nb; row += 32) {
-    int pos = sm.rowoff[row];
+  for (int rr = 1 + lane; rr < nb; rr += 32) {
+    int pos = sm.rowoff[rr];
     for (int w = 0; w < nw; ++w) {
-      uint32_t bits = sm.bits[row][w];
+      uint32_t bits = sm.bits[rr][w];
       while (bits) {
         const int bit = __ffs(bits) - 1;
         bits &= bits - 1;
         const int lo = w * 32 + bit;
-        out[pos++] = (uint16_t)(sm.perm[lo] | (sm.perm[lo + row] << 8));
+        out[pos++] = (uint16_t)(sm.perm[lo] | (sm.perm[lo + rr] << 8));
       }
     }
   }
   if (lane == 0) hdr[o] = (uint32_t)npairs;
 }
 
-// ---------------------------------------------------------------------------
-// Schedule, step 2: dependency levels of the canonical order and the pairs
-// bucketed by level (one thread per block).
-// ---------------------------------------------------------------------------
 // Levels, step 1: one thread per block walks that block's canonical list and
 // records the level of every pair (the longest chain of earlier pairs sharing
 // a particle).  A warp handles 32 consecutive blocks and moves their lists
@@ -797,8 +786,8 @@ void launch_fd_schedule(const Consts& c, const Workspace& w, int cur, cudaStream
   Arrays<P> a = view<P>(w, cur);
   uint16_t* canon = w.sched_pair + (size_t)c.ncell * kMaxPairs;
   const unsigned gs = (unsigned)((c.ncell + kSchedWarps - 1) / kSchedWarps);
-  k_sched_enum<P><<<gs, kSchedWarps * 32, 0, s>>>(c, a, w.cell_start, w.mrank, w.xmin[0], w.xmin[1],
-                                                   w.xmin[2], w.sched_hdr, canon, w.status);
+  k_sched_enum<P><<<gs, kSchedWarps * 32, 0, s>>>(c, a, w.cell_start, w.mrank, w.nlist, w.nbr_off,
+                                                   w.sched_hdr, canon, w.status);
   k_sched_walk<<<(unsigned)((c.ncell + kLevelThreads - 1) / kLevelThreads), kLevelThreads, 0, s>>>(
       c.ncell, w.sched_hdr, canon, w.level_of, w.status);
   k_sched_bucket<<<(unsigned)((c.ncell + kBucketWarps - 1) / kBucketWarps), kBucketWarps * 32, 0, s>>>(

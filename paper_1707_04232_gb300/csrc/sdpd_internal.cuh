@@ -234,6 +234,7 @@ struct Workspace {
   void* qp4;            // sorted (x, y, z, pi): positions and p/rho^2 for force passes
   uint32_t* nlist;      // neighbour lists, entry k of particle i at nlist[i * nbr_cap + k]
   int32_t* nn;          // neighbour count per particle
+  uint8_t* nbr_off;     // [N][28]: start of each of the 27 stencil cells' entries in the row, then the end
   // binning and sorting scratch
   int32_t* key;         // cell rank per particle (old order)
   int32_t* slot;        // arrival slot in the cell (old order)

@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(128) k_density(Consts c, Arrays<P> a, typename
                                                  const uint32_t* __restrict__ xmz, int update_eos,
                                                  int32_t* __restrict__ ncount_by_id,
                                                  uint32_t* __restrict__ nlist, int32_t* __restrict__ nn,
-                                                 int* __restrict__ status) {
+                                                 uint8_t* __restrict__ nbr_off, int* __restrict__ status) {
   using R = typename P::R;
   using V4 = typename P::V4;
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -128,6 +128,7 @@ __global__ void __launch_bounds__(128) k_density(Consts c, Arrays<P> a, typename
         const int r = __ldg(&mrank[nx + c.nc[0] * (ny + c.nc[1] * nz)]);
         const int beg = __ldg(&cell_start[r]), end = __ldg(&cell_start[r + 1]);
         home.frame(nx, ny, nz);
+        nbr_off[i * 28 + (ox + 1) + 3 * (oy + 1) + 9 * (oz + 1)] = (uint8_t)min(cnt, c.nbr_cap);
 #pragma unroll 4
         for (int j = beg; j < end; ++j) {
           if (j == i) continue;
@@ -146,6 +147,7 @@ __global__ void __launch_bounds__(128) k_density(Consts c, Arrays<P> a, typename
   }
   if (ncount_by_id) ncount_by_id[a.id[i]] = cnt;
   nn[i] = min(cnt, c.nbr_cap);
+  nbr_off[i * 28 + 27] = (uint8_t)min(cnt, c.nbr_cap);
   if (cnt > c.nbr_cap) atomicOr(status, kStNbrCap);
   const R rho_new = (R)c.m * ((R)c.W0 + acc);
   double e = a.eps[i];
@@ -268,11 +270,11 @@ void launch_density(const Consts& c, const Workspace& w, int cur, int update_eos
   if (c.kernel == SDPD_KERNEL_LUCY)
     k_density<P, SDPD_KERNEL_LUCY><<<blocks_for(c.N, 128), 128, 0, s>>>(
         c, a, qp4, w.cell_start, w.mrank, w.xmin[0], w.xmin[1], w.xmin[2], update_eos, ncount_by_id, w.nlist,
-        w.nn, w.status);
+        w.nn, w.nbr_off, w.status);
   else
     k_density<P, SDPD_KERNEL_CUBIC><<<blocks_for(c.N, 128), 128, 0, s>>>(
         c, a, qp4, w.cell_start, w.mrank, w.xmin[0], w.xmin[1], w.xmin[2], update_eos, ncount_by_id, w.nlist,
-        w.nn, w.status);
+        w.nn, w.nbr_off, w.status);
 }
 
 template <class P>

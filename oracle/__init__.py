@@ -108,6 +108,7 @@ def lib():
             "orc_neighbour_counts": (None, [P, _dp, _i32p]),
             "orc_forces": (None, [P, _dp, _dp, _dp, _dp]),
             "orc_density_at": (None, [P, _dp, _i64p, C.c_int64, _dp]),
+            "orc_neighbour_count_at": (None, [P, _dp, _i64p, C.c_int64, _i32p]),
             "orc_forces_at": (None, [P, _dp, _dp, _i64p, C.c_int64, _dp]),
             "orc_hamiltonian": (C.c_double, [P, _dp, _dp, _dp]),
             "orc_verlet": (None, [P, _dp, _dp, _dp, C.c_double]),
@@ -219,6 +220,15 @@ def density_at(P: Params, q, idx) -> np.ndarray:
     idx = np.ascontiguousarray(idx, dtype=np.int64)
     out = np.empty(len(idx))
     lib().orc_density_at(C.byref(P), _d(q), idx.ctypes.data_as(_i64p), len(idx), _d(out))
+    return out
+
+
+def neighbour_count_at(P: Params, q, idx) -> np.ndarray:
+    q = _f64(q)
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    out = np.empty(len(idx), dtype=np.int32)
+    lib().orc_neighbour_count_at(C.byref(P), _d(q), idx.ctypes.data_as(_i64p), len(idx),
+                                 out.ctypes.data_as(_i32p))
     return out
 
 

@@ -320,6 +320,23 @@ void orc_density_at(const orc_params* P, const double* q, const int64_t* idx, in
   }
 }
 
+/* Neighbour count (j != i, r_ij < h) of selected particles only. */
+void orc_neighbour_count_at(const orc_params* P, const double* q, const int64_t* idx, int64_t n, int32_t* count) {
+  const double h2 = P->h * P->h;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t k = 0; k < n; ++k) {
+    int64_t i = idx[k];
+    int32_t c = 0;
+    for (int64_t j = 0; j < P->N; ++j) {
+      if (j == i) continue;
+      double d[3];
+      displacement(P, q, i, j, d);
+      if (orc_r2(d[0], d[1], d[2]) < h2) ++c;
+    }
+    count[k] = c;
+  }
+}
+
 /* Conservative force on selected particles (Eq. cons-forces), with the
  * densities of the particle and of each of its neighbours recomputed by the
  * full sum: force[3k..3k+2] = F_{idx[k]}. */

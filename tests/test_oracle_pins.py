@@ -87,6 +87,7 @@ def test_sampled_density_and_force_equal_full_sums():
     f = O.forces(P, q, rho, eps)
     idx = np.array([0, 7, 123, 999])
     assert np.abs(O.density_at(P, q, idx) - rho[idx]).max() <= 1e-14 * rho.max()
+    assert (O.neighbour_count_at(P, q, idx) == O.neighbour_counts(P, q)[idx]).all()
     assert np.abs(O.forces_at(P, q, eps, idx) - f[idx]).max() <= 1e-12 * np.abs(f).max()
 
 

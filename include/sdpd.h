@@ -206,6 +206,36 @@ int sdpd_debug_get(sdpd_t* s, int what, void* dst, int64_t cap, int64_t* count);
 /* Free the handle (not the workspace). */
 void sdpd_destroy(sdpd_t* s);
 
+/* Density pass that allocates nothing -- the paper has no counterpart; this
+ * is a service for callers that cannot allocate device memory themselves:
+ * for example a plug-in that is handed raw device buffers by a host
+ * application which owns every allocation on the device, or a code path
+ * whose device-memory footprint has to be fixed before it runs.  Such a
+ * caller cannot create the workspace that sdpd_bind_workspace expects.
+ *
+ * Computes rho_i = sum_j m W(r_ij) over j = 1..N (self term included, Eq.
+ * sdpd-rho-v) in float64 for N particles at positions q[N][3] (device,
+ * float64, in [0, box)) into rho[N] (device, float64), with the kernel
+ * SDPD_KERNEL_CUBIC or SDPD_KERNEL_LUCY and the same neighbour rule as the
+ * rest of the library (cells of side >= h, minimum image, r^2 < h^2).
+ * Asynchronous on stream (a cudaStream_t, NULL = legacy default stream).
+ *
+ * The working memory (cell counts, cell starts, binned order: 1.25 MiB) is
+ * one static array inside the library, held by every device that loads the
+ * library until the process exits.  Limits: N <= 65536 and at most 65536
+ * cells (box[d] / h, rounded down to an even number, multiplied over the
+ * axes); larger inputs return SDPD_ERR_CAPACITY before any device work.
+ * The first call on a device looks up the device address of that array
+ * (one-time set-up, per device); make that first call before any stream
+ * capture.  Every call reuses the same array and clears what must start at
+ * zero; calls whose work overlaps on the GPU (other streams, other host
+ * threads) race on it and must be serialised by the caller.  The function
+ * calls no allocator.
+ * Errors: SDPD_ERR_INVALID_ARG, SDPD_ERR_BOX_TOO_SMALL, SDPD_ERR_CAPACITY,
+ * SDPD_ERR_CUDA. */
+int sdpd_density_static(int64_t N, const double box[3], double m, double h, int kernel, const double* q,
+                        double* rho, void* stream);
+
 /* Static text for a status code. */
 const char* sdpd_strerror(int status);
 

@@ -66,6 +66,8 @@ SIGNATURES = [
     ("sdpd_stage_times", C.c_int, [_H, _dp, C.POINTER(C.c_int64), C.c_int]),
     ("sdpd_debug_get", C.c_int, [_H, C.c_int, C.c_void_p, C.c_int64, C.POINTER(C.c_int64)]),
     ("sdpd_destroy", None, [_H]),
+    ("sdpd_density_static", C.c_int, [C.c_int64, _dp, C.c_double, C.c_double, C.c_int, C.c_void_p,
+                                      C.c_void_p, C.c_void_p]),
     ("sdpd_strerror", C.c_char_p, [C.c_int]),
 ]
 
@@ -179,6 +181,12 @@ def sdpd_debug_get(h, what, dst_ptr, cap):
     cnt = C.c_int64(0)
     st = load().sdpd_debug_get(h, int(what), C.c_void_p(dst_ptr), int(cap), C.byref(cnt))
     return st, cnt.value
+
+
+def sdpd_density_static(N, box, m, h, kernel, q_ptr: int, rho_ptr: int, stream: int = 0) -> int:
+    b = (C.c_double * 3)(*[float(x) for x in box])
+    return load().sdpd_density_static(int(N), b, float(m), float(h), int(kernel), C.c_void_p(q_ptr),
+                                      C.c_void_p(rho_ptr), C.c_void_p(stream))
 
 
 def sdpd_destroy(h):

@@ -405,7 +405,13 @@ __device__ __forceinline__ float expm1(float x) {
   return __expf(x) - 1.0f;
 }
 __device__ __forceinline__ double log1p(double x) { return ::log1p(x); }
-__device__ __forceinline__ float log1p(float x) { return log1pf(x); }
+// log(1 + x): alternating series for |x| < 1/16 (relative error < 2e-8),
+// the hardware logarithm of 1 + x above
+__device__ __forceinline__ float log1p(float x) {
+  if (fabsf(x) < 0.0625f)
+    return x * (1.0f - x * (0.5f - x * (1.0f / 3.0f - x * (0.25f - x * (0.2f - x * (1.0f / 6.0f))))));
+  return __logf(1.0f + x);
+}
 }  // namespace fm
 
 // Box-Muller normals and the uniform of one pair at one sweep (see
@@ -580,6 +586,7 @@ struct FdSmem {
   R G0[kChunk], G1[kChunk], G2[kChunk], U[kChunk];
   R ex[kChunk], ey[kChunk], ez[kChunk], base[kChunk];
   uint16_t pr[kChunk];
+  uint16_t off[kMaxLevels + 1];  // level offsets of the block's pair list
 };
 
 template <class P>
@@ -629,8 +636,9 @@ __global__ void __launch_bounds__(fd_warps<P>() * 32, P::mixed ? 8 : 4)
     sm.e[q] = (R)a.eps[g];
     sm.acc[q] = R(0);
   }
+  for (int L = gl; L <= nlev; L += kGroupLanes) sm.off[L] = lvl[o * (kMaxLevels + 1) + L];
   __syncwarp();
-  const uint16_t* off = lvl + o * (kMaxLevels + 1);
+  const uint16_t* off = sm.off;
   const uint16_t* pl = pairs + o * kMaxPairs;
   const R inv_h = k.inv_h, cF = k.cF;
   unsigned long long n_acc = 0, n_rb = 0, n_rm = 0, n_tot = 0;

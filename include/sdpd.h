@@ -160,7 +160,7 @@ int64_t sdpd_get_fd_step(const sdpd_t* s);
 int sdpd_reset_counters(sdpd_t* s);
 
 /* Number of CUDA kernels the handle has launched so far (a VV step launches
- * 8, a sweep 11, sdpd_set_state 7, sdpd_observables 2). */
+ * 8, a sweep 12, sdpd_set_state 8, sdpd_observables 2). */
 int64_t sdpd_kernel_launches(const sdpd_t* s);
 
 /* Per-stage timing with CUDA events recorded on the handle's stream around
@@ -205,6 +205,28 @@ int sdpd_debug_get(sdpd_t* s, int what, void* dst, int64_t cap, int64_t* count);
 
 /* Free the handle (not the workspace). */
 void sdpd_destroy(sdpd_t* s);
+
+/* Ensembles: many independent systems of uneven size and parameters stepped
+ * together (the paper treats one system; independent replicas are how the
+ * method is sampled in practice).  Each member is an ordinary handle with a
+ * bound workspace and a loaded state, on a stream of its own (distinct from
+ * the ensemble's stream), with theta = 1, stage timing off and debug off;
+ * the ensemble's stream must not be the legacy default stream (NULL).
+ * sdpd_ensemble_step advances every member by nsteps steps with its own seed
+ * (seeds[i] for member i).  Two steps of all members are captured once into
+ * one CUDA graph (forked from and joined into the ensemble stream; the
+ * capture is redone when dt or the seeds change) and the graph is replayed
+ * nsteps/2 times; an odd last step is enqueued directly.  Every member's
+ * result is the same as stepping it alone.  The members' own streams wait
+ * for the ensemble's work before later calls on them run.  Asynchronous.
+ * Errors: SDPD_ERR_INVALID_ARG (bad member, shared stream, theta != 1,
+ * timing or debug on), SDPD_ERR_NO_WORKSPACE, SDPD_ERR_CUDA. */
+typedef struct sdpd_ensemble sdpd_ens_t;
+int sdpd_ensemble_create(sdpd_t* const* members, int n, void* stream, sdpd_ens_t** out);
+int sdpd_ensemble_step(sdpd_ens_t* e, double dt, int64_t nsteps, const uint64_t* seeds);
+/* Kernel launches of the captured two-step graph (all members). */
+int64_t sdpd_ensemble_kernel_nodes(const sdpd_ens_t* e);
+void sdpd_ensemble_destroy(sdpd_ens_t* e);
 
 /* Density pass that allocates nothing -- the paper has no counterpart; this
  * is a service for callers that cannot allocate device memory themselves:

@@ -176,6 +176,7 @@ size_t layout(sdpd_handle* s, Workspace* w, char* base) {
   w->obs_partial = (double*)at(kObsBlocks * 8 * 8);
   w->obs = (double*)at(16 * 8);
   w->counters = (unsigned long long*)at(4 * 8);
+  w->sweep = (unsigned long long*)at(8);
   w->status = (int*)at(8);
   w->pair_rec_count = (unsigned long long*)at(8);
   w->pair_rec_cap = s->pair_rec_cap;
@@ -296,9 +297,10 @@ void do_steps(sdpd_handle* s, double dt, int64_t nsteps, uint64_t seed) {
       }
       {
         StageTimer t(s, 5, 8);
-        launch_fd_colours<P>(c, s->w, s->cur, dt_fd, seed, (uint64_t)s->fd_step, rec, s->stream);
+        launch_fd_colours<P>(c, s->w, s->cur, dt_fd, seed, rec, s->stream);
       }
-      s->launches += 11;
+      launch_advance_sweep(s->w, s->stream);
+      s->launches += 12;
       s->fd_step++;
     }
   }
@@ -492,6 +494,8 @@ int sdpd_set_state(sdpd_t* s, const double* q, const double* p, const double* ep
   if (e) return SDPD_ERR_CUDA;
   if (s->prm.precision == SDPD_MIXED) do_load<Mixed>(s);
   else do_load<Fp64>(s);
+  launch_set_sweep(s->w, 0ull, st);
+  s->launches += 1;
   if (!on_device && N > 0) {
     // host buffers may be reused by the caller as soon as we return
     if (cudaStreamSynchronize(st) != cudaSuccess) return SDPD_ERR_CUDA;
@@ -581,6 +585,12 @@ int sdpd_observables(sdpd_t* s, sdpd_obs* out) {
 int sdpd_set_fd_step(sdpd_t* s, int64_t v) {
   if (!s || v < 0) return SDPD_ERR_INVALID_ARG;
   s->fd_step = v;
+  if (s->ws) {
+    if (use_device(s) != SDPD_OK) return SDPD_ERR_CUDA;
+    launch_set_sweep(s->w, (unsigned long long)v, s->stream);
+    s->launches += 1;
+    return launch_status();
+  }
   return SDPD_OK;
 }
 
@@ -718,6 +728,148 @@ int sdpd_debug_get(sdpd_t* s, int what, void* dst, int64_t cap, int64_t* count) 
     default:
       return SDPD_ERR_INVALID_ARG;
   }
+}
+
+// ---------------------------------------------------------------------------
+// Ensembles of independent systems stepped by one CUDA graph.
+// ---------------------------------------------------------------------------
+struct sdpd_ensemble {
+  std::vector<sdpd_handle*> m;
+  cudaStream_t stream;
+  cudaEvent_t fork;
+  std::vector<cudaEvent_t> join;
+  cudaGraph_t graph;
+  cudaGraphExec_t exec;
+  double dt;
+  std::vector<uint64_t> seeds;
+  int64_t launches_per_unit;
+};
+
+namespace {
+
+void member_steps(sdpd_handle* h, double dt, int64_t n, uint64_t seed) {
+  if (h->prm.precision == SDPD_MIXED) do_steps<Mixed>(h, dt, n, seed);
+  else do_steps<Fp64>(h, dt, n, seed);
+}
+
+// Enqueue nsteps steps of every member on its own stream, forked from and
+// joined back into the ensemble stream.
+void ensemble_enqueue(sdpd_ensemble* e, double dt, int64_t nsteps, const uint64_t* seeds) {
+  cudaEventRecord(e->fork, e->stream);
+  for (size_t i = 0; i < e->m.size(); ++i) {
+    sdpd_handle* h = e->m[i];
+    cudaStreamWaitEvent(h->stream, e->fork, 0);
+    member_steps(h, dt, nsteps, seeds[i]);
+    cudaEventRecord(e->join[i], h->stream);
+    cudaStreamWaitEvent(e->stream, e->join[i], 0);
+  }
+}
+
+// Make `to` wait for the work already enqueued on `from`.
+int order_streams(cudaStream_t from, cudaStream_t to) {
+  cudaEvent_t ev;
+  if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return SDPD_ERR_CUDA;
+  int st = cuda_ok(cudaEventRecord(ev, from));
+  st |= cuda_ok(cudaStreamWaitEvent(to, ev, 0));
+  cudaEventDestroy(ev);
+  return st ? SDPD_ERR_CUDA : SDPD_OK;
+}
+
+}  // namespace
+
+int sdpd_ensemble_create(sdpd_t* const* members, int n, void* stream, sdpd_ens_t** out) {
+  if (!out) return SDPD_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!members || n < 1 || !stream) return SDPD_ERR_INVALID_ARG;  // the legacy default stream cannot be captured
+  sdpd_ensemble* e = new (std::nothrow) sdpd_ensemble();
+  if (!e) return SDPD_ERR_INVALID_ARG;
+  e->stream = (cudaStream_t)stream;
+  e->graph = nullptr;
+  e->exec = nullptr;
+  e->dt = 0.0;
+  for (int i = 0; i < n; ++i) {
+    sdpd_handle* h = members[i];
+    if (!h || !h->ws || !h->has_state || h->prm.theta != 1 || h->timing || h->w.pair_recs ||
+        h->stream == e->stream) {
+      delete e;
+      return !h || h->ws ? SDPD_ERR_INVALID_ARG : SDPD_ERR_NO_WORKSPACE;
+    }
+    for (int j = 0; j < i; ++j)
+      if (members[j] == h || members[j]->stream == h->stream) { delete e; return SDPD_ERR_INVALID_ARG; }
+    e->m.push_back(h);
+  }
+  if (use_device(e->m[0]) != SDPD_OK || cudaEventCreateWithFlags(&e->fork, cudaEventDisableTiming) != cudaSuccess) {
+    delete e;
+    return SDPD_ERR_CUDA;
+  }
+  e->join.resize((size_t)n);
+  for (int i = 0; i < n; ++i) cudaEventCreateWithFlags(&e->join[(size_t)i], cudaEventDisableTiming);
+  *out = e;
+  return SDPD_OK;
+}
+
+int sdpd_ensemble_step(sdpd_ens_t* e, double dt, int64_t nsteps, const uint64_t* seeds) {
+  if (!e || !seeds || !(dt > 0) || !isfinite(dt) || nsteps < 0) return SDPD_ERR_INVALID_ARG;
+  if (use_device(e->m[0]) != SDPD_OK) return SDPD_ERR_CUDA;
+  // the ensemble stream waits for everything already enqueued on the members
+  for (sdpd_handle* h : e->m)
+    if (order_streams(h->stream, e->stream) != SDPD_OK) return SDPD_ERR_CUDA;
+  const int64_t units = nsteps / 2;
+  const std::vector<uint64_t> sv(seeds, seeds + e->m.size());
+  if (units > 0) {
+    if (!e->exec || e->dt != dt || e->seeds != sv) {
+      if (e->exec) { cudaGraphExecDestroy(e->exec); e->exec = nullptr; }
+      if (e->graph) { cudaGraphDestroy(e->graph); e->graph = nullptr; }
+      // capture two steps: each step's sort flips the double-buffered
+      // state, so after two steps every member is back in its buffer and
+      // the graph can be replayed; host bookkeeping is restored after capture
+      std::vector<int> cur0;
+      std::vector<int64_t> fd0, vv0, l0;
+      for (sdpd_handle* h : e->m) {
+        cur0.push_back(h->cur); fd0.push_back(h->fd_step); vv0.push_back(h->vv_step); l0.push_back(h->launches);
+      }
+      if (cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return SDPD_ERR_CUDA;
+      ensemble_enqueue(e, dt, 2, seeds);
+      cudaError_t ce = cudaStreamEndCapture(e->stream, &e->graph);
+      e->launches_per_unit = 0;
+      for (size_t i = 0; i < e->m.size(); ++i) {
+        sdpd_handle* h = e->m[i];
+        e->launches_per_unit += h->launches - l0[i];
+        h->cur = cur0[i]; h->fd_step = fd0[i]; h->vv_step = vv0[i]; h->launches = l0[i];
+      }
+      if (ce != cudaSuccess || cudaGraphInstantiate(&e->exec, e->graph, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return SDPD_ERR_CUDA;
+      }
+      e->dt = dt;
+      e->seeds = sv;
+    }
+    for (int64_t u = 0; u < units; ++u)
+      if (cudaGraphLaunch(e->exec, e->stream) != cudaSuccess) return SDPD_ERR_CUDA;
+    for (sdpd_handle* h : e->m) {
+      if (!h->prm.fd_only) h->vv_step += 2 * units;
+      if (h->prm.scheme != SDPD_SCHEME_NONE) h->fd_step += 2 * units;
+    }
+    const int64_t per_member = e->launches_per_unit / (int64_t)e->m.size();
+    for (sdpd_handle* h : e->m) h->launches += per_member * units;
+  }
+  if (nsteps % 2) ensemble_enqueue(e, dt, 1, seeds);
+  // later calls on a member's own stream see the ensemble's work
+  for (sdpd_handle* h : e->m)
+    if (order_streams(e->stream, h->stream) != SDPD_OK) return SDPD_ERR_CUDA;
+  return launch_status();
+}
+
+int64_t sdpd_ensemble_kernel_nodes(const sdpd_ens_t* e) { return e ? e->launches_per_unit : -1; }
+
+void sdpd_ensemble_destroy(sdpd_ens_t* e) {
+  if (!e) return;
+  cudaStreamSynchronize(e->stream);
+  if (e->exec) cudaGraphExecDestroy(e->exec);
+  if (e->graph) cudaGraphDestroy(e->graph);
+  cudaEventDestroy(e->fork);
+  for (cudaEvent_t ev : e->join) cudaEventDestroy(ev);
+  delete e;
 }
 
 void sdpd_destroy(sdpd_t* s) {

@@ -599,11 +599,12 @@ __global__ void __launch_bounds__(fd_warps<P>() * 32, P::mixed ? 8 : 4)
                 const uint32_t* __restrict__ xmx, const uint32_t* __restrict__ xmy,
                 const uint32_t* __restrict__ xmz, const uint32_t* __restrict__ hdr,
                 const uint16_t* __restrict__ lvl, const uint16_t* __restrict__ pairs, int colour, uint64_t seed,
-                uint64_t sweep, unsigned long long* counters, int* status, sdpd_pair_rec* recs,
-                unsigned long long* rec_count, int64_t rec_cap) {
+                const unsigned long long* __restrict__ sweep_ptr, unsigned long long* counters, int* status,
+                sdpd_pair_rec* recs, unsigned long long* rec_count, int64_t rec_cap) {
   using R = typename P::R;
   constexpr int W = fd_warps<P>();
   __shared__ FdSmem<R> sm_all[W][kOwnersPerWarp];
+  const uint64_t sweep = *sweep_ptr;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int grp = lane / kGroupLanes, gl = lane % kGroupLanes;
   const int hx = c.nc[0] >> 1, hy = c.nc[1] >> 1, hz = c.nc[2] >> 1;
@@ -802,9 +803,17 @@ void launch_fd_schedule(const Consts& c, const Workspace& w, int cur, cudaStream
       c.ncell, w.sched_hdr, canon, w.level_of, w.sched_lvl, w.sched_pair);
 }
 
+__global__ void k_sweep_set(unsigned long long* sweep, unsigned long long v) { *sweep = v; }
+__global__ void k_sweep_advance(unsigned long long* sweep) { *sweep += 1ull; }
+
+void launch_set_sweep(const Workspace& w, unsigned long long value, cudaStream_t s) {
+  k_sweep_set<<<1, 1, 0, s>>>(w.sweep, value);
+}
+void launch_advance_sweep(const Workspace& w, cudaStream_t s) { k_sweep_advance<<<1, 1, 0, s>>>(w.sweep); }
+
 template <class P>
-void launch_fd_colours(const Consts& c, const Workspace& w, int cur, double dt, uint64_t seed, uint64_t sweep,
-                       int record, cudaStream_t s) {
+void launch_fd_colours(const Consts& c, const Workspace& w, int cur, double dt, uint64_t seed, int record,
+                       cudaStream_t s) {
   if (c.N == 0) return;
   using R = typename P::R;
   Arrays<P> a = view<P>(w, cur);
@@ -819,19 +828,17 @@ void launch_fd_colours(const Consts& c, const Workspace& w, int cur, double dt, 
     if (c.kernel == SDPD_KERNEL_LUCY)
       k_fd_colour<P, SDPD_KERNEL_LUCY><<<gf, W * 32, 0, s>>>(
           c, k, a, qp4, w.cell_start, w.mrank, w.xmin[0], w.xmin[1], w.xmin[2], w.sched_hdr, w.sched_lvl,
-          w.sched_pair, col, seed, sweep, w.counters, w.status, recs, w.pair_rec_count, w.pair_rec_cap);
+          w.sched_pair, col, seed, w.sweep, w.counters, w.status, recs, w.pair_rec_count, w.pair_rec_cap);
     else
       k_fd_colour<P, SDPD_KERNEL_CUBIC><<<gf, W * 32, 0, s>>>(
           c, k, a, qp4, w.cell_start, w.mrank, w.xmin[0], w.xmin[1], w.xmin[2], w.sched_hdr, w.sched_lvl,
-          w.sched_pair, col, seed, sweep, w.counters, w.status, recs, w.pair_rec_count, w.pair_rec_cap);
+          w.sched_pair, col, seed, w.sweep, w.counters, w.status, recs, w.pair_rec_count, w.pair_rec_cap);
   }
 }
 
 template void launch_fd_schedule<Fp64>(const Consts&, const Workspace&, int, cudaStream_t);
 template void launch_fd_schedule<Mixed>(const Consts&, const Workspace&, int, cudaStream_t);
-template void launch_fd_colours<Fp64>(const Consts&, const Workspace&, int, double, uint64_t, uint64_t, int,
-                                      cudaStream_t);
-template void launch_fd_colours<Mixed>(const Consts&, const Workspace&, int, double, uint64_t, uint64_t, int,
-                                       cudaStream_t);
+template void launch_fd_colours<Fp64>(const Consts&, const Workspace&, int, double, uint64_t, int, cudaStream_t);
+template void launch_fd_colours<Mixed>(const Consts&, const Workspace&, int, double, uint64_t, int, cudaStream_t);
 
 }  // namespace sdpd

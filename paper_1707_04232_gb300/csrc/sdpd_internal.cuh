@@ -261,6 +261,7 @@ struct Workspace {
   double* obs_partial;        // [kObsBlocks][8]
   double* obs;                // [8]
   unsigned long long* counters;  // [4]: pairs, accept, reject bound, reject metropolis
+  unsigned long long* sweep;     // sweep counter: the random-number step of the next sweep
   int* status;
   sdpd_pair_rec* pair_recs;   // debug
   unsigned long long* pair_rec_count;
@@ -303,9 +304,12 @@ void launch_force(const Consts& c, const Workspace& w, int cur, double half_dt, 
 template <class P>
 void launch_fd_schedule(const Consts& c, const Workspace& w, int cur, cudaStream_t s);
 template <class P>
-void launch_fd_colours(const Consts& c, const Workspace& w, int cur, double dt, uint64_t seed, uint64_t sweep,
-                       int record, cudaStream_t s);
+void launch_fd_colours(const Consts& c, const Workspace& w, int cur, double dt, uint64_t seed, int record,
+                       cudaStream_t s);
 template <class P>
 void launch_observables(const Consts& c, const Workspace& w, int cur, cudaStream_t s);
+// sweep counter on the device: set to a value, or advanced by one
+void launch_set_sweep(const Workspace& w, unsigned long long value, cudaStream_t s);
+void launch_advance_sweep(const Workspace& w, cudaStream_t s);
 
 }  // namespace sdpd

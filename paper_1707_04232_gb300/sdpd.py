@@ -66,6 +66,10 @@ SIGNATURES = [
     ("sdpd_stage_times", C.c_int, [_H, _dp, C.POINTER(C.c_int64), C.c_int]),
     ("sdpd_debug_get", C.c_int, [_H, C.c_int, C.c_void_p, C.c_int64, C.POINTER(C.c_int64)]),
     ("sdpd_destroy", None, [_H]),
+    ("sdpd_ensemble_create", C.c_int, [C.POINTER(_H), C.c_int, C.c_void_p, C.POINTER(_H)]),
+    ("sdpd_ensemble_step", C.c_int, [_H, C.c_double, C.c_int64, C.POINTER(C.c_uint64)]),
+    ("sdpd_ensemble_kernel_nodes", C.c_int64, [_H]),
+    ("sdpd_ensemble_destroy", None, [_H]),
     ("sdpd_density_static", C.c_int, [C.c_int64, _dp, C.c_double, C.c_double, C.c_int, C.c_void_p,
                                       C.c_void_p, C.c_void_p]),
     ("sdpd_strerror", C.c_char_p, [C.c_int]),
@@ -187,6 +191,26 @@ def sdpd_density_static(N, box, m, h, kernel, q_ptr: int, rho_ptr: int, stream: 
     b = (C.c_double * 3)(*[float(x) for x in box])
     return load().sdpd_density_static(int(N), b, float(m), float(h), int(kernel), C.c_void_p(q_ptr),
                                       C.c_void_p(rho_ptr), C.c_void_p(stream))
+
+
+def sdpd_ensemble_create(handles, stream: int):
+    arr = (_H * len(handles))(*handles)
+    out = _H()
+    st = load().sdpd_ensemble_create(arr, len(handles), C.c_void_p(stream), C.byref(out))
+    return st, out
+
+
+def sdpd_ensemble_step(e, dt, nsteps, seeds) -> int:
+    sv = (C.c_uint64 * len(seeds))(*[int(x) for x in seeds])
+    return load().sdpd_ensemble_step(e, float(dt), int(nsteps), sv)
+
+
+def sdpd_ensemble_kernel_nodes(e) -> int:
+    return load().sdpd_ensemble_kernel_nodes(e)
+
+
+def sdpd_ensemble_destroy(e):
+    load().sdpd_ensemble_destroy(e)
 
 
 def sdpd_destroy(h):
@@ -339,3 +363,33 @@ class SDPD:
         out = np.empty(cap, dtype=PAIR_REC_DTYPE)
         n = self._debug(DEBUG_PAIRS, out, cap)
         return out[:n].copy()
+
+
+class SDPDEnsemble:
+    """Independent systems stepped together by one CUDA graph.
+
+    ``members`` are SDPD objects with loaded states, each created with its
+    own stream; the ensemble launches on ``stream`` (default: a new stream)
+    and keeps the members alive."""
+
+    def __init__(self, members, stream=None):
+        import torch
+
+        self.members = list(members)
+        # a stream of its own: the legacy default stream cannot be captured
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        st, self.e = sdpd_ensemble_create([m.h for m in self.members], self.stream.cuda_stream)
+        _check(st, "sdpd_ensemble_create")
+
+    def __del__(self):
+        e = getattr(self, "e", None)
+        if e:
+            sdpd_ensemble_destroy(e)
+            self.e = None
+
+    def step(self, dt, nsteps, seeds):
+        _check(sdpd_ensemble_step(self.e, dt, nsteps, seeds), "sdpd_ensemble_step")
+
+    @property
+    def kernel_nodes(self) -> int:
+        return sdpd_ensemble_kernel_nodes(self.e)

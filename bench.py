@@ -55,6 +55,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-n", type=int, default=32, help="lattice sites per axis of the CPU sample")
+    ap.add_argument("--workload", default="fluid", choices=["fluid", "ensemble"],
+                    help="fluid: the single large fluid; ensemble: 256 independent replicas")
+    ap.add_argument("--replicas", type=int, default=256)
     return ap.parse_args()
 
 
@@ -284,6 +287,103 @@ def run_ours(args, rank, world, local_rank):
         print(json.dumps(line))
 
 
+def ensemble_members(args, rank):
+    """The batched-ensemble workload: replica sizes log-uniform in
+    [2048, 65536] rounded to cubes n^3, K uniform in {5, 20, 100}, kT uniform
+    in [0.1, 1.0].  A size whose 2x2x2 cell blocks would hold more than ~200
+    particles on average (L/h just below an even number) moves up to the next
+    size that fits the block capacity."""
+    rng = np.random.default_rng(1000 + rank)
+    out = []
+    for r in range(args.replicas):
+        N = float(np.exp(rng.uniform(np.log(2048.0), np.log(65536.0))))
+        n = int(round(N ** (1.0 / 3.0)))
+        n = min(max(n, 13), 40)
+        while True:
+            nc = int(np.floor(n / 2.5))
+            nc -= nc % 2
+            if (2.0 * n / nc) ** 3 <= 200.0:
+                break
+            n += 1
+        K = float(rng.choice([5.0, 20.0, 100.0]))
+        kT = float(rng.uniform(0.1, 1.0))
+        out.append(Workload(n=n, K=K, kT=kT, seed=1000 * rank + r))
+    return out
+
+
+def run_ensemble(args, rank, world, local_rank):
+    import torch
+    from paper_1707_04232_gb300 import sdpd
+
+    torch.cuda.set_device(local_rank)
+    dev_index = torch.cuda.current_device()
+    ws = ensemble_members(args, rank)
+    prec = sdpd.MIXED if args.precision == "mixed" else sdpd.FP64
+    scheme = {"ssa": sdpd.SCHEME_SSA, "ams": sdpd.SCHEME_AMS, "ems": sdpd.SCHEME_EMS, "none": sdpd.SCHEME_NONE}[args.scheme]
+    members = []
+    for w in ws:
+        q, p, e = lattice_state(w)
+        m = sdpd.SDPD(w.N, w.L, m=w.m, h=w.h, K=w.K, precision=prec, scheme=scheme, stream=torch.cuda.Stream())
+        m.set_state(q, p, e)
+        members.append(m)
+    ens = sdpd.SDPDEnsemble(members)
+    seeds = [7 + k for k in range(len(members))]
+    ntot = sum(w.N for w in ws)
+    ens.step(args.dt, 2 * max(2, args.warmup), seeds)  # capture + warm-up
+    torch.cuda.synchronize()
+    launches0 = sum(m.kernel_launches for m in members)
+    clocks = ClockSampler(dev_index)
+    clocks.start()
+    barrier(world)
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    start.record(ens.stream)
+    ens.step(args.dt, args.steps, seeds)
+    end.record(ens.stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    ms = start.elapsed_time(end)
+    launches = sum(m.kernel_launches for m in members) - launches0
+    # the same members stepped one after the other on one stream, no graph
+    seq_steps = 2
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for m in members:
+        m.step(args.dt, seq_steps, seed=3)
+    torch.cuda.synchronize()
+    seq_ps = ntot * seq_steps / (time.perf_counter() - t0)
+    # temperatures against the equilibrium value fixed by the energy
+    terr = []
+    for w, m in zip(ws, members):
+        o = m.observables()
+        C_K = 1.5 * (w.K - 1.0)
+        T_eq = o["E"] / (1.5 * (w.N - 1) + w.N * C_K)
+        terr.append(abs(o["T_int"] - T_eq) / T_eq)
+    ms_max = allreduce_max(ms, world)
+    value = ntot * world * args.steps / (ms_max * 1e-3)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "mixed" else "f64",
+        "data": "synthetic",
+        "config": {"workload": "batched ensemble: %d replicas, N log-uniform in [2048, 65536] (cubes), "
+                               "K in {5,20,100}, kT in [0.1,1], dt=%g, %s, %s" % (len(ws), args.dt,
+                                                                                 args.scheme.upper(), args.precision),
+                   "particles": ntot, "replicas": len(ws),
+                   "sizes": sorted({w.n for w in ws}),
+                   "graph_kernel_nodes_per_2_steps": ens.kernel_nodes,
+                   "l2": "inputs larger than L2"},
+        "unbatched_sequential": {"value": seq_ps, "unit": UNIT, "steps": seq_steps,
+                                 "note": "same replicas stepped one after the other on one stream"},
+        "temperature_error": {"max": max(terr), "mean": float(np.mean(terr)),
+                              "definition": "|<T_int> - T_eq| / T_eq, T_eq = E / (3(N-1)/2 + N C_K)"},
+        "gpu_launches": launches, "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+
+
 def run_e2e(args, s, q, p, e, stream, world, N):
     """Each e2e step: host->device copy of the state from pinned memory
     (sdpd_set_state), one time step, device->host copy of the new state
@@ -351,7 +451,10 @@ def main():
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
         _dist = dist
-    run_ours(args, rank, world, local_rank)
+    if args.workload == "ensemble":
+        run_ensemble(args, rank, world, local_rank)
+    else:
+        run_ours(args, rank, world, local_rank)
     if world > 1:
         _dist.destroy_process_group()
 

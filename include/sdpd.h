@@ -209,23 +209,28 @@ void sdpd_destroy(sdpd_t* s);
 /* Ensembles: many independent systems of uneven size and parameters stepped
  * together (the paper treats one system; independent replicas are how the
  * method is sampled in practice).  Each member is an ordinary handle with a
- * bound workspace and a loaded state, on a stream of its own (distinct from
- * the ensemble's stream), with theta = 1, stage timing off and debug off;
- * the ensemble's stream must not be the legacy default stream (NULL).
- * sdpd_ensemble_step advances every member by nsteps steps with its own seed
- * (seeds[i] for member i).  Two steps of all members are captured once into
- * one CUDA graph (forked from and joined into the ensemble stream; the
- * capture is redone when dt or the seeds change) and the graph is replayed
- * nsteps/2 times; an odd last step is enqueued directly.  Every member's
- * result is the same as stepping it alone.  The members' own streams wait
- * for the ensemble's work before later calls on them run.  Asynchronous.
- * Errors: SDPD_ERR_INVALID_ARG (bad member, shared stream, theta != 1,
- * timing or debug on), SDPD_ERR_NO_WORKSPACE, SDPD_ERR_CUDA. */
+ * bound workspace and a loaded state, with theta = 1, stage timing off and
+ * debug off.  Members may share streams (they then run one after the other)
+ * but not the ensemble's stream.  stream: the stream the ensemble launches
+ * on; NULL makes the ensemble create a non-blocking stream of its own
+ * (sdpd_ensemble_stream returns it).  sdpd_ensemble_step advances every
+ * member by nsteps steps with its own seed (seeds[i] for member i).  Two
+ * steps of all members are captured once into one CUDA graph (forked from and
+ * joined into the ensemble stream; the capture is redone when dt or the seeds
+ * change) and the graph is replayed nsteps/2 times; an odd last step is
+ * enqueued directly.  Every member's result is the same as stepping it
+ * alone.  The members' own streams wait for the ensemble's work before later
+ * calls on them run.  Asynchronous.
+ * Errors: SDPD_ERR_INVALID_ARG (bad or repeated member, a member on the
+ * ensemble's stream, theta != 1, timing or debug on), SDPD_ERR_NO_WORKSPACE,
+ * SDPD_ERR_CUDA. */
 typedef struct sdpd_ensemble sdpd_ens_t;
 int sdpd_ensemble_create(sdpd_t* const* members, int n, void* stream, sdpd_ens_t** out);
 int sdpd_ensemble_step(sdpd_ens_t* e, double dt, int64_t nsteps, const uint64_t* seeds);
 /* Kernel launches of the captured two-step graph (all members). */
 int64_t sdpd_ensemble_kernel_nodes(const sdpd_ens_t* e);
+/* The ensemble's stream (a cudaStream_t). */
+void* sdpd_ensemble_stream(const sdpd_ens_t* e);
 void sdpd_ensemble_destroy(sdpd_ens_t* e);
 
 /* Density pass that allocates nothing -- the paper has no counterpart; this

@@ -740,6 +740,7 @@ struct sdpd_ensemble {
   std::vector<cudaEvent_t> join;
   cudaGraph_t graph;
   cudaGraphExec_t exec;
+  bool own_stream;
   double dt;
   std::vector<uint64_t> seeds;
   int64_t launches_per_unit;
@@ -780,10 +781,11 @@ int order_streams(cudaStream_t from, cudaStream_t to) {
 int sdpd_ensemble_create(sdpd_t* const* members, int n, void* stream, sdpd_ens_t** out) {
   if (!out) return SDPD_ERR_INVALID_ARG;
   *out = nullptr;
-  if (!members || n < 1 || !stream) return SDPD_ERR_INVALID_ARG;  // the legacy default stream cannot be captured
+  if (!members || n < 1) return SDPD_ERR_INVALID_ARG;
   sdpd_ensemble* e = new (std::nothrow) sdpd_ensemble();
   if (!e) return SDPD_ERR_INVALID_ARG;
   e->stream = (cudaStream_t)stream;
+  e->own_stream = false;
   e->graph = nullptr;
   e->exec = nullptr;
   e->dt = 0.0;
@@ -795,12 +797,20 @@ int sdpd_ensemble_create(sdpd_t* const* members, int n, void* stream, sdpd_ens_t
       return !h || h->ws ? SDPD_ERR_INVALID_ARG : SDPD_ERR_NO_WORKSPACE;
     }
     for (int j = 0; j < i; ++j)
-      if (members[j] == h || members[j]->stream == h->stream) { delete e; return SDPD_ERR_INVALID_ARG; }
+      if (members[j] == h) { delete e; return SDPD_ERR_INVALID_ARG; }
     e->m.push_back(h);
   }
   if (use_device(e->m[0]) != SDPD_OK || cudaEventCreateWithFlags(&e->fork, cudaEventDisableTiming) != cudaSuccess) {
     delete e;
     return SDPD_ERR_CUDA;
+  }
+  if (!e->stream) {  // a stream of the ensemble's own (the legacy default stream cannot be captured)
+    if (cudaStreamCreateWithFlags(&e->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaEventDestroy(e->fork);
+      delete e;
+      return SDPD_ERR_CUDA;
+    }
+    e->own_stream = true;
   }
   e->join.resize((size_t)n);
   for (int i = 0; i < n; ++i) cudaEventCreateWithFlags(&e->join[(size_t)i], cudaEventDisableTiming);
@@ -862,6 +872,8 @@ int sdpd_ensemble_step(sdpd_ens_t* e, double dt, int64_t nsteps, const uint64_t*
 
 int64_t sdpd_ensemble_kernel_nodes(const sdpd_ens_t* e) { return e ? e->launches_per_unit : -1; }
 
+void* sdpd_ensemble_stream(const sdpd_ens_t* e) { return e ? (void*)e->stream : nullptr; }
+
 void sdpd_ensemble_destroy(sdpd_ens_t* e) {
   if (!e) return;
   cudaStreamSynchronize(e->stream);
@@ -869,6 +881,7 @@ void sdpd_ensemble_destroy(sdpd_ens_t* e) {
   if (e->graph) cudaGraphDestroy(e->graph);
   cudaEventDestroy(e->fork);
   for (cudaEvent_t ev : e->join) cudaEventDestroy(ev);
+  if (e->own_stream) cudaStreamDestroy(e->stream);
   delete e;
 }
 

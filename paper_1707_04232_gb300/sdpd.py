@@ -69,6 +69,7 @@ SIGNATURES = [
     ("sdpd_ensemble_create", C.c_int, [C.POINTER(_H), C.c_int, C.c_void_p, C.POINTER(_H)]),
     ("sdpd_ensemble_step", C.c_int, [_H, C.c_double, C.c_int64, C.POINTER(C.c_uint64)]),
     ("sdpd_ensemble_kernel_nodes", C.c_int64, [_H]),
+    ("sdpd_ensemble_stream", C.c_void_p, [_H]),
     ("sdpd_ensemble_destroy", None, [_H]),
     ("sdpd_density_static", C.c_int, [C.c_int64, _dp, C.c_double, C.c_double, C.c_int, C.c_void_p,
                                       C.c_void_p, C.c_void_p]),
@@ -207,6 +208,10 @@ def sdpd_ensemble_step(e, dt, nsteps, seeds) -> int:
 
 def sdpd_ensemble_kernel_nodes(e) -> int:
     return load().sdpd_ensemble_kernel_nodes(e)
+
+
+def sdpd_ensemble_stream(e) -> int:
+    return load().sdpd_ensemble_stream(e) or 0
 
 
 def sdpd_ensemble_destroy(e):
@@ -368,18 +373,20 @@ class SDPD:
 class SDPDEnsemble:
     """Independent systems stepped together by one CUDA graph.
 
-    ``members`` are SDPD objects with loaded states, each created with its
-    own stream; the ensemble launches on ``stream`` (default: a new stream)
+    ``members`` are SDPD objects with loaded states, created on streams
+    other than the ensemble's; the ensemble launches on ``stream`` (default:
+    a stream the library creates for it, exposed as a torch ExternalStream)
     and keeps the members alive."""
 
     def __init__(self, members, stream=None):
         import torch
 
         self.members = list(members)
-        # a stream of its own: the legacy default stream cannot be captured
-        self.stream = stream if stream is not None else torch.cuda.Stream()
-        st, self.e = sdpd_ensemble_create([m.h for m in self.members], self.stream.cuda_stream)
+        st, self.e = sdpd_ensemble_create([m.h for m in self.members],
+                                          stream.cuda_stream if stream is not None else 0)
         _check(st, "sdpd_ensemble_create")
+        self.stream = stream if stream is not None else torch.cuda.ExternalStream(
+            sdpd_ensemble_stream(self.e))
 
     def __del__(self):
         e = getattr(self, "e", None)

@@ -191,7 +191,10 @@ __global__ void __launch_bounds__(128) k_force(Consts c, Arrays<P> a, const type
                                                typename P::Q* __restrict__ qdz, int32_t* __restrict__ key,
                                                int32_t* __restrict__ slot, int32_t* __restrict__ cell_count,
                                                double* __restrict__ force_by_id,
-                                               const uint32_t* __restrict__ nlist, const int32_t* __restrict__ nn) {
+                                               const uint32_t* __restrict__ nlist, const int32_t* __restrict__ nn,
+                                               float3 drift3) {
+  // mixed path: dt / m * 2^32 / L per axis, computed on the host
+  const float drift_f[3] = {drift3.x, drift3.y, drift3.z};
   using R = typename P::R;
   using V4 = typename P::V4;
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -206,6 +209,7 @@ __global__ void __launch_bounds__(128) k_force(Consts c, Arrays<P> a, const type
   R fx = R(0), fy = R(0), fz = R(0);
   home.frames_all(c);
   const int n = nn[i];
+#pragma unroll 4
   for (int k = 0; k < n; ++k) {
     const uint32_t e = __ldg(&nlist[i * c.nbr_cap + k]);
     const V4 qj = ld4(&qp4[e >> 6]);
@@ -225,17 +229,16 @@ __global__ void __launch_bounds__(128) k_force(Consts c, Arrays<P> a, const type
     force_by_id[3 * k + 1] = fy;
     force_by_id[3 * k + 2] = fz;
   }
-  const R hdt = (R)half_dt;
+  const R hdt = (R)half_dt;  // one conversion per thread
   R px = a.px[i] + fx * hdt, py = a.py[i] + fy * hdt, pz = a.pz[i] + fz * hdt;
   a.px[i] = px; a.py[i] = py; a.pz[i] = pz;
   if (dt_drift != 0.0) {
     int nc3[3];
     if constexpr (P::mixed) {
       // fixed point: the displacement in units of L / 2^32, wrap-around = periodic
-      const float k = (float)(dt_drift / c.m);
-      uint32_t ux = a.qx[i] + (uint32_t)__float2int_rn(px * k * (float)c.inv_scale[0]);
-      uint32_t uy = a.qy[i] + (uint32_t)__float2int_rn(py * k * (float)c.inv_scale[1]);
-      uint32_t uz = a.qz[i] + (uint32_t)__float2int_rn(pz * k * (float)c.inv_scale[2]);
+      uint32_t ux = a.qx[i] + (uint32_t)__float2int_rn(px * drift_f[0]);
+      uint32_t uy = a.qy[i] + (uint32_t)__float2int_rn(py * drift_f[1]);
+      uint32_t uz = a.qz[i] + (uint32_t)__float2int_rn(pz * drift_f[2]);
       qdx[i] = ux; qdy[i] = uy; qdz[i] = uz;
       nc3[0] = (int)__umulhi(ux, (uint32_t)c.nc[0]);
       nc3[1] = (int)__umulhi(uy, (uint32_t)c.nc[1]);
@@ -286,14 +289,16 @@ void launch_force(const Consts& c, const Workspace& w, int cur, double half_dt, 
   auto qdx = (typename P::Q*)w.qdx;
   auto qdy = (typename P::Q*)w.qdy;
   auto qdz = (typename P::Q*)w.qdz;
+  const float3 drift3 = make_float3((float)(dt_drift / c.m * c.inv_scale[0]), (float)(dt_drift / c.m * c.inv_scale[1]),
+                                    (float)(dt_drift / c.m * c.inv_scale[2]));
   if (c.kernel == SDPD_KERNEL_LUCY)
     k_force<P, SDPD_KERNEL_LUCY><<<blocks_for(c.N, 128), 128, 0, s>>>(
         c, a, qp4, w.cell_start, w.mrank, w.xmin[0], w.xmin[1], w.xmin[2], half_dt, dt_drift, qdx, qdy,
-        qdz, w.key, w.slot, w.cell_count, force_by_id, w.nlist, w.nn);
+        qdz, w.key, w.slot, w.cell_count, force_by_id, w.nlist, w.nn, drift3);
   else
     k_force<P, SDPD_KERNEL_CUBIC><<<blocks_for(c.N, 128), 128, 0, s>>>(
         c, a, qp4, w.cell_start, w.mrank, w.xmin[0], w.xmin[1], w.xmin[2], half_dt, dt_drift, qdx, qdy,
-        qdz, w.key, w.slot, w.cell_count, force_by_id, w.nlist, w.nn);
+        qdz, w.key, w.slot, w.cell_count, force_by_id, w.nlist, w.nn, drift3);
 }
 
 template void launch_density<Fp64>(const Consts&, const Workspace&, int, int, int32_t*, cudaStream_t);

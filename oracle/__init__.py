@@ -122,6 +122,13 @@ def lib():
             "orc_run": (C.c_int, [P, _dp, _dp, _dp, C.c_double, C.c_int64, C.c_int, C.c_int,
                                   C.c_uint64, _u64p, C.POINTER(FDStats)]),
             "orc_observables": (None, [P, _dp, _dp, _dp]),
+            "orc_dF_dr": (C.c_double, [C.c_int, C.c_double, C.c_double]),
+            "orc_dW_dh": (C.c_double, [C.c_int, C.c_double, C.c_double]),
+            "orc_dF_dh": (C.c_double, [C.c_int, C.c_double, C.c_double]),
+            "orc_virial_pressure": (C.c_double, [P, _dp, _dp, _dp]),
+            "orc_density_vjp": (None, [P, _dp, _dp, _dp, _dp]),
+            "orc_virial_vjp": (C.c_double, [P, _dp, _dp, _dp, _dp, _dp, _dp, _dp]),
+            "orc_vv_vjp": (None, [P, _dp, _dp, _dp, C.c_double, C.c_int, _dp, _dp, _dp, _dp, _dp, _dp, _dp]),
             "orc_sizeof_params": (C.c_int, []),
             "orc_sizeof_pair_rec": (C.c_int, []),
         }
@@ -344,3 +351,66 @@ def observables(P: Params, p, eps) -> dict:
     lib().orc_observables(C.byref(P), _d(p), _d(eps), _d(out))
     return {"E": out[0], "E_int": out[1], "E_kin": out[2], "P": out[3:6].copy(),
             "T_kin": out[6], "T_int": out[7]}
+
+
+def dF_dr(kernel, r, h):
+    return lib().orc_dF_dr(kernel, r, h)
+
+
+def dW_dh(kernel, r, h):
+    return lib().orc_dW_dh(kernel, r, h)
+
+
+def dF_dh(kernel, r, h):
+    return lib().orc_dF_dh(kernel, r, h)
+
+
+def virial_pressure(P: Params, q, p, eps) -> float:
+    """Virial pressure (1/3V)[sum |p|^2/m + sum_{i<j} r_ij . F_ij] of a state."""
+    q, p, eps = _f64(q), _f64(p), _f64(eps)
+    return lib().orc_virial_pressure(C.byref(P), _d(q), _d(p), _d(eps))
+
+
+def virial_vjp(P: Params, q, p, eps):
+    """(P_virial, dP/dq, dP/dp, dP/deps, dP/d(h, c_rho, C_K)) at fixed energies."""
+    q, p, eps = _f64(q), _f64(p), _f64(eps)
+    gq = np.zeros((P.N, 3))
+    gp = np.zeros((P.N, 3))
+    ge = np.zeros(P.N)
+    gt = np.zeros(3)
+    val = lib().orc_virial_vjp(C.byref(P), _d(q), _d(p), _d(eps), _d(gq), _d(gp), _d(ge), _d(gt))
+    return val, gq, gp, ge, gt
+
+
+def vv_trajectory(P: Params, q0, p0, eps0, dt, nsteps):
+    """Final (q, p, eps) after nsteps Velocity Verlet steps (no sweep)."""
+    s = P.scheme
+    P.scheme = SCHEME_NONE
+    try:
+        _, q, p, e, _, _ = run(P, q0, p0, eps0, dt, nsteps, seed=0)
+    finally:
+        P.scheme = s
+    return q, p, e
+
+
+def vv_vjp(P: Params, q0, p0, eps0, dt, nsteps, gqn, gpn, gepsn):
+    """Cotangents of (q0, p0, eps0, (h, c_rho, C_K)) of nsteps Velocity
+    Verlet steps at fixed entropies, given those of the final state."""
+    q0, p0, eps0 = _f64(q0), _f64(p0), _f64(eps0)
+    gqn, gpn, gepsn = _f64(gqn), _f64(gpn), _f64(gepsn)
+    gq = np.empty((P.N, 3))
+    gp = np.empty((P.N, 3))
+    ge = np.empty(P.N)
+    gt = np.empty(3)
+    lib().orc_vv_vjp(C.byref(P), _d(q0), _d(p0), _d(eps0), dt, nsteps, _d(gqn), _d(gpn), _d(gepsn), _d(gq),
+                     _d(gp), _d(ge), _d(gt))
+    return gq, gp, ge, gt
+
+
+def vv_virial_grad(P: Params, q0, p0, eps0, dt, nsteps):
+    """Virial pressure after nsteps Velocity Verlet steps and its gradient
+    (dL/dq0, dL/dp0, dL/deps0, dL/d(h, c_rho, C_K))."""
+    qn, pn, en = vv_trajectory(P, q0, p0, eps0, dt, nsteps)
+    val, gq, gp, ge, gt = virial_vjp(P, qn, pn, en)
+    gq0, gp0, ge0, gt0 = vv_vjp(P, q0, p0, eps0, dt, nsteps, gq, gp, ge)
+    return val, gq0, gp0, ge0, gt0 + gt

@@ -45,6 +45,13 @@
  *      64-bit words give G0, G1 (Box-Muller on two 53-bit uniforms), G2
  *      (Box-Muller on two 32-bit uniforms taken from word 2) and U (53 bits
  *      of word 3).
+ *  R15 gradients: reverse mode of the Velocity Verlet dynamics of Section 3.1
+ *      with the entropies as its constants (eps = E(S, rho(q))), by the chain
+ *      rule through Eq. (pg-eos) and the density gradient of Eq.
+ *      (gradient-rho); parameters theta = (h, c_rho, C_K) with kB, m and the
+ *      box held fixed; the scalar observable is the virial pressure
+ *      (1/3V)[sum |p|^2/m + sum_{i<j} r_ij . F_ij].  The sweep is not
+ *      differentiated.
  */
 #include <math.h>
 #include <stdint.h>
@@ -828,6 +835,247 @@ void orc_observables(const orc_params* P, const double* p, const double* eps, do
   out[3] = px; out[4] = py; out[5] = pz;
   out[6] = P->N > 1 ? 2.0 * ke / (3.0 * (double)(P->N - 1)) : 0.0;
   out[7] = P->N > 0 ? st / (double)P->N : 0.0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Reverse-mode gradients of the conservative dynamics (Section 3.1)         */
+/* ------------------------------------------------------------------------ */
+/* A gradient here is the vector-Jacobian product of a map with a given
+ * cotangent of its outputs; every routine ADDS its contribution to the
+ * gradient arrays it is given.  The parameters differentiated are
+ * theta = (h, c_rho, C_K) (kB, m and the box are held fixed).  Entropies are
+ * the constants of the Velocity Verlet dynamics (the energies follow
+ * eps = E(S, rho(q)) as in Section 3.1). */
+
+/* dF/dr of the kernel function F(r) (grad W = -F r): Lucy -2c(1-x)/h; cubic
+ * -3c/h for x <= 1/2 and -(c/h)(1-x)(1+x)/x^2 above (c = the F prefactor). */
+double orc_dF_dr(int kernel, double r, double h) {
+  double x = r / h;
+  if (x >= 1.0) return 0.0;
+  double h5 = h * h * h * h * h;
+  if (kernel == ORC_KERNEL_CUBIC) {
+    double c = 48.0 / (M_PI * h5);
+    if (x <= 0.5) return -3.0 * c / h;
+    return -(c / h) * (1.0 - x) * (1.0 + x) / (x * x);
+  }
+  double c = 315.0 / (4.0 * M_PI * h5);
+  return -2.0 * c * (1.0 - x) / h;
+}
+
+/* dW/dh and dF/dh at fixed r.  W = h^-3 w(r/h), F = h^-5 phi(r/h) and
+ * dW/dr = -r F give dW/dh = (r^2 F - 3 W)/h and dF/dh = -(5 F + r dF/dr)/h. */
+double orc_dW_dh(int kernel, double r, double h) {
+  return (r * r * orc_F(kernel, r, h) - 3.0 * orc_W(kernel, r, h)) / h;
+}
+double orc_dF_dh(int kernel, double r, double h) {
+  return -(5.0 * orc_F(kernel, r, h) + r * orc_dF_dr(kernel, r, h)) / h;
+}
+
+/* Virial pressure of a state, (1/3V) [sum_i |p_i|^2/m + sum_{i<j} r_ij . F_ij]
+ * with the pair forces of Eq. (cons-forces) and pi_i = P_i/rho_i^2 from
+ * Eq. (pg-eos) at the state's own energies. */
+double orc_virial_pressure(const orc_params* P, const double* q, const double* p, const double* eps) {
+  int64_t N = P->N;
+  const double h2 = P->h * P->h, m2 = P->m * P->m;
+  double* rho = (double*)malloc(sizeof(double) * (size_t)(N ? N : 1));
+  orc_density(P, q, rho);
+  double kin = 0.0, vir = 0.0;
+  for (int64_t i = 0; i < N; ++i) {
+    kin += (p[3 * i] * p[3 * i] + p[3 * i + 1] * p[3 * i + 1] + p[3 * i + 2] * p[3 * i + 2]) / P->m;
+    double pi_i = orc_P(P, eps[i], rho[i]) / (rho[i] * rho[i]);
+    for (int64_t j = i + 1; j < N; ++j) {
+      double d[3];
+      displacement(P, q, i, j, d);
+      double r2 = orc_r2(d[0], d[1], d[2]);
+      if (r2 < h2) {
+        double pi_j = orc_P(P, eps[j], rho[j]) / (rho[j] * rho[j]);
+        vir += m2 * (pi_i + pi_j) * orc_F(P->kernel, sqrt(r2), P->h) * r2;
+      }
+    }
+  }
+  free(rho);
+  return (kin + vir) / (3.0 * P->L[0] * P->L[1] * P->L[2]);
+}
+
+/* Gradient through the density sum of Eq. (sdpd-rho-v): given rbar_i =
+ * dL/drho_i, adds dL/dq (Eq. gradient-rho: d rho_i/d q_i = -m sum_j F r_ij,
+ * d rho_j/d q_i = -m F r_ij) and dL/dh (the self term m W(0) included). */
+void orc_density_vjp(const orc_params* P, const double* q, const double* rbar, double* gq, double gth[3]) {
+  int64_t N = P->N;
+  const double h = P->h, h2 = h * h, m = P->m;
+  for (int64_t i = 0; i < N; ++i) gth[0] += rbar[i] * m * orc_dW_dh(P->kernel, 0.0, h);
+  for (int64_t i = 0; i < N; ++i)
+    for (int64_t j = i + 1; j < N; ++j) {
+      double d[3];
+      displacement(P, q, i, j, d);
+      double r2 = orc_r2(d[0], d[1], d[2]);
+      if (!(r2 < h2 && r2 > 0.0)) continue;
+      double r = sqrt(r2);
+      double f = orc_F(P->kernel, r, h);
+      for (int k = 0; k < 3; ++k) {
+        gq[3 * i + k] -= m * f * (rbar[i] + rbar[j]) * d[k];
+        gq[3 * j + k] += m * f * (rbar[i] + rbar[j]) * d[k];
+      }
+      gth[0] += m * orc_dW_dh(P->kernel, r, h) * (rbar[i] + rbar[j]);
+    }
+}
+
+/* Gradient of the pair sum
+ *   Phi(q) = weight * sum_{i<j} m^2 (pi_i + pi_j) F(r_ij) t_ij
+ * with t_ij = (v_i - v_j) . r_ij (mode 0: Phi = weight * sum_i v_i . F_i, the
+ * pull-back of a kick) or t_ij = |r_ij|^2 (mode 1: the virial sum).
+ * The pressures pi_i = c_rho eps_i / (C_K m rho_i) follow Eq. (pg-eos), with
+ * x = the entropies S (fixed_S = 1, eps = E(S, rho(q))) or x = the energies
+ * (fixed_S = 0).  Adds dPhi/dq to gq, dPhi/dx to gx and dPhi/dtheta to gth. */
+void orc_pair_vjp(const orc_params* P, const double* q, const double* x, int fixed_S, int mode, const double* v,
+                  double weight, double* gq, double* gx, double gth[3]) {
+  int64_t N = P->N;
+  const double h = P->h, h2 = h * h, m2 = P->m * P->m;
+  const double CK = P->C_K, cr = P->c_rho;
+  size_t n1 = (size_t)(N ? N : 1);
+  double* rho = (double*)malloc(sizeof(double) * n1);
+  double* pi = (double*)malloc(sizeof(double) * n1);
+  double* A = (double*)calloc(n1, sizeof(double));
+  double* rbar = (double*)malloc(sizeof(double) * n1);
+  orc_density(P, q, rho);
+  for (int64_t i = 0; i < N; ++i) {
+    double eps = fixed_S ? orc_E_of_S(P, x[i], rho[i]) : x[i];
+    pi[i] = orc_P(P, eps, rho[i]) / (rho[i] * rho[i]);
+  }
+  /* dPhi/dpi_i = weight * A_i, A_i = m^2 sum_{j != i} F(r_ij) t_ij */
+  for (int64_t i = 0; i < N; ++i)
+    for (int64_t j = i + 1; j < N; ++j) {
+      double d[3];
+      displacement(P, q, i, j, d);
+      double r2 = orc_r2(d[0], d[1], d[2]);
+      if (!(r2 < h2 && r2 > 0.0)) continue;
+      double t = 0.0;
+      for (int k = 0; k < 3; ++k) t += (mode == 0 ? v[3 * i + k] - v[3 * j + k] : d[k]) * d[k];
+      double a = m2 * orc_F(P->kernel, sqrt(r2), h) * t;
+      A[i] += a;
+      A[j] += a;
+    }
+  /* pi = c_rho eps / (C_K m rho).  At fixed S, eps = exp((S + c_rho ln rho)/C_K):
+   *   dpi/drho = pi (c_rho/C_K - 1)/rho, dpi/dS = pi/C_K,
+   *   dpi/dc_rho = pi (1/c_rho + ln(rho)/C_K), dpi/dC_K = -pi (1 + ln(eps))/C_K.
+   * At fixed eps: dpi/drho = -pi/rho, dpi/deps = pi/eps, dpi/dc_rho = pi/c_rho,
+   *   dpi/dC_K = -pi/C_K. */
+  for (int64_t i = 0; i < N; ++i) {
+    double g = weight * A[i] * pi[i];
+    if (fixed_S) {
+      double eps = orc_E_of_S(P, x[i], rho[i]);
+      rbar[i] = g * (cr / CK - 1.0) / rho[i];
+      gx[i] += g / CK;
+      gth[1] += g * (1.0 / cr + log(rho[i]) / CK);
+      gth[2] -= g * (1.0 + log(eps)) / CK;
+    } else {
+      rbar[i] = -g / rho[i];
+      gx[i] += g / x[i];
+      gth[1] += g / cr;
+      gth[2] -= g / CK;
+    }
+  }
+  orc_density_vjp(P, q, rbar, gq, gth);
+  /* the explicit dependence of each pair term on q and h */
+  for (int64_t i = 0; i < N; ++i)
+    for (int64_t j = i + 1; j < N; ++j) {
+      double d[3];
+      displacement(P, q, i, j, d);
+      double r2 = orc_r2(d[0], d[1], d[2]);
+      if (!(r2 < h2 && r2 > 0.0)) continue;
+      double r = sqrt(r2);
+      double f = orc_F(P->kernel, r, h), fp = orc_dF_dr(P->kernel, r, h);
+      double c = weight * m2 * (pi[i] + pi[j]);
+      double t = 0.0, dt_dqi[3];
+      for (int k = 0; k < 3; ++k) {
+        double u = mode == 0 ? v[3 * i + k] - v[3 * j + k] : d[k];
+        t += u * d[k];
+        dt_dqi[k] = mode == 0 ? u : 2.0 * d[k];
+      }
+      for (int k = 0; k < 3; ++k) {
+        double g = c * (fp / r * t * d[k] + f * dt_dqi[k]);
+        gq[3 * i + k] += g;
+        gq[3 * j + k] -= g;
+      }
+      gth[0] += c * t * orc_dF_dh(P->kernel, r, h);
+    }
+  free(rho); free(pi); free(A); free(rbar);
+}
+
+/* Gradient of the virial pressure of a state (q, p, eps) at its own
+ * energies; adds dP/dq, dP/dp, dP/deps, dP/dtheta and returns P. */
+double orc_virial_vjp(const orc_params* P, const double* q, const double* p, const double* eps, double* gq,
+                      double* gp, double* geps, double gth[3]) {
+  const double V3 = 3.0 * P->L[0] * P->L[1] * P->L[2];
+  for (int64_t k = 0; k < 3 * P->N; ++k) gp[k] += 2.0 * p[k] / (V3 * P->m);
+  orc_pair_vjp(P, q, eps, 0, 1, NULL, 1.0 / V3, gq, geps, gth);
+  return orc_virial_pressure(P, q, p, eps);
+}
+
+/* Gradient of nsteps Velocity Verlet steps (Eq. sdpd-verlet, no sweep) from
+ * (q0, p0, eps0) with the entropies S_i = S(eps0_i, rho_i(q0)) held fixed.
+ * Given the cotangents (gqn, gpn, gepsn) of the final state, writes those of
+ * the initial state and of theta (overwriting gq0, gp0, geps0, gth). */
+void orc_vv_vjp(const orc_params* P, const double* q0, const double* p0, const double* eps0, double dt,
+                int nsteps, const double* gqn, const double* gpn, const double* gepsn, double* gq0, double* gp0,
+                double* geps0, double gth[3]) {
+  int64_t N = P->N;
+  size_t n1 = (size_t)(N ? N : 1), n3 = 3 * n1;
+  double* qs = (double*)malloc(sizeof(double) * n3 * (size_t)(nsteps + 1));
+  double* p = (double*)malloc(sizeof(double) * n3);
+  double* eps = (double*)malloc(sizeof(double) * n1);
+  double* rho = (double*)malloc(sizeof(double) * n1);
+  double* S = (double*)malloc(sizeof(double) * n1);
+  double* gS = (double*)calloc(n1, sizeof(double));
+  double* rbar = (double*)malloc(sizeof(double) * n1);
+  double* v = (double*)malloc(sizeof(double) * n3);
+  orc_density(P, q0, rho);
+  for (int64_t i = 0; i < N; ++i) S[i] = orc_S(P, eps0[i], rho[i]);
+  /* forward, keeping every position */
+  memcpy(qs, q0, sizeof(double) * 3 * (size_t)N);
+  memcpy(p, p0, sizeof(double) * 3 * (size_t)N);
+  memcpy(eps, eps0, sizeof(double) * (size_t)N);
+  for (int n = 0; n < nsteps; ++n) {
+    memcpy(qs + n3 * (size_t)(n + 1), qs + n3 * (size_t)n, sizeof(double) * 3 * (size_t)N);
+    orc_verlet(P, qs + n3 * (size_t)(n + 1), p, eps, dt);
+  }
+  gth[0] = gth[1] = gth[2] = 0.0;
+  double* gq = gq0;
+  double* gp = gp0;
+  memcpy(gq, gqn, sizeof(double) * 3 * (size_t)N);
+  memcpy(gp, gpn, sizeof(double) * 3 * (size_t)N);
+  /* final energies eps_n = E(S, rho(q_n)): dE/dS = eps/C_K,
+   * dE/drho = eps c_rho/(C_K rho), dE/dc_rho = eps ln(rho)/C_K,
+   * dE/dC_K = -eps ln(eps)/C_K */
+  const double* qn = qs + n3 * (size_t)nsteps;
+  orc_density(P, qn, rho);
+  for (int64_t i = 0; i < N; ++i) {
+    double e = orc_E_of_S(P, S[i], rho[i]), ge = gepsn[i] * e / P->C_K;
+    gS[i] += ge;
+    rbar[i] = ge * P->c_rho / rho[i];
+    gth[1] += ge * log(rho[i]);
+    gth[2] -= ge * log(e);
+  }
+  orc_density_vjp(P, qn, rbar, gq, gth);
+  /* each step backwards: p1 = ph + dt/2 F(q1), q1 = q + dt ph/m,
+   * ph = p + dt/2 F(q) */
+  for (int n = nsteps - 1; n >= 0; --n) {
+    for (size_t k = 0; k < 3 * (size_t)N; ++k) v[k] = 0.5 * dt * gp[k];
+    orc_pair_vjp(P, qs + n3 * (size_t)(n + 1), S, 1, 0, v, 1.0, gq, gS, gth);
+    for (size_t k = 0; k < 3 * (size_t)N; ++k) gp[k] += dt / P->m * gq[k];
+    for (size_t k = 0; k < 3 * (size_t)N; ++k) v[k] = 0.5 * dt * gp[k];
+    orc_pair_vjp(P, qs + n3 * (size_t)n, S, 1, 0, v, 1.0, gq, gS, gth);
+  }
+  /* S_i = C_K ln eps0_i - c_rho ln rho_i(q0) */
+  orc_density(P, q0, rho);
+  for (int64_t i = 0; i < N; ++i) {
+    geps0[i] = gS[i] * P->C_K / eps0[i];
+    rbar[i] = -gS[i] * P->c_rho / rho[i];
+    gth[1] -= gS[i] * log(rho[i]);
+    gth[2] += gS[i] * log(eps0[i]);
+  }
+  orc_density_vjp(P, q0, rbar, gq, gth);
+  free(qs); free(p); free(eps); free(rho); free(S); free(gS); free(rbar); free(v);
 }
 
 int orc_sizeof_params(void) { return (int)sizeof(orc_params); }

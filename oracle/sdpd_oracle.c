@@ -909,7 +909,7 @@ void orc_density_vjp(const orc_params* P, const double* q, const double* rbar, d
       double d[3];
       displacement(P, q, i, j, d);
       double r2 = orc_r2(d[0], d[1], d[2]);
-      if (!(r2 < h2 && r2 > 0.0)) continue;
+      if (!(r2 < h2)) continue;
       double r = sqrt(r2);
       double f = orc_F(P->kernel, r, h);
       for (int k = 0; k < 3; ++k) {
@@ -948,7 +948,7 @@ void orc_pair_vjp(const orc_params* P, const double* q, const double* x, int fix
       double d[3];
       displacement(P, q, i, j, d);
       double r2 = orc_r2(d[0], d[1], d[2]);
-      if (!(r2 < h2 && r2 > 0.0)) continue;
+      if (!(r2 < h2)) continue;
       double t = 0.0;
       for (int k = 0; k < 3; ++k) t += (mode == 0 ? v[3 * i + k] - v[3 * j + k] : d[k]) * d[k];
       double a = m2 * orc_F(P->kernel, sqrt(r2), h) * t;
@@ -982,9 +982,12 @@ void orc_pair_vjp(const orc_params* P, const double* q, const double* x, int fix
       double d[3];
       displacement(P, q, i, j, d);
       double r2 = orc_r2(d[0], d[1], d[2]);
-      if (!(r2 < h2 && r2 > 0.0)) continue;
+      if (!(r2 < h2)) continue;
       double r = sqrt(r2);
       double f = orc_F(P->kernel, r, h), fp = orc_dF_dr(P->kernel, r, h);
+      /* d(F(r) r_ij)/dq_i = F I + (F'/r) r_ij r_ij^T; at r = 0 (coincident
+       * particles) the second term vanishes (t is O(r) or O(r^2)) */
+      double fpr = r2 > 0.0 ? fp / r : 0.0;
       double c = weight * m2 * (pi[i] + pi[j]);
       double t = 0.0, dt_dqi[3];
       for (int k = 0; k < 3; ++k) {
@@ -993,7 +996,7 @@ void orc_pair_vjp(const orc_params* P, const double* q, const double* x, int fix
         dt_dqi[k] = mode == 0 ? u : 2.0 * d[k];
       }
       for (int k = 0; k < 3; ++k) {
-        double g = c * (fp / r * t * d[k] + f * dt_dqi[k]);
+        double g = c * (fpr * t * d[k] + f * dt_dqi[k]);
         gq[3 * i + k] += g;
         gq[3 * j + k] -= g;
       }

@@ -185,3 +185,25 @@ def test_virial_loss_gradient_by_differences():
         base = getattr(P, name)
         ref = central(lambda d: loss(with_param(cfg, name, base + d * base), [q, p, e])) / base
         assert abs(gt[k] - ref) < 1e-6 * max(1.0, abs(ref))
+
+
+def test_coincident_particles():
+    """Two particles at the same position: the pair is inside the density sum
+    (m W(0) each way), so it is in dP/dh, and its force derivative is F(0) I
+    (the F'/r term vanishes with r); both against central differences."""
+    cfg, q, p, e = setup()
+    q[1] = q[0]
+    P = cfg.params()
+    dt, ns = 0.02, 3
+
+    def loss(Pp, x):
+        return O.virial_pressure(Pp, *O.vv_trajectory(Pp, *x, dt, ns))
+    val, gq, gp, ge, gt = O.vv_virial_grad(P, q, p, e, dt, ns)
+    u = np.zeros_like(q)
+    u[0] = [0.3, -0.2, 0.5]
+    u[1] = [-0.1, 0.4, 0.2]
+    ref = central(lambda d: loss(P, [q + d * u, p, e]))
+    assert abs((gq * u).sum() - ref) < 1e-6 * np.abs(gq * u).sum()
+    val, gq, gp, ge, gt = O.virial_vjp(P, q, p, e)
+    ref = central(lambda d: O.virial_pressure(with_param(cfg, "h", P.h * (1 + d)), q, p, e)) / P.h
+    assert abs(gt[0] - ref) < 1e-6 * abs(ref)

@@ -34,6 +34,13 @@ struct sdpd_handle {
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pending;
   double stage_ms[SDPD_NSTAGES];
   int64_t stage_launches[SDPD_NSTAGES];
+  // the trajectory last recorded by sdpd_vv_record (for sdpd_vv_adjoint)
+  struct {
+    const void* tape = nullptr;
+    size_t bytes = 0;
+    int64_t nsteps = 0, every = 1;
+    double dt = 0.0;
+  } rec;
 };
 
 namespace {
@@ -260,33 +267,38 @@ struct StageTimer {
   }
 };
 
+// One Velocity Verlet step, Eq. (sdpd-verlet), at fixed entropies.
+template <class P>
+void vv_step(sdpd_handle* s, double dt) {
+  const Consts& c = s->c;
+  {  // p^{n+1/2} = p^n + F^n dt/2, q^{n+1} = q^n + p^{n+1/2} dt/m
+    StageTimer t(s, 0, 1);
+    launch_force<P>(c, s->w, s->cur, 0.5 * dt, dt, nullptr, s->stream);
+  }
+  {
+    StageTimer t(s, 1, 5);
+    launch_sort<P>(c, s->w, s->cur, s->stream);
+  }
+  s->cur = 1 - s->cur;
+  {  // rho^{n+1}, eps^{n+1} = E(S, rho^{n+1})
+    StageTimer t(s, 2, 1);
+    launch_density<P>(c, s->w, s->cur, 1, nullptr, s->stream);
+  }
+  {  // p^{n+1} = p^{n+1/2} + F^{n+1} dt/2
+    StageTimer t(s, 3, 1);
+    launch_force<P>(c, s->w, s->cur, 0.5 * dt, 0.0, nullptr, s->stream);
+  }
+  s->launches += 8;
+  s->vv_step++;
+}
+
 template <class P>
 void do_steps(sdpd_handle* s, double dt, int64_t nsteps, uint64_t seed) {
   const Consts& c = s->c;
   const int theta = s->prm.theta < 1 ? 1 : s->prm.theta;
   const bool fd = s->prm.scheme != SDPD_SCHEME_NONE;
   for (int64_t n = 0; n < nsteps; ++n) {
-    if (!s->prm.fd_only) {
-      {  // p^{n+1/2} = p^n + F^n dt/2, q^{n+1} = q^n + p^{n+1/2} dt/m
-        StageTimer t(s, 0, 1);
-        launch_force<P>(c, s->w, s->cur, 0.5 * dt, dt, nullptr, s->stream);
-      }
-      {
-        StageTimer t(s, 1, 5);
-        launch_sort<P>(c, s->w, s->cur, s->stream);
-      }
-      s->cur = 1 - s->cur;
-      {  // rho^{n+1}, eps^{n+1} = E(S, rho^{n+1})
-        StageTimer t(s, 2, 1);
-        launch_density<P>(c, s->w, s->cur, 1, nullptr, s->stream);
-      }
-      {  // p^{n+1} = p^{n+1/2} + F^{n+1} dt/2
-        StageTimer t(s, 3, 1);
-        launch_force<P>(c, s->w, s->cur, 0.5 * dt, 0.0, nullptr, s->stream);
-      }
-      s->launches += 8;
-      s->vv_step++;
-    }
+    if (!s->prm.fd_only) vv_step<P>(s, dt);
     if (fd && (s->prm.fd_only || (n + 1) % theta == 0)) {
       const double dt_fd = s->prm.fd_only ? dt : theta * dt;
       const int rec = s->w.pair_recs != nullptr;
@@ -623,6 +635,218 @@ int sdpd_stage_times(sdpd_t* s, double* ms, int64_t* launches, int n) {
     if (launches) launches[k] = s->stage_launches[k];
   }
   return SDPD_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Gradients of the conservative dynamics (reverse mode, float64 handles)
+// ---------------------------------------------------------------------------
+namespace {
+
+// The tape (caller memory): scratch of the reverse pass, then stored states
+// in id order (q [N][3], p [N][3], eps [N]): the checkpoints at steps 0,
+// every, 2 every, ... below nsteps, the final state, and the every - 1 states
+// of the segment being replayed.
+struct Tape {
+  D4* vs4;
+  double *A, *Sbar, *qbar, *pbar, *thbar, *partial, *sums, *states;
+  int64_t n_ckpt, n_seg, stride;
+  double* ckpt(int64_t k) const { return states + k * stride; }
+  double* final_state() const { return ckpt(n_ckpt); }
+  double* seg(int64_t j) const { return ckpt(n_ckpt + 1 + j); }
+};
+
+size_t tape_layout(int64_t N, int64_t nsteps, int64_t every, char* base, Tape* t) {
+  const size_t n = (size_t)(N > 0 ? N : 1);
+  Layout L;
+  auto at = [&](size_t bytes) -> void* { return base ? base + L.take(bytes) : (L.take(bytes), nullptr); };
+  t->vs4 = (D4*)at(n * sizeof(D4));
+  t->A = (double*)at(n * 8);
+  t->Sbar = (double*)at(n * 8);
+  t->qbar = (double*)at(3 * n * 8);
+  t->pbar = (double*)at(3 * n * 8);
+  t->thbar = (double*)at(3 * n * 8);
+  t->partial = (double*)at(adj_sum_partial_doubles() * 8);
+  t->sums = (double*)at(4 * 8);
+  t->n_ckpt = (nsteps + every - 1) / every;
+  t->n_seg = nsteps > 0 ? std::min<int64_t>(every, nsteps) - 1 : 0;
+  t->stride = 7 * (int64_t)n;
+  t->states = (double*)at((size_t)(t->n_ckpt + 1 + t->n_seg) * (size_t)t->stride * 8);
+  return L.off;
+}
+
+bool tape_sizes_ok(int64_t nsteps, int64_t every) {
+  return nsteps >= 0 && every >= 1 && nsteps <= (int64_t)1 << 40 && every <= (int64_t)1 << 40;
+}
+
+// copy the current state, in id order, into a tape slot
+void store_state(sdpd_handle* s, double* slot) {
+  Workspace w = s->w;
+  w.io_q = slot;
+  w.io_p = slot + 3 * s->c.N;
+  w.io_e = slot + 6 * s->c.N;
+  launch_unload<Fp64>(s->c, w, s->cur, s->stream);
+  s->launches += 1;
+}
+
+// load a tape slot as the current state: bin, sort, density (eps kept)
+void load_state(sdpd_handle* s, const double* slot) {
+  Workspace w = s->w;
+  w.io_q = (double*)slot;
+  w.io_p = (double*)slot + 3 * s->c.N;
+  w.io_e = (double*)slot + 6 * s->c.N;
+  launch_load<Fp64>(s->c, w, s->stream);
+  launch_sort<Fp64>(s->c, s->w, 0, s->stream);
+  s->cur = 1;
+  launch_density<Fp64>(s->c, s->w, s->cur, 0, nullptr, s->stream);
+  s->launches += 7;
+}
+
+int check_adjoint_handle(sdpd_handle* s) {
+  if (!s) return SDPD_ERR_INVALID_ARG;
+  if (!s->ws) return SDPD_ERR_NO_WORKSPACE;
+  if (s->prm.precision != SDPD_FP64 || s->prm.fd_only) return SDPD_ERR_INVALID_ARG;
+  if (use_device(s) != SDPD_OK) return SDPD_ERR_CUDA;
+  return SDPD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t sdpd_tape_bytes(const sdpd_t* s, int64_t nsteps, int64_t every) {
+  if (!s || !tape_sizes_ok(nsteps, every)) return 0;
+  Tape t;
+  return tape_layout(s->c.N, nsteps, every, nullptr, &t);
+}
+
+int sdpd_vv_record(sdpd_t* s, double dt, int64_t nsteps, int64_t every, void* tape, size_t tape_bytes) {
+  int e = check_adjoint_handle(s);
+  if (e) return e;
+  if (!s->has_state) return SDPD_ERR_NO_STATE;
+  if (!(dt > 0) || !isfinite(dt) || !tape_sizes_ok(nsteps, every)) return SDPD_ERR_INVALID_ARG;
+  Tape t;
+  if (!tape || ((uintptr_t)tape % kAlign) != 0 || tape_bytes < tape_layout(s->c.N, nsteps, every, nullptr, &t))
+    return SDPD_ERR_INVALID_ARG;
+  tape_layout(s->c.N, nsteps, every, (char*)tape, &t);
+  s->rec.tape = nullptr;
+  for (int64_t n = 0; n < nsteps; ++n) {
+    if (n % every == 0) store_state(s, t.ckpt(n / every));
+    vv_step<Fp64>(s, dt);
+  }
+  store_state(s, t.final_state());
+  e = launch_status();
+  if (e) return e;
+  s->rec.tape = tape;
+  s->rec.bytes = tape_bytes;
+  s->rec.nsteps = nsteps;
+  s->rec.every = every;
+  s->rec.dt = dt;
+  return SDPD_OK;
+}
+
+int sdpd_vv_adjoint(sdpd_t* s, void* tape, size_t tape_bytes, const double* gq, const double* gp,
+                    const double* geps, double* gq0, double* gp0, double* geps0, double gtheta[3]) {
+  int e = check_adjoint_handle(s);
+  if (e) return e;
+  if (!tape || tape != s->rec.tape || tape_bytes != s->rec.bytes) return SDPD_ERR_INVALID_ARG;
+  const int64_t N = s->c.N;
+  if (!gtheta || (N > 0 && (!gq0 || !gp0 || !geps0))) return SDPD_ERR_INVALID_ARG;
+  const int64_t ns = s->rec.nsteps, every = s->rec.every;
+  const double dt = s->rec.dt;
+  Tape t;
+  tape_layout(N, ns, every, (char*)tape, &t);
+  const Consts& c = s->c;
+  cudaStream_t st = s->stream;
+  const size_t b1 = (size_t)N * 8, b3 = 3 * b1;
+  e = SDPD_OK;
+  if (N > 0) {
+    e |= cuda_ok(gq ? cudaMemcpyAsync(t.qbar, gq, b3, cudaMemcpyDeviceToDevice, st) : cudaMemsetAsync(t.qbar, 0, b3, st));
+    e |= cuda_ok(gp ? cudaMemcpyAsync(t.pbar, gp, b3, cudaMemcpyDeviceToDevice, st) : cudaMemsetAsync(t.pbar, 0, b3, st));
+    e |= cuda_ok(cudaMemsetAsync(t.Sbar, 0, b1, st));
+    e |= cuda_ok(cudaMemsetAsync(t.thbar, 0, b3, st));
+  }
+  if (e) return SDPD_ERR_CUDA;
+  // Positions k = n .. 0.  The kicks around position k (the second of step
+  // k-1, the first of step k) both pull back along dt/2 pbar_k, so each
+  // position is visited once with v = (dt/2)([k < n] + [k > 0]) pbar.
+  int64_t seg_loaded = -1;
+  for (int64_t k = ns; k >= 0; --k) {
+    if (k == ns) {
+      load_state(s, t.final_state());
+    } else if (k % every == 0) {
+      load_state(s, t.ckpt(k / every));
+    } else {
+      const int64_t sg = k / every, k0 = sg * every;
+      if (sg != seg_loaded) {  // replay the segment from its checkpoint
+        load_state(s, t.ckpt(sg));
+        const int64_t k1 = std::min(k0 + every, ns);
+        for (int64_t j = k0 + 1; j < k1; ++j) {
+          vv_step<Fp64>(s, dt);
+          s->vv_step--;
+          store_state(s, t.seg(j - k0 - 1));
+        }
+        seg_loaded = sg;
+      }
+      load_state(s, t.seg(k - k0 - 1));
+    }
+    const double coef = 0.5 * dt * ((k < ns ? 1 : 0) + (k > 0 ? 1 : 0));
+    if (coef != 0.0) {
+      launch_adj_gather(c, s->w, s->cur, t.pbar, coef, t.vs4, st);
+      launch_adj_pairsum(c, s->w, 0, t.vs4, t.A, st);
+    }
+    launch_adj_mid_traj(c, s->w, s->cur, coef != 0.0 ? t.A : nullptr, t.vs4, t.Sbar, t.thbar, geps, k == ns,
+                        k == 0 ? geps0 : nullptr, st);
+    launch_adj_back(c, s->w, s->cur, coef != 0.0 ? 0 : 2, 1.0, t.vs4, 1, t.qbar, t.thbar, st);
+    if (k > 0) launch_adj_axpy(3 * N, dt / c.m, t.qbar, t.pbar, st);
+    s->launches += (coef != 0.0 ? 2 : 0) + 2 + (k > 0 ? 1 : 0);
+  }
+  if (N > 0) {
+    e |= cuda_ok(cudaMemcpyAsync(gq0, t.qbar, b3, cudaMemcpyDeviceToDevice, st));
+    e |= cuda_ok(cudaMemcpyAsync(gp0, t.pbar, b3, cudaMemcpyDeviceToDevice, st));
+  }
+  launch_adj_sum(t.thbar, N, 3, t.partial, t.sums, st);
+  s->launches += 2;
+  double th[3] = {0.0, 0.0, 0.0};
+  e |= cuda_ok(cudaMemcpyAsync(th, t.sums, 3 * 8, cudaMemcpyDeviceToHost, st));
+  // leave the handle at the recorded final state
+  load_state(s, t.final_state());
+  if (e) return SDPD_ERR_CUDA;
+  e = sdpd_sync(s);
+  for (int k = 0; k < 3; ++k) gtheta[k] = th[k];
+  return e;
+}
+
+int sdpd_virial(sdpd_t* s, double* value, double* gq, double* gp, double* geps, double gtheta[3]) {
+  int e = check_adjoint_handle(s);
+  if (e) return e;
+  if (!s->has_state) return SDPD_ERR_NO_STATE;
+  const bool grad = gq || gp || geps;
+  if (!value || (grad && (!gq || !gp || !geps || !gtheta))) return SDPD_ERR_INVALID_ARG;
+  const Consts& c = s->c;
+  cudaStream_t st = s->stream;
+  const int other = 1 - s->cur;
+  // scratch: the sort target of the next step and the id-order staging
+  D4* vs4 = (D4*)s->w.q4[other];
+  double* A = (double*)s->w.rho[other];
+  double* val_id = s->w.io_e;
+  double* thbar = s->w.io_q;
+  double* sums = s->w.obs + 8;  // slots 8..11 of the observables' output block
+  const double wt = 1.0 / (3.0 * c.L[0] * c.L[1] * c.L[2]);
+  launch_adj_pairsum(c, s->w, 1, vs4, A, st);
+  launch_adj_mid_virial(c, s->w, s->cur, A, wt, vs4, val_id, grad ? gp : nullptr, geps, thbar, st);
+  if (grad) launch_adj_back(c, s->w, s->cur, 1, wt, vs4, 0, gq, thbar, st);
+  launch_adj_sum(val_id, c.N, 1, (double*)s->w.obs_partial, sums, st);
+  if (grad) launch_adj_sum(thbar, c.N, 3, (double*)s->w.obs_partial, sums + 1, st);
+  s->launches += 4 + (grad ? 3 : 0);
+  double out[4] = {0.0, 0.0, 0.0, 0.0};
+  if (cudaMemcpyAsync(out, sums, 4 * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess) return SDPD_ERR_CUDA;
+  e = sdpd_sync(s);
+  *value = out[0];
+  if (grad)
+    for (int k = 0; k < 3; ++k) gtheta[k] = out[1 + k];
+  return e;
 }
 
 int sdpd_debug_get(sdpd_t* s, int what, void* dst, int64_t cap, int64_t* count) {

@@ -312,4 +312,21 @@ void launch_observables(const Consts& c, const Workspace& w, int cur, cudaStream
 void launch_set_sweep(const Workspace& w, unsigned long long value, cudaStream_t s);
 void launch_advance_sweep(const Workspace& w, cudaStream_t s);
 
+// Reverse-mode passes (float64 storage layout, after a density pass has built
+// qp4 = (q, pi) and the neighbour lists).  vs4[i] = (v_i, rbar_i) in storage
+// order; qbar, pbar, Sbar, thbar (per-particle (h, c_rho, C_K) terms) in id
+// order.  mode: 0 kick pulled back along v, 1 virial, 2 density term only.
+void launch_adj_gather(const Consts& c, const Workspace& w, int cur, const double* pbar_id, double scale, D4* vs4,
+                       cudaStream_t s);
+void launch_adj_pairsum(const Consts& c, const Workspace& w, int mode, const D4* vs4, double* A, cudaStream_t s);
+void launch_adj_mid_traj(const Consts& c, const Workspace& w, int cur, const double* A, D4* vs4, double* Sbar,
+                         double* thbar, const double* epsbar_n, int final_pos, double* epsbar0, cudaStream_t s);
+void launch_adj_mid_virial(const Consts& c, const Workspace& w, int cur, const double* A, double wt, D4* vs4,
+                           double* val_id, double* gp, double* geps, double* thbar, cudaStream_t s);
+void launch_adj_back(const Consts& c, const Workspace& w, int cur, int mode, double wt, const D4* vs4,
+                     int accumulate, double* qbar, double* thbar, cudaStream_t s);
+void launch_adj_axpy(int64_t n, double a, const double* x, double* y, cudaStream_t s);
+size_t adj_sum_partial_doubles();
+void launch_adj_sum(const double* x, int64_t n, int ncols, double* partial, double* out, cudaStream_t s);
+
 }  // namespace sdpd

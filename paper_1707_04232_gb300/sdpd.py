@@ -73,6 +73,11 @@ SIGNATURES = [
     ("sdpd_ensemble_destroy", None, [_H]),
     ("sdpd_density_static", C.c_int, [C.c_int64, _dp, C.c_double, C.c_double, C.c_int, C.c_void_p,
                                       C.c_void_p, C.c_void_p]),
+    ("sdpd_tape_bytes", C.c_size_t, [_H, C.c_int64, C.c_int64]),
+    ("sdpd_vv_record", C.c_int, [_H, C.c_double, C.c_int64, C.c_int64, C.c_void_p, C.c_size_t]),
+    ("sdpd_vv_adjoint", C.c_int, [_H, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p, C.c_void_p,
+                                  C.c_void_p, C.c_void_p, C.c_void_p, _dp]),
+    ("sdpd_virial", C.c_int, [_H, _dp, C.c_void_p, C.c_void_p, C.c_void_p, _dp]),
     ("sdpd_strerror", C.c_char_p, [C.c_int]),
 ]
 
@@ -218,6 +223,24 @@ def sdpd_ensemble_destroy(e):
     load().sdpd_ensemble_destroy(e)
 
 
+def sdpd_tape_bytes(h, nsteps, every) -> int:
+    return load().sdpd_tape_bytes(h, int(nsteps), int(every))
+
+
+def sdpd_vv_record(h, dt, nsteps, every, tape_ptr: int, nbytes: int) -> int:
+    return load().sdpd_vv_record(h, float(dt), int(nsteps), int(every), tape_ptr, nbytes)
+
+
+def sdpd_vv_adjoint(h, tape_ptr, nbytes, gq, gp, geps, gq0, gp0, geps0, gtheta) -> int:
+    return load().sdpd_vv_adjoint(h, tape_ptr, nbytes, gq, gp, geps, gq0, gp0, geps0,
+                                  gtheta.ctypes.data_as(_dp))
+
+
+def sdpd_virial(h, value, gq, gp, geps, gtheta) -> int:
+    th = gtheta.ctypes.data_as(_dp) if gtheta is not None else None
+    return load().sdpd_virial(h, C.byref(value), gq, gp, geps, th)
+
+
 def sdpd_destroy(h):
     load().sdpd_destroy(h)
 
@@ -250,6 +273,7 @@ class SDPD:
             raise RuntimeError("SDPD needs a CUDA device")
         self.torch = torch
         self.N = int(N)
+        self.m, self.h_smooth, self.K = float(m), float(h), float(K)
         prm = sdpd_params(kB=kB, eta=eta, zeta=zeta, c_rho=c_rho, kernel=kernel, scheme=scheme,
                           precision=precision, fd_only=int(bool(fd_only)), theta=int(theta),
                           debug=int(bool(debug)))
@@ -298,6 +322,56 @@ class SDPD:
 
     def sync(self):
         return sdpd_sync(self.h)
+
+    # -- gradients of the conservative dynamics (float64 handles) ----------
+
+    def tape_bytes(self, nsteps, every=10) -> int:
+        return sdpd_tape_bytes(self.h, nsteps, every)
+
+    def vv_record(self, dt, nsteps, every=10):
+        """Velocity Verlet steps from the loaded state, recorded for
+        vv_adjoint with a checkpoint every ``every`` steps.  Returns the tape
+        (a CUDA uint8 tensor that must stay alive until the last adjoint)."""
+        n = self.tape_bytes(nsteps, every)
+        if n == 0:
+            raise ValueError("bad nsteps/every")
+        tape = self.torch.empty(n, dtype=self.torch.uint8, device=self.workspace.device)
+        _check(sdpd_vv_record(self.h, dt, nsteps, every, tape.data_ptr(), n), "sdpd_vv_record")
+        self._tape = tape
+        return tape
+
+    def vv_adjoint(self, tape, gq=None, gp=None, geps=None):
+        """Cotangents (gq0, gp0, geps0, gtheta) of the recorded trajectory's
+        initial state and of theta = (h, c_rho, C_K), given those of its
+        final state (float64 CUDA tensors in id order, None = zero)."""
+        torch = self.torch
+        dev = self.workspace.device
+        keep = [None if g is None else g.detach().contiguous().double() for g in (gq, gp, geps)]
+        ptr = [0 if g is None else g.data_ptr() for g in keep]
+        gq0 = torch.empty((self.N, 3), dtype=torch.float64, device=dev)
+        gp0 = torch.empty((self.N, 3), dtype=torch.float64, device=dev)
+        ge0 = torch.empty(self.N, dtype=torch.float64, device=dev)
+        gth = np.zeros(3)
+        _check(sdpd_vv_adjoint(self.h, tape.data_ptr(), tape.numel(), ptr[0] or None, ptr[1] or None,
+                               ptr[2] or None, gq0.data_ptr(), gp0.data_ptr(), ge0.data_ptr(), gth),
+               "sdpd_vv_adjoint")
+        return gq0, gp0, ge0, gth
+
+    def virial(self, grad=False):
+        """Virial pressure of the current state; with grad, also
+        (dP/dq, dP/dp, dP/deps) as CUDA tensors and dP/dtheta."""
+        value = C.c_double(0.0)
+        if not grad:
+            _check(sdpd_virial(self.h, value, None, None, None, None), "sdpd_virial")
+            return value.value
+        torch = self.torch
+        dev = self.workspace.device
+        gq = torch.empty((self.N, 3), dtype=torch.float64, device=dev)
+        gp = torch.empty((self.N, 3), dtype=torch.float64, device=dev)
+        ge = torch.empty(self.N, dtype=torch.float64, device=dev)
+        gth = np.zeros(3)
+        _check(sdpd_virial(self.h, value, gq.data_ptr(), gp.data_ptr(), ge.data_ptr(), gth), "sdpd_virial")
+        return value.value, gq, gp, ge, gth
 
     def observables(self, check=True) -> dict:
         o = sdpd_obs()

@@ -55,8 +55,13 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-n", type=int, default=32, help="lattice sites per axis of the CPU sample")
-    ap.add_argument("--workload", default="fluid", choices=["fluid", "ensemble"],
-                    help="fluid: the single large fluid; ensemble: 256 independent replicas")
+    ap.add_argument("--workload", default="fluid", choices=["fluid", "ensemble", "adjoint"],
+                    help="fluid: the single large fluid; ensemble: 256 independent replicas; "
+                         "adjoint: gradient of the virial pressure after 100 Velocity Verlet steps")
+    ap.add_argument("--adj-n", type=int, default=32, help="adjoint workload: lattice sites per axis")
+    ap.add_argument("--adj-K", type=float, default=100.0)
+    ap.add_argument("--adj-steps", type=int, default=100, help="adjoint workload: Verlet steps per gradient")
+    ap.add_argument("--adj-every", type=int, default=10, help="adjoint workload: checkpoint interval")
     ap.add_argument("--replicas", type=int, default=256)
     return ap.parse_args()
 
@@ -188,9 +193,13 @@ def workload_config(args):
             "l2": "inputs larger than L2 (per-step working set > 129 MB)"}
 
 
-# algorithmic float operations of the two pair passes, per neighbour pair
-# (r < h) visit, and of one pair update of the sweep; see the design doc
-FLOPS_PER_VISIT = {"density_eos": 18.0, "kick1_drift_bin": 24.0, "kick2": 24.0}
+# algorithmic float operations of the pair passes, per neighbour pair (r < h)
+# visit (counted from each kernel's arithmetic: displacement, r^2, sqrt,
+# kernel polynomial, accumulation; adj_pass_* are the reverse passes), and of
+# one pair update of the sweep
+FLOPS_PER_VISIT = {"density_eos": 18.0, "kick1_drift_bin": 24.0, "kick2": 24.0,
+                   "adj_pass_A": 23.0, "adj_pass_B": 66.0}
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 float64, nominal
 FLOPS_PER_PAIR_UPDATE = {"ems": 210.0, "ams": 150.0, "ssa": 140.0}
 
 
@@ -206,6 +215,7 @@ def run_ours(args, rank, world, local_rank):
     prec = sdpd.MIXED if args.precision == "mixed" else sdpd.FP64
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
+        fma = sdpd.sdpd_fma_peak(prec, stream.cuda_stream)
         s = sdpd.SDPD(w.N, w.L, m=w.m, h=w.h, K=w.K, precision=prec, scheme=scheme, stream=stream)
         s.set_state(q, p, e)
         for _ in range(args.warmup):
@@ -238,7 +248,8 @@ def run_ours(args, rank, world, local_rank):
     top_ms, top_launches = stages[top]
     per_launch_s = top_ms * 1e-3 / max(1, top_launches)
     sm_max = (clk or {}).get("sm_max_mhz") or NOMINAL_SM_MHZ
-    alu_peak = SMS * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12  # FP32 TFLOP/s
+    alu_peak = (SMS * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12 if args.precision == "mixed"
+                else FP64_NOMINAL_TFLOPS)  # TFLOP/s of the arithmetic the pair passes use
     if top == "fd_colours":
         units = o1["n_pairs"] / max(1, top_launches)  # pair updates per colour launch
         flops = FLOPS_PER_PAIR_UPDATE[args.scheme] * units
@@ -253,7 +264,8 @@ def run_ours(args, rank, world, local_rank):
         roof = {"kernel": top, "bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s",
                 "frac": ach / alu_peak, "traffic": None,
                 "peak_note": "FP32 FMA peak = 152 SMs x 128 lanes x 2 x %.0f MHz (recipe unit counts, "
-                             "sampled max clock)" % sm_max,
+                             "sampled max clock); measured %s FMA rate %.1f TFLOP/s (sdpd_fma_peak)"
+                             % (sm_max, "float32" if args.precision == "mixed" else "float64", fma / 1e12),
                 "per_launch_ms": per_launch_s * 1e3}
     hbm, hbm_note = hbm_peak()
     bpp = BYTES_PER_PARTICLE_STEP[args.precision]
@@ -384,6 +396,143 @@ def run_ensemble(args, rank, world, local_rank):
         print(json.dumps(line))
 
 
+def adjoint_cpu_sample(args):
+    """The oracle's gradient (forward Verlet steps kept in memory, then the
+    reverse pass; O(N^2) pair loops) on a 16^3 lattice of the same fluid,
+    2 steps."""
+    import oracle as O
+
+    w = Workload(n=16, K=args.adj_K, kT=1.0, seed=0)
+    q, p, e = lattice_state(w)
+    P = O.Config(N=w.N, L=w.L, K=w.K, scheme=O.SCHEME_NONE).params()
+    O.lib()
+    steps = 2
+    t0 = time.perf_counter()
+    O.vv_virial_grad(P, q, p, e, args.dt, steps)
+    dt = time.perf_counter() - t0
+    desc = ("FP64 oracle gradient of the virial pressure (O(N^2) pair loops, single thread), "
+            "16^3 = %d-particle lattice of the same fluid, %d steps, %.1f s" % (w.N, steps, dt))
+    return w.N * steps / dt, 1, desc
+
+
+def run_adjoint(args, rank, world, local_rank):
+    """One bench step = one gradient of the virial pressure after
+    args.adj_steps Velocity Verlet steps (float64, checkpoint every
+    args.adj_every steps) with respect to (q0, p0, eps0, h, c_rho, C_K):
+    set_state from device-resident inputs, the recorded forward run, the
+    virial pressure and its gradient, the reverse pass."""
+    import torch
+    from paper_1707_04232_gb300 import sdpd
+
+    torch.cuda.set_device(local_rank)
+    dev_index = torch.cuda.current_device()
+    w = Workload(n=args.adj_n, K=args.adj_K, kT=1.0, seed=rank)
+    q, p, e = lattice_state(w)
+    ns, every = args.adj_steps, args.adj_every
+    stream = torch.cuda.Stream()
+    steps = max(1, min(args.steps, 5))
+    with torch.cuda.stream(stream):
+        fma64 = sdpd.sdpd_fma_peak(sdpd.FP64, stream.cuda_stream)
+        s = sdpd.SDPD(w.N, w.L, m=w.m, h=w.h, K=w.K, precision=sdpd.FP64, scheme=sdpd.SCHEME_NONE,
+                      stream=stream)
+        qd, pd, ed = (torch.as_tensor(a, device="cuda") for a in (q, p, e))
+
+        def gradient():
+            s.set_state(qd, pd, ed)
+            tape = s.vv_record(args.dt, ns, every)
+            val, gq, gp, ge, gth = s.virial(grad=True)
+            return val, s.vv_adjoint(tape, gq, gp, ge), gth
+
+        for _ in range(max(1, args.warmup)):
+            gradient()
+        torch.cuda.synchronize()
+        s.reset_counters()
+        launches0 = s.kernel_launches
+        s.enable_stage_timing(True)
+        clocks = ClockSampler(dev_index)
+        clocks.start()
+        barrier(world)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        fwd_ms = adj_ms = 0.0
+        torch.cuda.synchronize()
+        ev[0].record(stream)
+        for _ in range(steps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            c = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            s.set_state(qd, pd, ed)
+            tape = s.vv_record(args.dt, ns, every)
+            b.record(stream)
+            val, gq, gp, ge, gth = s.virial(grad=True)
+            g0 = s.vv_adjoint(tape, gq, gp, ge)
+            c.record(stream)
+            c.synchronize()
+            fwd_ms += a.elapsed_time(b)
+            adj_ms += b.elapsed_time(c)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        clk = clocks.stop()
+        ms = ev[0].elapsed_time(ev[1])
+        stages = s.stage_times()
+        launches = s.kernel_launches - launches0
+        nbr_mean = float(s.neighbour_counts().mean())
+    ms_max = allreduce_max(ms, world)
+    value = w.N * ns * steps * world / (ms_max * 1e-3)
+    # roofline of the dominant stage (float64 arithmetic)
+    top = max((k for k in stages if k in FLOPS_PER_VISIT), key=lambda k: stages[k][0])
+    top_ms, top_launches = stages[top]
+    per_launch_s = top_ms * 1e-3 / max(1, top_launches)
+    flops = FLOPS_PER_VISIT[top] * w.N * nbr_mean
+    ach = flops / per_launch_s / 1e12
+    roof = {"kernel": top, "bound": "alu", "achieved": ach, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+            "frac": ach / FP64_NOMINAL_TFLOPS, "traffic": None,
+            "peak_note": "float64 nominal of GB300 (recipe); measured float64 FMA rate %.3f TFLOP/s "
+                         "(sdpd_fma_peak), frac of measured %.3f" % (fma64 / 1e12, ach / (fma64 / 1e12)),
+            "per_launch_ms": per_launch_s * 1e3, "visits_per_launch": w.N * nbr_mean}
+    # end to end: host inputs in, host gradients out
+    qh, ph, eh = (torch.from_numpy(a).pin_memory() for a in (q, p, e))
+    outs = [torch.empty((w.N, 3), dtype=torch.float64).pin_memory() for _ in range(2)]
+    outs.append(torch.empty(w.N, dtype=torch.float64).pin_memory())
+    t0 = time.perf_counter()
+    e2e_steps = 2
+    with torch.cuda.stream(stream):
+        for _ in range(e2e_steps):
+            qd.copy_(qh, non_blocking=True)
+            pd.copy_(ph, non_blocking=True)
+            ed.copy_(eh, non_blocking=True)
+            _, (gq0, gp0, ge0, _), _ = gradient()
+            for o, g in zip(outs, (gq0, gp0, ge0)):
+                o.copy_(g, non_blocking=True)
+        stream.synchronize()
+    e2e_s = allreduce_max(time.perf_counter() - t0, world)
+    line = {
+        "metric": "gradient particle-steps/s (virial pressure after %d Velocity Verlet steps, reverse mode)" % ns,
+        "value": value, "unit": UNIT, "n_gpus": world, "steps": steps, "warmup": args.warmup,
+        "ms_per_step": ms_max / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "adjoint: %d^3 = %d particles, jittered sc lattice, L=%d, Lucy h=2.5a, kT=1, "
+                               "K=%g, dt=%g, %d Verlet steps, checkpoint every %d, float64"
+                               % (w.n, w.N, w.n, w.K, args.dt, ns, every),
+                   "N": w.N, "K": w.K, "steps_per_gradient": ns, "checkpoint_every": every,
+                   "l2": "working set below L2 (the workload is fixed at 32^3)"},
+        "forward_ms_per_gradient": fwd_ms / steps, "reverse_ms_per_gradient": adj_ms / steps,
+        "reverse_over_forward": adj_ms / max(fwd_ms, 1e-9),
+        "roofline": roof,
+        "stages_ms_per_gradient": {k: v[0] / steps for k, v in stages.items()},
+        "gpu_launches": launches, "clocks": clk,
+        "e2e": {"value": w.N * ns * e2e_steps * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 56 * w.N,
+                "d2h_bytes_per_step": 56 * w.N, "steps": e2e_steps,
+                "note": "per gradient: state from pinned host, forward + reverse, gradients to pinned host"},
+        "physics": {"virial_pressure": val, "dP_dtheta(h,c_rho,C_K)": [float(x) for x in g0[3] + gth]},
+    }
+    if rank == 0 and not args.no_cpu and world == 1:
+        ps, threads, desc = adjoint_cpu_sample(args)
+        line["cpu_baseline"] = {"value": ps, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc}
+    if rank == 0:
+        print(json.dumps(line))
+
+
 def run_e2e(args, s, q, p, e, stream, world, N):
     """Each e2e step: host->device copy of the state from pinned memory
     (sdpd_set_state), one time step, device->host copy of the new state
@@ -453,6 +602,8 @@ def main():
         _dist = dist
     if args.workload == "ensemble":
         run_ensemble(args, rank, world, local_rank)
+    elif args.workload == "adjoint":
+        run_adjoint(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
     if world > 1:

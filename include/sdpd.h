@@ -166,10 +166,12 @@ int64_t sdpd_kernel_launches(const sdpd_t* s);
 /* Per-stage timing with CUDA events recorded on the handle's stream around
  * every stage that sdpd_step launches.  Stages: 0 first kick + drift +
  * binning, 1 sort, 2 density + EOS, 3 second kick, 4 sweep schedule,
- * 5 sweep colours (8 launches per sweep).  sdpd_stage_times synchronises and
+ * 5 sweep colours (8 launches per sweep); and of sdpd_vv_adjoint: 6 loading
+ * a stored position (bin, sort, density), 7 pair pass A, 8 pair pass B,
+ * 9 the elementwise steps between them.  sdpd_stage_times synchronises and
  * returns, per stage, the summed milliseconds and the number of kernel
- * launches since timing was enabled (arrays of n entries, n <= 6). */
-#define SDPD_NSTAGES 6
+ * launches since timing was enabled (arrays of n entries, n <= 10). */
+#define SDPD_NSTAGES 10
 int sdpd_enable_stage_timing(sdpd_t* s, int on);
 int sdpd_stage_times(sdpd_t* s, double* ms, int64_t* launches, int n);
 
@@ -283,6 +285,16 @@ int sdpd_vv_adjoint(sdpd_t* s, void* tape, size_t tape_bytes, const double* gq, 
  * state is not changed.  Errors: SDPD_ERR_INVALID_ARG, SDPD_ERR_NO_STATE,
  * SDPD_ERR_CUDA. */
 int sdpd_virial(sdpd_t* s, double* value, double* gq, double* gp, double* geps, double gtheta[3]);
+
+/* Fused multiply-add throughput of the current device, measured -- the paper
+ * has no counterpart; this is the denominator of the arithmetic rooflines of
+ * the pair passes.  precision SDPD_MIXED: float32 FMA, SDPD_FP64: float64
+ * FMA.  Runs 8 blocks of 256 threads per SM, each thread 8 independent FMA
+ * chains, on `stream` (a cudaStream_t, NULL = legacy default stream), times
+ * it with CUDA events after one warm-up launch and writes the achieved
+ * FLOP/s (2 per FMA) to *flops.  Synchronising; allocates nothing.
+ * Errors: SDPD_ERR_INVALID_ARG, SDPD_ERR_CUDA. */
+int sdpd_fma_peak(int precision, void* stream, double* flops);
 
 /* Density pass that allocates nothing -- the paper has no counterpart; this
  * is a service for callers that cannot allocate device memory themselves:

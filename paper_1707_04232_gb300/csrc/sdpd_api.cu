@@ -774,13 +774,18 @@ int sdpd_vv_adjoint(sdpd_t* s, void* tape, size_t tape_bytes, const double* gq, 
   int64_t seg_loaded = -1;
   for (int64_t k = ns; k >= 0; --k) {
     if (k == ns) {
+      StageTimer tm(s, 6, 7);
       load_state(s, t.final_state());
     } else if (k % every == 0) {
+      StageTimer tm(s, 6, 7);
       load_state(s, t.ckpt(k / every));
     } else {
       const int64_t sg = k / every, k0 = sg * every;
       if (sg != seg_loaded) {  // replay the segment from its checkpoint
-        load_state(s, t.ckpt(sg));
+        {
+          StageTimer tm(s, 6, 7);
+          load_state(s, t.ckpt(sg));
+        }
         const int64_t k1 = std::min(k0 + every, ns);
         for (int64_t j = k0 + 1; j < k1; ++j) {
           vv_step<Fp64>(s, dt);
@@ -789,17 +794,31 @@ int sdpd_vv_adjoint(sdpd_t* s, void* tape, size_t tape_bytes, const double* gq, 
         }
         seg_loaded = sg;
       }
+      StageTimer tm(s, 6, 7);
       load_state(s, t.seg(k - k0 - 1));
     }
     const double coef = 0.5 * dt * ((k < ns ? 1 : 0) + (k > 0 ? 1 : 0));
     if (coef != 0.0) {
-      launch_adj_gather(c, s->w, s->cur, t.pbar, coef, t.vs4, st);
+      {
+        StageTimer tm(s, 9, 1);
+        launch_adj_gather(c, s->w, s->cur, t.pbar, coef, t.vs4, st);
+      }
+      StageTimer tm(s, 7, 1);
       launch_adj_pairsum(c, s->w, 0, t.vs4, t.A, st);
     }
-    launch_adj_mid_traj(c, s->w, s->cur, coef != 0.0 ? t.A : nullptr, t.vs4, t.Sbar, t.thbar, geps, k == ns,
-                        k == 0 ? geps0 : nullptr, st);
-    launch_adj_back(c, s->w, s->cur, coef != 0.0 ? 0 : 2, 1.0, t.vs4, 1, t.qbar, t.thbar, st);
-    if (k > 0) launch_adj_axpy(3 * N, dt / c.m, t.qbar, t.pbar, st);
+    {
+      StageTimer tm(s, 9, 1);
+      launch_adj_mid_traj(c, s->w, s->cur, coef != 0.0 ? t.A : nullptr, t.vs4, t.Sbar, t.thbar, geps, k == ns,
+                          k == 0 ? geps0 : nullptr, st);
+    }
+    {
+      StageTimer tm(s, 8, 1);
+      launch_adj_back(c, s->w, s->cur, coef != 0.0 ? 0 : 2, 1.0, t.vs4, 1, t.qbar, t.thbar, st);
+    }
+    if (k > 0) {
+      StageTimer tm(s, 9, 1);
+      launch_adj_axpy(3 * N, dt / c.m, t.qbar, t.pbar, st);
+    }
     s->launches += (coef != 0.0 ? 2 : 0) + 2 + (k > 0 ? 1 : 0);
   }
   if (N > 0) {

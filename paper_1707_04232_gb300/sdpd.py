@@ -78,6 +78,7 @@ SIGNATURES = [
     ("sdpd_vv_adjoint", C.c_int, [_H, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p, C.c_void_p,
                                   C.c_void_p, C.c_void_p, C.c_void_p, _dp]),
     ("sdpd_virial", C.c_int, [_H, _dp, C.c_void_p, C.c_void_p, C.c_void_p, _dp]),
+    ("sdpd_fma_peak", C.c_int, [C.c_int, C.c_void_p, _dp]),
     ("sdpd_strerror", C.c_char_p, [C.c_int]),
 ]
 
@@ -172,8 +173,9 @@ def sdpd_kernel_launches(h) -> int:
     return load().sdpd_kernel_launches(h)
 
 
-NSTAGES = 6
-STAGE_NAMES = ["kick1_drift_bin", "sort", "density_eos", "kick2", "fd_schedule", "fd_colours"]
+NSTAGES = 10
+STAGE_NAMES = ["kick1_drift_bin", "sort", "density_eos", "kick2", "fd_schedule", "fd_colours",
+               "adj_load", "adj_pass_A", "adj_pass_B", "adj_elementwise"]
 
 
 def sdpd_enable_stage_timing(h, on) -> int:
@@ -239,6 +241,13 @@ def sdpd_vv_adjoint(h, tape_ptr, nbytes, gq, gp, geps, gq0, gp0, geps0, gtheta) 
 def sdpd_virial(h, value, gq, gp, geps, gtheta) -> int:
     th = gtheta.ctypes.data_as(_dp) if gtheta is not None else None
     return load().sdpd_virial(h, C.byref(value), gq, gp, geps, th)
+
+
+def sdpd_fma_peak(precision, stream: int = 0) -> float:
+    """Measured FMA throughput of the current device in FLOP/s."""
+    out = C.c_double(0.0)
+    _check(load().sdpd_fma_peak(precision, stream, C.byref(out)), "sdpd_fma_peak")
+    return out.value
 
 
 def sdpd_destroy(h):

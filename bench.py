@@ -263,9 +263,11 @@ def run_ours(args, rank, world, local_rank):
         ach = flops / per_launch_s / 1e12
         roof = {"kernel": top, "bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s",
                 "frac": ach / alu_peak, "traffic": None,
-                "peak_note": "FP32 FMA peak = 152 SMs x 128 lanes x 2 x %.0f MHz (recipe unit counts, "
-                             "sampled max clock); measured %s FMA rate %.1f TFLOP/s (sdpd_fma_peak)"
-                             % (sm_max, "float32" if args.precision == "mixed" else "float64", fma / 1e12),
+                "peak_note": ("FP32 FMA peak = 152 SMs x 128 lanes x 2 x %.0f MHz (recipe unit counts, "
+                              "sampled max clock)" % sm_max if args.precision == "mixed" else
+                              "float64 nominal of GB300 (recipe)")
+                             + "; measured %s FMA rate %.2f TFLOP/s (sdpd_fma_peak)"
+                             % ("float32" if args.precision == "mixed" else "float64", fma / 1e12),
                 "per_launch_ms": per_launch_s * 1e3}
     hbm, hbm_note = hbm_peak()
     bpp = BYTES_PER_PARTICLE_STEP[args.precision]

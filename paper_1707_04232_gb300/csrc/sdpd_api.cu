@@ -158,6 +158,7 @@ size_t layout(sdpd_handle* s, Workspace* w, char* base) {
     w->id[k] = (int32_t*)at(N * sizeof(int32_t));
   }
   w->qp4 = at(N * sizeof(V4));
+  w->qf4 = P::mixed ? nullptr : (float4*)at(N * sizeof(float4));
   w->nlist = (uint32_t*)at(N * (size_t)c.nbr_cap * 4);
   w->nn = (int32_t*)at(N * 4);
   w->nbr_off = (uint8_t*)at(N * 28);
@@ -409,6 +410,24 @@ int sdpd_create(int64_t N, const double box[3], double m, double h, double K, co
   }
   c.W0 = c.cW;
   c.nbr_cap = 160;
+  {
+    // Float32 pre-test of r^2 < h^2 (float64 path).  With u = 2^-24, each
+    // float32 coordinate, the float32 difference and the float32 minimum
+    // image are within D = 8 u L_max of the float64 displacement's image
+    // (three conversions and three roundings of size <= u L, with margin; an
+    // image chosen differently only where both images are within D of L/2),
+    // so |d_f| <= |d| + 3D per axis and the float32 r_f^2 <= (1 + 8u)
+    // (r + 3 sqrt(3) D)^2.  Hence r < h implies r_f^2 < h2_filter below.
+    const double u = 0x1.0p-24;
+    const double Lmax = std::max(c.L[0], std::max(c.L[1], c.L[2]));
+    const double D = 8.0 * u * Lmax;
+    const double rf = h + 3.0 * sqrt(3.0) * D;
+    c.h2_filter = nextafterf((float)((1.0 + 8.0 * u) * rf * rf), INFINITY);
+    for (int d = 0; d < 3; ++d) {
+      c.Lf[d] = (float)c.L[d];
+      c.halfLf[d] = 0.5f * c.Lf[d];
+    }
+  }
   c.kernel = prm->kernel;
   c.scheme = prm->scheme;
   s->prm = *prm;

@@ -39,6 +39,11 @@ struct Consts {
   double cW, cF, W0;         // kernel constants and W(0)
   int kernel, scheme;
   int nbr_cap;               // neighbour-list entries per particle
+  // float64 path: float32 pre-test of the neighbour predicate.  A candidate
+  // whose float32 r^2 (from float32 copies of the positions) is >= h2_filter
+  // has r^2 >= h^2 in float64 (bound on the conversion and rounding errors
+  // set on the host), so it is skipped without float64 arithmetic.
+  float Lf[3], halfLf[3], h2_filter;
 };
 
 // Neighbour-list entry: neighbour index << 6 | stencil offset code, the code
@@ -232,6 +237,7 @@ struct Workspace {
   void* rho[2];
   int32_t* id[2];
   void* qp4;            // sorted (x, y, z, pi): positions and p/rho^2 for force passes
+  float4* qf4;          // float64 path: float32 copies (x, y, z, 0) of the sorted positions
   uint32_t* nlist;      // neighbour lists, entry k of particle i at nlist[i * nbr_cap + k]
   int32_t* nn;          // neighbour count per particle
   uint8_t* nbr_off;     // [N][28]: start of each of the 27 stencil cells' entries in the row, then the end

@@ -103,12 +103,15 @@ __global__ void __launch_bounds__(128) k_density(Consts c, Arrays<P> a, typename
                                                  const uint32_t* __restrict__ xmz, int update_eos,
                                                  int32_t* __restrict__ ncount_by_id,
                                                  uint32_t* __restrict__ nlist, int32_t* __restrict__ nn,
-                                                 uint8_t* __restrict__ nbr_off, int* __restrict__ status) {
+                                                 uint8_t* __restrict__ nbr_off, int* __restrict__ status,
+                                                 const float4* __restrict__ qf4) {
   using R = typename P::R;
   using V4 = typename P::V4;
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= c.N) return;
   const V4 qi = ld4(&a.q4[i]);
+  float4 fi = make_float4(0.f, 0.f, 0.f, 0.f);
+  if constexpr (!P::mixed) fi = qf4[i];
   int cx, cy, cz;
   unpack_cell(w_to_cellbits(qi.w), cx, cy, cz);
   Home<P> home;
@@ -132,6 +135,14 @@ __global__ void __launch_bounds__(128) k_density(Consts c, Arrays<P> a, typename
 #pragma unroll 4
         for (int j = beg; j < end; ++j) {
           if (j == i) continue;
+          if constexpr (!P::mixed) {  // float32 pre-test: skips only pairs with r >= h
+            const float4 fj = __ldg(&qf4[j]);
+            float ex = fi.x - fj.x, ey = fi.y - fj.y, ez = fi.z - fj.z;
+            ex = ex > c.halfLf[0] ? ex - c.Lf[0] : (ex < -c.halfLf[0] ? ex + c.Lf[0] : ex);
+            ey = ey > c.halfLf[1] ? ey - c.Lf[1] : (ey < -c.halfLf[1] ? ey + c.Lf[1] : ey);
+            ez = ez > c.halfLf[2] ? ez - c.Lf[2] : (ez < -c.halfLf[2] ? ez + c.Lf[2] : ez);
+            if (ex * ex + ey * ey + ez * ez >= c.h2_filter) continue;
+          }
           const V4 qj = ld4(&a.q4[j]);
           R dx, dy, dz;
           home.disp(qj, dx, dy, dz);
@@ -273,11 +284,11 @@ void launch_density(const Consts& c, const Workspace& w, int cur, int update_eos
   if (c.kernel == SDPD_KERNEL_LUCY)
     k_density<P, SDPD_KERNEL_LUCY><<<blocks_for(c.N, 128), 128, 0, s>>>(
         c, a, qp4, w.cell_start, w.mrank, w.xmin[0], w.xmin[1], w.xmin[2], update_eos, ncount_by_id, w.nlist,
-        w.nn, w.nbr_off, w.status);
+        w.nn, w.nbr_off, w.status, w.qf4);
   else
     k_density<P, SDPD_KERNEL_CUBIC><<<blocks_for(c.N, 128), 128, 0, s>>>(
         c, a, qp4, w.cell_start, w.mrank, w.xmin[0], w.xmin[1], w.xmin[2], update_eos, ncount_by_id, w.nlist,
-        w.nn, w.nbr_off, w.status);
+        w.nn, w.nbr_off, w.status, w.qf4);
 }
 
 template <class P>

@@ -169,7 +169,8 @@ __global__ void k_gather(Consts c, const int32_t* __restrict__ tmp, const int32_
                          const uint32_t* __restrict__ rcoord, const typename P::Q* __restrict__ qdx,
                          const typename P::Q* __restrict__ qdy, const typename P::Q* __restrict__ qdz,
                          Arrays<P> src, Arrays<P> dst, const uint32_t* __restrict__ xmx,
-                         const uint32_t* __restrict__ xmy, const uint32_t* __restrict__ xmz) {
+                         const uint32_t* __restrict__ xmy, const uint32_t* __restrict__ xmz,
+                         float4* __restrict__ qf4) {
   using V4 = typename P::V4;
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= c.N) return;
@@ -194,6 +195,7 @@ __global__ void k_gather(Consts c, const int32_t* __restrict__ tmp, const int32_
     v.z = __uint2float_rn(z - xmz[cz]) * (float)c.scale[2];
   } else {
     v.x = x; v.y = y; v.z = z;
+    qf4[d] = make_float4((float)x, (float)y, (float)z, 0.0f);
   }
   v.w = cellbits_to_w(cb, (V4*)nullptr);
   st4(&dst.q4[d], v);
@@ -250,7 +252,7 @@ void launch_sort(const Consts& c, const Workspace& w, int from, cudaStream_t s) 
   k_gather<P><<<blocks_for(c.N, 256), 256, 0, s>>>(
       c, w.tmp, w.tmp + c.N, w.key, w.cell_start, w.rcoord, (const typename P::Q*)w.qdx,
       (const typename P::Q*)w.qdy, (const typename P::Q*)w.qdz, src, dst, w.xmin[0], w.xmin[1],
-      w.xmin[2]);
+      w.xmin[2], w.qf4);
 }
 
 template <class P>

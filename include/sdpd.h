@@ -73,7 +73,9 @@ typedef struct {
   int fd_only;   /* 1: skip Velocity Verlet, run the fluctuation/dissipation sweep
                     only (Section 4.1) */
   int theta;     /* multiple time step ratio (Section 4.2): one sweep with time
-                    step theta*dt after every theta Verlet steps; 1 = single step */
+                    step theta*dt after each Verlet step whose count since
+                    sdpd_set_state is a multiple of theta (however the steps
+                    are split over sdpd_step calls); 1 = single step */
   int debug;     /* 1: reserve workspace for per-pair records (sdpd_debug_get) */
 } sdpd_params;
 
@@ -160,7 +162,9 @@ int64_t sdpd_get_fd_step(const sdpd_t* s);
 int sdpd_reset_counters(sdpd_t* s);
 
 /* Number of CUDA kernels the handle has launched so far (a VV step launches
- * 8, a sweep 12, sdpd_set_state 8, sdpd_observables 2). */
+ * 8, a sweep 9 plus 3 when its schedule is rebuilt -- it is reused while the
+ * positions do not change, as in FD-only runs -- sdpd_set_state 8,
+ * sdpd_observables 2). */
 int64_t sdpd_kernel_launches(const sdpd_t* s);
 
 /* Per-stage timing with CUDA events recorded on the handle's stream around
@@ -174,6 +178,19 @@ int64_t sdpd_kernel_launches(const sdpd_t* s);
 #define SDPD_NSTAGES 10
 int sdpd_enable_stage_timing(sdpd_t* s, int on);
 int sdpd_stage_times(sdpd_t* s, double* ms, int64_t* launches, int n);
+
+/* Histogram of the internal energies of the current state, for the
+ * statistics of FD-only runs: the distribution of eps against the Gamma
+ * marginal of Eq. (dist-analytic) and its error, Eq. (error-dist)
+ * (Section 5.1).  With x_i = eps_i * scale and w = (hi - lo) / nbins, adds
+ * to counts (device memory, nbins + 2 uint64 entries, owned by the caller):
+ * counts[b] += #{i : lo + b w <= x_i < lo + (b + 1) w} for b < nbins
+ * (b = floor((x - lo) / w) in float64, capped at nbins - 1),
+ * counts[nbins] += #{x_i < lo}, counts[nbins + 1] += #{x_i >= hi or not
+ * finite}.  Asynchronous on the handle's stream.  Errors:
+ * SDPD_ERR_INVALID_ARG (nbins outside 1..4096, hi <= lo, non-finite bounds),
+ * SDPD_ERR_NO_STATE. */
+int sdpd_energy_histogram(sdpd_t* s, double lo, double hi, int nbins, double scale, unsigned long long* counts);
 
 /* Debug read-outs (synchronising).  what:
  *  SDPD_DEBUG_ORDER   int64[N]   ids in storage order (Morton order of cells, then id)
@@ -211,25 +228,27 @@ void sdpd_destroy(sdpd_t* s);
 /* Ensembles: many independent systems of uneven size and parameters stepped
  * together (the paper treats one system; independent replicas are how the
  * method is sampled in practice).  Each member is an ordinary handle with a
- * bound workspace and a loaded state, with theta = 1, stage timing off and
- * debug off.  Members may share streams (they then run one after the other)
- * but not the ensemble's stream.  stream: the stream the ensemble launches
- * on; NULL makes the ensemble create a non-blocking stream of its own
- * (sdpd_ensemble_stream returns it).  sdpd_ensemble_step advances every
- * member by nsteps steps with its own seed (seeds[i] for member i).  Two
- * steps of all members are captured once into one CUDA graph (forked from and
- * joined into the ensemble stream; the capture is redone when dt or the seeds
- * change) and the graph is replayed nsteps/2 times; an odd last step is
- * enqueued directly.  Every member's result is the same as stepping it
- * alone.  The members' own streams wait for the ensemble's work before later
- * calls on them run.  Asynchronous.
+ * bound workspace and a loaded state, with stage timing off and debug off;
+ * members may use multiple time steps (theta).  Members may share streams
+ * (they then run one after the other) but not the ensemble's stream.
+ * stream: the stream the ensemble launches on; NULL makes the ensemble create
+ * a non-blocking stream of its own (sdpd_ensemble_stream returns it).
+ * sdpd_ensemble_step advances every member by nsteps steps with its own seed
+ * (seeds[i] for member i).  U = lcm(2, theta of every member) steps of all
+ * members are captured once into one CUDA graph (forked from and joined into
+ * the ensemble stream; the capture is redone when dt, the seeds or a
+ * member's step count modulo its theta change) and the graph is replayed
+ * nsteps/U times; the nsteps mod U last steps are enqueued directly.  Every
+ * member's result is the same as stepping it alone.  The members' own
+ * streams wait for the ensemble's work before later calls on them run.
+ * Asynchronous.
  * Errors: SDPD_ERR_INVALID_ARG (bad or repeated member, a member on the
- * ensemble's stream, theta != 1, timing or debug on), SDPD_ERR_NO_WORKSPACE,
+ * ensemble's stream, timing or debug on, U > 64), SDPD_ERR_NO_WORKSPACE,
  * SDPD_ERR_CUDA. */
 typedef struct sdpd_ensemble sdpd_ens_t;
 int sdpd_ensemble_create(sdpd_t* const* members, int n, void* stream, sdpd_ens_t** out);
 int sdpd_ensemble_step(sdpd_ens_t* e, double dt, int64_t nsteps, const uint64_t* seeds);
-/* Kernel launches of the captured two-step graph (all members). */
+/* Kernel launches of the captured U-step graph (all members). */
 int64_t sdpd_ensemble_kernel_nodes(const sdpd_ens_t* e);
 /* The ensemble's stream (a cudaStream_t). */
 void* sdpd_ensemble_stream(const sdpd_ens_t* e);

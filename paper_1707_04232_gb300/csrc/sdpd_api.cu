@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <new>
+#include <numeric>
 #include <vector>
 
 #include "sdpd_internal.cuh"
@@ -23,6 +24,9 @@ struct sdpd_handle {
   bool has_state;
   int64_t fd_step, vv_step;
   int64_t launches;
+  // the sweep schedule on the device matches the current positions (it
+  // depends on them only; it is reused by the sweeps of FD-only runs)
+  bool sched_valid = false;
   std::vector<int32_t> mrank_h;
   std::vector<uint32_t> rcoord_h;
   std::vector<uint32_t> xmin_h[3];
@@ -218,6 +222,7 @@ void do_load(sdpd_handle* s) {
   s->cur = 1;
   launch_density<P>(s->c, s->w, s->cur, 0, nullptr, s->stream);
   s->launches += 7;
+  s->sched_valid = false;
 }
 
 cudaEvent_t take_event(sdpd_handle* s) {
@@ -291,6 +296,7 @@ void vv_step(sdpd_handle* s, double dt) {
   }
   s->launches += 8;
   s->vv_step++;
+  s->sched_valid = false;
 }
 
 template <class P>
@@ -300,20 +306,23 @@ void do_steps(sdpd_handle* s, double dt, int64_t nsteps, uint64_t seed) {
   const bool fd = s->prm.scheme != SDPD_SCHEME_NONE;
   for (int64_t n = 0; n < nsteps; ++n) {
     if (!s->prm.fd_only) vv_step<P>(s, dt);
-    if (fd && (s->prm.fd_only || (n + 1) % theta == 0)) {
+    // MTS: one sweep after every theta-th Verlet step since sdpd_set_state
+    if (fd && (s->prm.fd_only || s->vv_step % theta == 0)) {
       const double dt_fd = s->prm.fd_only ? dt : theta * dt;
       const int rec = s->w.pair_recs != nullptr;
       if (rec) cudaMemsetAsync(s->w.pair_rec_count, 0, 8, s->stream);
-      {
+      if (!s->sched_valid) {  // positions unchanged since the last sweep: reuse it
         StageTimer t(s, 4, 3);
         launch_fd_schedule<P>(c, s->w, s->cur, s->stream);
+        s->launches += 3;
+        s->sched_valid = true;
       }
       {
         StageTimer t(s, 5, 8);
         launch_fd_colours<P>(c, s->w, s->cur, dt_fd, seed, rec, s->stream);
       }
       launch_advance_sweep(s->w, s->stream);
-      s->launches += 12;
+      s->launches += 9;
       s->fd_step++;
     }
   }
@@ -485,6 +494,7 @@ int sdpd_bind_workspace(sdpd_t* s, void* ptr, size_t bytes) {
   s->device = attr.device;
   if (use_device(s) != SDPD_OK) return SDPD_ERR_CUDA;
   s->ws = (char*)ptr;
+  s->sched_valid = false;
   layout_any(s, &s->w, s->ws);
   const Consts& c = s->c;
   cudaStream_t st = s->stream;
@@ -720,6 +730,7 @@ void load_state(sdpd_handle* s, const double* slot) {
   s->cur = 1;
   launch_density<Fp64>(s->c, s->w, s->cur, 0, nullptr, s->stream);
   s->launches += 7;
+  s->sched_valid = false;
 }
 
 int check_adjoint_handle(sdpd_handle* s) {
@@ -887,6 +898,18 @@ int sdpd_virial(sdpd_t* s, double* value, double* gq, double* gp, double* geps, 
   return e;
 }
 
+int sdpd_energy_histogram(sdpd_t* s, double lo, double hi, int nbins, double scale, unsigned long long* counts) {
+  if (!s) return SDPD_ERR_INVALID_ARG;
+  if (!s->ws) return SDPD_ERR_NO_WORKSPACE;
+  if (!s->has_state) return SDPD_ERR_NO_STATE;
+  if (!counts || nbins < 1 || nbins > 4096 || !isfinite(lo) || !isfinite(hi) || !(hi > lo) || !isfinite(scale))
+    return SDPD_ERR_INVALID_ARG;
+  if (use_device(s) != SDPD_OK) return SDPD_ERR_CUDA;
+  launch_energy_hist(s->c, s->w, s->cur, lo, hi, nbins, scale, counts, s->stream);
+  s->launches += s->c.N > 0 ? 1 : 0;
+  return launch_status();
+}
+
 int sdpd_debug_get(sdpd_t* s, int what, void* dst, int64_t cap, int64_t* count) {
   if (!s || !dst) return SDPD_ERR_INVALID_ARG;
   if (!s->ws) return SDPD_ERR_NO_WORKSPACE;
@@ -995,6 +1018,9 @@ int sdpd_debug_get(sdpd_t* s, int what, void* dst, int64_t cap, int64_t* count) 
 // ---------------------------------------------------------------------------
 // Ensembles of independent systems stepped by one CUDA graph.
 // ---------------------------------------------------------------------------
+// longest graph replay unit (steps) of an ensemble: lcm(2, theta_i)
+constexpr int64_t kMaxEnsembleUnit = 64;
+
 struct sdpd_ensemble {
   std::vector<sdpd_handle*> m;
   cudaStream_t stream;
@@ -1006,6 +1032,8 @@ struct sdpd_ensemble {
   double dt;
   std::vector<uint64_t> seeds;
   int64_t launches_per_unit;
+  int64_t unit;                  // steps per graph replay: lcm of 2 and the members' theta
+  std::vector<int64_t> phase;    // members' vv_step mod theta when the graph was captured
 };
 
 namespace {
@@ -1053,14 +1081,19 @@ int sdpd_ensemble_create(sdpd_t* const* members, int n, void* stream, sdpd_ens_t
   e->dt = 0.0;
   for (int i = 0; i < n; ++i) {
     sdpd_handle* h = members[i];
-    if (!h || !h->ws || !h->has_state || h->prm.theta != 1 || h->timing || h->w.pair_recs ||
-        h->stream == e->stream) {
+    if (!h || !h->ws || !h->has_state || h->timing || h->w.pair_recs || h->stream == e->stream) {
       delete e;
       return !h || h->ws ? SDPD_ERR_INVALID_ARG : SDPD_ERR_NO_WORKSPACE;
     }
     for (int j = 0; j < i; ++j)
       if (members[j] == h) { delete e; return SDPD_ERR_INVALID_ARG; }
     e->m.push_back(h);
+  }
+  e->unit = 2;
+  for (sdpd_handle* h : e->m) {
+    const int64_t th = std::max(1, h->prm.theta);
+    e->unit = e->unit / std::gcd(e->unit, th) * th;
+    if (e->unit > kMaxEnsembleUnit) { delete e; return SDPD_ERR_INVALID_ARG; }
   }
   if (use_device(e->m[0]) != SDPD_OK || cudaEventCreateWithFlags(&e->fork, cudaEventDisableTiming) != cudaSuccess) {
     delete e;
@@ -1086,22 +1119,27 @@ int sdpd_ensemble_step(sdpd_ens_t* e, double dt, int64_t nsteps, const uint64_t*
   // the ensemble stream waits for everything already enqueued on the members
   for (sdpd_handle* h : e->m)
     if (order_streams(h->stream, e->stream) != SDPD_OK) return SDPD_ERR_CUDA;
-  const int64_t units = nsteps / 2;
+  const int64_t U = e->unit;
+  const int64_t units = nsteps / U;
   const std::vector<uint64_t> sv(seeds, seeds + e->m.size());
+  std::vector<int64_t> phase;
+  for (sdpd_handle* h : e->m) phase.push_back(h->vv_step % std::max(1, h->prm.theta));
   if (units > 0) {
-    if (!e->exec || e->dt != dt || e->seeds != sv) {
+    if (!e->exec || e->dt != dt || e->seeds != sv || e->phase != phase) {
       if (e->exec) { cudaGraphExecDestroy(e->exec); e->exec = nullptr; }
       if (e->graph) { cudaGraphDestroy(e->graph); e->graph = nullptr; }
-      // capture two steps: each step's sort flips the double-buffered
-      // state, so after two steps every member is back in its buffer and
-      // the graph can be replayed; host bookkeeping is restored after capture
+      // capture U steps: each step's sort flips the double-buffered state,
+      // so after an even number of steps every member is back in its
+      // buffer, and U is a multiple of every member's theta, so the sweeps
+      // fall on the same steps of every replay; host bookkeeping is
+      // restored after capture
       std::vector<int> cur0;
       std::vector<int64_t> fd0, vv0, l0;
       for (sdpd_handle* h : e->m) {
         cur0.push_back(h->cur); fd0.push_back(h->fd_step); vv0.push_back(h->vv_step); l0.push_back(h->launches);
       }
       if (cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return SDPD_ERR_CUDA;
-      ensemble_enqueue(e, dt, 2, seeds);
+      ensemble_enqueue(e, dt, U, seeds);
       cudaError_t ce = cudaStreamEndCapture(e->stream, &e->graph);
       e->launches_per_unit = 0;
       for (size_t i = 0; i < e->m.size(); ++i) {
@@ -1115,17 +1153,20 @@ int sdpd_ensemble_step(sdpd_ens_t* e, double dt, int64_t nsteps, const uint64_t*
       }
       e->dt = dt;
       e->seeds = sv;
+      e->phase = phase;
     }
     for (int64_t u = 0; u < units; ++u)
       if (cudaGraphLaunch(e->exec, e->stream) != cudaSuccess) return SDPD_ERR_CUDA;
     for (sdpd_handle* h : e->m) {
-      if (!h->prm.fd_only) h->vv_step += 2 * units;
-      if (h->prm.scheme != SDPD_SCHEME_NONE) h->fd_step += 2 * units;
+      if (!h->prm.fd_only) h->vv_step += U * units;
+      if (h->prm.scheme != SDPD_SCHEME_NONE)
+        h->fd_step += h->prm.fd_only ? U * units : U / std::max(1, h->prm.theta) * units;
+      h->sched_valid = h->prm.fd_only ? true : false;
     }
     const int64_t per_member = e->launches_per_unit / (int64_t)e->m.size();
     for (sdpd_handle* h : e->m) h->launches += per_member * units;
   }
-  if (nsteps % 2) ensemble_enqueue(e, dt, 1, seeds);
+  if (nsteps % U) ensemble_enqueue(e, dt, nsteps % U, seeds);
   // later calls on a member's own stream see the ensemble's work
   for (sdpd_handle* h : e->m)
     if (order_streams(e->stream, h->stream) != SDPD_OK) return SDPD_ERR_CUDA;

@@ -333,6 +333,10 @@ void launch_adj_back(const Consts& c, const Workspace& w, int cur, int mode, dou
                      int accumulate, double* qbar, double* thbar, cudaStream_t s);
 void launch_adj_axpy(int64_t n, double a, const double* x, double* y, cudaStream_t s);
 size_t adj_sum_partial_doubles();
+// histogram of eps * scale (sdpd_stats.cu): nbins bins over [lo, hi), then
+// the counts below lo and at or above hi; adds into counts[nbins + 2]
+void launch_energy_hist(const Consts& c, const Workspace& w, int cur, double lo, double hi, int nbins,
+                        double scale, unsigned long long* counts, cudaStream_t s);
 void launch_adj_sum(const double* x, int64_t n, int ncols, double* partial, double* out, cudaStream_t s);
 
 }  // namespace sdpd

@@ -79,6 +79,7 @@ SIGNATURES = [
                                   C.c_void_p, C.c_void_p, C.c_void_p, _dp]),
     ("sdpd_virial", C.c_int, [_H, _dp, C.c_void_p, C.c_void_p, C.c_void_p, _dp]),
     ("sdpd_fma_peak", C.c_int, [C.c_int, C.c_void_p, _dp]),
+    ("sdpd_energy_histogram", C.c_int, [_H, C.c_double, C.c_double, C.c_int, C.c_double, C.c_void_p]),
     ("sdpd_strerror", C.c_char_p, [C.c_int]),
 ]
 
@@ -331,6 +332,16 @@ class SDPD:
 
     def sync(self):
         return sdpd_sync(self.h)
+
+    def energy_histogram(self, lo, hi, nbins, scale=1.0, counts=None):
+        """Add the histogram of eps * scale over nbins bins of [lo, hi) (then
+        the counts below lo and at or above hi) into ``counts``, a CUDA int64
+        tensor of nbins + 2 entries (allocated zeroed when None); returns it."""
+        if counts is None:
+            counts = self.torch.zeros(nbins + 2, dtype=self.torch.int64, device=self.workspace.device)
+        _check(load().sdpd_energy_histogram(self.h, float(lo), float(hi), int(nbins), float(scale),
+                                            counts.data_ptr()), "sdpd_energy_histogram")
+        return counts
 
     # -- gradients of the conservative dynamics (float64 handles) ----------
 

@@ -77,3 +77,33 @@ def test_ensemble_member_matches_oracle():
     L = w.L
     assert np.abs((qg - qo + 0.5 * L) % L - 0.5 * L).max() < 1e-6
     assert np.abs(eg - eo).max() < 1e-6 * eo.max()
+
+
+def make_mts(n, K, kT, prec, seed, theta):
+    w = Workload(n=n, K=K, kT=kT, seed=seed)
+    q, p, e = lattice_state(w)
+    s = sdpd.SDPD(w.N, w.L, m=w.m, h=w.h, K=w.K, precision=prec, theta=theta, stream=torch.cuda.Stream())
+    s.set_state(q, p, e)
+    return s
+
+
+@pytest.mark.parametrize("nsteps,split", [(30, [30]), (37, [7, 30]), (65, [13, 52])])
+def test_ensemble_with_multiple_time_steps(nsteps, split):
+    """Members with theta = 3 and 5 (graph unit lcm(2, 3, 5) = 30 steps):
+    bitwise equal to each member stepped alone one step per call, also when
+    a call leaves the members at another phase of their theta cycle."""
+    spec = [(10, 5.0, 1.0, sdpd.FP64, 3), (12, 20.0, 0.5, sdpd.MIXED, 5), (11, 100.0, 1.0, sdpd.MIXED, 1)]
+    seeds = [5, 6, 7]
+    ens_m = [make_mts(n, K, kT, pr, k, th) for k, (n, K, kT, pr, th) in enumerate(spec)]
+    alone = [make_mts(n, K, kT, pr, k, th) for k, (n, K, kT, pr, th) in enumerate(spec)]
+    ens = sdpd.SDPDEnsemble(ens_m)
+    for part in split:
+        ens.step(0.005, part, seeds)
+    for s, a, seed, sp in zip(ens_m, alone, seeds, spec):
+        for _ in range(nsteps):
+            a.step(0.005, 1, seed=seed)
+        x, y = s.get_state(), a.get_state()
+        assert all((u == v).all() for u, v in zip(x, y))
+        os_, oa = s.observables(), a.observables()
+        assert os_["fd_step"] == oa["fd_step"] == nsteps // sp[4]
+        assert os_["vv_step"] == nsteps

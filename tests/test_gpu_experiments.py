@@ -1,0 +1,69 @@
+"""The paper's experiments of Section 5 on the GPU, at test size.
+
+FD-only statistics (Section 5.1): with the exact Metropolis scheme the only
+error of the internal-energy distribution is statistical, so the error of
+Eq. (error-dist) against the Gamma marginal of Eq. (dist-analytic) must stay
+within a few times the floor of independent sampling; the approximate scheme
+shows no bias at dt = 1 t_K either; EMS rejects more than AMS and more at
+larger steps; SSA breaks down (negative internal energy) at K = 5 where the
+Metropolised schemes stay stable.  The rejection rates themselves depend on
+the viscosity, which the paper gives in SI units only, so their values are
+not compared with the paper's.  The multiple-time-step driver runs and
+reports finite drift slopes.
+"""
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+pytest.importorskip("scipy")
+
+from paper_1707_04232_gb300 import experiments as X  # noqa: E402
+
+
+def test_gamma_bins_sum_to_one():
+    p = X.gamma_bin_probabilities(6.0, 1.0, 1e-9, 200.0, 1000)
+    assert abs(p.sum() - 1.0) < 1e-12
+
+
+def test_reduced_time_unit():
+    # m = 1, a = 1, kT = 1: t_K = 1 / sqrt(K)
+    assert abs(X.reduced_time_unit(5.0) - 1 / math.sqrt(5.0)) < 1e-15
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_fd_statistics_ems_and_ams(precision):
+    rows = {}
+    for scheme in ("ems", "ams"):
+        for dt in (1.0, 5.0):
+            r = X.fd_statistics(scheme, dt, n=20, K=5.0, precision=precision, n_configs=30)
+            assert not r["unstable"], r
+            rows[scheme, dt] = r
+    for (scheme, dt), r in rows.items():
+        d = r["distribution"]
+        assert d["error"] < 4.0 * d["floor_independent"] + 0.01, (scheme, dt, d)
+    ems1, ems5 = rows["ems", 1.0]["rejection"], rows["ems", 5.0]["rejection"]
+    ams1, ams5 = rows["ams", 1.0]["rejection"], rows["ams", 5.0]["rejection"]
+    assert 0 < ems1["total"] < ems5["total"] < 0.1
+    assert ams1["metropolis"] == 0 and ams5["metropolis"] == 0
+    assert ams5["total"] < ems5["total"]
+
+
+def test_ssa_breaks_down_where_metropolis_does_not():
+    ssa = X.fd_statistics("ssa", 5.0, n=20, K=5.0, n_configs=5)
+    assert ssa["unstable"]
+    ems = X.fd_statistics("ems", 5.0, n=20, K=5.0, n_configs=5)
+    assert not ems["unstable"]
+
+
+def test_mts_drift_runs():
+    r = X.mts_drift(0.392, thetas=(1, 5), replicas=3, t_sim=40.0, n_samples=10)
+    for th in ("1", "5"):
+        assert np.isfinite(r["slopes"][th]["mean"])
+        assert r["status"][th] == ["ok"]
+    assert np.isfinite(r["ratio_to_sts"]["5"])

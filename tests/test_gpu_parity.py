@@ -217,6 +217,78 @@ def test_trajectory_fp64_10_steps(kind, scheme, theta):
     assert obs["fd_step"] == nfd
 
 
+def test_mts_sweeps_follow_the_step_count_not_the_call():
+    """With theta = 5 a sweep follows every 5th Verlet step since
+    set_state, however the steps are split over calls; the result equals the
+    oracle's 10-step run."""
+    q, p, e, L, K = system("lattice1000")
+    N = len(e)
+    a = gpu(N, L, K, theta=5)
+    a.set_state(q, p, e)
+    for part in (1, 3, 2, 4):
+        a.step(DT, part, seed=3)
+    b = gpu(N, L, K, theta=5)
+    b.set_state(q, p, e)
+    b.step(DT, 10, seed=3)
+    x, y = a.get_state(), b.get_state()
+    assert all((u == v).all() for u, v in zip(x, y))
+    assert a.observables()["fd_step"] == 2
+
+
+@pytest.mark.parametrize("precision", [sdpd.FP64, sdpd.MIXED])
+def test_fd_only_sweeps_reuse_the_schedule(precision):
+    """FD-only: positions never move, so the sweep schedule built for the
+    first sweep serves the later ones; 4 sweeps match the oracle's (float64:
+    within 1e-9; mixed: per observable)."""
+    q, p, e, L, K = system("lattice_cold_K5")
+    N = len(e)
+    s = gpu(N, L, K, precision=precision, fd_only=True)
+    s.set_state(q, p, e)
+    s.reset_counters()
+    l0 = s.kernel_launches
+    s.step(0.2, 4, seed=5)
+    assert s.kernel_launches - l0 == 3 + 4 * 9  # one schedule, four sweeps
+    qg, pg, eg = s.get_state()
+    P = oparams(N, L, K)
+    st, qo, po, eo, stats, _ = O.run(P, q, p, e, 0.2, 4, seed=5, fd_only=True)
+    if precision == sdpd.FP64:
+        assert np.array_equal(qg, q)
+    else:  # positions held in 32-bit fixed point: within one unit L / 2^32
+        assert min_image_err(qg, q, L) <= max(L) * 2.0 ** -32
+    if precision == sdpd.FP64:
+        assert np.abs(pg - po).max() < 1e-9 * np.abs(po).max()
+        assert np.abs(eg - eo).max() < 1e-9 * eo.max()
+    else:
+        o_g, o_o = s.observables(), O.observables(P, po, eo)
+        assert abs(o_g["E"] - o_o["E"]) < 1e-6 * abs(o_o["E"])
+        assert abs(o_g["T_int"] - o_o["T_int"]) < 1e-3 * o_o["T_int"]
+
+
+@pytest.mark.parametrize("precision", [sdpd.FP64, sdpd.MIXED])
+def test_energy_histogram_is_exact(precision):
+    q, p, e, L, K = system("random_rect")
+    N = len(e)
+    s = gpu(N, L, K, precision=precision, fd_only=True)
+    s.set_state(q, p, e)
+    s.step(0.1, 3, seed=1)
+    _, _, eg = s.get_state()
+    lo, hi, nb, scale = 0.1, 20.0, 150, 1.0 / 3.0
+    got = s.energy_histogram(lo, hi, nb, scale).cpu().numpy()
+    x = eg * scale
+    w = (hi - lo) / nb
+    ref = np.zeros(nb + 2, dtype=np.int64)
+    under, over = x < lo, ~(x < hi)
+    ref[nb], ref[nb + 1] = under.sum(), over.sum()
+    inside = ~(under | over)
+    b = np.minimum(np.floor((x[inside] - lo) / w).astype(np.int64), nb - 1)
+    np.add.at(ref, b, 1)
+    assert np.array_equal(got, ref)
+    got2 = s.energy_histogram(lo, hi, nb, scale, counts=torch.as_tensor(got, device="cuda"))
+    assert np.array_equal(got2.cpu().numpy(), 2 * ref)
+    with pytest.raises(sdpd.SDPDError):
+        s.energy_histogram(1.0, 1.0, 10)
+
+
 @pytest.mark.parametrize("kind", ["lattice1000", "random_rect"])
 def test_trajectory_mixed_verlet_10_steps(kind):
     """Deterministic part (Velocity Verlet only): float32 pair arithmetic and

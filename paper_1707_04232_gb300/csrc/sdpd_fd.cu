@@ -120,8 +120,10 @@ struct SchedSmem {
   int32_t id[kMaxBlock];
   uint8_t rank[kMaxBlock];
   uint8_t perm[kMaxBlock];
-  uint32_t bits[kMaxBlock][kRowWords];  // row = rank difference, bit = lower rank
+  uint32_t bits[kRowWords][kMaxBlock];  // bit (lower rank) of row (rank difference); word-major, so
+                                        // that lanes reading consecutive rows hit distinct banks
   int32_t rowoff[kMaxBlock + 1];
+  int32_t cstart[8], cbase[8], ccnt[8];  // the block's cells: first storage index, offset in the block, count
 };
 
 // The owned pairs are read from the neighbour lists of the density pass: a
@@ -141,27 +143,54 @@ __global__ void __launch_bounds__(kSchedWarps * 32)
   SchedSmem& sm = sm_all[warp];
   int ox, oy, oz;
   owner_coords(c, o, ox, oy, oz);
-  BlockCells b;
-  block_cells(c, ox, oy, oz, mrank, cell_start, b);
-  const int nb = b.base[8];
+  // the block's 8 cells, one per lane: storage start, count, offset in the
+  // block (kept in shared memory, where they are indexed by cell code)
+  int ccnt = 0, cst = 0;
+  if (lane < 8) {
+    int cx = ox + (lane & 1), cy = oy + ((lane >> 1) & 1), cz = oz + ((lane >> 2) & 1);
+    if (cx >= c.nc[0]) cx -= c.nc[0];
+    if (cy >= c.nc[1]) cy -= c.nc[1];
+    if (cz >= c.nc[2]) cz -= c.nc[2];
+    const int r = __ldg(&mrank[cx + c.nc[0] * (cy + c.nc[1] * cz)]);
+    cst = __ldg(&cell_start[r]);
+    ccnt = __ldg(&cell_start[r + 1]) - cst;
+  }
+  int cinc = ccnt;
+#pragma unroll
+  for (int sh = 1; sh < 8; sh <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, cinc, sh);
+    if (lane >= sh) cinc += t;
+  }
+  const int nb = __shfl_sync(0xffffffffu, cinc, 7);
+  int maxcnt = ccnt;
+#pragma unroll
+  for (int sh = 4; sh > 0; sh >>= 1) maxcnt = max(maxcnt, __shfl_xor_sync(0xffffffffu, maxcnt, sh));
+  maxcnt = __shfl_sync(0xffffffffu, maxcnt, 0);
   if (nb > kMaxBlock) {
     if (lane == 0) { atomicOr(status, kStCapacity); hdr[o] = 0; }
     return;
   }
-  const int nw = (nb + 31) >> 5;  // bitmap words in use per row
-  for (int t = lane; t < nb * kRowWords; t += 32) {
-    const int row = t / kRowWords, wd = t - row * kRowWords;
-    if (wd < nw) sm.bits[row][wd] = 0u;
+  if (lane < 8) {
+    sm.cstart[lane] = cst;
+    sm.cbase[lane] = cinc - ccnt;
+    sm.ccnt[lane] = ccnt;
   }
+  const int nw = (nb + 31) >> 5;  // bitmap words in use per row
+  for (int w = 0; w < nw; ++w)
+    for (int row = lane; row < nb; row += 32) sm.bits[w][row] = 0u;
+  __syncwarp();
+  auto code_of = [&](int k) {
+    int d = 0;
+#pragma unroll
+    for (int t = 1; t < 8; ++t) d += (k >= sm.cbase[t]);
+    return d;
+  };
   for (int k = lane; k < nb; k += 32) {
-    const int d = cell_code_of(b, k);
-    sm.id[k] = a.id[b.start[d] + (k - b.base[d])];
+    const int d = code_of(k);
+    sm.id[k] = a.id[sm.cstart[d] + (k - sm.cbase[d])];
   }
   __syncwarp();
   // rank of each id among the block's ids: every cell's ids are ascending
-  int maxcnt = 0;
-#pragma unroll
-  for (int d = 0; d < 8; ++d) maxcnt = max(maxcnt, b.cnt[d]);
   int steps = 0;
   while ((1 << steps) <= maxcnt) ++steps;
   for (int k = lane; k < nb; k += 32) {
@@ -170,7 +199,7 @@ __global__ void __launch_bounds__(kSchedWarps * 32)
     // fixed number of halvings, the 8 searches independent of each other)
     int pos[8], len[8];
 #pragma unroll
-    for (int d = 0; d < 8; ++d) { pos[d] = b.base[d]; len[d] = b.cnt[d]; }
+    for (int d = 0; d < 8; ++d) { pos[d] = sm.cbase[d]; len[d] = sm.ccnt[d]; }
     for (int it = 0; it < steps; ++it) {
 #pragma unroll
       for (int d = 0; d < 8; ++d) {
@@ -182,58 +211,95 @@ __global__ void __launch_bounds__(kSchedWarps * 32)
     }
     int r = 0;
 #pragma unroll
-    for (int d = 0; d < 8; ++d) r += pos[d] - b.base[d];
+    for (int d = 0; d < 8; ++d) r += pos[d] - sm.cbase[d];
     sm.rank[k] = (uint8_t)r;
     sm.perm[r] = (uint8_t)k;
   }
   __syncwarp();
-  for (int k = lane; k < nb; k += 32) {
-    const int dA = cell_code_of(b, k);
-    const int g = b.start[dA] + (k - b.base[dA]);
-    const int rk = sm.rank[k];
+  // Owned entries, spread over the warp: for a chunk of 32 particles (one per
+  // lane) and the s-th partner cell of each, a warp prefix sum of the entry
+  // counts maps the chunk's entries to lanes, so that the lanes load
+  // consecutive entries of a row together and share the work evenly (an
+  // owner-cell particle has up to ~80 owned entries, a far-corner one ~3).
+  for (int k0 = 0; k0 < nb; k0 += 32) {
+    const int k = k0 + lane;
+    const bool live = k < nb;
+    int dA = 0, g = 0, rk = 0;
+    if (live) {
+      dA = code_of(k);
+      g = sm.cstart[dA] + (k - sm.cbase[dA]);
+      rk = sm.rank[k];
+    }
     const uint8_t* off = nbr_off + (int64_t)g * 28;
-    const uint32_t* row = nlist + (int64_t)g * c.nbr_cap;
-    // partner cells dB: subsets of the complement of dA
     const int free = 7 & ~dA;
     int dB = free;
-    while (true) {
-      const int sx = ((dB & 1) - (dA & 1)) + 1, sy = (((dB >> 1) & 1) - ((dA >> 1) & 1)) + 1,
-                sz = (((dB >> 2) & 1) - ((dA >> 2) & 1)) + 1;
-      const int st = sx + 3 * sy + 9 * sz;
-      const int e0 = off[st], e1 = off[st + 1];
-      const int sB = b.start[dB], bB = b.base[dB];
-      for (int q = e0; q < e1; ++q) {
-        const int j = (int)(__ldg(&row[q]) >> 6);
-        const int rj = sm.rank[bB + (j - sB)];
-        if (rk < rj) atomicOr(&sm.bits[rj - rk][rk >> 5], 1u << (rk & 31));
+    bool more = live;
+    for (int sgi = 0; sgi < 8; ++sgi) {  // partner cells dB: subsets of the complement of dA
+      int e0 = 0, n = 0, myB = 0;
+      if (more) {
+        const int sx = ((dB & 1) - (dA & 1)) + 1, sy = (((dB >> 1) & 1) - ((dA >> 1) & 1)) + 1,
+                  sz = (((dB >> 2) & 1) - ((dA >> 2) & 1)) + 1;
+        const int st = sx + 3 * sy + 9 * sz;
+        e0 = off[st];
+        n = off[st + 1] - e0;
+        myB = dB;
+        if (dB == 0) more = false;
+        else dB = (dB - 1) & free;
       }
-      if (dB == 0) break;
-      dB = (dB - 1) & free;
+      int incl = n;
+#pragma unroll
+      for (int sh = 1; sh < 32; sh <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, sh);
+        if (lane >= sh) incl += t;
+      }
+      const int total = __shfl_sync(0xffffffffu, incl, 31);
+      if (total == 0) {
+        if (!__any_sync(0xffffffffu, more)) break;
+        continue;
+      }
+      const int excl = incl - n;
+      const int packed = (myB << 8) | e0;  // partner cell and first entry of this lane's segment
+      for (int t0 = 0; t0 < total; t0 += 32) {
+        const int t = t0 + lane;
+        // owner lane: the number of lanes whose inclusive count is <= t
+        int pos = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+          const int v = __shfl_sync(0xffffffffu, incl, pos + step - 1);
+          if (v <= t) pos += step;
+        }
+        const int src = min(pos, 31);
+        const int o_pk = __shfl_sync(0xffffffffu, packed, src);
+        const int o_ex = __shfl_sync(0xffffffffu, excl, src);
+        const int o_g = __shfl_sync(0xffffffffu, g, src);
+        const int o_rk = __shfl_sync(0xffffffffu, rk, src);
+        if (t < total) {
+          const int q = (o_pk & 255) + (t - o_ex);
+          const int oB = o_pk >> 8;
+          const int j = (int)(__ldg(&nlist[(int64_t)o_g * c.nbr_cap + q]) >> 6);
+          const int rj = sm.rank[sm.cbase[oB] + (j - sm.cstart[oB])];
+          if (o_rk < rj) atomicOr(&sm.bits[o_rk >> 5][rj - o_rk], 1u << (o_rk & 31));
+        }
+      }
+      if (!__any_sync(0xffffffffu, more)) break;
     }
   }
   __syncwarp();
-  // exclusive scan of the row populations (8 rows per lane)
-  int cnt8[8], sum = 0;
-#pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const int rr = lane * 8 + q;
+  // exclusive scan of the row populations, 32 consecutive rows at a time
+  int npairs = 0;
+  for (int r0 = 0; r0 < nb; r0 += 32) {
+    const int rr = r0 + lane;
     int n = 0;
     if (rr >= 1 && rr < nb)
-      for (int w = 0; w < nw; ++w) n += __popc(sm.bits[rr][w]);
-    cnt8[q] = n;
-    sum += n;
-  }
-  int incl = sum;
-  for (int s = 1; s < 32; s <<= 1) {
-    int t = __shfl_up_sync(0xffffffffu, incl, s);
-    if (lane >= s) incl += t;
-  }
-  const int npairs = __shfl_sync(0xffffffffu, incl, 31);
-  int run = incl - sum;
+      for (int w = 0; w < nw; ++w) n += __popc(sm.bits[w][rr]);
+    int incl = n;
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    sm.rowoff[lane * 8 + q] = run;
-    run += cnt8[q];
+    for (int sh = 1; sh < 32; sh <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, sh);
+      if (lane >= sh) incl += t;
+    }
+    sm.rowoff[rr] = npairs + incl - n;
+    npairs += __shfl_sync(0xffffffffu, incl, 31);
   }
   if (npairs > kMaxPairs) {
     if (lane == 0) { atomicOr(status, kStCapacity); hdr[o] = 0; }
@@ -245,7 +311,7 @@ __global__ void __launch_bounds__(kSchedWarps * 32)
   for (int rr = 1 + lane; rr < nb; rr += 32) {
     int pos = sm.rowoff[rr];
     for (int w = 0; w < nw; ++w) {
-      uint32_t bits = sm.bits[rr][w];
+      uint32_t bits = sm.bits[w][rr];
       while (bits) {
         const int bit = __ffs(bits) - 1;
         bits &= bits - 1;

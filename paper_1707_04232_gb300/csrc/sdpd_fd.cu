@@ -712,8 +712,16 @@ __global__ void __launch_bounds__(fd_warps<P>() * 32, P::mixed ? 8 : 4)
   bool negative = false, bad = false;
   int L = 0, pos = 0;
   while (__any_sync(0xffffffffu, pos < np)) {
-    // stage pairs [cbeg, cend) of the level-ordered list
-    const int cbeg = pos, cend = min(pos + kChunk, np);
+    // stage pairs [cbeg, cend) of the level-ordered list; the chunk ends on
+    // a level boundary when at least one whole level fits, so that no level
+    // is split over two chunks (a split level costs an extra round)
+    const int cbeg = pos;
+    int cend = min(pos + kChunk, np);
+    if (pos < np && (int)off[L + 1] <= cend) {
+      int Le = L + 1;
+      while (Le < nlev && (int)off[Le + 1] <= cend) ++Le;
+      cend = off[Le];
+    }
     for (int t = cbeg + gl; t < cend; t += kGroupLanes) {
       const uint16_t pr = pl[t];
       const int ia = pr & 255, ib = pr >> 8;  // ia holds the lower id

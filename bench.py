@@ -209,7 +209,7 @@ def run_ours(args, rank, world, local_rank):
 
     torch.cuda.set_device(local_rank)
     dev_index = torch.cuda.current_device()
-    w = Workload(n=args.n, K=args.K, kT=1.0, seed=rank)
+    w = replica_workload(args, rank)
     q, p, e = lattice_state(w)
     scheme = {"ssa": sdpd.SCHEME_SSA, "ams": sdpd.SCHEME_AMS, "ems": sdpd.SCHEME_EMS, "none": sdpd.SCHEME_NONE}[args.scheme]
     prec = sdpd.MIXED if args.precision == "mixed" else sdpd.FP64
@@ -240,9 +240,7 @@ def run_ours(args, rank, world, local_rank):
         stages = s.stage_times()
         launches = s.kernel_launches - launches0
         o1 = s.observables()
-    ms_max = allreduce_max(ms, world)
-    total_ps = w.N * args.steps * world
-    value = total_ps / (ms_max * 1e-3)
+    value, ms_max = aggregate(w.N, args.steps, ms, world)
     # ---- roofline of the dominant stage ----
     top = max(stages, key=lambda k: stages[k][0])
     top_ms, top_launches = stages[top]
@@ -573,22 +571,42 @@ def run_e2e(args, s, q, p, e, stream, world, N):
 _dist = None
 
 
+def set_process_group(dist_module):
+    """Use an initialised torch.distributed (NCCL on GPUs, gloo on CPU) for
+    the barrier and the max-over-ranks of the timings."""
+    global _dist
+    _dist = dist_module
+
+
 def barrier(world):
     if world > 1:
         _dist.barrier()
 
 
 def allreduce_max(x, world):
+    """The largest of the ranks' values of x (every rank gets it)."""
     if world == 1:
         return x
     import torch
-    t = torch.tensor([float(x)], device="cuda")
+    dev = "cuda" if _dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
     _dist.all_reduce(t, op=_dist.ReduceOp.MAX)
     return float(t.item())
 
 
+def replica_workload(args, rank):
+    """Each rank's independent replica: the same fluid, its own seed."""
+    return Workload(n=args.n, K=args.K, kT=1.0, seed=rank)
+
+
+def aggregate(n_local, steps, ms_local, world):
+    """Whole-job throughput of weakly scaled replicas: all ranks'
+    particle-steps over the slowest rank's time.  Returns (value, ms_max)."""
+    ms_max = allreduce_max(ms_local, world)
+    return n_local * steps * world / (ms_max * 1e-3), ms_max
+
+
 def main():
-    global _dist
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -601,7 +619,7 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
-        _dist = dist
+        set_process_group(dist)
     if args.workload == "ensemble":
         run_ensemble(args, rank, world, local_rank)
     elif args.workload == "adjoint":

@@ -34,11 +34,31 @@ __device__ __forceinline__ double kernel_dF(double x, double cF, double inv_h) {
   return -cF * inv_h * (1.0 - x) * (1.0 + x) / (x * x);
 }
 
-__device__ __forceinline__ void pair_disp(const Consts& c, const D4& qi, const D4& qj, double& dx, double& dy,
-                                          double& dz) {
-  dx = min_image(__dsub_rn(qi.x, qj.x), c.L[0], c.halfL[0]);
-  dy = min_image(__dsub_rn(qi.y, qj.y), c.L[1], c.halfL[1]);
-  dz = min_image(__dsub_rn(qi.z, qj.z), c.L[2], c.halfL[2]);
+// Displacement r_ij with the periodic image taken from the neighbour-list
+// entry's stencil code (offset + 1 per axis, 2 bits each) and the home cell.
+struct Images {
+  double m[3], p[3];  // shifts of the offsets -1 and +1 per axis
+  __device__ void init(const Consts& c, double cellbits_w) {
+    int ci[3];
+    unpack_cell(w_to_cellbits(cellbits_w), ci[0], ci[1], ci[2]);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      m[d] = image_shift(ci[d], -1, c.nc[d], c.L[d]);
+      p[d] = image_shift(ci[d], 1, c.nc[d], c.L[d]);
+    }
+  }
+};
+
+__device__ __forceinline__ void pair_disp(const Images& im, uint32_t code, const D4& qi, const D4& qj, double& dx,
+                                          double& dy, double& dz) {
+  double d[3] = {__dsub_rn(qi.x, qj.x), __dsub_rn(qi.y, qj.y), __dsub_rn(qi.z, qj.z)};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const uint32_t k = (code >> (2 * a)) & 3u;
+    const double s = k == 0 ? im.m[a] : (k == 2 ? im.p[a] : 0.0);
+    if (s != 0.0) d[a] = __dadd_rn(d[a], s);
+  }
+  dx = d[0]; dy = d[1]; dz = d[2];
 }
 
 // v_i = scale * pbar[id_i], rbar slot cleared
@@ -52,12 +72,14 @@ __global__ void k_adj_gather(int64_t N, const int32_t* __restrict__ id, const do
 
 // pass A: A_i = m^2 sum_j F(r_ij) t_ij
 template <int KIND, int MODE>
-__global__ void __launch_bounds__(128) k_adj_pairsum(Consts c, const D4* __restrict__ qp4,
+__global__ void __launch_bounds__(128) k_adj_pairsum(Consts c, const D4* __restrict__ qp4, const D4* __restrict__ q4,
                                                      const D4* __restrict__ vs4, const uint32_t* __restrict__ nlist,
                                                      const int32_t* __restrict__ nn, double* __restrict__ A) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= c.N) return;
   const D4 qi = ld4(&qp4[i]);
+  Images im;
+  im.init(c, q4[i].w);
   D4 vi{0.0, 0.0, 0.0, 0.0};
   if (MODE == 0) vi = ld4(&vs4[i]);
   const double inv_h = 1.0 / c.h;
@@ -65,14 +87,14 @@ __global__ void __launch_bounds__(128) k_adj_pairsum(Consts c, const D4* __restr
   const int n = nn[i];
 #pragma unroll 2
   for (int k = 0; k < n; ++k) {
-    const uint32_t j = __ldg(&nlist[i * c.nbr_cap + k]) >> 6;
-    const D4 qj = ld4(&qp4[j]);
+    const uint32_t e = __ldg(&nlist[i * c.nbr_cap + k]);
+    const D4 qj = ld4(&qp4[e >> 6]);
     double dx, dy, dz;
-    pair_disp(c, qi, qj, dx, dy, dz);
+    pair_disp(im, e & 63u, qi, qj, dx, dy, dz);
     const double r2 = r2_of(dx, dy, dz);
     double t;
     if (MODE == 0) {
-      const D4 vj = ld4(&vs4[j]);
+      const D4 vj = ld4(&vs4[e >> 6]);
       t = (vi.x - vj.x) * dx + (vi.y - vj.y) * dy + (vi.z - vj.z) * dz;
     } else {
       t = r2;
@@ -156,8 +178,8 @@ __global__ void k_adj_mid_virial(Consts c, const D4* __restrict__ qp4, const dou
 
 // pass B (MODE 0: kick pulled back along v; 1: virial; 2: density term only)
 template <int KIND, int MODE>
-__global__ void __launch_bounds__(128) k_adj_back(Consts c, const D4* __restrict__ qp4, const D4* __restrict__ vs4,
-                                                  const int32_t* __restrict__ id,
+__global__ void __launch_bounds__(128) k_adj_back(Consts c, const D4* __restrict__ qp4, const D4* __restrict__ q4,
+                                                  const D4* __restrict__ vs4, const int32_t* __restrict__ id,
                                                   const uint32_t* __restrict__ nlist,
                                                   const int32_t* __restrict__ nn, double wt, int accumulate,
                                                   double* __restrict__ qbar, double* __restrict__ thbar) {
@@ -165,16 +187,18 @@ __global__ void __launch_bounds__(128) k_adj_back(Consts c, const D4* __restrict
   if (i >= c.N) return;
   const D4 qi = ld4(&qp4[i]);
   const D4 vi = ld4(&vs4[i]);
+  Images im;
+  im.init(c, q4[i].w);
   const double inv_h = 1.0 / c.h, m = c.m, cm2 = wt * c.m * c.m;
   double gx = 0.0, gy = 0.0, gz = 0.0, gh = 0.0;
   const int n = nn[i];
 #pragma unroll 2
   for (int k = 0; k < n; ++k) {
-    const uint32_t j = __ldg(&nlist[i * c.nbr_cap + k]) >> 6;
-    const D4 qj = ld4(&qp4[j]);
-    const D4 vj = ld4(&vs4[j]);
+    const uint32_t e = __ldg(&nlist[i * c.nbr_cap + k]);
+    const D4 qj = ld4(&qp4[e >> 6]);
+    const D4 vj = ld4(&vs4[e >> 6]);
     double dx, dy, dz;
-    pair_disp(c, qi, qj, dx, dy, dz);
+    pair_disp(im, e & 63u, qi, qj, dx, dy, dz);
     const double r2 = r2_of(dx, dy, dz);
     const double r = sqrt(r2), x = r * inv_h;
     const double f = kernel_F<KIND>(x, c.cF);
@@ -261,16 +285,18 @@ void launch_adj_gather(const Consts& c, const Workspace& w, int cur, const doubl
   k_adj_gather<<<nblocks(c.N, 256), 256, 0, s>>>(c.N, w.id[cur], pbar_id, scale, vs4);
 }
 
-void launch_adj_pairsum(const Consts& c, const Workspace& w, int mode, const D4* vs4, double* A, cudaStream_t s) {
+void launch_adj_pairsum(const Consts& c, const Workspace& w, int cur, int mode, const D4* vs4, double* A,
+                        cudaStream_t s) {
   if (c.N == 0) return;
   const D4* qp4 = (const D4*)w.qp4;
+  const D4* q4 = (const D4*)w.q4[cur];
   const unsigned nb = nblocks(c.N, 128);
   if (c.kernel == SDPD_KERNEL_LUCY) {
-    if (mode == 0) k_adj_pairsum<SDPD_KERNEL_LUCY, 0><<<nb, 128, 0, s>>>(c, qp4, vs4, w.nlist, w.nn, A);
-    else k_adj_pairsum<SDPD_KERNEL_LUCY, 1><<<nb, 128, 0, s>>>(c, qp4, vs4, w.nlist, w.nn, A);
+    if (mode == 0) k_adj_pairsum<SDPD_KERNEL_LUCY, 0><<<nb, 128, 0, s>>>(c, qp4, q4, vs4, w.nlist, w.nn, A);
+    else k_adj_pairsum<SDPD_KERNEL_LUCY, 1><<<nb, 128, 0, s>>>(c, qp4, q4, vs4, w.nlist, w.nn, A);
   } else {
-    if (mode == 0) k_adj_pairsum<SDPD_KERNEL_CUBIC, 0><<<nb, 128, 0, s>>>(c, qp4, vs4, w.nlist, w.nn, A);
-    else k_adj_pairsum<SDPD_KERNEL_CUBIC, 1><<<nb, 128, 0, s>>>(c, qp4, vs4, w.nlist, w.nn, A);
+    if (mode == 0) k_adj_pairsum<SDPD_KERNEL_CUBIC, 0><<<nb, 128, 0, s>>>(c, qp4, q4, vs4, w.nlist, w.nn, A);
+    else k_adj_pairsum<SDPD_KERNEL_CUBIC, 1><<<nb, 128, 0, s>>>(c, qp4, q4, vs4, w.nlist, w.nn, A);
   }
 }
 
@@ -294,10 +320,11 @@ void launch_adj_back(const Consts& c, const Workspace& w, int cur, int mode, dou
                      int accumulate, double* qbar, double* thbar, cudaStream_t s) {
   if (c.N == 0) return;
   const D4* qp4 = (const D4*)w.qp4;
+  const D4* q4 = (const D4*)w.q4[cur];
   const unsigned nb = nblocks(c.N, 128);
   const int32_t* id = w.id[cur];
 #define SDPD_ADJ_BACK(KIND, MODE) \
-  k_adj_back<KIND, MODE><<<nb, 128, 0, s>>>(c, qp4, vs4, id, w.nlist, w.nn, wt, accumulate, qbar, thbar)
+  k_adj_back<KIND, MODE><<<nb, 128, 0, s>>>(c, qp4, q4, vs4, id, w.nlist, w.nn, wt, accumulate, qbar, thbar)
   if (c.kernel == SDPD_KERNEL_LUCY) {
     if (mode == 0) SDPD_ADJ_BACK(SDPD_KERNEL_LUCY, 0);
     else if (mode == 1) SDPD_ADJ_BACK(SDPD_KERNEL_LUCY, 1);

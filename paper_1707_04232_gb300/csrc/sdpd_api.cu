@@ -834,7 +834,7 @@ int sdpd_vv_adjoint(sdpd_t* s, void* tape, size_t tape_bytes, const double* gq, 
         launch_adj_gather(c, s->w, s->cur, t.pbar, coef, t.vs4, st);
       }
       StageTimer tm(s, 7, 1);
-      launch_adj_pairsum(c, s->w, 0, t.vs4, t.A, st);
+      launch_adj_pairsum(c, s->w, s->cur, 0, t.vs4, t.A, st);
     }
     {
       StageTimer tm(s, 9, 1);
@@ -883,7 +883,7 @@ int sdpd_virial(sdpd_t* s, double* value, double* gq, double* gp, double* geps, 
   double* thbar = s->w.io_q;
   double* sums = s->w.obs + 8;  // slots 8..11 of the observables' output block
   const double wt = 1.0 / (3.0 * c.L[0] * c.L[1] * c.L[2]);
-  launch_adj_pairsum(c, s->w, 1, vs4, A, st);
+  launch_adj_pairsum(c, s->w, s->cur, 1, vs4, A, st);
   launch_adj_mid_virial(c, s->w, s->cur, A, wt, vs4, val_id, grad ? gp : nullptr, geps, thbar, st);
   if (grad) launch_adj_back(c, s->w, s->cur, 1, wt, vs4, 0, gq, thbar, st);
   launch_adj_sum(val_id, c.N, 1, (double*)s->w.obs_partial, sums, st);

@@ -199,6 +199,16 @@ __device__ __forceinline__ double min_image(double d, double L, double halfL) {
 __device__ __forceinline__ double r2_of(double dx, double dy, double dz) {
   return __fma_rn(dz, dz, __fma_rn(dy, dy, __dmul_rn(dx, dx)));
 }
+// Periodic image of a neighbour in the cell at offset o in {-1, 0, +1} from
+// cell index ci (of n cells, box side L): +L if the offset wraps below 0, -L
+// if it wraps above n - 1, else 0.  Neighbour cells are at most one cell
+// away, so the float64 displacement (x_i - x_j) + shift equals the minimum
+// image (x_i - x_j) -/+ L whenever the pair can be within h: a wrapped
+// difference exceeds L/2 in magnitude (n >= 4), an unwrapped one is below it.
+__device__ __forceinline__ double image_shift(int ci, int o, int n, double L) {
+  return (o < 0 && ci == 0) ? L : ((o > 0 && ci == n - 1) ? -L : 0.0);
+}
+
 __device__ __forceinline__ float r2_of(float dx, float dy, float dz) {
   return __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
 }
@@ -324,7 +334,8 @@ void launch_advance_sweep(const Workspace& w, cudaStream_t s);
 // order.  mode: 0 kick pulled back along v, 1 virial, 2 density term only.
 void launch_adj_gather(const Consts& c, const Workspace& w, int cur, const double* pbar_id, double scale, D4* vs4,
                        cudaStream_t s);
-void launch_adj_pairsum(const Consts& c, const Workspace& w, int mode, const D4* vs4, double* A, cudaStream_t s);
+void launch_adj_pairsum(const Consts& c, const Workspace& w, int cur, int mode, const D4* vs4, double* A,
+                        cudaStream_t s);
 void launch_adj_mid_traj(const Consts& c, const Workspace& w, int cur, const double* A, D4* vs4, double* Sbar,
                          double* thbar, const double* epsbar_n, int final_pos, double* epsbar0, cudaStream_t s);
 void launch_adj_mid_virial(const Consts& c, const Workspace& w, int cur, const double* A, double wt, D4* vs4,

@@ -20,21 +20,46 @@ struct Home;
 
 template <>
 struct Home<Fp64> {
-  double x, y, z, L[3], halfL[3];
-  __device__ void init(const Consts& c, const D4& q, int, int, int, const uint32_t*, const uint32_t*,
+  double x, y, z;
+  int cx, cy, cz;
+  double mx, my, mz, px_, py_, pz_;  // image shifts of the neighbour offsets -1 and +1 per axis
+  double fx, fy, fz;                 // shifts of the current neighbour cell
+  __device__ void init(const Consts& c, const D4& q, int cx_, int cy_, int cz_, const uint32_t*, const uint32_t*,
                        const uint32_t*) {
     x = q.x; y = q.y; z = q.z;
-    for (int d = 0; d < 3; ++d) { L[d] = c.L[d]; halfL[d] = c.halfL[d]; }
+    cx = cx_; cy = cy_; cz = cz_;
+    mx = image_shift(cx, -1, c.nc[0], c.L[0]); px_ = image_shift(cx, 1, c.nc[0], c.L[0]);
+    my = image_shift(cy, -1, c.nc[1], c.L[1]); py_ = image_shift(cy, 1, c.nc[1], c.L[1]);
+    mz = image_shift(cz, -1, c.nc[2], c.L[2]); pz_ = image_shift(cz, 1, c.nc[2], c.L[2]);
+    fx = fy = fz = 0.0;
   }
-  __device__ __forceinline__ void frame(int, int, int) {}
+  // neighbour cell (nx, ny, nz) = (cx + ox, ...) wrapped: its image shifts
+  __device__ __forceinline__ void frame(int nx, int ny, int nz) {
+    fx = nx - cx > 1 ? mx : (nx - cx < -1 ? px_ : 0.0);
+    fy = ny - cy > 1 ? my : (ny - cy < -1 ? py_ : 0.0);
+    fz = nz - cz > 1 ? mz : (nz - cz < -1 ? pz_ : 0.0);
+  }
   __device__ __forceinline__ void frames_all(const Consts&) {}
-  __device__ __forceinline__ void disp_code(uint32_t, const D4& qj, double& dx, double& dy, double& dz) const {
-    disp(qj, dx, dy, dz);
+  __device__ __forceinline__ static double pick(uint32_t k, double m, double p) {
+    return k == 0 ? m : (k == 2 ? p : 0.0);
+  }
+  __device__ __forceinline__ void disp_code(uint32_t code, const D4& qj, double& dx, double& dy, double& dz) const {
+    const double sx = pick(code & 3u, mx, px_), sy = pick((code >> 2) & 3u, my, py_),
+                 sz = pick((code >> 4) & 3u, mz, pz_);
+    dx = __dsub_rn(x, qj.x);
+    dy = __dsub_rn(y, qj.y);
+    dz = __dsub_rn(z, qj.z);
+    if (sx != 0.0) dx = __dadd_rn(dx, sx);
+    if (sy != 0.0) dy = __dadd_rn(dy, sy);
+    if (sz != 0.0) dz = __dadd_rn(dz, sz);
   }
   __device__ __forceinline__ void disp(const D4& qj, double& dx, double& dy, double& dz) const {
-    dx = min_image(__dsub_rn(x, qj.x), L[0], halfL[0]);
-    dy = min_image(__dsub_rn(y, qj.y), L[1], halfL[1]);
-    dz = min_image(__dsub_rn(z, qj.z), L[2], halfL[2]);
+    dx = __dsub_rn(x, qj.x);
+    dy = __dsub_rn(y, qj.y);
+    dz = __dsub_rn(z, qj.z);
+    if (fx != 0.0) dx = __dadd_rn(dx, fx);
+    if (fy != 0.0) dy = __dadd_rn(dy, fy);
+    if (fz != 0.0) dz = __dadd_rn(dz, fz);
   }
 };
 

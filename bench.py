@@ -200,6 +200,11 @@ def workload_config(args):
 FLOPS_PER_VISIT = {"density_eos": 18.0, "kick1_drift_bin": 24.0, "kick2": 24.0,
                    "adj_pass_A": 23.0, "adj_pass_B": 66.0}
 FP64_NOMINAL_TFLOPS = 1.25  # GB300 float64, nominal
+# DRAM traffic of one colour launch of the mixed-precision sweep, per
+# particle: dram__bytes_read.sum + dram__bytes_write.sum of one launch at
+# N = 96^3 (49.28 MB + 1.18 MB), divided by the particles every colour
+# launch visits once; a launch's traffic scales with N
+FD_COLOUR_DRAM_BYTES_PER_PARTICLE = (49.284864e6 + 1.1776e6) / 96 ** 3
 FLOPS_PER_PAIR_UPDATE = {"ems": 210.0, "ams": 150.0, "ssa": 140.0}
 
 
@@ -259,8 +264,10 @@ def run_ours(args, rank, world, local_rank):
     roof = None
     if flops is not None:
         ach = flops / per_launch_s / 1e12
+        traffic = (FD_COLOUR_DRAM_BYTES_PER_PARTICLE * w.N
+                   if top == "fd_colours" and args.precision == "mixed" else None)
         roof = {"kernel": top, "bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s",
-                "frac": ach / alu_peak, "traffic": None,
+                "frac": ach / alu_peak, "traffic": traffic,
                 "peak_note": ("FP32 FMA peak = 152 SMs x 128 lanes x 2 x %.0f MHz (recipe unit counts, "
                               "sampled max clock)" % sm_max if args.precision == "mixed" else
                               "float64 nominal of GB300 (recipe)")

@@ -389,6 +389,29 @@ def test_ssa_negative_energy_is_reported_not_fatal():
         assert obs["status"] == 0 and obs["eps_min"] > 0 and obs["n_reject_bound"] > 0
 
 
+@pytest.mark.parametrize("precision", [sdpd.FP64, sdpd.MIXED])
+def test_capacity_overflow_is_reported(precision):
+    """A dense cluster (300 particles in a unit cube) overflows the
+    neighbour-list rows (160 entries) and its 2x2x2 cell block (256
+    particles): the library reports SDPD_ERR_CAPACITY after the step and the
+    context stays usable."""
+    L = 12.0
+    rng = np.random.default_rng(5)
+    q = np.concatenate([rng.random((800, 3)) * L, 5.0 + rng.random((300, 3))])
+    p = rng.standard_normal(q.shape)
+    e = np.full(len(q), 30.0)
+    s = gpu(len(q), (L,) * 3, 20.0, precision=precision)
+    s.set_state(q, p, e)
+    s.step(DT, 2, seed=1)
+    obs = s.observables(check=False)
+    assert obs["status"] == sdpd.ERR_CAPACITY
+    ok = gpu(1000, (10.0,) * 3, 100.0, precision=precision)
+    qq, pp, ee, _, _ = system("lattice1000")
+    ok.set_state(qq, pp, ee)
+    ok.step(DT, 1, seed=1)
+    assert ok.observables()["status"] == 0
+
+
 def test_bad_state_and_empty_system():
     q, p, e, L, K = system("lattice1000")
     s = gpu(len(e), L, K)

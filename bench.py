@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--K", type=float, default=50.0)
     ap.add_argument("--dt", type=float, default=0.005)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the float64 form of the same step")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-n", type=int, default=32, help="lattice sites per axis of the CPU sample")
     ap.add_argument("--workload", default="fluid", choices=["fluid", "ensemble", "adjoint"],
@@ -299,11 +300,40 @@ def run_ours(args, rank, world, local_rank):
         e2e = run_e2e(args, s, q, p, e, stream, world, w.N)
         line["e2e"] = e2e
     del s
+    # ---- the float64 form of the same step (same workload, a few steps) ----
+    if args.precision == "mixed" and not args.no_fp64:
+        line["vs_fp64"] = run_fp64_form(args, w, q, p, e, scheme, stream, world, value)
     if rank == 0 and not args.no_cpu and world == 1:
         ps, threads, desc = cpu_sample(args, 2)
         line["cpu_baseline"] = {"value": ps, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc}
     if rank == 0:
         print(json.dumps(line))
+
+
+def run_fp64_form(args, w, q, p, e, scheme, stream, world, mixed_value):
+    """Particle-steps/s of the float64 form of the same workload (3 steps
+    after 1 warm-up step, CUDA events on the handle's stream), and the
+    mixed-precision speed-up over it."""
+    import torch
+    from paper_1707_04232_gb300 import sdpd
+
+    steps = 3
+    with torch.cuda.stream(stream):
+        s = sdpd.SDPD(w.N, w.L, m=w.m, h=w.h, K=w.K, precision=sdpd.FP64, scheme=scheme, stream=stream)
+        s.set_state(q, p, e)
+        s.step(args.dt, 1, seed=77)
+        s.sync()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier(world)
+        a.record(stream)
+        s.step(args.dt, steps, seed=77)
+        b.record(stream)
+        b.synchronize()
+        ms = allreduce_max(a.elapsed_time(b), world)
+        del s
+    ps = w.N * steps * world / (ms * 1e-3)
+    return {"value": ps, "unit": UNIT, "ms_per_step": ms / steps, "steps": steps,
+            "speedup_of_mixed": mixed_value / ps}
 
 
 def ensemble_members(args, rank):

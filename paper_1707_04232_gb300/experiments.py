@@ -13,6 +13,12 @@ rejections.  The temperature T_eq = E / (3(N-1)/2 + N C_K/kB) follows from
 the conserved energy E (the Gamma marginal and equipartition of the kinetic
 energy with the total momentum fixed at 0).
 
+``run_statistics``: one full run (Velocity Verlet and sweep) from the
+lattice: rejection rates, energy drift and mean temperatures; the ``stats``
+command runs it over K, kT, dt, scheme and precision, so that the mixed
+path's statistics at scale can be set against those of the float64 path
+(which matches the float64 oracle step by step).
+
 ``mts_drift``: the full dynamics with single (STS) and multiple (MTS) time
 steps (Section 5.2).  Independent replicas (seeds) run as one ensemble; the
 total energy is read at regular intervals and its drift is the slope of a
@@ -20,7 +26,7 @@ least-squares line through E(t).  The ratio of the MTS and STS slopes at the
 same Verlet step is the paper's measure of the benefit of MTS.
 
 Both are plain drivers over the library's public API; every step runs in the
-CUDA library.  ``python -m paper_1707_04232_gb300.experiments fd|mts`` prints
+CUDA library.  ``python -m paper_1707_04232_gb300.experiments fd|mts|stats`` prints
 one JSON document.
 """
 from __future__ import annotations
@@ -170,6 +176,44 @@ def mts_drift(dt_reduced=0.392, thetas=(1, 5, 10), scheme="ems", n=10, K=5.0, kT
     return out
 
 
+def run_statistics(precision="mixed", scheme="ems", K=100.0, kT=1.0, dt=0.005, n=64, steps=200, every=10,
+                   seed=2) -> dict:
+    """Full SDPD run of ``steps`` steps from the jittered lattice: rejection
+    rates (energy bound, Metropolis), the energy-drift slope (least squares
+    through E(t), per unit time and per particle), and the time averages of
+    the kinetic and internal temperatures against T_eq = E / (3(N-1)/2 +
+    N C_K/kB)."""
+    w = Workload(n=n, K=K, kT=kT, seed=seed)
+    q, p, e = lattice_state(w)
+    s = sdpd.SDPD(w.N, w.L, m=w.m, h=w.h, K=K, scheme=SCHEMES[scheme], precision=PRECISIONS[precision])
+    s.set_state(q, p, e)
+    t0 = time.perf_counter()
+    ts, Es, Tk, Ti = [], [], [], []
+    k = 0
+    while True:
+        o = s.observables(check=False)
+        ts.append(k * dt)
+        Es.append(o["E"])
+        Tk.append(o["T_kin"])
+        Ti.append(o["T_int"])
+        if k >= steps or o["status"] != 0:
+            break
+        s.step(dt, every, seed=seed)
+        k += every
+    wall = time.perf_counter() - t0
+    pairs = max(1, o["n_pairs"])
+    C = 1.5 * (K - 1.0)
+    T_eq = Es[0] / (1.5 * (w.N - 1) + w.N * C)
+    return {"precision": precision, "scheme": scheme, "K": K, "kT": kT, "dt": dt, "N": w.N, "steps": k,
+            "status": sdpd.sdpd_strerror(o["status"]),
+            "rejection": {"total": (o["n_reject_bound"] + o["n_reject_metropolis"]) / pairs,
+                          "energy_bound": o["n_reject_bound"] / pairs,
+                          "metropolis": o["n_reject_metropolis"] / pairs, "pairs": int(o["n_pairs"])},
+            "drift_per_particle": energy_drift_slope(np.array(ts), np.array(Es)) / w.N,
+            "T_eq": T_eq, "T_kin_mean": float(np.mean(Tk[1:])) if len(Tk) > 1 else Tk[0],
+            "T_int_mean": float(np.mean(Ti[1:])) if len(Ti) > 1 else Ti[0], "wall_s": wall}
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     sub = ap.add_subparsers(dest="what", required=True)
@@ -186,8 +230,16 @@ def main():
     b.add_argument("--replicas", type=int, default=10)
     b.add_argument("--t-sim", type=float, default=1000.0)
     b.add_argument("--precision", default="fp64", choices=list(PRECISIONS))
+    c = sub.add_parser("stats", help="rejection rates, energy drift and temperatures of full runs (M2 grid)")
+    c.add_argument("--n", type=int, default=64)
+    c.add_argument("--steps", type=int, default=200)
     args = ap.parse_args()
-    if args.what == "fd":
+    if args.what == "stats":
+        rows = [run_statistics(pr, sc, K, kT, dt, n=args.n, steps=args.steps)
+                for K, kT in ((100.0, 1.0), (5.0, 0.1)) for dt in (0.001, 0.005, 0.02)
+                for sc in ("ems", "ams") for pr in ("fp64", "mixed")]
+        print(json.dumps({"experiment": "statistics", "rows": rows}))
+    elif args.what == "fd":
         rows = [fd_statistics(sc, float(d), n=args.n, K=args.K, precision=args.precision, n_configs=args.configs)
                 for sc in args.schemes.split(",") for d in args.dts.split(",")]
         print(json.dumps({"experiment": "fd_statistics", "rows": rows}))

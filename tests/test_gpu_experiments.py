@@ -67,3 +67,17 @@ def test_mts_drift_runs():
         assert np.isfinite(r["slopes"][th]["mean"])
         assert r["status"][th] == ["ok"]
     assert np.isfinite(r["ratio_to_sts"]["5"])
+
+
+def test_mixed_statistics_agree_with_float64():
+    """Full runs at 20^3 (EMS, K = 100, kT = 1, dt = 0.005, 60 steps): the
+    mixed path's rejection rate, mean temperatures and energy drift agree
+    with those of the float64 path, which matches the float64 oracle."""
+    a = X.run_statistics("fp64", "ems", n=20, steps=60)
+    b = X.run_statistics("mixed", "ems", n=20, steps=60)
+    assert a["status"] == b["status"] == "ok"
+    assert abs(a["T_int_mean"] - b["T_int_mean"]) < 1e-4 * a["T_int_mean"]
+    assert abs(a["T_kin_mean"] - b["T_kin_mean"]) < 2e-3 * a["T_kin_mean"]
+    ra, rb = a["rejection"]["total"], b["rejection"]["total"]
+    assert abs(ra - rb) < 0.2 * ra + 5.0 / a["rejection"]["pairs"] ** 0.5
+    assert abs(a["drift_per_particle"] - b["drift_per_particle"]) < 1e-3 * a["T_eq"]

@@ -512,12 +512,13 @@ __device__ __forceinline__ void pair_randoms_fast(uint64_t seed, uint64_t sweep,
 // d = kB Ti Tj / (Ti + Tj)^2 * 2 / C_K.
 template <class R>
 __device__ __forceinline__ void pair_coeffs(const FDConst<R>& k, R kpar, R kperp, R ei, R ej, R& apar,
-                                            R& aperp, R& zpar, R& zperp) {
+                                            R& aperp, R& zpar, R& zperp, R& xpar, R& xperp) {
   const R Ti = ei * k.inv_C_K, Tj = ej * k.inv_C_K;
   const R sT = Ti + Tj;
   const R hT = fm::div(Ti * Tj, sT);
   const R omd = R(1) - fm::div(k.kB * hT * k.two_over_CK, sT);
-  const R xpar = R(-2) * kpar * omd * k.dt_over_m, xperp = R(-2) * kperp * omd * k.dt_over_m;
+  xpar = R(-2) * kpar * omd * k.dt_over_m;  // log alpha per direction
+  xperp = R(-2) * kperp * omd * k.dt_over_m;
   apar = fm::exp(xpar);
   aperp = fm::exp(xperp);
   const R s = fm::div(k.four_kB_over_m * hT, omd);
@@ -546,7 +547,8 @@ __device__ __forceinline__ int fd_pair(const FDConst<typename P::R>& k, typename
   if (!(kperp > R(0)) || !(kpar > R(0))) return 0;  // at r = h the pair does nothing
   const R vx = (pi[0] - pj[0]) * k.inv_m, vy = (pi[1] - pj[1]) * k.inv_m, vz = (pi[2] - pj[2]) * k.inv_m;
   R apar, aperp, zpar, zperp;
-  pair_coeffs(k, kpar, kperp, ei, ej, apar, aperp, zpar, zperp);
+  R xfpar, xfperp;
+  pair_coeffs(k, kpar, kperp, ei, ej, apar, aperp, zpar, zperp, xfpar, xfperp);
   // proposal, Eq. (proposal): v' = sum_theta P^theta (alpha^theta v + zt^theta G)
   const R vpar = ex * vx + ey * vy + ez * vz;
   const R gpar = ex * G[0] + ey * G[1] + ez * G[2];
@@ -587,16 +589,33 @@ __device__ __forceinline__ int fd_pair(const FDConst<typename P::R>& k, typename
   } else if (k.scheme == SDPD_SCHEME_EMS) {
     // Metropolis ratio, Eq. (metropolis-ratio): the reverse move from v'
     // with the coefficients at the proposed energies
-    R bpar, bperp, ypar, yperp;
-    pair_coeffs(k, kpar, kperp, ei + deps, ej + deps, bpar, bperp, ypar, yperp);
-    const R wpar = ex * wx + ey * wy + ez * wz;
-    const R cb = (bpar - bperp) * wpar;
-    const R bx = vx - (bperp * wx + cb * ex), by = vy - (bperp * wy + cb * ey), bz = vz - (bperp * wz + cb * ez);
-    const R spar = ex * bx + ey * by + ez * bz;
-    const R ip = fm::div(R(1), yperp);
-    const R cq = (fm::div(R(1), ypar) - ip) * spar;
-    const R qx = bx * ip + cq * ex, qy = by * ip + cq * ey, qz = bz * ip + cq * ez;
-    const R quad = qx * qx + qy * qy + qz * qz;
+    R bpar, bperp, ypar, yperp, xrpar, xrperp;
+    pair_coeffs(k, kpar, kperp, ei + deps, ej + deps, bpar, bperp, ypar, yperp, xrpar, xrperp);
+    R quad;
+    if constexpr (P::mixed) {
+      // reverse noise of the proposal v' = A v + B G:
+      // B'^-1 (v - A' v') = B'^-1 [(I - A' A) v - A' B G], each direction
+      // scaled separately, I - A' A from expm1 of the summed exponents; in
+      // float32 the literal v - A' v' loses its digits to cancellation when
+      // zt -> 0 (pairs near the cut-off)
+      const R cpar_r = -fm::expm1(xfpar + xrpar), cperp_r = -fm::expm1(xfperp + xrperp);
+      const R qpar = fm::div(cpar_r * vpar - bpar * zpar * gpar, ypar);
+      const R ip = fm::div(R(1), yperp);
+      const R qx = (cperp_r * (vx - vpar * ex) - bperp * zperp * (G[0] - gpar * ex)) * ip;
+      const R qy = (cperp_r * (vy - vpar * ey) - bperp * zperp * (G[1] - gpar * ey)) * ip;
+      const R qz = (cperp_r * (vz - vpar * ez) - bperp * zperp * (G[2] - gpar * ez)) * ip;
+      quad = qpar * qpar + qx * qx + qy * qy + qz * qz;
+    } else {
+      // reverse noise B'^-1 (v - A' v') from the proposed v' itself
+      const R wpar = ex * wx + ey * wy + ez * wz;
+      const R cb = (bpar - bperp) * wpar;
+      const R bx = vx - (bperp * wx + cb * ex), by = vy - (bperp * wy + cb * ey), bz = vz - (bperp * wz + cb * ez);
+      const R spar = ex * bx + ey * by + ez * bz;
+      const R ip = fm::div(R(1), yperp);
+      const R cq = (fm::div(R(1), ypar) - ip) * spar;
+      const R qx = bx * ip + cq * ex, qy = by * ip + cq * ey, qz = bz * ip + cq * ez;
+      quad = qx * qx + qy * qy + qz * qz;
+    }
     const R g2 = G[0] * G[0] + G[1] * G[1] + G[2] * G[2];
     // log|B(v)| - log|B(v')| with |B| = zt_par zt_perp^2
     const R ldet = fm::log(fm::div(zpar * zperp * zperp, ypar * yperp * yperp));

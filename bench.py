@@ -203,9 +203,9 @@ FLOPS_PER_VISIT = {"density_eos": 18.0, "kick1_drift_bin": 24.0, "kick2": 24.0,
 FP64_NOMINAL_TFLOPS = 1.25  # GB300 float64, nominal
 # DRAM traffic of one colour launch of the mixed-precision sweep, per
 # particle: dram__bytes_read.sum + dram__bytes_write.sum of one launch at
-# N = 96^3 (49.28 MB + 1.18 MB), divided by the particles every colour
+# N = 96^3 (49.28 MB + 1.08 MB), divided by the particles every colour
 # launch visits once; a launch's traffic scales with N
-FD_COLOUR_DRAM_BYTES_PER_PARTICLE = (49.284864e6 + 1.1776e6) / 96 ** 3
+FD_COLOUR_DRAM_BYTES_PER_PARTICLE = (49.280512e6 + 1.082368e6) / 96 ** 3
 FLOPS_PER_PAIR_UPDATE = {"ems": 210.0, "ams": 150.0, "ssa": 140.0}
 
 

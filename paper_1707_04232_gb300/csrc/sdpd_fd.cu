@@ -17,11 +17,12 @@
 // in dependency levels (level = length of the longest chain of earlier pairs
 // sharing a particle), so the pairs of a level touch disjoint particles.
 //
-// Three kernels per sweep prepare the schedule of every block (positions are
-// fixed during the sweep): k_sched_enum (one warp per block: owned pairs,
-// canonical order), k_sched_levels (one thread per block: dependency levels,
-// pairs bucketed by level); then k_fd_colour runs once per colour (one warp
-// per block: the pair updates level by level in shared memory).
+// Three kernels prepare the schedule of every block (it depends on the
+// positions only, which are fixed during the sweep): k_sched_enum (one warp
+// per block: owned pairs in canonical order), k_sched_walk (one thread per
+// block: the dependency level of every pair) and k_sched_bucket (one warp per
+// block: pairs bucketed by level); then k_fd_colour runs once per colour (two
+// blocks per warp: the pair updates level by level in shared memory).
 #include "sdpd_internal.cuh"
 
 namespace sdpd {

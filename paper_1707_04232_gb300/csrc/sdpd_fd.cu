@@ -667,7 +667,7 @@ struct FdSmem {
   R px[kMaxBlock], py[kMaxBlock], pz[kMaxBlock];
   R e[kMaxBlock];    // energy at hand (float64 path: the energy itself)
   R acc[kMaxBlock];  // mixed path: float32 sum of this visit's energy changes
-  int32_t g[kMaxBlock];
+  int32_t cst[8], cbs[8];  // the block's cells: first storage index, offset in the block
   // staged pair data of the current chunk
   R G0[kChunk], G1[kChunk], G2[kChunk], U[kChunk];
   R ex[kChunk], ey[kChunk], ez[kChunk], base[kChunk];
@@ -715,10 +715,23 @@ __global__ void __launch_bounds__(fd_warps<P>() * 32, P::mixed ? 8 : 4)
   const int nb = np > 0 ? b.base[8] : 0;
   BlockGeom<P> geo;
   geo.init(c, ox, oy, oz, xmx, xmy, xmz);
+#pragma unroll
+  for (int t = 0; t < 8; ++t)
+    if (gl == t) {
+      sm.cst[t] = b.start[t];
+      sm.cbs[t] = b.base[t];
+    }
+  __syncwarp();
+  // storage index of block particle q (recomputed where needed, which keeps
+  // shared memory small enough for eight thread blocks per SM)
+  auto gidx = [&](int q) {
+    int d = 0;
+#pragma unroll
+    for (int t = 1; t < 8; ++t) d += (q >= sm.cbs[t]);
+    return sm.cst[d] + (q - sm.cbs[d]);
+  };
   for (int q = gl; q < nb; q += kGroupLanes) {
-    const int d = cell_code_of(b, q);
-    const int g = b.start[d] + (q - b.base[d]);
-    sm.g[q] = g;
+    const int g = gidx(q);
     sm.px[q] = a.px[g]; sm.py[q] = a.py[g]; sm.pz[q] = a.pz[g];
     sm.e[q] = (R)a.eps[g];
     sm.acc[q] = R(0);
@@ -745,7 +758,7 @@ __global__ void __launch_bounds__(fd_warps<P>() * 32, P::mixed ? 8 : 4)
     for (int t = cbeg + gl; t < cend; t += kGroupLanes) {
       const uint16_t pr = pl[t];
       const int ia = pr & 255, ib = pr >> 8;  // ia holds the lower id
-      const int ga = sm.g[ia], gb = sm.g[ib];
+      const int ga = gidx(ia), gb = gidx(ib);
       R xa, ya, za, xb, yb, zb, rx, ry, rz;
       const typename P::V4 qa = ld4(&a.q4[ga]), qb = ld4(&a.q4[gb]);
       geo.local(qa, block_code(qa.w, ox, oy, oz), xa, ya, za);
@@ -783,8 +796,8 @@ __global__ void __launch_bounds__(fd_warps<P>() * 32, P::mixed ? 8 : 4)
         R deps, margin;
         // float64 bound for the mixed path: energies at load plus this visit's sums
         auto exact = [&](R dv) -> double {
-          const double da = a.eps[sm.g[ia]] + (double)sm.acc[ia];
-          const double db = a.eps[sm.g[ib]] + (double)sm.acc[ib];
+          const double da = a.eps[gidx(ia)] + (double)sm.acc[ia];
+          const double db = a.eps[gidx(ib)] + (double)sm.acc[ib];
           return fmin(da, db) + (double)dv;
         };
         const int dcs = fd_pair<P>(k, sm.ex[slot], sm.ey[slot], sm.ez[slot], sm.base[slot], G, sm.U[slot], pa,
@@ -808,8 +821,8 @@ __global__ void __launch_bounds__(fd_warps<P>() * 32, P::mixed ? 8 : 4)
           const unsigned long long s = atomicAdd(rec_count, 1ull);
           if ((int64_t)s < rec_cap) {
             sdpd_pair_rec rc;
-            rc.id_i = a.id[sm.g[ia]];
-            rc.id_j = a.id[sm.g[ib]];
+            rc.id_i = a.id[gidx(ia)];
+            rc.id_j = a.id[gidx(ib)];
             rc.colour = colour;
             rc.owner = (int32_t)o;
             rc.decision = dcs;
@@ -834,7 +847,7 @@ __global__ void __launch_bounds__(fd_warps<P>() * 32, P::mixed ? 8 : 4)
   }
   const R pi_coef = (R)(c.c_rho / (c.C_K * c.m));
   for (int q = gl; q < nb; q += kGroupLanes) {
-    const int g = sm.g[q];
+    const int g = gidx(q);
     a.px[g] = sm.px[q]; a.py[g] = sm.py[q]; a.pz[g] = sm.pz[q];
     double e;
     if constexpr (P::mixed) e = a.eps[g] + (double)sm.acc[q];  // one float64 update per visit

@@ -245,17 +245,26 @@ __global__ void __launch_bounds__(128) k_force(Consts c, Arrays<P> a, const type
   R fx = R(0), fy = R(0), fz = R(0);
   home.frames_all(c);
   const int n = nn[i];
-#pragma unroll 4
-  for (int k = 0; k < n; ++k) {
-    const uint32_t e = __ldg(&nlist[i * c.nbr_cap + k]);
-    const V4 qj = ld4(&qp4[e >> 6]);
-    R dx, dy, dz;
-    home.disp_code(e & 63u, qj, dx, dy, dz);
-    const R r2 = r2_of(dx, dy, dz);
-    const R s = (pi_i + qj.w) * kernel_F<KIND>(sqrt(r2) * inv_h, cF);
-    fx += s * dx;
-    fy += s * dy;
-    fz += s * dz;
+  // the row is 16-byte aligned (nbr_cap is a multiple of 4): four entries
+  // per load, then four independent neighbour gathers
+  const uint4* row4 = reinterpret_cast<const uint4*>(nlist + i * c.nbr_cap);
+  for (int k = 0; k < n; k += 4) {
+    const uint4 e4 = __ldg(&row4[k >> 2]);
+    const uint32_t ev[4] = {e4.x, e4.y, e4.z, e4.w};
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (k + u < n) {
+        const uint32_t e = ev[u];
+        const V4 qj = ld4(&qp4[e >> 6]);
+        R dx, dy, dz;
+        home.disp_code(e & 63u, qj, dx, dy, dz);
+        const R r2 = r2_of(dx, dy, dz);
+        const R s = (pi_i + qj.w) * kernel_F<KIND>(sqrt(r2) * inv_h, cF);
+        fx += s * dx;
+        fy += s * dy;
+        fz += s * dz;
+      }
+    }
   }
   const R m2 = (R)(c.m * c.m);
   fx *= m2; fy *= m2; fz *= m2;

@@ -260,26 +260,37 @@ __global__ void __launch_bounds__(kSchedWarps * 32)
       }
       const int excl = incl - n;
       const int packed = (myB << 8) | e0;  // partner cell and first entry of this lane's segment
-      for (int t0 = 0; t0 < total; t0 += 32) {
-        const int t = t0 + lane;
-        // owner lane: the number of lanes whose inclusive count is <= t
-        int pos = 0;
+      // two rounds of 32 entries per iteration, both list loads issued
+      // before either is used
+      for (int t0 = 0; t0 < total; t0 += 64) {
+        int o_pk[2], o_rk[2], o_q[2];
+        uint32_t ent[2];
 #pragma unroll
-        for (int step = 16; step > 0; step >>= 1) {
-          const int v = __shfl_sync(0xffffffffu, incl, pos + step - 1);
-          if (v <= t) pos += step;
+        for (int h = 0; h < 2; ++h) {
+          const int t = t0 + 32 * h + lane;
+          // owner lane: the number of lanes whose inclusive count is <= t
+          int pos = 0;
+#pragma unroll
+          for (int step = 16; step > 0; step >>= 1) {
+            const int v = __shfl_sync(0xffffffffu, incl, pos + step - 1);
+            if (v <= t) pos += step;
+          }
+          const int src = min(pos, 31);
+          o_pk[h] = __shfl_sync(0xffffffffu, packed, src);
+          const int o_ex = __shfl_sync(0xffffffffu, excl, src);
+          const int o_g = __shfl_sync(0xffffffffu, g, src);
+          o_rk[h] = __shfl_sync(0xffffffffu, rk, src);
+          o_q[h] = t < total ? (o_pk[h] & 255) + (t - o_ex) : -1;
+          ent[h] = o_q[h] >= 0 ? __ldg(&nlist[(int64_t)o_g * c.nbr_cap + o_q[h]]) : 0u;
         }
-        const int src = min(pos, 31);
-        const int o_pk = __shfl_sync(0xffffffffu, packed, src);
-        const int o_ex = __shfl_sync(0xffffffffu, excl, src);
-        const int o_g = __shfl_sync(0xffffffffu, g, src);
-        const int o_rk = __shfl_sync(0xffffffffu, rk, src);
-        if (t < total) {
-          const int q = (o_pk & 255) + (t - o_ex);
-          const int oB = o_pk >> 8;
-          const int j = (int)(__ldg(&nlist[(int64_t)o_g * c.nbr_cap + q]) >> 6);
-          const int rj = sm.rank[sm.cbase[oB] + (j - sm.cstart[oB])];
-          if (o_rk < rj) atomicOr(&sm.bits[o_rk >> 5][rj - o_rk], 1u << (o_rk & 31));
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          if (o_q[h] >= 0) {
+            const int oB = o_pk[h] >> 8;
+            const int j = (int)(ent[h] >> 6);
+            const int rj = sm.rank[sm.cbase[oB] + (j - sm.cstart[oB])];
+            if (o_rk[h] < rj) atomicOr(&sm.bits[o_rk[h] >> 5][rj - o_rk[h]], 1u << (o_rk[h] & 31));
+          }
         }
       }
       if (!__any_sync(0xffffffffu, more)) break;

@@ -260,13 +260,14 @@ __global__ void __launch_bounds__(kSchedWarps * 32)
       }
       const int excl = incl - n;
       const int packed = (myB << 8) | e0;  // partner cell and first entry of this lane's segment
-      // two rounds of 32 entries per iteration, both list loads issued
-      // before either is used
-      for (int t0 = 0; t0 < total; t0 += 64) {
-        int o_pk[2], o_rk[2], o_q[2];
-        uint32_t ent[2];
+      // kDeep rounds of 32 entries per iteration, all list loads issued
+      // before any is used
+      constexpr int kDeep = 4;
+      for (int t0 = 0; t0 < total; t0 += 32 * kDeep) {
+        int o_pk[kDeep], o_rk[kDeep], o_q[kDeep];
+        uint32_t ent[kDeep];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
+        for (int h = 0; h < kDeep; ++h) {
           const int t = t0 + 32 * h + lane;
           // owner lane: the number of lanes whose inclusive count is <= t
           int pos = 0;
@@ -284,7 +285,7 @@ __global__ void __launch_bounds__(kSchedWarps * 32)
           ent[h] = o_q[h] >= 0 ? __ldg(&nlist[(int64_t)o_g * c.nbr_cap + o_q[h]]) : 0u;
         }
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
+        for (int h = 0; h < kDeep; ++h) {
           if (o_q[h] >= 0) {
             const int oB = o_pk[h] >> 8;
             const int j = (int)(ent[h] >> 6);

@@ -129,6 +129,9 @@ def lib():
             "orc_density_vjp": (None, [P, _dp, _dp, _dp, _dp]),
             "orc_virial_vjp": (C.c_double, [P, _dp, _dp, _dp, _dp, _dp, _dp, _dp]),
             "orc_vv_vjp": (None, [P, _dp, _dp, _dp, C.c_double, C.c_int, _dp, _dp, _dp, _dp, _dp, _dp, _dp]),
+            "orc_frozen_run": (None, [P, _dp, _dp, _dp, C.c_double, C.c_int, _dp, _dp]),
+            "orc_frozen_vjp": (None, [P, _dp, _dp, _dp, C.c_double, C.c_int, _dp, _dp, _dp, _dp, _dp, _dp, _dp,
+                                      _dp, _dp]),
             "orc_sizeof_params": (C.c_int, []),
             "orc_sizeof_pair_rec": (C.c_int, []),
         }
@@ -414,3 +417,50 @@ def vv_virial_grad(P: Params, q0, p0, eps0, dt, nsteps):
     val, gq, gp, ge, gt = virial_vjp(P, qn, pn, en)
     gq0, gp0, ge0, gt0 = vv_vjp(P, q0, p0, eps0, dt, nsteps, gq, gp, ge)
     return val, gq0, gp0, ge0, gt0 + gt
+
+
+def _incr(a, shape):
+    return None if a is None else np.ascontiguousarray(np.broadcast_to(_f64(a), shape))
+
+
+def frozen_run(P: Params, q0, p0, eps0, dt, nsteps, dp=None, deps=None):
+    """Final (q, p, eps) of nsteps steps x <- VV(x) + increment_k, the
+    increments dp [nsteps][N][3] and deps [nsteps][N] held fixed (None: 0)."""
+    q, p, e = _f64(q0).copy(), _f64(p0).copy(), _f64(eps0).copy()
+    dp = _incr(dp, (nsteps, P.N, 3))
+    deps = _incr(deps, (nsteps, P.N))
+    lib().orc_frozen_run(C.byref(P), _d(q), _d(p), _d(e), dt, nsteps, _d(dp) if dp is not None else None,
+                         _d(deps) if deps is not None else None)
+    return q, p, e
+
+
+def frozen_vjp(P: Params, q0, p0, eps0, dt, nsteps, dp, deps, gqn, gpn, gepsn):
+    """Cotangents of (q0, p0, eps0, (h, c_rho, C_K)) of frozen_run, given
+    those of its final state."""
+    q0, p0, eps0 = _f64(q0), _f64(p0), _f64(eps0)
+    gqn, gpn, gepsn = _f64(gqn), _f64(gpn), _f64(gepsn)
+    dp = _incr(dp, (nsteps, P.N, 3))
+    deps = _incr(deps, (nsteps, P.N))
+    gq = np.empty((P.N, 3))
+    gp = np.empty((P.N, 3))
+    ge = np.empty(P.N)
+    gt = np.empty(3)
+    lib().orc_frozen_vjp(C.byref(P), _d(q0), _d(p0), _d(eps0), dt, nsteps,
+                         _d(dp) if dp is not None else None, _d(deps) if deps is not None else None,
+                         _d(gqn), _d(gpn), _d(gepsn), _d(gq), _d(gp), _d(ge), _d(gt))
+    return gq, gp, ge, gt
+
+
+def sweep_increments(P: Params, q0, p0, eps0, dt, nsteps, seed):
+    """Increments (dp, deps) of the sweeps of an nsteps full run (Velocity
+    Verlet then one sweep per step, sweep counter from 0), and the final
+    state of the frozen run that reproduces it."""
+    q, p, e = _f64(q0).copy(), _f64(p0).copy(), _f64(eps0).copy()
+    dps, des = [], []
+    for k in range(nsteps):
+        q, p, e = frozen_run(P, q, p, e, dt, 1)
+        st, p2, e2, _, _ = fd_sweep(P, q, p, e, dt, seed, k)
+        dps.append(p2 - p)
+        des.append(e2 - e)
+        p, e = p + dps[-1], e + des[-1]
+    return np.array(dps), np.array(des), (q, p, e)

@@ -1081,5 +1081,100 @@ void orc_vv_vjp(const orc_params* P, const double* q0, const double* p0, const d
   free(qs); free(p); free(eps); free(rho); free(S); free(gS); free(rbar); free(v);
 }
 
+/* Trajectory with the sweeps frozen: n steps of x_{k+1} = VV(x_k) + D_k,
+ * where D_k = (dp_k [N][3], deps_k [N]) are given increments of the momenta
+ * and internal energies (those that step k's fluctuation/dissipation sweep
+ * produced, held fixed); NULL increments are zero.  Velocity Verlet
+ * recomputes the entropies at every step from the current energies
+ * (Section 3.1).  Updates (q, p, eps) in place. */
+void orc_frozen_run(const orc_params* P, double* q, double* p, double* eps, double dt, int nsteps,
+                    const double* dp, const double* deps) {
+  int64_t N = P->N;
+  for (int k = 0; k < nsteps; ++k) {
+    orc_verlet(P, q, p, eps, dt);
+    if (dp)
+      for (int64_t i = 0; i < 3 * N; ++i) p[i] += dp[(size_t)k * 3 * (size_t)N + (size_t)i];
+    if (deps)
+      for (int64_t i = 0; i < N; ++i) eps[i] += deps[(size_t)k * (size_t)N + (size_t)i];
+  }
+}
+
+/* Reverse mode of orc_frozen_run: given the cotangents (gqn, gpn, gepsn) of
+ * the final state, writes those of (q0, p0, eps0) and of theta = (h, c_rho,
+ * C_K).  Step k backwards: the increments pass cotangents through; the
+ * final energies eps' = E(S_k, rho(q_{k+1})) and the two kicks at fixed S_k
+ * are pulled back; then S_k = C_K ln eps_k - c_rho ln rho(q_k) carries the
+ * entropy cotangent to the energies and positions at the start of step k. */
+void orc_frozen_vjp(const orc_params* P, const double* q0, const double* p0, const double* eps0, double dt,
+                    int nsteps, const double* dp, const double* deps, const double* gqn, const double* gpn,
+                    const double* gepsn, double* gq0, double* gp0, double* geps0, double gth[3]) {
+  int64_t N = P->N;
+  size_t n1 = (size_t)(N ? N : 1), n3 = 3 * n1;
+  double* qs = (double*)malloc(sizeof(double) * n3 * (size_t)(nsteps + 1));
+  double* es = (double*)malloc(sizeof(double) * n1 * (size_t)(nsteps + 1));
+  double* p = (double*)malloc(sizeof(double) * n3);
+  double* rho = (double*)malloc(sizeof(double) * n1);
+  double* S = (double*)malloc(sizeof(double) * n1);
+  double* gS = (double*)malloc(sizeof(double) * n1);
+  double* ge = (double*)malloc(sizeof(double) * n1);
+  double* rbar = (double*)malloc(sizeof(double) * n1);
+  double* v = (double*)malloc(sizeof(double) * n3);
+  /* forward, keeping the positions and energies at every step start */
+  memcpy(qs, q0, sizeof(double) * 3 * (size_t)N);
+  memcpy(es, eps0, sizeof(double) * (size_t)N);
+  memcpy(p, p0, sizeof(double) * 3 * (size_t)N);
+  for (int k = 0; k < nsteps; ++k) {
+    double* q = qs + n3 * (size_t)(k + 1);
+    double* e = es + n1 * (size_t)(k + 1);
+    memcpy(q, qs + n3 * (size_t)k, sizeof(double) * 3 * (size_t)N);
+    memcpy(e, es + n1 * (size_t)k, sizeof(double) * (size_t)N);
+    orc_frozen_run(P, q, p, e, dt, 1, dp ? dp + (size_t)k * 3 * (size_t)N : NULL,
+                   deps ? deps + (size_t)k * (size_t)N : NULL);
+  }
+  gth[0] = gth[1] = gth[2] = 0.0;
+  double* gq = gq0;
+  double* gp = gp0;
+  memcpy(gq, gqn, sizeof(double) * 3 * (size_t)N);
+  memcpy(gp, gpn, sizeof(double) * 3 * (size_t)N);
+  memcpy(ge, gepsn, sizeof(double) * (size_t)N);
+  for (int k = nsteps - 1; k >= 0; --k) {
+    const double* qk = qs + n3 * (size_t)k;
+    const double* q1 = qs + n3 * (size_t)(k + 1);
+    const double* ek = es + n1 * (size_t)k;
+    orc_density(P, qk, rho);
+    for (int64_t i = 0; i < N; ++i) {
+      S[i] = orc_S(P, ek[i], rho[i]);
+      gS[i] = 0.0;
+    }
+    /* eps' = E(S_k, rho(q_{k+1})) at the end of the Verlet step */
+    orc_density(P, q1, rho);
+    for (int64_t i = 0; i < N; ++i) {
+      double e = orc_E_of_S(P, S[i], rho[i]), g = ge[i] * e / P->C_K;
+      gS[i] += g;
+      rbar[i] = g * P->c_rho / rho[i];
+      gth[1] += g * log(rho[i]);
+      gth[2] -= g * log(e);
+    }
+    orc_density_vjp(P, q1, rbar, gq, gth);
+    /* second kick at q_{k+1}, drift, first kick at q_k (fixed S_k) */
+    for (size_t j = 0; j < 3 * (size_t)N; ++j) v[j] = 0.5 * dt * gp[j];
+    orc_pair_vjp(P, q1, S, 1, 0, v, 1.0, gq, gS, gth);
+    for (size_t j = 0; j < 3 * (size_t)N; ++j) gp[j] += dt / P->m * gq[j];
+    for (size_t j = 0; j < 3 * (size_t)N; ++j) v[j] = 0.5 * dt * gp[j];
+    orc_pair_vjp(P, qk, S, 1, 0, v, 1.0, gq, gS, gth);
+    /* S_k = C_K ln eps_k - c_rho ln rho(q_k) */
+    orc_density(P, qk, rho);
+    for (int64_t i = 0; i < N; ++i) {
+      ge[i] = gS[i] * P->C_K / ek[i];
+      rbar[i] = -gS[i] * P->c_rho / rho[i];
+      gth[1] -= gS[i] * log(rho[i]);
+      gth[2] += gS[i] * log(ek[i]);
+    }
+    orc_density_vjp(P, qk, rbar, gq, gth);
+  }
+  memcpy(geps0, ge, sizeof(double) * (size_t)N);
+  free(qs); free(es); free(p); free(rho); free(S); free(gS); free(ge); free(rbar); free(v);
+}
+
 int orc_sizeof_params(void) { return (int)sizeof(orc_params); }
 int orc_sizeof_pair_rec(void) { return (int)sizeof(orc_pair_rec); }

@@ -208,3 +208,67 @@ def test_coincident_particles():
     val, gq, gp, ge, gt = O.virial_vjp(P, q, p, e)
     ref = central(lambda d: O.virial_pressure(with_param(cfg, "h", P.h * (1 + d)), q, p, e)) / P.h
     assert abs(gt[0] - ref) < 1e-6 * abs(ref)
+
+
+def frozen_setup(kernel=O.KERNEL_LUCY, scheme=O.SCHEME_EMS, K=5.0, seed=3, dt=0.02, ns=3):
+    cfg, q, p, e = setup(kernel, K=K, seed=seed)
+    cfg_fd = O.Config(N=cfg.N, L=cfg.L, K=K, kernel=kernel, scheme=scheme)
+    dp, de, _ = O.sweep_increments(cfg_fd.params(), q, p, e, dt, ns, seed=7)
+    return cfg, q, p, e, dp, de, dt, ns
+
+
+def test_frozen_run_reproduces_the_full_run():
+    """Velocity Verlet plus the recorded sweep increments retraces the full
+    run (Velocity Verlet then the sweep, every step) to rounding."""
+    cfg, q, p, e, dp, de, dt, ns = frozen_setup()
+    P = O.Config(N=cfg.N, L=cfg.L, K=5.0, scheme=O.SCHEME_EMS).params()
+    st, qr, pr, er, _, _ = O.run(P, q, p, e, dt, ns, seed=7)
+    qf, pf, ef = O.frozen_run(cfg.params(), q, p, e, dt, ns, dp, de)
+    assert np.abs(qf - qr).max() < 1e-12 and np.abs(pf - pr).max() < 1e-12
+    assert np.abs(ef - er).max() < 1e-12 * er.max()
+    assert np.abs(dp).max() > 1e-3  # the sweeps did move the momenta
+
+
+def test_frozen_gradient_with_zero_increments_is_the_verlet_gradient():
+    """Without increments every step recomputes the same entropies, so the
+    per-step reverse pass equals the fixed-entropy one."""
+    cfg, q, p, e = setup()
+    P = cfg.params()
+    rng = np.random.default_rng(9)
+    c = [rng.standard_normal(x.shape) for x in (q, p, e)]
+    a = O.frozen_vjp(P, q, p, e, 0.02, 3, None, None, *c)
+    b = O.vv_vjp(P, q, p, e, 0.02, 3, *c)
+    for x, y in zip(a, b):
+        assert np.abs(x - y).max() <= 1e-9 * np.abs(y).max()
+    z = O.frozen_vjp(P, q, p, e, 0.02, 0, None, None, *c)  # no step: the identity
+    assert np.array_equal(z[0], c[0]) and np.array_equal(z[1], c[1]) and np.array_equal(z[2], c[2])
+
+
+@pytest.mark.parametrize("kernel", [O.KERNEL_CUBIC, O.KERNEL_LUCY])
+def test_frozen_virial_gradient_by_differences(kernel):
+    """The virial pressure after 3 steps with the sweeps' increments frozen:
+    the reverse pass against central differences in (q0, p0, eps0) and
+    theta (the increments, not recomputed, make the map smooth)."""
+    cfg, q, p, e, dp, de, dt, ns = frozen_setup(kernel)
+    P = cfg.params()
+
+    def loss(Pp, x):
+        return O.virial_pressure(Pp, *O.frozen_run(Pp, *x, dt, ns, dp, de))
+    qn, pn, en = O.frozen_run(P, q, p, e, dt, ns, dp, de)
+    val, gqn, gpn, gen, gtn = O.virial_vjp(P, qn, pn, en)
+    gq, gp, ge, gt = O.frozen_vjp(P, q, p, e, dt, ns, dp, de, gqn, gpn, gen)
+    gt = gt + gtn
+    rng = np.random.default_rng(4)
+    for k, g in enumerate((gq, gp, ge)):
+        u = rng.standard_normal(g.shape) * (e if k == 2 else 1.0)
+
+        def f(d, k=k, u=u):
+            x = [q, p, e]
+            x[k] = x[k] + d * u
+            return loss(P, x)
+        ref = central(f)
+        assert abs((g * u).sum() - ref) < 1e-6 * np.abs(g * u).sum()
+    for k, name in enumerate(THETA):
+        base = getattr(P, name)
+        ref = central(lambda d: loss(with_param(cfg, name, base + d * base), [q, p, e])) / base
+        assert abs(gt[k] - ref) < 1e-6 * max(1.0, abs(ref))

@@ -434,27 +434,31 @@ def run_ensemble(args, rank, world, local_rank):
 
 
 def adjoint_cpu_sample(args):
-    """The oracle's gradient (forward Verlet steps kept in memory, then the
-    reverse pass; O(N^2) pair loops) on a 16^3 lattice of the same fluid,
-    2 steps."""
+    """The oracle's gradient on a 16^3 lattice of the same fluid, 2 steps:
+    the full steps with their exact Metropolised sweeps (increments kept),
+    the virial pressure's gradient, the reverse pass of the frozen map
+    (O(N^2) pair loops, forward states kept in memory)."""
     import oracle as O
 
     w = Workload(n=16, K=args.adj_K, kT=1.0, seed=0)
     q, p, e = lattice_state(w)
-    P = O.Config(N=w.N, L=w.L, K=w.K, scheme=O.SCHEME_NONE).params()
+    P = O.Config(N=w.N, L=w.L, K=w.K, scheme=O.SCHEME_EMS).params()
     O.lib()
     steps = 2
     t0 = time.perf_counter()
-    O.vv_virial_grad(P, q, p, e, args.dt, steps)
+    dps, des, (qn, pn, en) = O.sweep_increments(P, q, p, e, args.dt, steps, 3)
+    _, gq, gp, ge, _ = O.virial_vjp(P, qn, pn, en)
+    O.frozen_vjp(P, q, p, e, args.dt, steps, dps, des, gq, gp, ge)
     dt = time.perf_counter() - t0
-    desc = ("FP64 oracle gradient of the virial pressure (O(N^2) pair loops, single thread), "
-            "16^3 = %d-particle lattice of the same fluid, %d steps, %.1f s" % (w.N, steps, dt))
+    desc = ("FP64 oracle gradient of the virial pressure with the EMS sweeps frozen (O(N^2) pair loops, "
+            "single thread), 16^3 = %d-particle lattice of the same fluid, %d steps, %.1f s" % (w.N, steps, dt))
     return w.N * steps / dt, 1, desc
 
 
 def run_adjoint(args, rank, world, local_rank):
     """One bench step = one gradient of the virial pressure after
-    args.adj_steps Velocity Verlet steps (float64, checkpoint every
+    args.adj_steps steps (float64 Velocity Verlet, then the exact
+    Metropolised sweep with its increments frozen; checkpoint every
     args.adj_every steps) with respect to (q0, p0, eps0, h, c_rho, C_K):
     set_state from device-resident inputs, the recorded forward run, the
     virial pressure and its gradient, the reverse pass."""
@@ -470,13 +474,13 @@ def run_adjoint(args, rank, world, local_rank):
     steps = max(1, min(args.steps, 5))
     with torch.cuda.stream(stream):
         fma64 = sdpd.sdpd_fma_peak(sdpd.FP64, stream.cuda_stream)
-        s = sdpd.SDPD(w.N, w.L, m=w.m, h=w.h, K=w.K, precision=sdpd.FP64, scheme=sdpd.SCHEME_NONE,
+        s = sdpd.SDPD(w.N, w.L, m=w.m, h=w.h, K=w.K, precision=sdpd.FP64, scheme=sdpd.SCHEME_EMS,
                       stream=stream)
         qd, pd, ed = (torch.as_tensor(a, device="cuda") for a in (q, p, e))
 
         def gradient():
             s.set_state(qd, pd, ed)
-            tape = s.vv_record(args.dt, ns, every)
+            tape = s.vv_record(args.dt, ns, every, 3)
             val, gq, gp, ge, gth = s.virial(grad=True)
             return val, s.vv_adjoint(tape, gq, gp, ge), gth
 
@@ -498,7 +502,7 @@ def run_adjoint(args, rank, world, local_rank):
             c = torch.cuda.Event(enable_timing=True)
             a.record(stream)
             s.set_state(qd, pd, ed)
-            tape = s.vv_record(args.dt, ns, every)
+            tape = s.vv_record(args.dt, ns, every, 3)
             b.record(stream)
             val, gq, gp, ge, gth = s.virial(grad=True)
             g0 = s.vv_adjoint(tape, gq, gp, ge)
@@ -544,12 +548,13 @@ def run_adjoint(args, rank, world, local_rank):
         stream.synchronize()
     e2e_s = allreduce_max(time.perf_counter() - t0, world)
     line = {
-        "metric": "gradient particle-steps/s (virial pressure after %d Velocity Verlet steps, reverse mode)" % ns,
+        "metric": "gradient particle-steps/s (virial pressure after %d steps, EMS sweeps frozen, reverse mode)" % ns,
         "value": value, "unit": UNIT, "n_gpus": world, "steps": steps, "warmup": args.warmup,
         "ms_per_step": ms_max / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
         "config": {"workload": "adjoint: %d^3 = %d particles, jittered sc lattice, L=%d, Lucy h=2.5a, kT=1, "
-                               "K=%g, dt=%g, %d Verlet steps, checkpoint every %d, float64"
+                               "K=%g, dt=%g, %d steps (Verlet + EMS sweep, increments frozen), "
+                               "checkpoint every %d, float64"
                                % (w.n, w.N, w.n, w.K, args.dt, ns, every),
                    "N": w.N, "K": w.K, "steps_per_gradient": ns, "checkpoint_every": every,
                    "l2": "working set below L2 (the workload is fixed at 32^3)"},

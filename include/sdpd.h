@@ -255,46 +255,72 @@ void* sdpd_ensemble_stream(const sdpd_ens_t* e);
 void sdpd_ensemble_destroy(sdpd_ens_t* e);
 
 /* ---------------------------------------------------------------------------
- * Gradients of the conservative dynamics (reverse mode; float64 handles
- * without fd_only, else SDPD_ERR_INVALID_ARG).
+ * Gradients of the conservative dynamics with the sweeps frozen (reverse
+ * mode; float64 handles without fd_only, else SDPD_ERR_INVALID_ARG).
  *
- * The differentiated map is nsteps Velocity Verlet steps, Eq. (sdpd-verlet),
- * with the entropies S_i = C_K ln eps_i - c_rho ln rho_i(q^0) held fixed
- * (Section 3.1: eps_i = E(S_i, rho_i(q)) after every drift, pressures from
- * Eq. (pg-eos)), from the loaded state (q^0, p^0, eps^0) to (q^n, p^n,
- * eps^n).  No fluctuation/dissipation sweep runs.  The parameters
- * differentiated are theta = (h, c_rho, C_K); kB, m and the box are fixed.
- * Pair derivatives use the density gradient of Eq. (gradient-rho) and dW/dh,
- * dF/dh of the chosen kernel.  Cotangent arrays are device float64 in
- * particle-id order: [N][3] for q and p, [N] for eps.
+ * The differentiated map is nsteps steps x_{k+1} = VV(x_k) + D_k from the
+ * loaded state (q^0, p^0, eps^0): one Velocity Verlet step, Eq.
+ * (sdpd-verlet), with the entropies S_i = C_K ln eps_i - c_rho ln rho_i(q)
+ * of the state at its start held fixed (Section 3.1: eps_i = E(S_i,
+ * rho_i(q)) after the drift, pressures from Eq. (pg-eos)), then the
+ * increments D_k of the momenta and internal energies that step k's
+ * fluctuation/dissipation sweep (Sections 3.2-3.3, the handle's scheme and
+ * theta) produced when the trajectory was recorded, held fixed: the sweep's
+ * decisions and random numbers are frozen and so is its effect.  With
+ * SDPD_SCHEME_NONE every D_k is zero and the map is Velocity Verlet alone.
+ * The parameters differentiated are theta = (h, c_rho, C_K); kB, m and the
+ * box are fixed.  Pair derivatives use the density gradient of Eq.
+ * (gradient-rho) and dW/dh, dF/dh of the chosen kernel.  Cotangent and
+ * increment arrays are device float64 in particle-id order: [N][3] for q
+ * and p, [N] for eps.
  * ------------------------------------------------------------------------- */
 
 /* Bytes of the tape for nsteps steps with a checkpoint every `every` steps:
- * ((ceil(nsteps/every) + max(1, min(every, nsteps))) * 56 + 120) * N bytes plus a few
- * KiB.  0 for bad arguments (nsteps < 0, every < 1). */
+ * ((ceil(nsteps/every) + max(1, min(every, nsteps))) * 56
+ *  + max(1, nsteps) * 32 + 160) * N bytes plus a few KiB.
+ * 0 for bad arguments (nsteps < 0, every < 1). */
 size_t sdpd_tape_bytes(const sdpd_t* s, int64_t nsteps, int64_t every);
 
-/* Runs nsteps Velocity Verlet steps from the loaded state (as sdpd_step with
- * SDPD_SCHEME_NONE would) and records on `tape` (device memory of at least
- * sdpd_tape_bytes(s, nsteps, every) bytes, 256-byte aligned, owned by the
- * caller and kept unchanged until the matching sdpd_vv_adjoint calls are
- * done) the state at every `every`-th step and the final state.  Leaves the
- * handle at the final state; asynchronous.  Errors: SDPD_ERR_INVALID_ARG,
- * SDPD_ERR_NO_STATE, SDPD_ERR_NO_WORKSPACE, SDPD_ERR_CUDA. */
-int sdpd_vv_record(sdpd_t* s, double dt, int64_t nsteps, int64_t every, void* tape, size_t tape_bytes);
+/* Runs nsteps full steps from the loaded state (Velocity Verlet, then the
+ * sweep whenever sdpd_step would run one, random numbers keyed by seed) and
+ * records on `tape` (device memory of at least sdpd_tape_bytes(s, nsteps,
+ * every) bytes, 256-byte aligned, owned by the caller and kept unchanged
+ * until the matching sdpd_vv_adjoint / sdpd_vv_replay calls are done) the
+ * increments D_k of every step and the state at every `every`-th step and
+ * at the end.  Each step's result is stored as before + D_k, which makes the
+ * recorded trajectory the frozen map itself (it differs from sdpd_step's by
+ * rounding only).  Leaves the handle at the final state; asynchronous.
+ * Errors: SDPD_ERR_INVALID_ARG, SDPD_ERR_NO_STATE, SDPD_ERR_NO_WORKSPACE,
+ * SDPD_ERR_CUDA. */
+int sdpd_vv_record(sdpd_t* s, double dt, int64_t nsteps, int64_t every, uint64_t seed, void* tape,
+                   size_t tape_bytes);
 
 /* Reverse pass of the trajectory last recorded on this handle (`tape` and
  * `tape_bytes` as given to sdpd_vv_record).  Given the cotangents gq, gp,
  * geps of the final state (device; NULL = zero), writes those of the initial
  * state to gq0, gp0, geps0 (device) and of theta = (h, c_rho, C_K) to
  * gtheta[3] (host).  Positions between checkpoints are recomputed from the
- * tape, bit-identical to the recorded run, so the result does not depend on
- * `every`.  Uses the handle's workspace and leaves the handle at the recorded
- * final state again.  Synchronising; returns the sticky device status.
- * May be called again with other cotangents.  Errors: SDPD_ERR_INVALID_ARG
- * (no matching record), SDPD_ERR_CAPACITY, SDPD_ERR_CUDA. */
+ * tape (Verlet plus the stored increments), bit-identical to the recorded
+ * run, so the result does not depend on `every`.  Uses the handle's
+ * workspace and leaves the handle at the recorded final state again.
+ * Synchronising; returns the sticky device status.  May be called again
+ * with other cotangents.  Errors: SDPD_ERR_INVALID_ARG (no matching
+ * record), SDPD_ERR_CAPACITY, SDPD_ERR_CUDA. */
 int sdpd_vv_adjoint(sdpd_t* s, void* tape, size_t tape_bytes, const double* gq, const double* gp,
                     const double* geps, double* gq0, double* gp0, double* geps0, double gtheta[3]);
+
+/* The frozen map of the last record, evaluated from the currently loaded
+ * state: nsteps Velocity Verlet steps, each followed by the recorded
+ * increments (no sweep runs).  From the recorded initial state it retraces
+ * the recording bit for bit; from another state it is the map that
+ * sdpd_vv_adjoint differentiates.  Asynchronous.  Errors:
+ * SDPD_ERR_INVALID_ARG (no matching record), SDPD_ERR_NO_STATE. */
+int sdpd_vv_replay(sdpd_t* s, const void* tape, size_t tape_bytes);
+
+/* Copies the recorded increments of step `step` (0 <= step < nsteps):
+ * momenta to dp [N][3] and energies to deps [N] (device, id order).
+ * Asynchronous.  Errors: SDPD_ERR_INVALID_ARG. */
+int sdpd_tape_increments(sdpd_t* s, const void* tape, size_t tape_bytes, int64_t step, double* dp, double* deps);
 
 /* Virial pressure of the current state at its own energies,
  * P = (1/3V) [sum_i |p_i|^2/m + sum_{i<j} r_ij . F_ij] with the pair forces

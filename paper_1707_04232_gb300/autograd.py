@@ -1,8 +1,11 @@
 """torch.autograd functions over the library's reverse-mode entry points.
 
 ``VerletTrajectory`` maps (q0, p0, eps0, theta) to the state after nsteps
-Velocity Verlet steps at fixed entropies (Section 3.1); its backward is the
-library's checkpointed reverse pass.  ``VirialPressure`` maps a state to its
+steps x_{k+1} = VV(x_k) + D_k: a Velocity Verlet step at fixed entropies
+(Section 3.1), then the increments D_k that the handle's fluctuation/
+dissipation sweep (Sections 3.2-3.3) produced in the forward run, held fixed
+(no sweep on a SCHEME_NONE handle, D_k = 0).  Its backward is the library's
+checkpointed reverse pass.  ``VirialPressure`` maps a state to its
 virial pressure.  theta = (h, c_rho, C_K) is a float64 tensor that must hold
 the handle's own values (the library evaluates at those); it carries the
 parameter gradient.  Both run on a float64 SDPD handle.  Argument marshalling
@@ -32,10 +35,10 @@ def _check_theta(sim: SDPD, theta: torch.Tensor):
 
 class VerletTrajectory(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, q0, p0, eps0, theta, sim: SDPD, dt: float, nsteps: int, every: int):
+    def forward(ctx, q0, p0, eps0, theta, sim: SDPD, dt: float, nsteps: int, every: int, seed: int):
         _check_theta(sim, theta)
         sim.set_state(q0.detach(), p0.detach(), eps0.detach())
-        tape = sim.vv_record(dt, nsteps, every)
+        tape = sim.vv_record(dt, nsteps, every, seed)
         dev = q0.device
         q = torch.empty((sim.N, 3), dtype=torch.float64, device=dev)
         p = torch.empty((sim.N, 3), dtype=torch.float64, device=dev)
@@ -48,7 +51,7 @@ class VerletTrajectory(torch.autograd.Function):
     def backward(ctx, gq, gp, ge):
         gq0, gp0, ge0, gth = ctx.sim.vv_adjoint(ctx.tape, gq, gp, ge)
         gth = torch.as_tensor(gth, dtype=torch.float64, device=ctx.theta_device)
-        return gq0, gp0, ge0, gth, None, None, None, None
+        return gq0, gp0, ge0, gth, None, None, None, None, None
 
 
 class VirialPressure(torch.autograd.Function):
@@ -67,8 +70,8 @@ class VirialPressure(torch.autograd.Function):
         return g * gq, g * gp, g * ge, g.to(ctx.gth.device) * ctx.gth, None
 
 
-def verlet_trajectory(sim, q0, p0, eps0, theta, dt, nsteps, every=10):
-    return VerletTrajectory.apply(q0, p0, eps0, theta, sim, dt, nsteps, every)
+def verlet_trajectory(sim, q0, p0, eps0, theta, dt, nsteps, every=10, seed=0):
+    return VerletTrajectory.apply(q0, p0, eps0, theta, sim, dt, nsteps, every, seed)
 
 
 def virial_pressure(sim, q, p, eps, theta):

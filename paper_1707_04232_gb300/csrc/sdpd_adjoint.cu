@@ -104,46 +104,104 @@ __global__ void __launch_bounds__(128) k_adj_pairsum(Consts c, const D4* __restr
   A[i] = c.m * c.m * acc;
 }
 
-// Elementwise step of the trajectory's reverse pass at fixed entropy:
-// pi = c_rho eps / (C_K m rho) with eps = E(S, rho), so
+// Elementwise step of the trajectory's reverse pass at position k (state
+// after the sweep increments of step k - 1).  Pressures pi = c_rho eps /
+// (C_K m rho); at fixed entropy (eps = E(S, rho))
 //   dpi/drho = pi (c_rho/C_K - 1)/rho, dpi/dS = pi/C_K,
 //   dpi/dc_rho = pi (1/c_rho + ln rho / C_K), dpi/dC_K = -pi (1 + ln eps)/C_K.
-// FINAL: the cotangent of the final energies eps_n = E(S, rho(q_n)) enters;
-// INITIAL: S = C_K ln eps_0 - c_rho ln rho(q_0) is pulled back to eps_0 and q_0.
-constexpr int kAdjFinal = 1;
-constexpr int kAdjInitial = 2;
+// KICK1 (k < n): first kick of step k at S_k, with eps_k; then the entropy
+//   S_k = C_K ln eps_k - c_rho ln rho_k carries Sbar_cur (complete now) to
+//   eps_k and rho_k.  Without KICK1 the cotangent of eps_k is epsbar_n.
+// KICK2 (k > 0): second kick of step k - 1 at S_{k-1}, with the energies
+//   before the increments, eps'_k = eps_k - deps_{k-1}, and the final
+//   energies eps'_k = E(S_{k-1}, rho_k) (the increments pass cotangents
+//   through); they start Sbar_prev, the entropy cotangent of step k - 1.
+// Both kicks pull back along the same v, so the pair pass that follows uses
+// the summed pressures (written to qp4.w) and rbar (vs4.w).
+constexpr int kAdjKick1 = 1;
+constexpr int kAdjKick2 = 2;
 
-__global__ void k_adj_mid_traj(Consts c, const D4* __restrict__ qp4, const double* __restrict__ rho,
+__global__ void k_adj_mid_step(Consts c, D4* __restrict__ qp4, const double* __restrict__ rho,
                                const double* __restrict__ eps, const int32_t* __restrict__ id,
-                               const double* __restrict__ A, D4* __restrict__ vs4, double* __restrict__ Sbar,
-                               double* __restrict__ thbar, const double* __restrict__ epsbar_n, int flags,
-                               double* __restrict__ epsbar0) {
+                               const double* __restrict__ A, int flags, const double* __restrict__ deps_prev,
+                               double* __restrict__ Sbar_cur, double* __restrict__ Sbar_prev,
+                               const double* __restrict__ epsbar_n, double* __restrict__ epsbar0,
+                               D4* __restrict__ vs4, double* __restrict__ thbar) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= c.N) return;
   const int64_t k = id[i];
-  const double e = eps[i], r = rho[i], CK = c.C_K, cr = c.c_rho;
-  const double lr = log(r), le = log(e);
-  const double g = A ? A[i] * qp4[i].w : 0.0;
-  double sbar = Sbar[k] + g / CK;
-  double rb = g * (cr / CK - 1.0) / r;
-  double tcr = g * (1.0 / cr + lr / CK), tck = -g * (1.0 + le) / CK;
-  if (flags & kAdjFinal) {  // dE/dS = eps/C_K, dE/drho = eps c_rho/(C_K rho)
-    const double ge = (epsbar_n ? epsbar_n[k] : 0.0) * e / CK;
-    sbar += ge;
-    rb += ge * cr / r;
-    tcr += ge * lr;
-    tck -= ge * le;
+  const double CK = c.C_K, cr = c.c_rho, r = rho[i], lr = log(r);
+  const double pif = cr / (CK * c.m * r);  // pi per unit energy
+  const double a_i = A ? A[i] : 0.0;
+  double rb = 0.0, tcr = 0.0, tck = 0.0, pisum = 0.0, ge;
+  if (flags & kAdjKick1) {
+    const double e = eps[i], le = log(e), pi = e * pif, g = a_i * pi;
+    const double sb = Sbar_cur[k] + g / CK;
+    rb += g * (cr / CK - 1.0) / r;
+    tcr += g * (1.0 / cr + lr / CK);
+    tck -= g * (1.0 + le) / CK;
+    pisum += pi;
+    ge = sb * CK / e;  // S_k = C_K ln eps_k - c_rho ln rho_k
+    rb -= sb * cr / r;
+    tcr -= sb * lr;
+    tck += sb * le;
+  } else {
+    ge = epsbar_n ? epsbar_n[k] : 0.0;
   }
-  if (flags & kAdjInitial) {
-    epsbar0[k] = sbar * CK / e;
-    rb -= sbar * cr / r;
-    tcr -= sbar * lr;
-    tck += sbar * le;
+  if (flags & kAdjKick2) {
+    const double e = eps[i] - deps_prev[k], le = log(e), pi = e * pif, g = a_i * pi;
+    const double gf = ge * e / CK;  // eps' = E(S_{k-1}, rho_k)
+    rb += gf * cr / r + g * (cr / CK - 1.0) / r;
+    tcr += gf * lr + g * (1.0 / cr + lr / CK);
+    tck -= gf * le + g * (1.0 + le) / CK;
+    pisum += pi;
+    Sbar_prev[k] = gf + g / CK;
   }
-  Sbar[k] = sbar;
+  if (epsbar0) epsbar0[k] = ge;
   thbar[3 * k + 1] += tcr;
   thbar[3 * k + 2] += tck;
   vs4[i].w = rb;
+  qp4[i].w = pisum;
+}
+
+// Recording a step with its sweep frozen: the increments d = after - before
+// of the momenta and energies (id order) are stored, and the state is set to
+// before + d, the value a replay that adds d reproduces bit for bit.  The
+// pressure the next first kick uses, pi = c_rho eps / (C_K m rho) (Eq.
+// pg-eos), is recomputed from the stored energy, as the replay does.
+__global__ void k_adj_freeze(int64_t N, double pi_coef, const int32_t* __restrict__ id, double* __restrict__ px,
+                             double* __restrict__ py, double* __restrict__ pz, double* __restrict__ eps,
+                             const double* __restrict__ rho, D4* __restrict__ qp4, const double* __restrict__ pre,
+                             double* __restrict__ dp, double* __restrict__ de) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int64_t k = id[i];
+  double* v[4] = {px, py, pz, eps};
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const double b = pre[a * N + i], d = v[a][i] - b;
+    v[a][i] = b + d;
+    if (a < 3) dp[3 * k + a] = d;
+    else de[k] = d;
+  }
+  qp4[i].w = eps[i] * pi_coef / rho[i];
+}
+
+// Replaying a frozen step: the stored increments added to the state, and
+// the pressures recomputed from the new energies.
+__global__ void k_adj_increment(int64_t N, double pi_coef, const int32_t* __restrict__ id, double* __restrict__ px,
+                                double* __restrict__ py, double* __restrict__ pz, double* __restrict__ eps,
+                                const double* __restrict__ rho, D4* __restrict__ qp4, const double* __restrict__ dp,
+                                const double* __restrict__ de) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int64_t k = id[i];
+  px[i] = px[i] + dp[3 * k];
+  py[i] = py[i] + dp[3 * k + 1];
+  pz[i] = pz[i] + dp[3 * k + 2];
+  const double e = eps[i] + de[k];
+  eps[i] = e;
+  qp4[i].w = e * pi_coef / rho[i];
 }
 
 // Elementwise step of the virial pressure's gradient at fixed energies:
@@ -300,12 +358,30 @@ void launch_adj_pairsum(const Consts& c, const Workspace& w, int cur, int mode, 
   }
 }
 
-void launch_adj_mid_traj(const Consts& c, const Workspace& w, int cur, const double* A, D4* vs4, double* Sbar,
-                         double* thbar, const double* epsbar_n, int final_pos, double* epsbar0, cudaStream_t s) {
+void launch_adj_mid_step(const Consts& c, const Workspace& w, int cur, const double* A, bool kick1, bool kick2,
+                         const double* deps_prev, double* Sbar_cur, double* Sbar_prev, const double* epsbar_n,
+                         double* epsbar0, D4* vs4, double* thbar, cudaStream_t s) {
   if (c.N == 0) return;
-  const int flags = (final_pos ? kAdjFinal : 0) | (epsbar0 ? kAdjInitial : 0);
-  k_adj_mid_traj<<<nblocks(c.N, 256), 256, 0, s>>>(c, (const D4*)w.qp4, (const double*)w.rho[cur], w.eps[cur],
-                                                    w.id[cur], A, vs4, Sbar, thbar, epsbar_n, flags, epsbar0);
+  const int flags = (kick1 ? kAdjKick1 : 0) | (kick2 ? kAdjKick2 : 0);
+  k_adj_mid_step<<<nblocks(c.N, 256), 256, 0, s>>>(c, (D4*)w.qp4, (const double*)w.rho[cur], w.eps[cur], w.id[cur],
+                                                    A, flags, deps_prev, Sbar_cur, Sbar_prev, epsbar_n, epsbar0,
+                                                    vs4, thbar);
+}
+
+void launch_adj_freeze(const Consts& c, const Workspace& w, int cur, const double* pre, double* dp, double* de,
+                       cudaStream_t s) {
+  if (c.N == 0) return;
+  k_adj_freeze<<<nblocks(c.N, 256), 256, 0, s>>>(c.N, c.c_rho / (c.C_K * c.m), w.id[cur], (double*)w.px[cur],
+                                                  (double*)w.py[cur], (double*)w.pz[cur], w.eps[cur],
+                                                  (const double*)w.rho[cur], (D4*)w.qp4, pre, dp, de);
+}
+
+void launch_adj_increment(const Consts& c, const Workspace& w, int cur, const double* dp, const double* de,
+                          cudaStream_t s) {
+  if (c.N == 0) return;
+  k_adj_increment<<<nblocks(c.N, 256), 256, 0, s>>>(c.N, c.c_rho / (c.C_K * c.m), w.id[cur], (double*)w.px[cur],
+                                                     (double*)w.py[cur], (double*)w.pz[cur], w.eps[cur],
+                                                     (const double*)w.rho[cur], (D4*)w.qp4, dp, de);
 }
 
 void launch_adj_mid_virial(const Consts& c, const Workspace& w, int cur, const double* A, double wt, D4* vs4,

@@ -299,32 +299,40 @@ void vv_step(sdpd_handle* s, double dt) {
   s->sched_valid = false;
 }
 
+// MTS: one sweep after every theta-th Verlet step since sdpd_set_state
+// (after every step in FD-only runs).
+bool sweep_due(const sdpd_handle* s) {
+  const int theta = s->prm.theta < 1 ? 1 : s->prm.theta;
+  return s->prm.scheme != SDPD_SCHEME_NONE && (s->prm.fd_only || s->vv_step % theta == 0);
+}
+
+// One fluctuation/dissipation sweep with step dt_fd.
+template <class P>
+void fd_sweep_step(sdpd_handle* s, double dt_fd, uint64_t seed) {
+  const Consts& c = s->c;
+  const int rec = s->w.pair_recs != nullptr;
+  if (rec) cudaMemsetAsync(s->w.pair_rec_count, 0, 8, s->stream);
+  if (!s->sched_valid) {  // positions unchanged since the last sweep: reuse it
+    StageTimer t(s, 4, 3);
+    launch_fd_schedule<P>(c, s->w, s->cur, s->stream);
+    s->launches += 3;
+    s->sched_valid = true;
+  }
+  {
+    StageTimer t(s, 5, 8);
+    launch_fd_colours<P>(c, s->w, s->cur, dt_fd, seed, rec, s->stream);
+  }
+  launch_advance_sweep(s->w, s->stream);
+  s->launches += 9;
+  s->fd_step++;
+}
+
 template <class P>
 void do_steps(sdpd_handle* s, double dt, int64_t nsteps, uint64_t seed) {
-  const Consts& c = s->c;
   const int theta = s->prm.theta < 1 ? 1 : s->prm.theta;
-  const bool fd = s->prm.scheme != SDPD_SCHEME_NONE;
   for (int64_t n = 0; n < nsteps; ++n) {
     if (!s->prm.fd_only) vv_step<P>(s, dt);
-    // MTS: one sweep after every theta-th Verlet step since sdpd_set_state
-    if (fd && (s->prm.fd_only || s->vv_step % theta == 0)) {
-      const double dt_fd = s->prm.fd_only ? dt : theta * dt;
-      const int rec = s->w.pair_recs != nullptr;
-      if (rec) cudaMemsetAsync(s->w.pair_rec_count, 0, 8, s->stream);
-      if (!s->sched_valid) {  // positions unchanged since the last sweep: reuse it
-        StageTimer t(s, 4, 3);
-        launch_fd_schedule<P>(c, s->w, s->cur, s->stream);
-        s->launches += 3;
-        s->sched_valid = true;
-      }
-      {
-        StageTimer t(s, 5, 8);
-        launch_fd_colours<P>(c, s->w, s->cur, dt_fd, seed, rec, s->stream);
-      }
-      launch_advance_sweep(s->w, s->stream);
-      s->launches += 9;
-      s->fd_step++;
-    }
+    if (sweep_due(s)) fd_sweep_step<P>(s, s->prm.fd_only ? dt : theta * dt, seed);
   }
 }
 
@@ -673,31 +681,39 @@ int sdpd_stage_times(sdpd_t* s, double* ms, int64_t* launches, int n) {
 // ---------------------------------------------------------------------------
 namespace {
 
-// The tape (caller memory): scratch of the reverse pass, then stored states
+// The tape (caller memory): scratch of the reverse pass; the increments of
+// every step's sweep (momenta [N][3], then energies [N], id order); the
+// sorted momenta and energies before the current sweep; then stored states
 // in id order (q [N][3], p [N][3], eps [N]): the checkpoints at steps 0,
-// every, 2 every, ... below nsteps, the final state, and the every - 1 states
-// of the segment being replayed.
+// every, 2 every, ... below nsteps, the final state, and the every - 1
+// states of the segment being replayed.
 struct Tape {
   D4* vs4;
-  double *A, *Sbar, *qbar, *pbar, *thbar, *partial, *sums, *states;
-  int64_t n_ckpt, n_seg, stride;
+  double *A, *Sbar, *Sbar2, *qbar, *pbar, *thbar, *partial, *sums, *incr, *pre, *states;
+  int64_t n_ckpt, n_seg, stride, N;
   double* ckpt(int64_t k) const { return states + k * stride; }
   double* final_state() const { return ckpt(n_ckpt); }
   double* seg(int64_t j) const { return ckpt(n_ckpt + 1 + j); }
+  double* dp(int64_t step) const { return incr + step * 4 * N; }
+  double* de(int64_t step) const { return incr + step * 4 * N + 3 * N; }
 };
 
 size_t tape_layout(int64_t N, int64_t nsteps, int64_t every, char* base, Tape* t) {
   const size_t n = (size_t)(N > 0 ? N : 1);
   Layout L;
   auto at = [&](size_t bytes) -> void* { return base ? base + L.take(bytes) : (L.take(bytes), nullptr); };
+  t->N = N;
   t->vs4 = (D4*)at(n * sizeof(D4));
   t->A = (double*)at(n * 8);
   t->Sbar = (double*)at(n * 8);
+  t->Sbar2 = (double*)at(n * 8);
   t->qbar = (double*)at(3 * n * 8);
   t->pbar = (double*)at(3 * n * 8);
   t->thbar = (double*)at(3 * n * 8);
   t->partial = (double*)at(adj_sum_partial_doubles() * 8);
   t->sums = (double*)at(4 * 8);
+  t->incr = (double*)at((size_t)(nsteps > 0 ? nsteps : 1) * 4 * n * 8);
+  t->pre = (double*)at(4 * n * 8);
   t->n_ckpt = (nsteps + every - 1) / every;
   t->n_seg = nsteps > 0 ? std::min<int64_t>(every, nsteps) - 1 : 0;
   t->stride = 7 * (int64_t)n;
@@ -751,7 +767,8 @@ size_t sdpd_tape_bytes(const sdpd_t* s, int64_t nsteps, int64_t every) {
   return tape_layout(s->c.N, nsteps, every, nullptr, &t);
 }
 
-int sdpd_vv_record(sdpd_t* s, double dt, int64_t nsteps, int64_t every, void* tape, size_t tape_bytes) {
+int sdpd_vv_record(sdpd_t* s, double dt, int64_t nsteps, int64_t every, uint64_t seed, void* tape,
+                   size_t tape_bytes) {
   int e = check_adjoint_handle(s);
   if (e) return e;
   if (!s->has_state) return SDPD_ERR_NO_STATE;
@@ -761,9 +778,24 @@ int sdpd_vv_record(sdpd_t* s, double dt, int64_t nsteps, int64_t every, void* ta
     return SDPD_ERR_INVALID_ARG;
   tape_layout(s->c.N, nsteps, every, (char*)tape, &t);
   s->rec.tape = nullptr;
+  const int theta = s->prm.theta < 1 ? 1 : s->prm.theta;
+  const size_t b1 = (size_t)s->c.N * 8;
   for (int64_t n = 0; n < nsteps; ++n) {
     if (n % every == 0) store_state(s, t.ckpt(n / every));
     vv_step<Fp64>(s, dt);
+    // the sweep of this step, frozen: its increments are stored and the
+    // state becomes before + increment (zero increments without a sweep)
+    if (s->c.N > 0) {
+      e = SDPD_OK;
+      e |= cuda_ok(cudaMemcpyAsync(t.pre, s->w.px[s->cur], b1, cudaMemcpyDeviceToDevice, s->stream));
+      e |= cuda_ok(cudaMemcpyAsync(t.pre + s->c.N, s->w.py[s->cur], b1, cudaMemcpyDeviceToDevice, s->stream));
+      e |= cuda_ok(cudaMemcpyAsync(t.pre + 2 * s->c.N, s->w.pz[s->cur], b1, cudaMemcpyDeviceToDevice, s->stream));
+      e |= cuda_ok(cudaMemcpyAsync(t.pre + 3 * s->c.N, s->w.eps[s->cur], b1, cudaMemcpyDeviceToDevice, s->stream));
+      if (e) return SDPD_ERR_CUDA;
+    }
+    if (sweep_due(s)) fd_sweep_step<Fp64>(s, theta * dt, seed);
+    launch_adj_freeze(s->c, s->w, s->cur, t.pre, t.dp(n), t.de(n), s->stream);
+    s->launches += 1;
   }
   store_state(s, t.final_state());
   e = launch_status();
@@ -774,6 +806,36 @@ int sdpd_vv_record(sdpd_t* s, double dt, int64_t nsteps, int64_t every, void* ta
   s->rec.every = every;
   s->rec.dt = dt;
   return SDPD_OK;
+}
+
+int sdpd_vv_replay(sdpd_t* s, const void* tape, size_t tape_bytes) {
+  int e = check_adjoint_handle(s);
+  if (e) return e;
+  if (!s->has_state) return SDPD_ERR_NO_STATE;
+  if (!tape || tape != s->rec.tape || tape_bytes != s->rec.bytes) return SDPD_ERR_INVALID_ARG;
+  Tape t;
+  tape_layout(s->c.N, s->rec.nsteps, s->rec.every, (char*)tape, &t);
+  for (int64_t n = 0; n < s->rec.nsteps; ++n) {
+    vv_step<Fp64>(s, s->rec.dt);
+    launch_adj_increment(s->c, s->w, s->cur, t.dp(n), t.de(n), s->stream);
+    s->launches += 1;
+  }
+  return launch_status();
+}
+
+int sdpd_tape_increments(sdpd_t* s, const void* tape, size_t tape_bytes, int64_t step, double* dp, double* deps) {
+  int e = check_adjoint_handle(s);
+  if (e) return e;
+  if (!tape || tape != s->rec.tape || tape_bytes != s->rec.bytes || step < 0 || step >= s->rec.nsteps)
+    return SDPD_ERR_INVALID_ARG;
+  if (s->c.N > 0 && (!dp || !deps)) return SDPD_ERR_INVALID_ARG;
+  Tape t;
+  tape_layout(s->c.N, s->rec.nsteps, s->rec.every, (char*)tape, &t);
+  const size_t b1 = (size_t)s->c.N * 8;
+  if (s->c.N == 0) return SDPD_OK;
+  e = cuda_ok(cudaMemcpyAsync(dp, t.dp(step), 3 * b1, cudaMemcpyDeviceToDevice, s->stream));
+  e |= cuda_ok(cudaMemcpyAsync(deps, t.de(step), b1, cudaMemcpyDeviceToDevice, s->stream));
+  return e ? SDPD_ERR_CUDA : SDPD_OK;
 }
 
 int sdpd_vv_adjoint(sdpd_t* s, void* tape, size_t tape_bytes, const double* gq, const double* gp,
@@ -798,10 +860,16 @@ int sdpd_vv_adjoint(sdpd_t* s, void* tape, size_t tape_bytes, const double* gq, 
     e |= cuda_ok(cudaMemsetAsync(t.thbar, 0, b3, st));
   }
   if (e) return SDPD_ERR_CUDA;
-  // Positions k = n .. 0.  The kicks around position k (the second of step
-  // k-1, the first of step k) both pull back along dt/2 pbar_k, so each
-  // position is visited once with v = (dt/2)([k < n] + [k > 0]) pbar.
+  // Positions k = n .. 0 (states after the frozen increments of step k - 1).
+  // The kicks around position k (the second of step k - 1, the first of
+  // step k) both pull back along (dt/2) pbar_k, so each position is visited
+  // once; their entropies differ (S_{k-1} and S_k, the sweep changed the
+  // energies in between).
   int64_t seg_loaded = -1;
+  // entropy cotangents of the step ending at the current position (started
+  // there) and of the step starting there (completed there)
+  double* Sbar_cur = t.Sbar;
+  double* Sbar_prev = t.Sbar2;
   for (int64_t k = ns; k >= 0; --k) {
     if (k == ns) {
       StageTimer tm(s, 6, 7);
@@ -817,9 +885,11 @@ int sdpd_vv_adjoint(sdpd_t* s, void* tape, size_t tape_bytes, const double* gq, 
           load_state(s, t.ckpt(sg));
         }
         const int64_t k1 = std::min(k0 + every, ns);
-        for (int64_t j = k0 + 1; j < k1; ++j) {
+        for (int64_t j = k0 + 1; j < k1; ++j) {  // step j - 1, its sweep frozen
           vv_step<Fp64>(s, dt);
           s->vv_step--;
+          launch_adj_increment(c, s->w, s->cur, t.dp(j - 1), t.de(j - 1), st);
+          s->launches += 1;
           store_state(s, t.seg(j - k0 - 1));
         }
         seg_loaded = sg;
@@ -827,29 +897,33 @@ int sdpd_vv_adjoint(sdpd_t* s, void* tape, size_t tape_bytes, const double* gq, 
       StageTimer tm(s, 6, 7);
       load_state(s, t.seg(k - k0 - 1));
     }
-    const double coef = 0.5 * dt * ((k < ns ? 1 : 0) + (k > 0 ? 1 : 0));
-    if (coef != 0.0) {
+    // the first kick of step k (k < n) and the second of step k - 1 (k > 0)
+    // both pull back along (dt/2) pbar
+    const bool kick1 = k < ns, kick2 = k > 0;
+    if (kick1 || kick2) {
       {
         StageTimer tm(s, 9, 1);
-        launch_adj_gather(c, s->w, s->cur, t.pbar, coef, t.vs4, st);
+        launch_adj_gather(c, s->w, s->cur, t.pbar, 0.5 * dt, t.vs4, st);
       }
       StageTimer tm(s, 7, 1);
       launch_adj_pairsum(c, s->w, s->cur, 0, t.vs4, t.A, st);
     }
     {
       StageTimer tm(s, 9, 1);
-      launch_adj_mid_traj(c, s->w, s->cur, coef != 0.0 ? t.A : nullptr, t.vs4, t.Sbar, t.thbar, geps, k == ns,
-                          k == 0 ? geps0 : nullptr, st);
+      launch_adj_mid_step(c, s->w, s->cur, (kick1 || kick2) ? t.A : nullptr, kick1, kick2,
+                          kick2 ? t.de(k - 1) : nullptr, Sbar_cur, Sbar_prev, k == ns ? geps : nullptr,
+                          k == 0 ? geps0 : nullptr, t.vs4, t.thbar, st);
     }
     {
       StageTimer tm(s, 8, 1);
-      launch_adj_back(c, s->w, s->cur, coef != 0.0 ? 0 : 2, 1.0, t.vs4, 1, t.qbar, t.thbar, st);
+      launch_adj_back(c, s->w, s->cur, (kick1 || kick2) ? 0 : 2, 1.0, t.vs4, 1, t.qbar, t.thbar, st);
     }
     if (k > 0) {
       StageTimer tm(s, 9, 1);
       launch_adj_axpy(3 * N, dt / c.m, t.qbar, t.pbar, st);
     }
-    s->launches += (coef != 0.0 ? 2 : 0) + 2 + (k > 0 ? 1 : 0);
+    std::swap(Sbar_cur, Sbar_prev);
+    s->launches += ((kick1 || kick2) ? 2 : 0) + 2 + (k > 0 ? 1 : 0);
   }
   if (N > 0) {
     e |= cuda_ok(cudaMemcpyAsync(gq0, t.qbar, b3, cudaMemcpyDeviceToDevice, st));

@@ -336,8 +336,15 @@ void launch_adj_gather(const Consts& c, const Workspace& w, int cur, const doubl
                        cudaStream_t s);
 void launch_adj_pairsum(const Consts& c, const Workspace& w, int cur, int mode, const D4* vs4, double* A,
                         cudaStream_t s);
-void launch_adj_mid_traj(const Consts& c, const Workspace& w, int cur, const double* A, D4* vs4, double* Sbar,
-                         double* thbar, const double* epsbar_n, int final_pos, double* epsbar0, cudaStream_t s);
+void launch_adj_mid_step(const Consts& c, const Workspace& w, int cur, const double* A, bool kick1, bool kick2,
+                         const double* deps_prev, double* Sbar_cur, double* Sbar_prev, const double* epsbar_n,
+                         double* epsbar0, D4* vs4, double* thbar, cudaStream_t s);
+// frozen sweeps: record (increments stored, state set to before + increment)
+// and replay (increments added); pre = the sorted px, py, pz, eps before
+void launch_adj_freeze(const Consts& c, const Workspace& w, int cur, const double* pre, double* dp, double* de,
+                       cudaStream_t s);
+void launch_adj_increment(const Consts& c, const Workspace& w, int cur, const double* dp, const double* de,
+                          cudaStream_t s);
 void launch_adj_mid_virial(const Consts& c, const Workspace& w, int cur, const double* A, double wt, D4* vs4,
                            double* val_id, double* gp, double* geps, double* thbar, cudaStream_t s);
 void launch_adj_back(const Consts& c, const Workspace& w, int cur, int mode, double wt, const D4* vs4,

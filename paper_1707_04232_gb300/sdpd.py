@@ -74,7 +74,9 @@ SIGNATURES = [
     ("sdpd_density_static", C.c_int, [C.c_int64, _dp, C.c_double, C.c_double, C.c_int, C.c_void_p,
                                       C.c_void_p, C.c_void_p]),
     ("sdpd_tape_bytes", C.c_size_t, [_H, C.c_int64, C.c_int64]),
-    ("sdpd_vv_record", C.c_int, [_H, C.c_double, C.c_int64, C.c_int64, C.c_void_p, C.c_size_t]),
+    ("sdpd_vv_record", C.c_int, [_H, C.c_double, C.c_int64, C.c_int64, C.c_uint64, C.c_void_p, C.c_size_t]),
+    ("sdpd_vv_replay", C.c_int, [_H, C.c_void_p, C.c_size_t]),
+    ("sdpd_tape_increments", C.c_int, [_H, C.c_void_p, C.c_size_t, C.c_int64, C.c_void_p, C.c_void_p]),
     ("sdpd_vv_adjoint", C.c_int, [_H, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p, C.c_void_p,
                                   C.c_void_p, C.c_void_p, C.c_void_p, _dp]),
     ("sdpd_virial", C.c_int, [_H, _dp, C.c_void_p, C.c_void_p, C.c_void_p, _dp]),
@@ -230,8 +232,16 @@ def sdpd_tape_bytes(h, nsteps, every) -> int:
     return load().sdpd_tape_bytes(h, int(nsteps), int(every))
 
 
-def sdpd_vv_record(h, dt, nsteps, every, tape_ptr: int, nbytes: int) -> int:
-    return load().sdpd_vv_record(h, float(dt), int(nsteps), int(every), tape_ptr, nbytes)
+def sdpd_vv_record(h, dt, nsteps, every, seed, tape_ptr: int, nbytes: int) -> int:
+    return load().sdpd_vv_record(h, float(dt), int(nsteps), int(every), int(seed) & (2**64 - 1), tape_ptr, nbytes)
+
+
+def sdpd_vv_replay(h, tape_ptr: int, nbytes: int) -> int:
+    return load().sdpd_vv_replay(h, tape_ptr, nbytes)
+
+
+def sdpd_tape_increments(h, tape_ptr: int, nbytes: int, step: int, dp: int, deps: int) -> int:
+    return load().sdpd_tape_increments(h, tape_ptr, nbytes, int(step), dp, deps)
 
 
 def sdpd_vv_adjoint(h, tape_ptr, nbytes, gq, gp, geps, gq0, gp0, geps0, gtheta) -> int:
@@ -348,17 +358,34 @@ class SDPD:
     def tape_bytes(self, nsteps, every=10) -> int:
         return sdpd_tape_bytes(self.h, nsteps, every)
 
-    def vv_record(self, dt, nsteps, every=10):
-        """Velocity Verlet steps from the loaded state, recorded for
-        vv_adjoint with a checkpoint every ``every`` steps.  Returns the tape
-        (a CUDA uint8 tensor that must stay alive until the last adjoint)."""
+    def vv_record(self, dt, nsteps, every=10, seed=0):
+        """Full steps from the loaded state (Velocity Verlet, then the
+        handle's sweep with random numbers keyed by ``seed``), recorded for
+        vv_adjoint with a checkpoint every ``every`` steps and each sweep's
+        increments frozen.  Returns the tape (a CUDA uint8 tensor that must
+        stay alive until the last adjoint)."""
         n = self.tape_bytes(nsteps, every)
         if n == 0:
             raise ValueError("bad nsteps/every")
         tape = self.torch.empty(n, dtype=self.torch.uint8, device=self.workspace.device)
-        _check(sdpd_vv_record(self.h, dt, nsteps, every, tape.data_ptr(), n), "sdpd_vv_record")
+        _check(sdpd_vv_record(self.h, dt, nsteps, every, seed, tape.data_ptr(), n), "sdpd_vv_record")
         self._tape = tape
         return tape
+
+    def vv_replay(self, tape):
+        """Applies the recorded frozen map (Verlet steps plus the recorded
+        sweep increments) to the currently loaded state."""
+        _check(sdpd_vv_replay(self.h, tape.data_ptr(), tape.numel()), "sdpd_vv_replay")
+
+    def tape_increments(self, tape, step):
+        """The recorded sweep increments (dp [N,3], deps [N]) of one step."""
+        torch = self.torch
+        dev = self.workspace.device
+        dp = torch.empty((self.N, 3), dtype=torch.float64, device=dev)
+        de = torch.empty(self.N, dtype=torch.float64, device=dev)
+        _check(sdpd_tape_increments(self.h, tape.data_ptr(), tape.numel(), step, dp.data_ptr(), de.data_ptr()),
+               "sdpd_tape_increments")
+        return dp, de
 
     def vv_adjoint(self, tape, gq=None, gp=None, geps=None):
         """Cotangents (gq0, gp0, geps0, gtheta) of the recorded trajectory's

@@ -521,16 +521,24 @@ def run_adjoint(args, rank, world, local_rank):
     ms_max = allreduce_max(ms, world)
     value = w.N * ns * steps * world / (ms_max * 1e-3)
     # roofline of the dominant stage (float64 arithmetic)
-    top = max((k for k in stages if k in FLOPS_PER_VISIT), key=lambda k: stages[k][0])
+    top = max((k for k in stages if k in FLOPS_PER_VISIT or k == "fd_colours"), key=lambda k: stages[k][0])
     top_ms, top_launches = stages[top]
     per_launch_s = top_ms * 1e-3 / max(1, top_launches)
-    flops = FLOPS_PER_VISIT[top] * w.N * nbr_mean
+    if top == "fd_colours":
+        # pair updates per colour launch: every neighbour pair once per sweep,
+        # over 8 colour launches
+        units = w.N * nbr_mean / 2.0 / 8.0
+        flops = FLOPS_PER_PAIR_UPDATE["ems"] * units
+    else:
+        units = w.N * nbr_mean
+        flops = FLOPS_PER_VISIT[top] * units
     ach = flops / per_launch_s / 1e12
     roof = {"kernel": top, "bound": "alu", "achieved": ach, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
             "frac": ach / FP64_NOMINAL_TFLOPS, "traffic": None,
             "peak_note": "float64 nominal of GB300 (recipe); measured float64 FMA rate %.3f TFLOP/s "
                          "(sdpd_fma_peak), frac of measured %.3f" % (fma64 / 1e12, ach / (fma64 / 1e12)),
-            "per_launch_ms": per_launch_s * 1e3, "visits_per_launch": w.N * nbr_mean}
+            "per_launch_ms": per_launch_s * 1e3,
+            ("pair_updates_per_launch" if top == "fd_colours" else "visits_per_launch"): units}
     # end to end: host inputs in, host gradients out
     qh, ph, eh = (torch.from_numpy(a).pin_memory() for a in (q, p, e))
     outs = [torch.empty((w.N, 3), dtype=torch.float64).pin_memory() for _ in range(2)]

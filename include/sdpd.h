@@ -77,6 +77,11 @@ typedef struct {
                     sdpd_set_state is a multiple of theta (however the steps
                     are split over sdpd_step calls); 1 = single step */
   int debug;     /* 1: reserve workspace for per-pair records (sdpd_debug_get) */
+  int nc[3];     /* cells per axis; 0 = the largest even n with box/n >= h.  Else
+                    an even n >= 4 with box/n >= h (SDPD_ERR_INVALID_ARG if odd
+                    or < 4, SDPD_ERR_BOX_TOO_SMALL if box/n < h).  The cell grid
+                    fixes the colouring and so the order of the sweep's pair
+                    updates; any grid gives a valid sweep of Section 3.2. */
 } sdpd_params;
 
 /* Observables of the current state (Section 2.2: E and the total momentum
@@ -236,8 +241,9 @@ void sdpd_destroy(sdpd_t* s);
  * sdpd_ensemble_step advances every member by nsteps steps with its own seed
  * (seeds[i] for member i).  U = lcm(2, theta of every member) steps of all
  * members are captured once into one CUDA graph (forked from and joined into
- * the ensemble stream; the capture is redone when dt, the seeds or a
- * member's step count modulo its theta change) and the graph is replayed
+ * the ensemble stream; the capture is redone when dt, the seeds, a
+ * member's step count modulo its theta, its state buffer (after
+ * sdpd_set_state or sdpd_autotune) or its launch shapes change) and the graph is replayed
  * nsteps/U times; the nsteps mod U last steps are enqueued directly.  Every
  * member's result is the same as stepping it alone.  The members' own
  * streams wait for the ensemble's work before later calls on them run.
@@ -248,11 +254,52 @@ void sdpd_destroy(sdpd_t* s);
 typedef struct sdpd_ensemble sdpd_ens_t;
 int sdpd_ensemble_create(sdpd_t* const* members, int n, void* stream, sdpd_ens_t** out);
 int sdpd_ensemble_step(sdpd_ens_t* e, double dt, int64_t nsteps, const uint64_t* seeds);
+/* Runs sdpd_autotune on every member alone (seeds[i] or 0 when seeds is
+ * NULL); ms_per_step[i] (may be NULL) receives each member's time per step
+ * with its chosen shapes.  The next sdpd_ensemble_step recaptures its graph
+ * with the new shapes.  Errors: those of sdpd_autotune (the first failing
+ * member stops the tuning). */
+int sdpd_ensemble_autotune(sdpd_ens_t* e, double dt, int64_t steps, const uint64_t* seeds, double* ms_per_step);
 /* Kernel launches of the captured U-step graph (all members). */
 int64_t sdpd_ensemble_kernel_nodes(const sdpd_ens_t* e);
 /* The ensemble's stream (a cudaStream_t). */
 void* sdpd_ensemble_stream(const sdpd_ens_t* e);
 void sdpd_ensemble_destroy(sdpd_ens_t* e);
+
+/* ---------------------------------------------------------------------------
+ * Launch shapes and the autotuner (no counterpart in the paper: they choose
+ * how the same arithmetic is mapped onto the GPU, never what it computes).
+ * ------------------------------------------------------------------------- */
+
+#define SDPD_FD_VARIANTS 5 /* block schedules of the sweep's colour launches */
+
+typedef struct {
+  int fd_variant;   /* blocks per warp x warps per thread block of the colour
+                       launches: 0 (2 x 2), 1 (2 x 1), 2 (1 x 1), 3 (1 x 2),
+                       4 (2 x 4); -1 = the precision's default (0 mixed, 1 float64) */
+  int pair_threads; /* threads per block of the density and force passes:
+                       32, 64 or 128; 0 = 128 */
+} sdpd_tuning;
+
+/* Current launch shapes.  Errors: SDPD_ERR_INVALID_ARG. */
+int sdpd_get_tuning(const sdpd_t* s, sdpd_tuning* out);
+
+/* Sets the launch shapes used from the next launch on.  Results are
+ * bitwise the same under every shape.  Errors: SDPD_ERR_INVALID_ARG. */
+int sdpd_set_tuning(sdpd_t* s, const sdpd_tuning* t);
+
+/* Measures the launch shapes on the loaded state and keeps the fastest:
+ * first every colour-launch schedule (pair passes at 128 threads), then every
+ * pair-pass block size with the best schedule.  Each candidate runs one
+ * warm-up step and `steps` (1..1000) timed steps of dt from the same state,
+ * timed with CUDA events on the handle's stream.  The loaded state, the step
+ * counters, the random-number counter and the pair counters are restored
+ * afterwards, so the next sdpd_step continues as if nothing had run.
+ * best / ms_per_step (may be NULL) receive the chosen shapes and their time
+ * per step.  Synchronising.  Errors: SDPD_ERR_INVALID_ARG, SDPD_ERR_NO_STATE,
+ * SDPD_ERR_NO_WORKSPACE, SDPD_ERR_CUDA, or the sticky device status if the
+ * state already carried an error. */
+int sdpd_autotune(sdpd_t* s, double dt, int64_t steps, uint64_t seed, sdpd_tuning* best, double* ms_per_step);
 
 /* ---------------------------------------------------------------------------
  * Gradients of the conservative dynamics with the sweeps frozen (reverse

@@ -168,6 +168,7 @@ class Config:
     c_rho: float | None = None
     kernel: int = KERNEL_LUCY
     scheme: int = SCHEME_EMS
+    n_c: tuple | None = None  # cells per axis; None: the largest even n with L/n >= h
 
     def params(self) -> Params:
         P = Params()
@@ -175,8 +176,13 @@ class Config:
         Ls = self.L if isinstance(self.L, (tuple, list)) else (self.L,) * 3
         for k in range(3):
             P.L[k] = float(Ls[k])
-            n = int(np.floor(Ls[k] / self.h))
-            n -= n % 2
+            if self.n_c is not None:
+                n = int(self.n_c[k])
+                if n < 4 or n % 2 or Ls[k] / n < self.h:
+                    raise ValueError("cell grid: need an even n_c >= 4 with L/n_c >= h")
+            else:
+                n = int(np.floor(Ls[k] / self.h))
+                n -= n % 2
             if n < 4:
                 raise ValueError("box too small: need an even n_c >= 4 with L/n_c >= h")
             P.n_c[k] = n

@@ -396,10 +396,17 @@ int sdpd_create(int64_t N, const double box[3], double m, double h, double K, co
   int64_t ncell = 1;
   for (int d = 0; d < 3; ++d) {
     if (!(box[d] > 0) || !isfinite(box[d])) { delete s; return SDPD_ERR_INVALID_ARG; }
-    double ratio = floor(box[d] / h);
-    int64_t n = ratio > 1024.0 ? 1024 : (int64_t)ratio;
-    n -= n % 2;
-    if (n < 4) { delete s; return SDPD_ERR_BOX_TOO_SMALL; }
+    int64_t n;
+    if (prm->nc[d] != 0) {  // a chosen grid: even, >= 4, cells of side >= h
+      n = prm->nc[d];
+      if (n < 4 || n % 2 != 0 || n > 1024) { delete s; return SDPD_ERR_INVALID_ARG; }
+      if (box[d] / (double)n < h) { delete s; return SDPD_ERR_BOX_TOO_SMALL; }
+    } else {
+      double ratio = floor(box[d] / h);
+      n = ratio > 1024.0 ? 1024 : (int64_t)ratio;
+      n -= n % 2;
+      if (n < 4) { delete s; return SDPD_ERR_BOX_TOO_SMALL; }
+    }
     c.nc[d] = (int)n;
     c.L[d] = box[d];
     c.halfL[d] = 0.5 * box[d];
@@ -446,6 +453,8 @@ int sdpd_create(int64_t N, const double box[3], double m, double h, double K, co
     }
   }
   c.kernel = prm->kernel;
+  c.fd_variant = fd_default_variant(prm->precision == SDPD_MIXED);
+  c.pair_threads = 128;
   c.scheme = prm->scheme;
   s->prm = *prm;
   s->K = K;
@@ -672,6 +681,106 @@ int sdpd_stage_times(sdpd_t* s, double* ms, int64_t* launches, int n) {
     if (launches) launches[k] = s->stage_launches[k];
   }
   return SDPD_OK;
+}
+
+int sdpd_get_tuning(const sdpd_t* s, sdpd_tuning* out) {
+  if (!s || !out) return SDPD_ERR_INVALID_ARG;
+  out->fd_variant = s->c.fd_variant;
+  out->pair_threads = s->c.pair_threads;
+  return SDPD_OK;
+}
+
+int sdpd_set_tuning(sdpd_t* s, const sdpd_tuning* t) {
+  if (!s || !t) return SDPD_ERR_INVALID_ARG;
+  const int v = t->fd_variant < 0 ? fd_default_variant(s->prm.precision == SDPD_MIXED) : t->fd_variant;
+  const int pt = t->pair_threads == 0 ? 128 : t->pair_threads;
+  if (v >= kFdVariants || !fd_variant_fits(s->prm.precision == SDPD_MIXED, v) || !pair_threads_ok(pt))
+    return SDPD_ERR_INVALID_ARG;
+  s->c.fd_variant = v;
+  s->c.pair_threads = pt;
+  return SDPD_OK;
+}
+
+int sdpd_autotune(sdpd_t* s, double dt, int64_t steps, uint64_t seed, sdpd_tuning* best, double* ms_per_step) {
+  if (!s || !(dt > 0) || !isfinite(dt) || steps < 1 || steps > 1000) return SDPD_ERR_INVALID_ARG;
+  if (!s->ws) return SDPD_ERR_NO_WORKSPACE;
+  if (!s->has_state) return SDPD_ERR_NO_STATE;
+  int e = sdpd_sync(s);
+  if (e) return e;
+  const bool mixed = s->prm.precision == SDPD_MIXED;
+  cudaStream_t st = s->stream;
+  // the state in id order in the staging buffers (the load path reads them
+  // back), and every counter the trial steps advance
+  if (mixed) launch_unload<Mixed>(s->c, s->w, s->cur, st);
+  else launch_unload<Fp64>(s->c, s->w, s->cur, st);
+  unsigned long long counters[4] = {0, 0, 0, 0};
+  if (cudaMemcpyAsync(counters, s->w.counters, sizeof(counters), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return SDPD_ERR_CUDA;
+  const int64_t fd0 = s->fd_step, vv0 = s->vv_step, l0 = s->launches;
+  const bool timing0 = s->timing;
+  s->timing = false;
+  auto reload = [&]() {
+    if (mixed) do_load<Mixed>(s);
+    else do_load<Fp64>(s);
+    launch_set_sweep(s->w, (unsigned long long)fd0, st);
+    s->fd_step = fd0;
+    s->vv_step = vv0;
+  };
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  if (cudaEventCreate(&ev[0]) != cudaSuccess || cudaEventCreate(&ev[1]) != cudaSuccess) {
+    if (ev[0]) cudaEventDestroy(ev[0]);
+    s->timing = timing0;
+    return SDPD_ERR_CUDA;
+  }
+  // time per step of one candidate; infinity when it failed
+  auto trial = [&](int v, int pt) -> double {
+    s->c.fd_variant = v;
+    s->c.pair_threads = pt;
+    reload();
+    if (mixed) do_steps<Mixed>(s, dt, 1, seed);
+    else do_steps<Fp64>(s, dt, 1, seed);
+    cudaEventRecord(ev[0], st);
+    if (mixed) do_steps<Mixed>(s, dt, steps, seed);
+    else do_steps<Fp64>(s, dt, steps, seed);
+    cudaEventRecord(ev[1], st);
+    float ms = 0.0f;
+    if (sdpd_sync(s) != SDPD_OK || cudaEventElapsedTime(&ms, ev[0], ev[1]) != cudaSuccess) {
+      cudaGetLastError();
+      cudaMemsetAsync(s->w.status, 0, 8, st);
+      return INFINITY;
+    }
+    return (double)ms / (double)steps;
+  };
+  const sdpd_tuning start = {s->c.fd_variant, s->c.pair_threads};
+  int bv = start.fd_variant, bt = 128;
+  double bms = INFINITY;
+  for (int v = 0; v < kFdVariants; ++v) {
+    if (!fd_variant_fits(mixed, v)) continue;
+    const double ms = trial(v, 128);
+    if (ms < bms) { bms = ms; bv = v; }
+  }
+  for (int pt : {32, 64}) {
+    const double ms = trial(bv, pt);
+    if (ms < bms) { bms = ms; bt = pt; }
+  }
+  cudaEventDestroy(ev[0]);
+  cudaEventDestroy(ev[1]);
+  if (!isfinite(bms)) { bv = start.fd_variant; bt = start.pair_threads; }
+  s->c.fd_variant = bv;
+  s->c.pair_threads = bt;
+  // back to the state and counters the call started from
+  reload();
+  e = cuda_ok(cudaMemcpyAsync(s->w.counters, counters, sizeof(counters), cudaMemcpyHostToDevice, st));
+  e |= cuda_ok(cudaMemsetAsync(s->w.status, 0, 8, st));
+  s->launches = l0;
+  s->timing = timing0;
+  if (e) return SDPD_ERR_CUDA;
+  e = sdpd_sync(s);  // the host counters above must outlive the copy
+  if (e) return e;
+  if (best) { best->fd_variant = bv; best->pair_threads = bt; }
+  if (ms_per_step) *ms_per_step = bms;
+  return isfinite(bms) ? SDPD_OK : SDPD_ERR_CUDA;
 }
 
 }  // extern "C"
@@ -1108,6 +1217,7 @@ struct sdpd_ensemble {
   int64_t launches_per_unit;
   int64_t unit;                  // steps per graph replay: lcm of 2 and the members' theta
   std::vector<int64_t> phase;    // members' vv_step mod theta when the graph was captured
+  std::vector<int> shape;        // members' state buffer and launch shapes at capture
 };
 
 namespace {
@@ -1197,9 +1307,16 @@ int sdpd_ensemble_step(sdpd_ens_t* e, double dt, int64_t nsteps, const uint64_t*
   const int64_t units = nsteps / U;
   const std::vector<uint64_t> sv(seeds, seeds + e->m.size());
   std::vector<int64_t> phase;
-  for (sdpd_handle* h : e->m) phase.push_back(h->vv_step % std::max(1, h->prm.theta));
+  std::vector<int> shape;
+  for (sdpd_handle* h : e->m) {
+    phase.push_back(h->vv_step % std::max(1, h->prm.theta));
+    // the graph holds the buffer pointers and launch shapes of its capture
+    shape.push_back(h->cur);
+    shape.push_back(h->c.fd_variant);
+    shape.push_back(h->c.pair_threads);
+  }
   if (units > 0) {
-    if (!e->exec || e->dt != dt || e->seeds != sv || e->phase != phase) {
+    if (!e->exec || e->dt != dt || e->seeds != sv || e->phase != phase || e->shape != shape) {
       if (e->exec) { cudaGraphExecDestroy(e->exec); e->exec = nullptr; }
       if (e->graph) { cudaGraphDestroy(e->graph); e->graph = nullptr; }
       // capture U steps: each step's sort flips the double-buffered state,
@@ -1228,6 +1345,7 @@ int sdpd_ensemble_step(sdpd_ens_t* e, double dt, int64_t nsteps, const uint64_t*
       e->dt = dt;
       e->seeds = sv;
       e->phase = phase;
+      e->shape = shape;
     }
     for (int64_t u = 0; u < units; ++u)
       if (cudaGraphLaunch(e->exec, e->stream) != cudaSuccess) return SDPD_ERR_CUDA;
@@ -1245,6 +1363,20 @@ int sdpd_ensemble_step(sdpd_ens_t* e, double dt, int64_t nsteps, const uint64_t*
   for (sdpd_handle* h : e->m)
     if (order_streams(e->stream, h->stream) != SDPD_OK) return SDPD_ERR_CUDA;
   return launch_status();
+}
+
+int sdpd_ensemble_autotune(sdpd_ens_t* e, double dt, int64_t steps, const uint64_t* seeds, double* ms_per_step) {
+  if (!e) return SDPD_ERR_INVALID_ARG;
+  // members' streams may still hold work of the ensemble stream
+  for (sdpd_handle* h : e->m)
+    if (order_streams(e->stream, h->stream) != SDPD_OK) return SDPD_ERR_CUDA;
+  for (size_t i = 0; i < e->m.size(); ++i) {
+    double ms = 0.0;
+    const int r = sdpd_autotune(e->m[i], dt, steps, seeds ? seeds[i] : 0ull, nullptr, &ms);
+    if (r != SDPD_OK) return r;
+    if (ms_per_step) ms_per_step[i] = ms;
+  }
+  return SDPD_OK;
 }
 
 int64_t sdpd_ensemble_kernel_nodes(const sdpd_ens_t* e) { return e ? e->launches_per_unit : -1; }

@@ -44,7 +44,19 @@ struct Consts {
   // has r^2 >= h^2 in float64 (bound on the conversion and rounding errors
   // set on the host), so it is skipped without float64 arithmetic.
   float Lf[3], halfLf[3], h2_filter;
+  // launch shapes (results do not depend on them): the block schedule of the
+  // sweep's colour launches and the threads per block of the pair passes
+  int fd_variant, pair_threads;
 };
+
+// Block schedules of the colour kernel (see launch_fd_colours) and the
+// thread-block sizes the pair passes accept.
+constexpr int kFdVariants = 5;
+__host__ __device__ constexpr int fd_default_variant(bool mixed) { return mixed ? 0 : 1; }
+__host__ __device__ constexpr bool pair_threads_ok(int t) { return t == 32 || t == 64 || t == 128; }
+// whether a block schedule's shared memory fits a thread block (float64
+// blocks take twice the bytes of mixed ones)
+bool fd_variant_fits(bool mixed, int v);
 
 // Neighbour-list entry: neighbour index << 6 | stencil offset code, the code
 // holding (o + 1) per axis in 2 bits (x lowest) for o in {-1, 0, +1}.

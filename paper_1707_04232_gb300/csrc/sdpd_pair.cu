@@ -309,18 +309,23 @@ __global__ void __launch_bounds__(128) k_force(Consts c, Arrays<P> a, const type
 
 static inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
+// threads per block of the pair passes (one thread per particle, no shared
+// memory, so any of the accepted sizes gives the same results)
+static inline int pair_block(const Consts& c) { return pair_threads_ok(c.pair_threads) ? c.pair_threads : 128; }
+
 template <class P>
 void launch_density(const Consts& c, const Workspace& w, int cur, int update_eos, int32_t* ncount_by_id,
                     cudaStream_t s) {
   if (c.N == 0) return;
   Arrays<P> a = view<P>(w, cur);
   auto qp4 = (typename P::V4*)w.qp4;
+  const int t = pair_block(c);
   if (c.kernel == SDPD_KERNEL_LUCY)
-    k_density<P, SDPD_KERNEL_LUCY><<<blocks_for(c.N, 128), 128, 0, s>>>(
+    k_density<P, SDPD_KERNEL_LUCY><<<blocks_for(c.N, t), t, 0, s>>>(
         c, a, qp4, w.cell_start, w.mrank, w.xmin[0], w.xmin[1], w.xmin[2], update_eos, ncount_by_id, w.nlist,
         w.nn, w.nbr_off, w.status, w.qf4);
   else
-    k_density<P, SDPD_KERNEL_CUBIC><<<blocks_for(c.N, 128), 128, 0, s>>>(
+    k_density<P, SDPD_KERNEL_CUBIC><<<blocks_for(c.N, t), t, 0, s>>>(
         c, a, qp4, w.cell_start, w.mrank, w.xmin[0], w.xmin[1], w.xmin[2], update_eos, ncount_by_id, w.nlist,
         w.nn, w.nbr_off, w.status, w.qf4);
 }
@@ -336,12 +341,13 @@ void launch_force(const Consts& c, const Workspace& w, int cur, double half_dt, 
   auto qdz = (typename P::Q*)w.qdz;
   const float3 drift3 = make_float3((float)(dt_drift / c.m * c.inv_scale[0]), (float)(dt_drift / c.m * c.inv_scale[1]),
                                     (float)(dt_drift / c.m * c.inv_scale[2]));
+  const int t = pair_block(c);
   if (c.kernel == SDPD_KERNEL_LUCY)
-    k_force<P, SDPD_KERNEL_LUCY><<<blocks_for(c.N, 128), 128, 0, s>>>(
+    k_force<P, SDPD_KERNEL_LUCY><<<blocks_for(c.N, t), t, 0, s>>>(
         c, a, qp4, w.cell_start, w.mrank, w.xmin[0], w.xmin[1], w.xmin[2], half_dt, dt_drift, qdx, qdy,
         qdz, w.key, w.slot, w.cell_count, force_by_id, w.nlist, w.nn, drift3);
   else
-    k_force<P, SDPD_KERNEL_CUBIC><<<blocks_for(c.N, 128), 128, 0, s>>>(
+    k_force<P, SDPD_KERNEL_CUBIC><<<blocks_for(c.N, t), t, 0, s>>>(
         c, a, qp4, w.cell_start, w.mrank, w.xmin[0], w.xmin[1], w.xmin[2], half_dt, dt_drift, qdx, qdy,
         qdz, w.key, w.slot, w.cell_count, force_by_id, w.nlist, w.nn, drift3);
 }

@@ -26,8 +26,15 @@ class sdpd_params(C.Structure):
     _fields_ = [
         ("kB", C.c_double), ("eta", C.c_double), ("zeta", C.c_double), ("c_rho", C.c_double),
         ("kernel", C.c_int), ("scheme", C.c_int), ("precision", C.c_int), ("fd_only", C.c_int),
-        ("theta", C.c_int), ("debug", C.c_int),
+        ("theta", C.c_int), ("debug", C.c_int), ("nc", C.c_int * 3),
     ]
+
+
+class sdpd_tuning(C.Structure):
+    _fields_ = [("fd_variant", C.c_int), ("pair_threads", C.c_int)]
+
+
+FD_VARIANTS = 5
 
 
 class sdpd_obs(C.Structure):
@@ -73,6 +80,10 @@ SIGNATURES = [
     ("sdpd_ensemble_destroy", None, [_H]),
     ("sdpd_density_static", C.c_int, [C.c_int64, _dp, C.c_double, C.c_double, C.c_int, C.c_void_p,
                                       C.c_void_p, C.c_void_p]),
+    ("sdpd_get_tuning", C.c_int, [_H, C.POINTER(sdpd_tuning)]),
+    ("sdpd_set_tuning", C.c_int, [_H, C.POINTER(sdpd_tuning)]),
+    ("sdpd_autotune", C.c_int, [_H, C.c_double, C.c_int64, C.c_uint64, C.POINTER(sdpd_tuning), _dp]),
+    ("sdpd_ensemble_autotune", C.c_int, [_H, C.c_double, C.c_int64, C.POINTER(C.c_uint64), _dp]),
     ("sdpd_tape_bytes", C.c_size_t, [_H, C.c_int64, C.c_int64]),
     ("sdpd_vv_record", C.c_int, [_H, C.c_double, C.c_int64, C.c_int64, C.c_uint64, C.c_void_p, C.c_size_t]),
     ("sdpd_vv_replay", C.c_int, [_H, C.c_void_p, C.c_size_t]),
@@ -286,7 +297,7 @@ class SDPD:
 
     def __init__(self, N, box, m=1.0, h=2.5, K=100.0, *, kB=1.0, eta=1.0, zeta=0.0, c_rho=-1.0,
                  kernel=KERNEL_LUCY, scheme=SCHEME_EMS, precision=FP64, fd_only=False, theta=1,
-                 debug=False, stream=None):
+                 debug=False, nc=None, stream=None):
         import torch
 
         if not torch.cuda.is_available():
@@ -297,6 +308,9 @@ class SDPD:
         prm = sdpd_params(kB=kB, eta=eta, zeta=zeta, c_rho=c_rho, kernel=kernel, scheme=scheme,
                           precision=precision, fd_only=int(bool(fd_only)), theta=int(theta),
                           debug=int(bool(debug)))
+        if nc is not None:  # cells per axis (0 = the default grid on that axis)
+            for d, n in enumerate(nc if np.ndim(nc) else (nc,) * 3):
+                prm.nc[d] = int(n)
         self.params = prm
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         st, self.h = sdpd_create(N, box if np.ndim(box) else (box,) * 3, m, h, K, prm,
@@ -352,6 +366,27 @@ class SDPD:
         _check(load().sdpd_energy_histogram(self.h, float(lo), float(hi), int(nbins), float(scale),
                                             counts.data_ptr()), "sdpd_energy_histogram")
         return counts
+
+    # -- launch shapes and the autotuner ------------------------------------
+
+    @property
+    def tuning(self) -> dict:
+        t = sdpd_tuning()
+        _check(load().sdpd_get_tuning(self.h, C.byref(t)), "sdpd_get_tuning")
+        return {"fd_variant": t.fd_variant, "pair_threads": t.pair_threads}
+
+    def set_tuning(self, fd_variant=-1, pair_threads=0):
+        t = sdpd_tuning(fd_variant=int(fd_variant), pair_threads=int(pair_threads))
+        _check(load().sdpd_set_tuning(self.h, C.byref(t)), "sdpd_set_tuning")
+
+    def autotune(self, dt, steps=3, seed=0):
+        """Times every launch shape on the loaded state, keeps the fastest
+        and restores the state; returns (tuning, ms per step)."""
+        t = sdpd_tuning()
+        ms = C.c_double(0.0)
+        _check(load().sdpd_autotune(self.h, float(dt), int(steps), int(seed) & (2**64 - 1), C.byref(t),
+                                    C.byref(ms)), "sdpd_autotune")
+        return {"fd_variant": t.fd_variant, "pair_threads": t.pair_threads}, ms.value
 
     # -- gradients of the conservative dynamics (float64 handles) ----------
 
@@ -517,6 +552,17 @@ class SDPDEnsemble:
 
     def step(self, dt, nsteps, seeds):
         _check(sdpd_ensemble_step(self.e, dt, nsteps, seeds), "sdpd_ensemble_step")
+
+    def autotune(self, dt, steps=3, seeds=None):
+        """Autotunes every member alone (states restored); returns each
+        member's time per step with its chosen launch shapes."""
+        n = len(self.members)
+        arr = None
+        if seeds is not None:
+            arr = (C.c_uint64 * n)(*[int(x) & (2**64 - 1) for x in seeds])
+        ms = (C.c_double * n)()
+        _check(load().sdpd_ensemble_autotune(self.e, float(dt), int(steps), arr, ms), "sdpd_ensemble_autotune")
+        return list(ms)
 
     @property
     def kernel_nodes(self) -> int:

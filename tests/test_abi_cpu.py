@@ -33,7 +33,11 @@ def _params(**kw):
     p = sdpd.sdpd_params(kB=1.0, eta=1.0, zeta=0.0, c_rho=-1.0, kernel=1, scheme=2, precision=0,
                          fd_only=0, theta=1, debug=0)
     for k, v in kw.items():
-        setattr(p, k, v)
+        if k == "nc":
+            for d in range(3):
+                p.nc[d] = v[d]
+        else:
+            setattr(p, k, v)
     return p
 
 
@@ -45,6 +49,11 @@ def _params(**kw):
     ({"zeta": 2.0}, (10.0, 10.0, 10.0), 100.0, sdpd.ERR_INVALID_ARG),  # zeta >= 5 eta / 3
     ({"kernel": 7}, (10.0, 10.0, 10.0), 100.0, sdpd.ERR_INVALID_ARG),
     ({"theta": 0}, (10.0, 10.0, 10.0), 100.0, sdpd.ERR_INVALID_ARG),
+    ({"nc": (4, 4, 4)}, (10.0, 10.0, 10.0), 100.0, sdpd.OK),           # the default grid, chosen
+    ({"nc": (4, 0, 6)}, (10.0, 10.0, 16.0), 100.0, sdpd.OK),           # 0 = default on that axis
+    ({"nc": (6, 4, 4)}, (10.0, 10.0, 10.0), 100.0, sdpd.ERR_BOX_TOO_SMALL),  # cells below h
+    ({"nc": (5, 4, 4)}, (20.0, 10.0, 10.0), 100.0, sdpd.ERR_INVALID_ARG),    # odd
+    ({"nc": (2, 4, 4)}, (20.0, 10.0, 10.0), 100.0, sdpd.ERR_INVALID_ARG),    # fewer than 4
 ])
 def test_create_validates_on_host(kw, box, K, expect):
     st, h = sdpd.sdpd_create(1000, box, 1.0, 2.5, K, _params(**kw), 0)
@@ -72,3 +81,39 @@ def test_workspace_scales_with_precision():
 def test_strerror_covers_codes():
     for code in range(11):
         assert sdpd.sdpd_strerror(code) != "unknown status"
+
+
+def test_coarser_cell_grid_needs_less_workspace():
+    st, h1 = sdpd.sdpd_create(32768, (32.0,) * 3, 1.0, 2.5, 100.0, _params(precision=1), 0)
+    st2, h2 = sdpd.sdpd_create(32768, (32.0,) * 3, 1.0, 2.5, 100.0, _params(precision=1, nc=(10, 10, 10)), 0)
+    assert st == st2 == sdpd.OK
+    assert sdpd.sdpd_workspace_bytes(h2) < sdpd.sdpd_workspace_bytes(h1)
+    sdpd.sdpd_destroy(h1)
+    sdpd.sdpd_destroy(h2)
+
+
+@pytest.mark.parametrize("precision,default,fits", [
+    (0, 1, {1, 2, 3}),          # float64: four or more block groups exceed 48 KB
+    (1, 0, {0, 1, 2, 3, 4}),
+])
+def test_launch_shapes_on_host(precision, default, fits):
+    lib = sdpd.load()
+    st, h = sdpd.sdpd_create(8000, (20.0,) * 3, 1.0, 2.5, 100.0, _params(precision=precision), 0)
+    assert st == sdpd.OK
+    t = sdpd.sdpd_tuning()
+    assert lib.sdpd_get_tuning(h, C.byref(t)) == sdpd.OK
+    assert (t.fd_variant, t.pair_threads) == (default, 128)
+    for v in range(-1, sdpd.FD_VARIANTS + 1):
+        for pt in (0, 32, 48, 64, 128, 256):
+            want = (v == -1 or v in fits) and pt in (0, 32, 64, 128)
+            r = lib.sdpd_set_tuning(h, C.byref(sdpd.sdpd_tuning(fd_variant=v, pair_threads=pt)))
+            assert r == (sdpd.OK if want else sdpd.ERR_INVALID_ARG), (v, pt)
+            if want:
+                assert lib.sdpd_get_tuning(h, C.byref(t)) == sdpd.OK
+                assert t.fd_variant == (default if v == -1 else v)
+                assert t.pair_threads == (128 if pt == 0 else pt)
+    # the autotuner needs a workspace and a state; refused without touching a device
+    assert lib.sdpd_autotune(h, 0.005, 2, 0, None, None) == sdpd.ERR_NO_WORKSPACE
+    assert lib.sdpd_autotune(h, -1.0, 2, 0, None, None) == sdpd.ERR_INVALID_ARG
+    assert lib.sdpd_autotune(h, 0.005, 0, 0, None, None) == sdpd.ERR_INVALID_ARG
+    sdpd.sdpd_destroy(h)

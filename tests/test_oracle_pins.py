@@ -357,10 +357,13 @@ def test_ems_reverse_ratio_antisymmetric():
 # Pair colouring of the sweep
 # --------------------------------------------------------------------------
 
-def test_colouring_is_conflict_free():
-    w = Workload(n=12, jitter=0.2, seed=8)
+@pytest.mark.parametrize("n,n_c", [(12, None), (16, (4, 6, 4))])  # the default grid; a coarser one
+def test_colouring_is_conflict_free(n, n_c):
+    w = Workload(n=n, jitter=0.2, seed=8)
     q, p, eps = lattice_state(w)
-    P = O.Config(N=w.N, L=w.L, K=w.K).params()
+    P = O.Config(N=w.N, L=w.L, K=w.K, n_c=n_c).params()
+    if n_c is not None:
+        assert tuple(P.n_c[:]) == n_c
     s, _, _, st, recs = O.fd_sweep(P, q, p, eps, 0.005, 1, 0, records=True)
     assert s == O.OK
     # the pair set is exactly the brute-force neighbour set

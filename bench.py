@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--adj-steps", type=int, default=100, help="adjoint workload: Verlet steps per gradient")
     ap.add_argument("--adj-every", type=int, default=10, help="adjoint workload: checkpoint interval")
     ap.add_argument("--replicas", type=int, default=256)
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default launch shapes instead of timing the candidates first")
     return ap.parse_args()
 
 
@@ -209,6 +211,15 @@ FD_COLOUR_DRAM_BYTES_PER_PARTICLE = (49.280512e6 + 1.082368e6) / 96 ** 3
 FLOPS_PER_PAIR_UPDATE = {"ems": 210.0, "ams": 150.0, "ssa": 140.0}
 
 
+def autotune(args, s, seed):
+    """The library's autotuner on the loaded state (it restores the state):
+    the chosen launch shapes and their time per step, or the defaults."""
+    if args.no_autotune:
+        return {"autotuned": False, **s.tuning}
+    t, ms = s.autotune(args.dt, steps=2, seed=seed)
+    return {"autotuned": True, **t, "trial_ms_per_step": ms}
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     from paper_1707_04232_gb300 import sdpd
@@ -226,6 +237,7 @@ def run_ours(args, rank, world, local_rank):
         s.set_state(q, p, e)
         for _ in range(args.warmup):
             s.step(args.dt, 1, seed=1234 + rank)
+        tuning = autotune(args, s, 1234 + rank)
         s.sync()
         o0 = s.observables()
         s.reset_counters()
@@ -290,6 +302,7 @@ def run_ours(args, rank, world, local_rank):
         "stages_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
         "gpu_launches": launches,
         "clocks": clk,
+        "launch_shapes": tuning,
         "physics": {"E0": o0["E"], "E1": o1["E"], "T_kin": o1["T_kin"], "T_int": o1["T_int"],
                     "eps_min": o1["eps_min"], "n_pairs": o1["n_pairs"],
                     "reject_rate": (o1["n_reject_bound"] + o1["n_reject_metropolis"]) / max(1, o1["n_pairs"]),
@@ -322,6 +335,10 @@ def run_fp64_form(args, w, q, p, e, scheme, stream, world, mixed_value):
         s = sdpd.SDPD(w.N, w.L, m=w.m, h=w.h, K=w.K, precision=sdpd.FP64, scheme=scheme, stream=stream)
         s.set_state(q, p, e)
         s.step(args.dt, 1, seed=77)
+        tuning = None
+        if not args.no_autotune:
+            t, _ = s.autotune(args.dt, steps=1, seed=77)
+            tuning = t
         s.sync()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         barrier(world)
@@ -333,7 +350,7 @@ def run_fp64_form(args, w, q, p, e, scheme, stream, world, mixed_value):
         del s
     ps = w.N * steps * world / (ms * 1e-3)
     return {"value": ps, "unit": UNIT, "ms_per_step": ms / steps, "steps": steps,
-            "speedup_of_mixed": mixed_value / ps}
+            "speedup_of_mixed": mixed_value / ps, "launch_shapes": tuning}
 
 
 def ensemble_members(args, rank):
@@ -380,6 +397,28 @@ def run_ensemble(args, rank, world, local_rank):
     ntot = sum(w.N for w in ws)
     ens.step(args.dt, 2 * max(2, args.warmup), seeds)  # capture + warm-up
     torch.cuda.synchronize()
+    tuning = {"autotuned": False}
+    if not args.no_autotune:
+        # the default shapes first, then every member tuned alone, then the
+        # graph recaptured with the chosen shapes
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(ens.stream)
+        ens.step(args.dt, args.steps, seeds)
+        b.record(ens.stream)
+        torch.cuda.synchronize()
+        untuned_ms = a.elapsed_time(b)
+        tuned_trial_ms = ens.autotune(args.dt, steps=4, seeds=seeds)
+        ens.step(args.dt, 2 * max(2, args.warmup), seeds)
+        torch.cuda.synchronize()
+        shapes = {}
+        for m in members:
+            t = m.tuning
+            key = "%d/%d" % (t["fd_variant"], t["pair_threads"])
+            shapes[key] = shapes.get(key, 0) + 1
+        tuning = {"autotuned": True, "members_by_shape(fd_variant/pair_threads)": shapes,
+                  "tuner_ms_per_step": tuned_trial_ms,
+                  "untuned_ms_per_step": untuned_ms / args.steps,
+                  "untuned_value": ntot * args.steps / (untuned_ms * 1e-3)}
     launches0 = sum(m.kernel_launches for m in members)
     clocks = ClockSampler(dev_index)
     clocks.start()
@@ -428,6 +467,7 @@ def run_ensemble(args, rank, world, local_rank):
         "temperature_error": {"max": max(terr), "mean": float(np.mean(terr)),
                               "definition": "|<T_int> - T_eq| / T_eq, T_eq = E / (3(N-1)/2 + N C_K)"},
         "gpu_launches": launches, "clocks": clk,
+        "launch_shapes": tuning,
     }
     if rank == 0:
         print(json.dumps(line))
@@ -477,6 +517,9 @@ def run_adjoint(args, rank, world, local_rank):
         s = sdpd.SDPD(w.N, w.L, m=w.m, h=w.h, K=w.K, precision=sdpd.FP64, scheme=sdpd.SCHEME_EMS,
                       stream=stream)
         qd, pd, ed = (torch.as_tensor(a, device="cuda") for a in (q, p, e))
+
+        s.set_state(qd, pd, ed)
+        tuning = autotune(args, s, 3)
 
         def gradient():
             s.set_state(qd, pd, ed)
@@ -574,6 +617,7 @@ def run_adjoint(args, rank, world, local_rank):
         "e2e": {"value": w.N * ns * e2e_steps * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 56 * w.N,
                 "d2h_bytes_per_step": 56 * w.N, "steps": e2e_steps,
                 "note": "per gradient: state from pinned host, forward + reverse, gradients to pinned host"},
+        "launch_shapes": tuning,
         "physics": {"virial_pressure": val, "dP_dtheta(h,c_rho,C_K)": [float(x) for x in g0[3] + gth]},
     }
     if rank == 0 and not args.no_cpu and world == 1:

@@ -254,11 +254,18 @@ void sdpd_destroy(sdpd_t* s);
 typedef struct sdpd_ensemble sdpd_ens_t;
 int sdpd_ensemble_create(sdpd_t* const* members, int n, void* stream, sdpd_ens_t** out);
 int sdpd_ensemble_step(sdpd_ens_t* e, double dt, int64_t nsteps, const uint64_t* seeds);
-/* Runs sdpd_autotune on every member alone (seeds[i] or 0 when seeds is
- * NULL); ms_per_step[i] (may be NULL) receives each member's time per step
- * with its chosen shapes.  The next sdpd_ensemble_step recaptures its graph
- * with the new shapes.  Errors: those of sdpd_autotune (the first failing
- * member stops the tuning). */
+/* Chooses every member's launch shapes for the ensemble as a whole.  First
+ * sdpd_autotune runs on every member alone (seeds[i], or 0 when seeds is
+ * NULL).  Then the ensemble's graph is timed under each candidate
+ * assignment: the defaults, the shapes each member chose alone, and each
+ * colour-launch schedule given to every member (pair passes at 128 threads).
+ * Each candidate gets one warm-up unit of U steps and then at least `steps`
+ * timed steps, all from the saved states.  The fastest assignment is kept.
+ * Shapes that win alone can lose when hundreds of members share the GPU,
+ * which is why this second stage exists.  Every member's state and counters
+ * are restored.  *ms_per_step (may be NULL) receives the ensemble's time
+ * per step under the chosen shapes.  Synchronising.  Errors: those of
+ * sdpd_autotune and sdpd_ensemble_step. */
 int sdpd_ensemble_autotune(sdpd_ens_t* e, double dt, int64_t steps, const uint64_t* seeds, double* ms_per_step);
 /* Kernel launches of the captured U-step graph (all members). */
 int64_t sdpd_ensemble_kernel_nodes(const sdpd_ens_t* e);

@@ -683,6 +683,58 @@ int sdpd_stage_times(sdpd_t* s, double* ms, int64_t* launches, int n) {
   return SDPD_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// What the autotuners save before their trial steps and put back after:
+// the state (in id order, in the staging buffers that the load path reads),
+// the host step counters and the device pair counters.
+struct SavedHandle {
+  unsigned long long counters[4];
+  int64_t fd_step, vv_step, launches;
+  bool timing;
+};
+
+int save_handle(sdpd_handle* s, SavedHandle* sv) {
+  cudaStream_t st = s->stream;
+  if (s->prm.precision == SDPD_MIXED) launch_unload<Mixed>(s->c, s->w, s->cur, st);
+  else launch_unload<Fp64>(s->c, s->w, s->cur, st);
+  if (cudaMemcpyAsync(sv->counters, s->w.counters, sizeof(sv->counters), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return SDPD_ERR_CUDA;
+  sv->fd_step = s->fd_step;
+  sv->vv_step = s->vv_step;
+  sv->launches = s->launches;
+  sv->timing = s->timing;
+  s->timing = false;
+  return SDPD_OK;
+}
+
+// the saved state loaded again (bin, sort, density) with its step counters
+void reload_handle(sdpd_handle* s, const SavedHandle& sv) {
+  if (s->prm.precision == SDPD_MIXED) do_load<Mixed>(s);
+  else do_load<Fp64>(s);
+  launch_set_sweep(s->w, (unsigned long long)sv.fd_step, s->stream);
+  s->fd_step = sv.fd_step;
+  s->vv_step = sv.vv_step;
+}
+
+// the device counters and status put back; synchronising (the host copy of
+// the counters must outlive the transfer)
+int finish_restore(sdpd_handle* s, const SavedHandle& sv) {
+  int e = cuda_ok(cudaMemcpyAsync(s->w.counters, sv.counters, sizeof(sv.counters), cudaMemcpyHostToDevice, s->stream));
+  e |= cuda_ok(cudaMemsetAsync(s->w.status, 0, 8, s->stream));
+  s->launches = sv.launches;
+  s->timing = sv.timing;
+  if (e) return SDPD_ERR_CUDA;
+  return sdpd_sync(s);
+}
+
+}  // namespace
+
+extern "C" {
+
 int sdpd_get_tuning(const sdpd_t* s, sdpd_tuning* out) {
   if (!s || !out) return SDPD_ERR_INVALID_ARG;
   out->fd_variant = s->c.fd_variant;
@@ -709,35 +761,20 @@ int sdpd_autotune(sdpd_t* s, double dt, int64_t steps, uint64_t seed, sdpd_tunin
   if (e) return e;
   const bool mixed = s->prm.precision == SDPD_MIXED;
   cudaStream_t st = s->stream;
-  // the state in id order in the staging buffers (the load path reads them
-  // back), and every counter the trial steps advance
-  if (mixed) launch_unload<Mixed>(s->c, s->w, s->cur, st);
-  else launch_unload<Fp64>(s->c, s->w, s->cur, st);
-  unsigned long long counters[4] = {0, 0, 0, 0};
-  if (cudaMemcpyAsync(counters, s->w.counters, sizeof(counters), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-      cudaStreamSynchronize(st) != cudaSuccess)
-    return SDPD_ERR_CUDA;
-  const int64_t fd0 = s->fd_step, vv0 = s->vv_step, l0 = s->launches;
-  const bool timing0 = s->timing;
-  s->timing = false;
-  auto reload = [&]() {
-    if (mixed) do_load<Mixed>(s);
-    else do_load<Fp64>(s);
-    launch_set_sweep(s->w, (unsigned long long)fd0, st);
-    s->fd_step = fd0;
-    s->vv_step = vv0;
-  };
+  SavedHandle sv;
+  e = save_handle(s, &sv);
+  if (e) return e;
   cudaEvent_t ev[2] = {nullptr, nullptr};
   if (cudaEventCreate(&ev[0]) != cudaSuccess || cudaEventCreate(&ev[1]) != cudaSuccess) {
     if (ev[0]) cudaEventDestroy(ev[0]);
-    s->timing = timing0;
+    s->timing = sv.timing;
     return SDPD_ERR_CUDA;
   }
   // time per step of one candidate; infinity when it failed
   auto trial = [&](int v, int pt) -> double {
     s->c.fd_variant = v;
     s->c.pair_threads = pt;
-    reload();
+    reload_handle(s, sv);
     if (mixed) do_steps<Mixed>(s, dt, 1, seed);
     else do_steps<Fp64>(s, dt, 1, seed);
     cudaEventRecord(ev[0], st);
@@ -752,8 +789,8 @@ int sdpd_autotune(sdpd_t* s, double dt, int64_t steps, uint64_t seed, sdpd_tunin
     }
     return (double)ms / (double)steps;
   };
-  const sdpd_tuning start = {s->c.fd_variant, s->c.pair_threads};
-  int bv = start.fd_variant, bt = 128;
+  const int v0 = s->c.fd_variant, t0 = s->c.pair_threads;
+  int bv = v0, bt = 128;
   double bms = INFINITY;
   for (int v = 0; v < kFdVariants; ++v) {
     if (!fd_variant_fits(mixed, v)) continue;
@@ -766,17 +803,11 @@ int sdpd_autotune(sdpd_t* s, double dt, int64_t steps, uint64_t seed, sdpd_tunin
   }
   cudaEventDestroy(ev[0]);
   cudaEventDestroy(ev[1]);
-  if (!isfinite(bms)) { bv = start.fd_variant; bt = start.pair_threads; }
+  if (!isfinite(bms)) { bv = v0; bt = t0; }
   s->c.fd_variant = bv;
   s->c.pair_threads = bt;
-  // back to the state and counters the call started from
-  reload();
-  e = cuda_ok(cudaMemcpyAsync(s->w.counters, counters, sizeof(counters), cudaMemcpyHostToDevice, st));
-  e |= cuda_ok(cudaMemsetAsync(s->w.status, 0, 8, st));
-  s->launches = l0;
-  s->timing = timing0;
-  if (e) return SDPD_ERR_CUDA;
-  e = sdpd_sync(s);  // the host counters above must outlive the copy
+  reload_handle(s, sv);  // back to the state and counters the call started from
+  e = finish_restore(s, sv);
   if (e) return e;
   if (best) { best->fd_variant = bv; best->pair_threads = bt; }
   if (ms_per_step) *ms_per_step = bms;
@@ -1366,17 +1397,89 @@ int sdpd_ensemble_step(sdpd_ens_t* e, double dt, int64_t nsteps, const uint64_t*
 }
 
 int sdpd_ensemble_autotune(sdpd_ens_t* e, double dt, int64_t steps, const uint64_t* seeds, double* ms_per_step) {
-  if (!e) return SDPD_ERR_INVALID_ARG;
+  if (!e || !(dt > 0) || !isfinite(dt) || steps < 1 || steps > 1000) return SDPD_ERR_INVALID_ARG;
+  const size_t n = e->m.size();
+  std::vector<uint64_t> sd(n, 0ull);
+  if (seeds) sd.assign(seeds, seeds + n);
   // members' streams may still hold work of the ensemble stream
   for (sdpd_handle* h : e->m)
     if (order_streams(e->stream, h->stream) != SDPD_OK) return SDPD_ERR_CUDA;
-  for (size_t i = 0; i < e->m.size(); ++i) {
-    double ms = 0.0;
-    const int r = sdpd_autotune(e->m[i], dt, steps, seeds ? seeds[i] : 0ull, nullptr, &ms);
+  // 1. every member alone
+  std::vector<sdpd_tuning> alone(n);
+  for (size_t i = 0; i < n; ++i) {
+    const int r = sdpd_autotune(e->m[i], dt, steps, sd[i], &alone[i], nullptr);
     if (r != SDPD_OK) return r;
-    if (ms_per_step) ms_per_step[i] = ms;
   }
-  return SDPD_OK;
+  // 2. the whole ensemble, through its graph, under candidate assignments:
+  // the defaults, the shapes each member chose alone, and every colour
+  // schedule given to all members; the fastest assignment is kept
+  std::vector<std::vector<sdpd_tuning>> cand;
+  std::vector<sdpd_tuning> dflt(n);
+  for (size_t i = 0; i < n; ++i) dflt[i] = {fd_default_variant(e->m[i]->prm.precision == SDPD_MIXED), 128};
+  cand.push_back(dflt);
+  cand.push_back(alone);
+  for (int v = 0; v < kFdVariants; ++v) {
+    std::vector<sdpd_tuning> u(n);
+    for (size_t i = 0; i < n; ++i) {
+      const bool mixed = e->m[i]->prm.precision == SDPD_MIXED;
+      u[i] = {fd_variant_fits(mixed, v) ? v : fd_default_variant(mixed), 128};
+    }
+    cand.push_back(u);
+  }
+  std::vector<SavedHandle> sv(n);
+  for (size_t i = 0; i < n; ++i) {
+    const int r = save_handle(e->m[i], &sv[i]);
+    if (r != SDPD_OK) {
+      for (size_t k = 0; k < i; ++k) e->m[k]->timing = sv[k].timing;
+      return r;
+    }
+  }
+  const int64_t U = e->unit;
+  const int64_t timed = ((steps + U - 1) / U) * U;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  int err = SDPD_OK;
+  if (cudaEventCreate(&ev[0]) != cudaSuccess || cudaEventCreate(&ev[1]) != cudaSuccess) err = SDPD_ERR_CUDA;
+  double bms = INFINITY;
+  size_t best = 0;
+  for (size_t c = 0; c < cand.size() && !err; ++c) {
+    for (size_t i = 0; i < n; ++i) {
+      e->m[i]->c.fd_variant = cand[c][i].fd_variant;
+      e->m[i]->c.pair_threads = cand[c][i].pair_threads;
+      reload_handle(e->m[i], sv[i]);
+    }
+    double ms = INFINITY;
+    if (sdpd_ensemble_step(e, dt, U, sd.data()) == SDPD_OK) {  // capture and warm up
+      cudaEventRecord(ev[0], e->stream);
+      const int r = sdpd_ensemble_step(e, dt, timed, sd.data());
+      cudaEventRecord(ev[1], e->stream);
+      float t = 0.0f;
+      bool ok = r == SDPD_OK && cudaEventSynchronize(ev[1]) == cudaSuccess &&
+                cudaEventElapsedTime(&t, ev[0], ev[1]) == cudaSuccess;
+      for (sdpd_handle* h : e->m) ok = (sdpd_sync(h) == SDPD_OK) && ok;
+      if (ok) ms = (double)t / (double)timed;
+    }
+    if (!isfinite(ms)) {
+      cudaGetLastError();
+      for (sdpd_handle* h : e->m) cudaMemsetAsync(h->w.status, 0, 8, h->stream);
+    }
+    if (ms < bms) { bms = ms; best = c; }
+  }
+  if (ev[0]) cudaEventDestroy(ev[0]);
+  if (ev[1]) cudaEventDestroy(ev[1]);
+  if (!isfinite(bms)) best = 0;
+  // the chosen shapes, and every member back where the call found it
+  for (size_t i = 0; i < n; ++i) {
+    e->m[i]->c.fd_variant = cand[best][i].fd_variant;
+    e->m[i]->c.pair_threads = cand[best][i].pair_threads;
+    reload_handle(e->m[i], sv[i]);
+  }
+  for (size_t i = 0; i < n; ++i) {
+    const int r = finish_restore(e->m[i], sv[i]);
+    if (!err) err = r;
+  }
+  if (err) return err;
+  if (ms_per_step) *ms_per_step = bms;
+  return isfinite(bms) ? SDPD_OK : SDPD_ERR_CUDA;
 }
 
 int64_t sdpd_ensemble_kernel_nodes(const sdpd_ens_t* e) { return e ? e->launches_per_unit : -1; }

@@ -553,16 +553,17 @@ class SDPDEnsemble:
     def step(self, dt, nsteps, seeds):
         _check(sdpd_ensemble_step(self.e, dt, nsteps, seeds), "sdpd_ensemble_step")
 
-    def autotune(self, dt, steps=3, seeds=None):
-        """Autotunes every member alone (states restored); returns each
-        member's time per step with its chosen launch shapes."""
+    def autotune(self, dt, steps=4, seeds=None):
+        """Chooses the members' launch shapes for the ensemble as a whole
+        (states restored); returns the ensemble's time per step with them."""
         n = len(self.members)
         arr = None
         if seeds is not None:
             arr = (C.c_uint64 * n)(*[int(x) & (2**64 - 1) for x in seeds])
-        ms = (C.c_double * n)()
-        _check(load().sdpd_ensemble_autotune(self.e, float(dt), int(steps), arr, ms), "sdpd_ensemble_autotune")
-        return list(ms)
+        ms = C.c_double(0.0)
+        _check(load().sdpd_ensemble_autotune(self.e, float(dt), int(steps), arr, C.byref(ms)),
+               "sdpd_ensemble_autotune")
+        return ms.value
 
     @property
     def kernel_nodes(self) -> int:

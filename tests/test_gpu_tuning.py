@@ -25,7 +25,7 @@ from paper_1707_04232_gb300 import sdpd  # noqa: E402
 FITS = {sdpd.FP64: (1, 2, 3), sdpd.MIXED: (0, 1, 2, 3, 4)}
 
 
-def fluid(n=14, K=20.0, seed=2):
+def fluid(n=15, K=20.0, seed=2):
     w = Workload(n=n, K=K, jitter=0.2, seed=seed)
     q, p, e = lattice_state(w)
     return q, p, e, w
@@ -77,7 +77,7 @@ def test_autotune_restores_the_handle(precision, theta):
 
 
 def test_ensemble_autotune_keeps_every_member_bitwise():
-    sizes = [(8, 5.0, 0.3), (11, 100.0, 1.0), (13, 20.0, 0.7)]
+    sizes = [(10, 5.0, 0.3), (11, 100.0, 1.0), (12, 20.0, 0.7)]  # blocks of 125, 216, 216
     members, alone, states = [], [], []
     for k, (n, K, kT) in enumerate(sizes):
         w = Workload(n=n, K=K, kT=kT, seed=30 + k)
@@ -91,7 +91,7 @@ def test_ensemble_autotune_keeps_every_member_bitwise():
     seeds = [3, 4, 5]
     ens.step(0.005, 4, seeds)
     ms = ens.autotune(0.005, steps=2, seeds=seeds)
-    assert len(ms) == 3 and min(ms) > 0
+    assert ms > 0
     ens.step(0.005, 6, seeds)
     torch.cuda.synchronize()
     for s, seed in zip(alone, seeds):

@@ -190,6 +190,7 @@ size_t layout(sdpd_handle* s, Workspace* w, char* base) {
   w->counters = (unsigned long long*)at(4 * 8);
   w->sweep = (unsigned long long*)at(8);
   w->status = (int*)at(8);
+  w->fd_queue = (unsigned*)at(16 * 4);
   w->pair_rec_count = (unsigned long long*)at(8);
   w->pair_rec_cap = s->pair_rec_cap;
   w->pair_recs = s->pair_rec_cap > 0 ? (sdpd_pair_rec*)at((size_t)s->pair_rec_cap * sizeof(sdpd_pair_rec)) : nullptr;
@@ -524,7 +525,13 @@ int sdpd_bind_workspace(sdpd_t* s, void* ptr, size_t bytes) {
   e |= cuda_ok(cudaMemsetAsync(s->w.counters, 0, 4 * 8, st));
   e |= cuda_ok(cudaMemsetAsync(s->w.status, 0, 8, st));
   e |= cuda_ok(cudaMemsetAsync(s->w.sched_hdr, 0, (size_t)c.ncell * 4, st));
+  e |= cuda_ok(cudaMemsetAsync(s->w.fd_queue, 0, 16 * 4, st));
   e |= cuda_ok(cudaStreamSynchronize(st));
+  // launch sizes of the sweep's colour kernels, queried here rather than
+  // inside a later stream capture
+  if (s->prm.precision == SDPD_MIXED) fd_prepare<Mixed>();
+  else fd_prepare<Fp64>();
+  e |= launch_status();
   s->has_state = false;
   return e ? SDPD_ERR_CUDA : SDPD_OK;
 }
@@ -549,6 +556,7 @@ int sdpd_set_state(sdpd_t* s, const double* q, const double* p, const double* ep
   }
   e |= cuda_ok(cudaMemsetAsync(s->w.counters, 0, 4 * 8, st));
   e |= cuda_ok(cudaMemsetAsync(s->w.status, 0, 8, st));
+  e |= cuda_ok(cudaMemsetAsync(s->w.fd_queue, 0, 16 * 4, st));
   if (e) return SDPD_ERR_CUDA;
   if (s->prm.precision == SDPD_MIXED) do_load<Mixed>(s);
   else do_load<Fp64>(s);

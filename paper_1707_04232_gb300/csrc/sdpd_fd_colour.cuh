@@ -3,6 +3,8 @@
 // by level.  Included by one translation unit per precision, each of which
 // instantiates the block-schedule variants of its precision.
 #pragma once
+#include <algorithm>
+
 #include "sdpd_fd_common.cuh"
 
 namespace sdpd {
@@ -262,7 +264,7 @@ __global__ void __launch_bounds__(W * 32, fd_min_blocks<P, W>())
                 const uint32_t* __restrict__ xmz, const uint32_t* __restrict__ hdr,
                 const uint16_t* __restrict__ lvl, const uint16_t* __restrict__ pairs, int colour, uint64_t seed,
                 const unsigned long long* __restrict__ sweep_ptr, unsigned long long* counters, int* status,
-                sdpd_pair_rec* recs, unsigned long long* rec_count, int64_t rec_cap) {
+                sdpd_pair_rec* recs, unsigned long long* rec_count, int64_t rec_cap, unsigned* __restrict__ queue) {
   using R = typename P::R;
   constexpr int kGroupLanes = 32 / OPW;
   __shared__ FdSmem<R> sm_all[W][OPW];
@@ -271,166 +273,186 @@ __global__ void __launch_bounds__(W * 32, fd_min_blocks<P, W>())
   const int grp = lane / kGroupLanes, gl = lane % kGroupLanes;
   const int hx = c.nc[0] >> 1, hy = c.nc[1] >> 1, hz = c.nc[2] >> 1;
   const int64_t nown = (int64_t)hx * hy * hz;
-  const int64_t w = ((int64_t)blockIdx.x * W + warp) * OPW + grp;
   FdSmem<R>& sm = sm_all[warp][grp];
-  int np = 0, nlev = 0;
-  int64_t o = 0;
-  int ox = 0, oy = 0, oz = 0;
-  if (w < nown) {
-    ox = 2 * (int)(w % hx) + (colour & 1);
-    oy = 2 * (int)((w / hx) % hy) + ((colour >> 1) & 1);
-    oz = 2 * (int)(w / ((int64_t)hx * hy)) + ((colour >> 2) & 1);
-    o = ox + (int64_t)c.nc[0] * (oy + (int64_t)c.nc[1] * oz);
-    const uint32_t hd = hdr[o];
-    np = (int)(hd & 0xffffu);
-    nlev = (int)(hd >> 16);
-  }
-  BlockCells b;
-  b.base[8] = 0;
-  if (np > 0) block_cells(c, ox, oy, oz, mrank, cell_start, b);
-  const int nb = np > 0 ? b.base[8] : 0;
-  BlockGeom<P> geo;
-  geo.init(c, ox, oy, oz, xmx, xmy, xmz);
-#pragma unroll
-  for (int t = 0; t < 8; ++t)
-    if (gl == t) {
-      sm.cst[t] = b.start[t];
-      sm.cbs[t] = b.base[t];
-    }
-  __syncwarp();
-  // storage index of block particle q (recomputed where needed, which keeps
-  // shared memory small enough for eight thread blocks per SM)
-  auto gidx = [&](int q) {
-    int d = 0;
-#pragma unroll
-    for (int t = 1; t < 8; ++t) d += (q >= sm.cbs[t]);
-    return sm.cst[d] + (q - sm.cbs[d]);
-  };
-  for (int q = gl; q < nb; q += kGroupLanes) {
-    const int g = gidx(q);
-    sm.px[q] = a.px[g]; sm.py[q] = a.py[g]; sm.pz[q] = a.pz[g];
-    sm.e[q] = (R)a.eps[g];
-    sm.acc[q] = R(0);
-  }
-  for (int L = gl; L <= nlev; L += kGroupLanes) sm.off[L] = lvl[o * (kMaxLevels + 1) + L];
-  __syncwarp();
-  const uint16_t* off = sm.off;
-  const uint16_t* pl = pairs + o * kMaxPairs;
   const R inv_h = k.inv_h, cF = k.cF;
+  const R pi_coef = (R)(c.c_rho / (c.C_K * c.m));
   unsigned long long n_acc = 0, n_rb = 0, n_rm = 0, n_tot = 0;
   bool negative = false, bad = false;
-  int L = 0, pos = 0;
-  while (__any_sync(0xffffffffu, pos < np)) {
-    // stage pairs [cbeg, cend) of the level-ordered list; the chunk ends on
-    // a level boundary when at least one whole level fits, so that no level
-    // is split over two chunks (a split level costs an extra round)
-    const int cbeg = pos;
-    int cend = min(pos + kChunk, np);
-    if (pos < np && (int)off[L + 1] <= cend) {
-      int Le = L + 1;
-      while (Le < nlev && (int)off[Le + 1] <= cend) ++Le;
-      cend = off[Le];
+  // The grid holds as many thread blocks as fit on the GPU at once; each
+  // warp takes the colour's blocks OPW at a time from queue[0] until they
+  // run out, so no partial last wave of thread blocks idles the GPU and
+  // blocks of uneven depth balance out.  queue[1] counts the warps that are
+  // done; the last one sets both back to zero for the next launch.
+  for (;;) {
+    unsigned w0 = 0;
+    if (lane == 0) w0 = atomicAdd(queue, (unsigned)OPW);
+    w0 = __shfl_sync(0xffffffffu, w0, 0);
+    if ((int64_t)w0 >= nown) break;
+    const int64_t w = (int64_t)w0 + grp;
+    int np = 0, nlev = 0;
+    int64_t o = 0;
+    int ox = 0, oy = 0, oz = 0;
+    if (w < nown) {
+      ox = 2 * (int)(w % hx) + (colour & 1);
+      oy = 2 * (int)((w / hx) % hy) + ((colour >> 1) & 1);
+      oz = 2 * (int)(w / ((int64_t)hx * hy)) + ((colour >> 2) & 1);
+      o = ox + (int64_t)c.nc[0] * (oy + (int64_t)c.nc[1] * oz);
+      const uint32_t hd = hdr[o];
+      np = (int)(hd & 0xffffu);
+      nlev = (int)(hd >> 16);
     }
-    for (int t = cbeg + gl; t < cend; t += kGroupLanes) {
-      const uint16_t pr = pl[t];
-      const int ia = pr & 255, ib = pr >> 8;  // ia holds the lower id
-      const int ga = gidx(ia), gb = gidx(ib);
-      R xa, ya, za, xb, yb, zb, rx, ry, rz;
-      const typename P::V4 qa = ld4(&a.q4[ga]), qb = ld4(&a.q4[gb]);
-      geo.local(qa, block_code(qa.w, ox, oy, oz), xa, ya, za);
-      geo.local(qb, block_code(qb.w, ox, oy, oz), xb, yb, zb);
-      geo.disp(xa, ya, za, xb, yb, zb, rx, ry, rz);
-      const R r2 = r2_of(rx, ry, rz);
-      const R inv_r = fm::rsqrt(r2);
-      const int slot = t - cbeg;
-      sm.pr[slot] = pr;
-      sm.ex[slot] = rx * inv_r;
-      sm.ey[slot] = ry * inv_r;
-      sm.ez[slot] = rz * inv_r;
-      sm.base[slot] = fm::div(kernel_F<KIND>(r2 * inv_r * inv_h, cF), a.rho[ga] * a.rho[gb]);
-      R G[3], U;
-      pair_randoms_fast(seed, sweep, (uint64_t)a.id[ga], (uint64_t)a.id[gb], G, &U);
-      sm.G0[slot] = G[0]; sm.G1[slot] = G[1]; sm.G2[slot] = G[2]; sm.U[slot] = U;
-    }
-    __syncwarp();
-    // the chunk's levels, or parts of them
-    bool more = cbeg < cend;
-    while (__any_sync(0xffffffffu, more)) {
-      int lb = 0, le = 0;
-      if (more) {
-        lb = max((int)off[L], cbeg);
-        le = min((int)off[L + 1], cend);
+    BlockCells b;
+    b.base[8] = 0;
+    if (np > 0) block_cells(c, ox, oy, oz, mrank, cell_start, b);
+    const int nb = np > 0 ? b.base[8] : 0;
+    BlockGeom<P> geo;
+    geo.init(c, ox, oy, oz, xmx, xmy, xmz);
+#pragma unroll
+    for (int t = 0; t < 8; ++t)
+      if (gl == t) {
+        sm.cst[t] = b.start[t];
+        sm.cbs[t] = b.base[t];
       }
-      for (int t = lb + gl; t < le; t += kGroupLanes) {
+    __syncwarp();
+    // storage index of block particle q (recomputed where needed, which keeps
+    // shared memory small enough for eight thread blocks per SM)
+    auto gidx = [&](int q) {
+      int d = 0;
+#pragma unroll
+      for (int t = 1; t < 8; ++t) d += (q >= sm.cbs[t]);
+      return sm.cst[d] + (q - sm.cbs[d]);
+    };
+    for (int q = gl; q < nb; q += kGroupLanes) {
+      const int g = gidx(q);
+      sm.px[q] = a.px[g]; sm.py[q] = a.py[g]; sm.pz[q] = a.pz[g];
+      sm.e[q] = (R)a.eps[g];
+      sm.acc[q] = R(0);
+    }
+    for (int L = gl; L <= nlev; L += kGroupLanes) sm.off[L] = lvl[o * (kMaxLevels + 1) + L];
+    __syncwarp();
+    const uint16_t* off = sm.off;
+    const uint16_t* pl = pairs + o * kMaxPairs;
+    int L = 0, pos = 0;
+    while (__any_sync(0xffffffffu, pos < np)) {
+      // stage pairs [cbeg, cend) of the level-ordered list; the chunk ends on
+      // a level boundary when at least one whole level fits, so that no level
+      // is split over two chunks (a split level costs an extra round)
+      const int cbeg = pos;
+      int cend = min(pos + kChunk, np);
+      if (pos < np && (int)off[L + 1] <= cend) {
+        int Le = L + 1;
+        while (Le < nlev && (int)off[Le + 1] <= cend) ++Le;
+        cend = off[Le];
+      }
+      for (int t = cbeg + gl; t < cend; t += kGroupLanes) {
+        const uint16_t pr = pl[t];
+        const int ia = pr & 255, ib = pr >> 8;  // ia holds the lower id
+        const int ga = gidx(ia), gb = gidx(ib);
+        R xa, ya, za, xb, yb, zb, rx, ry, rz;
+        const typename P::V4 qa = ld4(&a.q4[ga]), qb = ld4(&a.q4[gb]);
+        geo.local(qa, block_code(qa.w, ox, oy, oz), xa, ya, za);
+        geo.local(qb, block_code(qb.w, ox, oy, oz), xb, yb, zb);
+        geo.disp(xa, ya, za, xb, yb, zb, rx, ry, rz);
+        const R r2 = r2_of(rx, ry, rz);
+        const R inv_r = fm::rsqrt(r2);
         const int slot = t - cbeg;
-        const uint16_t pr = sm.pr[slot];
-        const int ia = pr & 255, ib = pr >> 8;
-        R pa[3] = {sm.px[ia], sm.py[ia], sm.pz[ia]};
-        R pb[3] = {sm.px[ib], sm.py[ib], sm.pz[ib]};
-        const R ea = sm.e[ia], eb = sm.e[ib];
-        const R G[3] = {sm.G0[slot], sm.G1[slot], sm.G2[slot]};
-        R deps, margin;
-        // float64 bound for the mixed path: energies at load plus this visit's sums
-        auto exact = [&](R dv) -> double {
-          const double da = a.eps[gidx(ia)] + (double)sm.acc[ia];
-          const double db = a.eps[gidx(ib)] + (double)sm.acc[ib];
-          return fmin(da, db) + (double)dv;
-        };
-        const int dcs = fd_pair<P>(k, sm.ex[slot], sm.ey[slot], sm.ez[slot], sm.base[slot], G, sm.U[slot], pa,
-                                   pb, ea, eb, deps, margin, negative, exact);
-        if (dcs == 0) {
-          sm.px[ia] = pa[0]; sm.py[ia] = pa[1]; sm.pz[ia] = pa[2];
-          sm.px[ib] = pb[0]; sm.py[ib] = pb[1]; sm.pz[ib] = pb[2];
-          sm.e[ia] = ea + deps;
-          sm.e[ib] = eb + deps;
-          if constexpr (P::mixed) {
-            sm.acc[ia] += deps;
-            sm.acc[ib] += deps;
-          }
-          bad |= !isfinite(sm.e[ia]) || !isfinite(sm.e[ib]);
-        }
-        ++n_tot;
-        n_acc += dcs == 0;
-        n_rb += dcs == 1;
-        n_rm += dcs == 2;
-        if (recs) {
-          const unsigned long long s = atomicAdd(rec_count, 1ull);
-          if ((int64_t)s < rec_cap) {
-            sdpd_pair_rec rc;
-            rc.id_i = a.id[gidx(ia)];
-            rc.id_j = a.id[gidx(ib)];
-            rc.colour = colour;
-            rc.owner = (int32_t)o;
-            rc.decision = dcs;
-            rc.level = L;
-            rc.margin = (double)margin;
-            recs[s] = rc;
-          }
-        }
+        sm.pr[slot] = pr;
+        sm.ex[slot] = rx * inv_r;
+        sm.ey[slot] = ry * inv_r;
+        sm.ez[slot] = rz * inv_r;
+        sm.base[slot] = fm::div(kernel_F<KIND>(r2 * inv_r * inv_h, cF), a.rho[ga] * a.rho[gb]);
+        R G[3], U;
+        pair_randoms_fast(seed, sweep, (uint64_t)a.id[ga], (uint64_t)a.id[gb], G, &U);
+        sm.G0[slot] = G[0]; sm.G1[slot] = G[1]; sm.G2[slot] = G[2]; sm.U[slot] = U;
       }
       __syncwarp();
-      if (more) {
-        if ((int)off[L + 1] <= cend) {  // level L done
-          ++L;
-          more = L < nlev && (int)off[L] < cend;
-        } else {
-          more = false;  // level L continues in the next chunk
+      // the chunk's levels, or parts of them
+      bool more = cbeg < cend;
+      while (__any_sync(0xffffffffu, more)) {
+        int lb = 0, le = 0;
+        if (more) {
+          lb = max((int)off[L], cbeg);
+          le = min((int)off[L + 1], cend);
+        }
+        for (int t = lb + gl; t < le; t += kGroupLanes) {
+          const int slot = t - cbeg;
+          const uint16_t pr = sm.pr[slot];
+          const int ia = pr & 255, ib = pr >> 8;
+          R pa[3] = {sm.px[ia], sm.py[ia], sm.pz[ia]};
+          R pb[3] = {sm.px[ib], sm.py[ib], sm.pz[ib]};
+          const R ea = sm.e[ia], eb = sm.e[ib];
+          const R G[3] = {sm.G0[slot], sm.G1[slot], sm.G2[slot]};
+          R deps, margin;
+          // float64 bound for the mixed path: energies at load plus this visit's sums
+          auto exact = [&](R dv) -> double {
+            const double da = a.eps[gidx(ia)] + (double)sm.acc[ia];
+            const double db = a.eps[gidx(ib)] + (double)sm.acc[ib];
+            return fmin(da, db) + (double)dv;
+          };
+          const int dcs = fd_pair<P>(k, sm.ex[slot], sm.ey[slot], sm.ez[slot], sm.base[slot], G, sm.U[slot], pa,
+                                     pb, ea, eb, deps, margin, negative, exact);
+          if (dcs == 0) {
+            sm.px[ia] = pa[0]; sm.py[ia] = pa[1]; sm.pz[ia] = pa[2];
+            sm.px[ib] = pb[0]; sm.py[ib] = pb[1]; sm.pz[ib] = pb[2];
+            sm.e[ia] = ea + deps;
+            sm.e[ib] = eb + deps;
+            if constexpr (P::mixed) {
+              sm.acc[ia] += deps;
+              sm.acc[ib] += deps;
+            }
+            bad |= !isfinite(sm.e[ia]) || !isfinite(sm.e[ib]);
+          }
+          ++n_tot;
+          n_acc += dcs == 0;
+          n_rb += dcs == 1;
+          n_rm += dcs == 2;
+          if (recs) {
+            const unsigned long long s = atomicAdd(rec_count, 1ull);
+            if ((int64_t)s < rec_cap) {
+              sdpd_pair_rec rc;
+              rc.id_i = a.id[gidx(ia)];
+              rc.id_j = a.id[gidx(ib)];
+              rc.colour = colour;
+              rc.owner = (int32_t)o;
+              rc.decision = dcs;
+              rc.level = L;
+              rc.margin = (double)margin;
+              recs[s] = rc;
+            }
+          }
+        }
+        __syncwarp();
+        if (more) {
+          if ((int)off[L + 1] <= cend) {  // level L done
+            ++L;
+            more = L < nlev && (int)off[L] < cend;
+          } else {
+            more = false;  // level L continues in the next chunk
+          }
         }
       }
+      pos = cend;
+      __syncwarp();
     }
-    pos = cend;
-    __syncwarp();
+    for (int q = gl; q < nb; q += kGroupLanes) {
+      const int g = gidx(q);
+      a.px[g] = sm.px[q]; a.py[g] = sm.py[q]; a.pz[g] = sm.pz[q];
+      double e;
+      if constexpr (P::mixed) e = a.eps[g] + (double)sm.acc[q];  // one float64 update per visit
+      else e = sm.e[q];
+      a.eps[g] = e;
+      // pressure over rho^2 of the new energy, Eq. (pg-eos): pi = c_rho eps / (C_K m rho)
+      qp4[g].w = (R)e * pi_coef / a.rho[g];
+    }
+    __syncwarp();  // the group's shared memory is refilled by the next block
   }
-  const R pi_coef = (R)(c.c_rho / (c.C_K * c.m));
-  for (int q = gl; q < nb; q += kGroupLanes) {
-    const int g = gidx(q);
-    a.px[g] = sm.px[q]; a.py[g] = sm.py[q]; a.pz[g] = sm.pz[q];
-    double e;
-    if constexpr (P::mixed) e = a.eps[g] + (double)sm.acc[q];  // one float64 update per visit
-    else e = sm.e[q];
-    a.eps[g] = e;
-    // pressure over rho^2 of the new energy, Eq. (pg-eos): pi = c_rho eps / (C_K m rho)
-    qp4[g].w = (R)e * pi_coef / a.rho[g];
+  if (lane == 0) {
+    const unsigned total = gridDim.x * (unsigned)W;
+    __threadfence();  // this warp's last take from queue[0] is performed before it counts as done
+    if (atomicAdd(&queue[1], 1u) == total - 1u) {  // every warp has taken its last block
+      queue[0] = 0u;
+      queue[1] = 0u;
+    }
   }
   // counters
   for (int s = 16; s > 0; s >>= 1) {
@@ -472,6 +494,21 @@ static FDConst<R> fd_const(const Consts& c, double dt) {
   return k;
 }
 
+// Thread blocks of a colour kernel that the device holds at once (SMs x
+// blocks per SM, from the occupancy calculator; at least one), computed once
+// per kernel on the device current at the first launch.
+template <class P, int KIND, int OPW, int W>
+int fd_resident_blocks() {
+  static const int n = [] {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fd_colour<P, KIND, OPW, W>, W * 32, 0);
+    return std::max(1, sms) * std::max(1, per_sm);
+  }();
+  return n;
+}
+
 // A block schedule fits when its groups' shared memory stays within the 48 KB
 // a thread block may declare statically.
 template <class P, int OPW, int W>
@@ -490,11 +527,13 @@ void launch_colour(const Consts& c, const FDConst<typename P::R>& k, const Array
   } else {
     const int64_t nown = (int64_t)(c.nc[0] / 2) * (c.nc[1] / 2) * (c.nc[2] / 2);
     const int64_t per_block = (int64_t)W * OPW;
-    const unsigned gf = (unsigned)((nown + per_block - 1) / per_block);
+    const int64_t need = (nown + per_block - 1) / per_block;
+    const int64_t resident = (int64_t)fd_resident_blocks<P, KIND, OPW, W>();
+    const unsigned gf = (unsigned)std::max<int64_t>(1, std::min(need, resident));
     k_fd_colour<P, KIND, OPW, W><<<gf, W * 32, 0, s>>>(
         c, k, a, (typename P::V4*)w.qp4, w.cell_start, w.mrank, w.xmin[0], w.xmin[1], w.xmin[2], w.sched_hdr,
         w.sched_lvl, w.sched_pair, col, seed, w.sweep, w.counters, w.status, recs, w.pair_rec_count,
-        w.pair_rec_cap);
+        w.pair_rec_cap, w.fd_queue + 2 * col);
   }
 }
 
@@ -516,6 +555,22 @@ void launch_colours_kind(const Consts& c, const Workspace& w, int cur, double dt
       default: launch_colour<P, KIND, 1, 4>(c, k, a, w, col, seed, recs, s); break;
     }
   }
+}
+
+// Fills the resident-block counts of every block schedule ahead of time (a
+// host query, kept out of stream captures).
+template <class P>
+void fd_prepare() {
+  fd_resident_blocks<P, SDPD_KERNEL_LUCY, 2, 2>();
+  fd_resident_blocks<P, SDPD_KERNEL_LUCY, 2, 1>();
+  fd_resident_blocks<P, SDPD_KERNEL_LUCY, 1, 1>();
+  fd_resident_blocks<P, SDPD_KERNEL_LUCY, 1, 2>();
+  fd_resident_blocks<P, SDPD_KERNEL_LUCY, 1, 4>();
+  fd_resident_blocks<P, SDPD_KERNEL_CUBIC, 2, 2>();
+  fd_resident_blocks<P, SDPD_KERNEL_CUBIC, 2, 1>();
+  fd_resident_blocks<P, SDPD_KERNEL_CUBIC, 1, 1>();
+  fd_resident_blocks<P, SDPD_KERNEL_CUBIC, 1, 2>();
+  fd_resident_blocks<P, SDPD_KERNEL_CUBIC, 1, 4>();
 }
 
 template <class P>

@@ -5,6 +5,7 @@
 
 namespace sdpd {
 
+template void fd_prepare<Fp64>();
 template void launch_fd_colours<Fp64>(const Consts&, const Workspace&, int, double, uint64_t, int,
                                     cudaStream_t);
 

@@ -5,6 +5,7 @@
 
 namespace sdpd {
 
+template void fd_prepare<Mixed>();
 template void launch_fd_colours<Mixed>(const Consts&, const Workspace&, int, double, uint64_t, int,
                                     cudaStream_t);
 

@@ -291,6 +291,8 @@ struct Workspace {
   unsigned long long* counters;  // [4]: pairs, accept, reject bound, reject metropolis
   unsigned long long* sweep;     // sweep counter: the random-number step of the next sweep
   int* status;
+  unsigned* fd_queue;            // [8][2]: next block and finished warps of each colour launch;
+                                 // zero between launches
   sdpd_pair_rec* pair_recs;   // debug
   unsigned long long* pair_rec_count;
   int64_t pair_rec_cap;
@@ -331,6 +333,8 @@ void launch_force(const Consts& c, const Workspace& w, int cur, double half_dt, 
                   double* force_by_id, cudaStream_t s);
 template <class P>
 void launch_fd_schedule(const Consts& c, const Workspace& w, int cur, cudaStream_t s);
+template <class P>
+void fd_prepare();
 template <class P>
 void launch_fd_colours(const Consts& c, const Workspace& w, int cur, double dt, uint64_t seed, int record,
                        cudaStream_t s);

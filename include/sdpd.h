@@ -283,7 +283,9 @@ void sdpd_ensemble_destroy(sdpd_ens_t* e);
 typedef struct {
   int fd_variant;   /* blocks per warp x warps per thread block of the colour
                        launches: 0 (2 x 2), 1 (2 x 1), 2 (1 x 1), 3 (1 x 2),
-                       4 (2 x 4); -1 = the precision's default (0 mixed, 1 float64) */
+                       4 (1 x 4); -1 = the precision's default (0 mixed,
+                       1 float64).  Float64 handles take 1, 2 and 3 only (the
+                       others need more than 48 KB of shared memory) */
   int pair_threads; /* threads per block of the density and force passes:
                        32, 64 or 128; 0 = 128 */
 } sdpd_tuning;

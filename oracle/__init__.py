@@ -116,7 +116,8 @@ def lib():
             "orc_pair_randoms": (None, [C.c_uint64, C.c_uint64, C.c_uint64, C.c_uint64, _dp, _dp]),
             "orc_fd_pair": (C.c_int, [P, _dp, C.c_double, C.c_double, _dp, _dp, _dp, _dp,
                                       C.c_double, _dp, C.c_double, _dp, C.POINTER(C.c_int)]),
-            "orc_pair_owner": (C.c_int, [P, _i32p, _i32p, _i32p]),
+            "orc_pair_owner": (C.c_int, [P, _i32p, _i32p, C.c_int64, _i32p]),
+            "orc_owner_bits": (C.c_uint, [C.c_int64]),
             "orc_fd_sweep": (C.c_int, [P, _dp, _dp, _dp, C.c_double, C.c_uint64, C.c_uint64,
                                        C.POINTER(FDStats), C.c_void_p, C.c_int64]),
             "orc_run": (C.c_int, [P, _dp, _dp, _dp, C.c_double, C.c_int64, C.c_int, C.c_int,
@@ -317,11 +318,19 @@ def fd_pair(P: Params, r, rho_i, rho_j, p_i, p_j, eps_i, eps_j, dt, G, U):
     return d, margin.value, neg.value, pi, pj, ei.value, ej.value
 
 
-def pair_owner(P: Params, ca, cb):
+def owner_bits(pid) -> int:
+    """The three bits of a particle id that choose the owner block along axes
+    where a pair's two cells coincide (bit k for axis k)."""
+    return int(lib().orc_owner_bits(int(pid)))
+
+
+def pair_owner(P: Params, ca, cb, id_lo=0):
+    """Owner cell of a pair whose lower-id particle (id_lo) sits in cell ca
+    and whose other particle sits in cell cb."""
     a = np.ascontiguousarray(ca, dtype=np.int32)
     b = np.ascontiguousarray(cb, dtype=np.int32)
     o = np.empty(3, dtype=np.int32)
-    s = lib().orc_pair_owner(C.byref(P), a.ctypes.data_as(_i32p), b.ctypes.data_as(_i32p),
+    s = lib().orc_pair_owner(C.byref(P), a.ctypes.data_as(_i32p), b.ctypes.data_as(_i32p), int(id_lo),
                              o.ctypes.data_as(_i32p))
     return s, o
 

@@ -34,7 +34,10 @@
  *      then, inside the owner's 2x2x2 block of cells, pairs by
  *      (rank(j) - rank(i), rank(i)), where rank(x) is the position of x's id
  *      among the ids of all particles in the block's 8 cells and i is the
- *      lower id.  Colour and owner are defined in orc_pair_owner below.
+ *      lower id.  Colour and owner are defined in orc_pair_owner below: along
+ *      an axis where the two cells coincide, three bits drawn from the lower
+ *      id choose which of the two blocks holding that coordinate owns the
+ *      pair, which spreads a particle's pairs over the colours.
  *  R13 the energy bound of Eq. (energy-bound) rejects iff the smaller new
  *      internal energy is <= 0; the Metropolis step rejects iff U > exp(a).
  *      The internal-energy change is -1/2 of the change of the pair's kinetic
@@ -602,18 +605,36 @@ int orc_fd_pair(const orc_params* P, const double r[3], double rho_i, double rho
 /* Pair colouring of the sequential sweep (reading R12)                      */
 /* ------------------------------------------------------------------------ */
 
-/* The owner cell of a pair whose particles sit in cells a and b: along each
- * axis, a and b are equal or adjacent (the cell side is >= h); the owner
- * takes the lower of the two in the periodic sense.  Both cells then lie in
+/* Three bits of a particle id: a multiply / xor-shift mix of the id as a
+ * 32-bit unsigned integer, top three bits (bit k for axis k). */
+unsigned orc_owner_bits(int64_t id) {
+  uint32_t x = (uint32_t)id;
+  x *= 2654435761u;
+  x ^= x >> 15;
+  x *= 2246822519u;
+  x ^= x >> 13;
+  x *= 3266489917u;
+  x ^= x >> 16;
+  return x >> 29;
+}
+
+/* The owner cell of a pair whose lower-id particle (id_lo) sits in cell a
+ * and whose other particle sits in cell b.  Along each axis a and b are equal
+ * or adjacent (the cell side is >= h).  Where they are adjacent the owner
+ * takes the lower of the two in the periodic sense.  Where they are equal
+ * the pair lies in the two blocks starting at a_k and a_k - 1; bit k of
+ * orc_owner_bits(id_lo) picks a_k (0) or a_k - 1 (1).  Both cells then lie in
  * the 2x2x2 block of cells starting at the owner.  The pair's colour is the
  * parity pattern of the owner, (ox & 1) | (oy & 1) << 1 | (oz & 1) << 2.
  * Owners of one colour have disjoint blocks when every n_c is even and >= 4,
  * so the pairs of one colour touch disjoint particles. */
-int orc_pair_owner(const orc_params* P, const int32_t ca[3], const int32_t cb[3], int32_t o[3]) {
+int orc_pair_owner(const orc_params* P, const int32_t ca[3], const int32_t cb[3], int64_t id_lo, int32_t o[3]) {
+  const unsigned bits = orc_owner_bits(id_lo);
   for (int k = 0; k < 3; ++k) {
     int n = P->n_c[k];
     int diff = ((cb[k] - ca[k]) % n + n) % n;
-    if (diff == 0 || diff == 1) o[k] = ca[k];
+    if (diff == 0) o[k] = (ca[k] - (int)((bits >> k) & 1u) + n) % n;
+    else if (diff == 1) o[k] = ca[k];
     else if (diff == n - 1) o[k] = cb[k];
     else return ORC_ERR_NOT_ADJACENT;
   }
@@ -720,7 +741,7 @@ int orc_enumerate_pairs(const orc_params* P, const double* q, orc_pair** out, in
       if (!(r2 < h2 && r2 > 0.0)) continue;
       int32_t cj[3], o[3];
       for (int k = 0; k < 3; ++k) cj[k] = orc_cell_1d(P, k, q[3 * j + k]);
-      if (orc_pair_owner(P, ci, cj, o) != ORC_OK) {
+      if (orc_pair_owner(P, ci, cj, i, o) != ORC_OK) {  /* i < j: i is the lower id */
 #pragma omp atomic write
         err = ORC_ERR_NOT_ADJACENT;
         o[0] = o[1] = o[2] = 0;

@@ -401,10 +401,47 @@ def test_colouring_is_conflict_free(n, n_c):
 
 def test_owner_rule():
     P = small_cfg(n=12).params()  # n_c = 4
-    s, o = O.pair_owner(P, [0, 3, 1], [3, 0, 2])
-    assert s == O.OK and list(o) == [3, 3, 1]
+    # adjacent on every axis: the lower cell per axis (periodically), whatever the ids
+    for pid in (0, 1, 12345):
+        s, o = O.pair_owner(P, [0, 3, 1], [3, 0, 2], pid)
+        assert s == O.OK and list(o) == [3, 3, 1]
     s, o = O.pair_owner(P, [0, 0, 0], [2, 0, 0])
     assert s == O.ERR_NOT_ADJACENT
+    # coinciding on an axis: the block starting at the coordinate or one cell
+    # below, as the lower id's bit for that axis says
+    for pid in range(64):
+        bits = O.owner_bits(pid)
+        s, o = O.pair_owner(P, [2, 1, 0], [2, 2, 3], pid)  # x equal, y +1, z -1 periodically
+        assert s == O.OK and list(o) == [(2 - (bits & 1)) % 4, 1, 3]
+        s, o = O.pair_owner(P, [0, 3, 1], [0, 3, 1], pid)  # the same cell: any of its 8 blocks
+        assert list(o) == [(0 - (bits & 1)) % 4, (3 - ((bits >> 1) & 1)) % 4, (1 - ((bits >> 2) & 1)) % 4]
+    # exhaustively: every adjacent pair of cells, for several ids, is owned by
+    # a block that contains both cells
+    rng = np.random.default_rng(0)
+    ids = rng.integers(0, 2**31 - 1, size=6)
+    offs = [(x, y, z) for x in (-1, 0, 1) for y in (-1, 0, 1) for z in (-1, 0, 1)]
+    for a in np.ndindex(4, 4, 4):
+        for off in offs:
+            b = [(a[k] + off[k]) % 4 for k in range(3)]
+            for pid in ids:
+                s, o = O.pair_owner(P, list(a), b, int(pid))
+                assert s == O.OK
+                for c in (a, b):
+                    assert all((c[k] - o[k]) % 4 in (0, 1) for k in range(3))
+
+
+def test_owner_bits_spread_over_the_eight_blocks():
+    """The owner bits of consecutive ids (lattice neighbours get nearby ids)
+    hit all eight patterns evenly, so a particle's same-cell pairs spread over
+    the eight colours."""
+    n = 1 << 15
+    bits = np.array([O.owner_bits(k) for k in range(n)])
+    assert bits.min() == 0 and bits.max() == 7
+    counts = np.bincount(bits, minlength=8)
+    assert np.abs(counts - n / 8).max() < 5 * np.sqrt(n / 8)
+    # no strong correlation between an id and the next one
+    same = np.mean(bits[1:] == bits[:-1])
+    assert abs(same - 1 / 8) < 0.02
 
 
 # --------------------------------------------------------------------------

@@ -2,13 +2,19 @@
 // made data-parallel by a conflict-free pair colouring.
 //
 // Colouring.  A pair whose particles sit in cells a and b (equal or adjacent
-// along each axis, since the cell side is >= h) is owned by the cell o that is
-// the lower of a and b along each axis (periodically); both cells then lie in
-// the 2x2x2 block o + {0,1}^3.  With local cell codes delta in 0..7 (bit k =
-// offset along axis k) a pair of cells (dA, dB) of the block is owned by o iff
-// dA & dB == 0.  The colour of o is its parity pattern; blocks of one colour
-// are disjoint when every cell count is even, so the 8 colours are swept one
-// after the other and the blocks of a colour in parallel.
+// along each axis, since the cell side is >= h) is owned by a cell o such that
+// both cells lie in the 2x2x2 block o + {0,1}^3: along an axis where a and b
+// are adjacent o takes the lower of the two (periodically); along an axis
+// where they coincide either block holding the coordinate would do, and bit
+// k of owner_bits(lower id) picks the one where the shared cell is the lower
+// (0) or upper (1) cell of the block.  With local cell codes dA, dB in 0..7
+// (bit k = offset along axis k, A the lower id) the block owns the pair iff
+// dA and dB agree with the owner bits wherever they coincide.  Spreading a
+// particle's pairs over the colours this way roughly halves the longest
+// chain of pairs in a block compared with always taking the lower block.
+// The colour of o is its parity pattern; blocks of one colour are disjoint
+// when every cell count is even, so the 8 colours are swept one after the
+// other and the blocks of a colour in parallel.
 //
 // Order inside a block.  Pairs go by (rank(j) - rank(i), rank(i)), rank = the
 // position of the id among the block's particles, i the lower id.  Any
@@ -41,13 +47,20 @@ struct SchedSmem {
                                         // that lanes reading consecutive rows hit distinct banks
   int32_t rowoff[kMaxBlock + 1];
   int32_t cstart[8], cbase[8], ccnt[8];  // the block's cells: first storage index, offset in the block, count
+  // the partner segments of the 32 particles of the current chunk, one row
+  // per lane: entries before segment s (cum, 0xff past the last), and the
+  // segment's first entry and partner cell (first | cell << 8)
+  uint8_t seg_cum[32][8];
+  uint16_t seg_pk[32][8];
 };
 
-// The owned pairs are read from the neighbour lists of the density pass: a
-// particle in block cell dA pairs with owned partners only in the cells
-// dB with dA & dB == 0, whose entries sit in known stencil groups of its
-// list row.  Each owned pair is met from both of its particles and kept from
-// the one with the lower rank.
+// The owned pairs are read from the neighbour lists of the density pass: as
+// the lower id of a pair, a particle in block cell dA has owned partners only
+// in the cells dB that agree with dA exactly where dA agrees with its owner
+// bits (and differ from dA elsewhere), whose entries sit in known stencil
+// groups of its list row; entries with a lower-ranked partner belong to the
+// partner's side.  Over the 8 blocks holding a particle these groups cover
+// its list once.
 template <class P>
 __global__ void __launch_bounds__(kSchedWarps * 32)
     k_sched_enum(Consts c, Arrays<P> a, const int32_t* __restrict__ cell_start, const int32_t* __restrict__ mrank,
@@ -133,11 +146,12 @@ __global__ void __launch_bounds__(kSchedWarps * 32)
     sm.perm[r] = (uint8_t)k;
   }
   __syncwarp();
-  // Owned entries, spread over the warp: for a chunk of 32 particles (one per
-  // lane) and the s-th partner cell of each, a warp prefix sum of the entry
-  // counts maps the chunk's entries to lanes, so that the lanes load
-  // consecutive entries of a row together and share the work evenly (an
-  // owner-cell particle has up to ~80 owned entries, a far-corner one ~3).
+  // Owned entries, spread over the warp: each lane lists the partner
+  // segments of one particle of a chunk of 32, a warp prefix sum over the
+  // lanes' entry totals maps the chunk's entries to lanes, and each entry
+  // finds its segment in the owner lane's row, so that the lanes load
+  // consecutive entries of a row together and share the work evenly (a
+  // particle has from one to eight partner segments, ~3 to ~80 entries).
   for (int k0 = 0; k0 < nb; k0 += 32) {
     const int k = k0 + lane;
     const bool live = k < nb;
@@ -147,71 +161,87 @@ __global__ void __launch_bounds__(kSchedWarps * 32)
       g = sm.cstart[dA] + (k - sm.cbase[dA]);
       rk = sm.rank[k];
     }
-    const uint8_t* off = nbr_off + (int64_t)g * 28;
-    const int free = 7 & ~dA;
-    int dB = free;
-    bool more = live;
-    for (int sgi = 0; sgi < 8; ++sgi) {  // partner cells dB: subsets of the complement of dA
-      int e0 = 0, n = 0, myB = 0;
-      if (more) {
+    // Partner cells of a pair this block owns with k as the lower id: along
+    // an axis where k's block-cell bit equals k's owner bit the partner may
+    // share the coordinate or sit across (free axes); elsewhere it must sit
+    // across.
+    const int hb = live ? (int)owner_bits(sm.id[k]) : 0;
+    const int free = 7 & ~(dA ^ hb);
+    const int fixed = 7 & ~dA & ~free;
+    int tot = 0, ns = 0;
+    if (live) {
+      const uint8_t* off = nbr_off + (int64_t)g * 28;
+      int sub = free;
+      for (;;) {  // partner cells dB = fixed | (subsets of free)
+        const int dB = fixed | sub;
         const int sx = ((dB & 1) - (dA & 1)) + 1, sy = (((dB >> 1) & 1) - ((dA >> 1) & 1)) + 1,
                   sz = (((dB >> 2) & 1) - ((dA >> 2) & 1)) + 1;
         const int st = sx + 3 * sy + 9 * sz;
-        e0 = off[st];
-        n = off[st + 1] - e0;
-        myB = dB;
-        if (dB == 0) more = false;
-        else dB = (dB - 1) & free;
-      }
-      int incl = n;
-#pragma unroll
-      for (int sh = 1; sh < 32; sh <<= 1) {
-        const int t = __shfl_up_sync(0xffffffffu, incl, sh);
-        if (lane >= sh) incl += t;
-      }
-      const int total = __shfl_sync(0xffffffffu, incl, 31);
-      if (total == 0) {
-        if (!__any_sync(0xffffffffu, more)) break;
-        continue;
-      }
-      const int excl = incl - n;
-      const int packed = (myB << 8) | e0;  // partner cell and first entry of this lane's segment
-      // kDeep rounds of 32 entries per iteration, all list loads issued
-      // before any is used
-      constexpr int kDeep = 4;
-      for (int t0 = 0; t0 < total; t0 += 32 * kDeep) {
-        int o_pk[kDeep], o_rk[kDeep], o_q[kDeep];
-        uint32_t ent[kDeep];
-#pragma unroll
-        for (int h = 0; h < kDeep; ++h) {
-          const int t = t0 + 32 * h + lane;
-          // owner lane: the number of lanes whose inclusive count is <= t
-          int pos = 0;
-#pragma unroll
-          for (int step = 16; step > 0; step >>= 1) {
-            const int v = __shfl_sync(0xffffffffu, incl, pos + step - 1);
-            if (v <= t) pos += step;
-          }
-          const int src = min(pos, 31);
-          o_pk[h] = __shfl_sync(0xffffffffu, packed, src);
-          const int o_ex = __shfl_sync(0xffffffffu, excl, src);
-          const int o_g = __shfl_sync(0xffffffffu, g, src);
-          o_rk[h] = __shfl_sync(0xffffffffu, rk, src);
-          o_q[h] = t < total ? (o_pk[h] & 255) + (t - o_ex) : -1;
-          ent[h] = o_q[h] >= 0 ? __ldg(&nlist[(int64_t)o_g * c.nbr_cap + o_q[h]]) : 0u;
+        const int e0 = off[st], n = off[st + 1] - e0;
+        if (n > 0) {
+          sm.seg_cum[lane][ns] = (uint8_t)tot;
+          sm.seg_pk[lane][ns] = (uint16_t)(e0 | (dB << 8));
+          tot += n;
+          ++ns;
         }
-#pragma unroll
-        for (int h = 0; h < kDeep; ++h) {
-          if (o_q[h] >= 0) {
-            const int oB = o_pk[h] >> 8;
-            const int j = (int)(ent[h] >> 6);
-            const int rj = sm.rank[sm.cbase[oB] + (j - sm.cstart[oB])];
-            if (o_rk[h] < rj) atomicOr(&sm.bits[o_rk[h] >> 5][rj - o_rk[h]], 1u << (o_rk[h] & 31));
-          }
-        }
+        if (sub == 0) break;
+        sub = (sub - 1) & free;
       }
-      if (!__any_sync(0xffffffffu, more)) break;
     }
+    for (int t = ns; t < 8; ++t) sm.seg_cum[lane][t] = 0xff;
+    __syncwarp();
+    int incl = tot;
+#pragma unroll
+    for (int sh = 1; sh < 32; sh <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, sh);
+      if (lane >= sh) incl += t;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    const int excl = incl - tot;
+    // kDeep rounds of 32 entries per iteration, all list loads issued before
+    // any is used
+    constexpr int kDeep = 4;
+    for (int t0 = 0; t0 < total; t0 += 32 * kDeep) {
+      int o_rk[kDeep], o_q[kDeep], o_b[kDeep];
+      uint32_t ent[kDeep];
+#pragma unroll
+      for (int h = 0; h < kDeep; ++h) {
+        const int t = t0 + 32 * h + lane;
+        // owner lane: the number of lanes whose inclusive count is <= t
+        int pos = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+          const int v = __shfl_sync(0xffffffffu, incl, pos + step - 1);
+          if (v <= t) pos += step;
+        }
+        const int src = min(pos, 31);
+        const int o_ex = __shfl_sync(0xffffffffu, excl, src);
+        const int o_g = __shfl_sync(0xffffffffu, g, src);
+        o_rk[h] = __shfl_sync(0xffffffffu, rk, src);
+        o_q[h] = -1;
+        o_b[h] = 0;
+        if (t < total) {
+          const int u = t - o_ex;  // entry of the owner lane's particle
+          int sg = 0;
+#pragma unroll
+          for (int s2 = 1; s2 < 8; ++s2) sg += (int)sm.seg_cum[src][s2] <= u;
+          const int pk = sm.seg_pk[src][sg];
+          o_q[h] = (pk & 255) + (u - sm.seg_cum[src][sg]);
+          o_b[h] = pk >> 8;
+        }
+        ent[h] = o_q[h] >= 0 ? __ldg(&nlist[(int64_t)o_g * c.nbr_cap + o_q[h]]) : 0u;
+      }
+#pragma unroll
+      for (int h = 0; h < kDeep; ++h) {
+        if (o_q[h] >= 0) {
+          const int oB = o_b[h];
+          const int j = (int)(ent[h] >> 6);
+          const int rj = sm.rank[sm.cbase[oB] + (j - sm.cstart[oB])];
+          if (o_rk[h] < rj) atomicOr(&sm.bits[o_rk[h] >> 5][rj - o_rk[h]], 1u << (o_rk[h] & 31));
+        }
+      }
+    }
+    __syncwarp();  // the segment rows are refilled by the next chunk
   }
   __syncwarp();
   // exclusive scan of the row populations, 32 consecutive rows at a time

@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--replicas", type=int, default=256)
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default launch shapes instead of timing the candidates first")
+    ap.add_argument("--shapes", default=None,
+                    help="fixed launch shapes fd_variant/pair_threads (e.g. 2/32) instead of the autotuner")
     return ap.parse_args()
 
 
@@ -205,15 +207,20 @@ FLOPS_PER_VISIT = {"density_eos": 18.0, "kick1_drift_bin": 24.0, "kick2": 24.0,
 FP64_NOMINAL_TFLOPS = 1.25  # GB300 float64, nominal
 # DRAM traffic of one colour launch of the mixed-precision sweep, per
 # particle: dram__bytes_read.sum + dram__bytes_write.sum of one launch at
-# N = 96^3 (49.28 MB + 1.08 MB), divided by the particles every colour
+# N = 96^3 (49.36 MB + 0.30 MB), divided by the particles every colour
 # launch visits once; a launch's traffic scales with N
-FD_COLOUR_DRAM_BYTES_PER_PARTICLE = (49.280512e6 + 1.082368e6) / 96 ** 3
+FD_COLOUR_DRAM_BYTES_PER_PARTICLE = (49.359104e6 + 0.300800e6) / 96 ** 3
 FLOPS_PER_PAIR_UPDATE = {"ems": 210.0, "ams": 150.0, "ssa": 140.0}
 
 
 def autotune(args, s, seed):
     """The library's autotuner on the loaded state (it restores the state):
-    the chosen launch shapes and their time per step, or the defaults."""
+    the chosen launch shapes and their time per step, or the defaults, or
+    the shapes given on the command line."""
+    if args.shapes:
+        v, t = (int(x) for x in args.shapes.split("/"))
+        s.set_tuning(v, t)
+        return {"autotuned": False, **s.tuning}
     if args.no_autotune:
         return {"autotuned": False, **s.tuning}
     t, ms = s.autotune(args.dt, steps=2, seed=seed)
@@ -336,7 +343,7 @@ def run_fp64_form(args, w, q, p, e, scheme, stream, world, mixed_value):
         s.set_state(q, p, e)
         s.step(args.dt, 1, seed=77)
         tuning = None
-        if not args.no_autotune:
+        if not args.no_autotune and not args.shapes:
             t, _ = s.autotune(args.dt, steps=1, seed=77)
             tuning = t
         s.sync()
@@ -398,7 +405,7 @@ def run_ensemble(args, rank, world, local_rank):
     ens.step(args.dt, 2 * max(2, args.warmup), seeds)  # capture + warm-up
     torch.cuda.synchronize()
     tuning = {"autotuned": False}
-    if not args.no_autotune:
+    if not args.no_autotune and not args.shapes:
         # the default shapes first, then every member tuned alone, then the
         # graph recaptured with the chosen shapes
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

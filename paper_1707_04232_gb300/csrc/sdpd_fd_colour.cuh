@@ -86,25 +86,32 @@ __device__ __forceinline__ void pair_randoms_fast(uint64_t seed, uint64_t sweep,
 // zt^2 = sigma^2 (1 - alpha^2) / (m gamma) = 4 kB Ti Tj / ((Ti+Tj) m (1-d)) (1 - alpha^2)
 // (kappa cancels).  Ideal gas: T = eps / C_K and C = C_K, so
 // d = kB Ti Tj / (Ti + Tj)^2 * 2 / C_K.
+//
+// One expm1 per direction gives both alpha = 1 + expm1(x) and
+// 1 - alpha^2 = -expm1(x) (2 + expm1(x)), and one reciprocal of Ti + Tj
+// serves both quotients: the float64 dependency chain of a pair update is
+// what bounds the sweep when a colour has few blocks.
 template <class R>
 __device__ __forceinline__ void pair_coeffs(const FDConst<R>& k, R kpar, R kperp, R ei, R ej, R& apar,
                                             R& aperp, R& zpar, R& zperp, R& xpar, R& xperp) {
   const R Ti = ei * k.inv_C_K, Tj = ej * k.inv_C_K;
-  const R sT = Ti + Tj;
-  const R hT = fm::div(Ti * Tj, sT);
-  const R omd = R(1) - fm::div(k.kB * hT * k.two_over_CK, sT);
+  const R isT = fm::div(R(1), Ti + Tj);
+  const R hT = Ti * Tj * isT;
+  const R omd = R(1) - k.kB * k.two_over_CK * hT * isT;
   xpar = R(-2) * kpar * omd * k.dt_over_m;  // log alpha per direction
   xperp = R(-2) * kperp * omd * k.dt_over_m;
-  apar = fm::exp(xpar);
-  aperp = fm::exp(xperp);
+  const R mpar = fm::expm1(xpar), mperp = fm::expm1(xperp);
+  apar = R(1) + mpar;
+  aperp = R(1) + mperp;
   const R s = fm::div(k.four_kB_over_m * hT, omd);
-  zpar = fm::sqrt(s * -fm::expm1(R(2) * xpar));
-  zperp = fm::sqrt(s * -fm::expm1(R(2) * xperp));
+  zpar = fm::sqrt(s * (-mpar * (R(2) + mpar)));
+  zperp = fm::sqrt(s * (-mperp * (R(2) + mperp)));
 }
 
 // State-dependent part of one pair update on (p_i, p_j) with internal
 // energies (ei, ej) in the arithmetic type R, given the pair's unit vector
-// e = r_ij / r_ij, base = F(r_ij) / (rho_i rho_j) and its random numbers.
+// e = r_ij / r_ij, base = F(r_ij) / (rho_i rho_j), its Gaussians G and the
+// logarithm lnU of its uniform.
 // Returns 0 accept, 1 energy-bound reject, 2 Metropolis reject; deps receives
 // the energy change shared by the two particles (applied by the caller on
 // acceptance).  exact_bound: float64 re-check of the energy bound for the
@@ -113,7 +120,7 @@ __device__ __forceinline__ void pair_coeffs(const FDConst<R>& k, R kpar, R kperp
 template <class P, class ExactBound>
 __device__ __forceinline__ int fd_pair(const FDConst<typename P::R>& k, typename P::R ex, typename P::R ey,
                                        typename P::R ez, typename P::R base, const typename P::R G[3],
-                                       typename P::R U, typename P::R* pi, typename P::R* pj,
+                                       typename P::R lnU, typename P::R* pi, typename P::R* pj,
                                        typename P::R ei, typename P::R ej, typename P::R& deps,
                                        typename P::R& margin, bool& negative, ExactBound exact_bound) {
   using R = typename P::R;
@@ -167,6 +174,9 @@ __device__ __forceinline__ int fd_pair(const FDConst<typename P::R>& k, typename
     // with the coefficients at the proposed energies
     R bpar, bperp, ypar, yperp, xrpar, xrperp;
     pair_coeffs(k, kpar, kperp, ei + deps, ej + deps, bpar, bperp, ypar, yperp, xrpar, xrperp);
+    // one reciprocal for both directions of the reverse move's noise scale
+    const R ryy = fm::div(R(1), ypar * yperp);
+    const R ipar = yperp * ryy, ip = ypar * ryy;  // 1 / zt'_par, 1 / zt'_perp
     R quad;
     if constexpr (P::mixed) {
       // reverse noise of the proposal v' = A v + B G:
@@ -175,8 +185,7 @@ __device__ __forceinline__ int fd_pair(const FDConst<typename P::R>& k, typename
       // float32 the literal v - A' v' loses its digits to cancellation when
       // zt -> 0 (pairs near the cut-off)
       const R cpar_r = -fm::expm1(xfpar + xrpar), cperp_r = -fm::expm1(xfperp + xrperp);
-      const R qpar = fm::div(cpar_r * vpar - bpar * zpar * gpar, ypar);
-      const R ip = fm::div(R(1), yperp);
+      const R qpar = (cpar_r * vpar - bpar * zpar * gpar) * ipar;
       const R qx = (cperp_r * (vx - vpar * ex) - bperp * zperp * (G[0] - gpar * ex)) * ip;
       const R qy = (cperp_r * (vy - vpar * ey) - bperp * zperp * (G[1] - gpar * ey)) * ip;
       const R qz = (cperp_r * (vz - vpar * ez) - bperp * zperp * (G[2] - gpar * ez)) * ip;
@@ -187,20 +196,19 @@ __device__ __forceinline__ int fd_pair(const FDConst<typename P::R>& k, typename
       const R cb = (bpar - bperp) * wpar;
       const R bx = vx - (bperp * wx + cb * ex), by = vy - (bperp * wy + cb * ey), bz = vz - (bperp * wz + cb * ez);
       const R spar = ex * bx + ey * by + ez * bz;
-      const R ip = fm::div(R(1), yperp);
-      const R cq = (fm::div(R(1), ypar) - ip) * spar;
+      const R cq = (ipar - ip) * spar;
       const R qx = bx * ip + cq * ex, qy = by * ip + cq * ey, qz = bz * ip + cq * ez;
       quad = qx * qx + qy * qy + qz * qz;
     }
     const R g2 = G[0] * G[0] + G[1] * G[1] + G[2] * G[2];
     // log|B(v)| - log|B(v')| with |B| = zt_par zt_perp^2
-    const R ldet = fm::log(fm::div(zpar * zperp * zperp, ypar * yperp * yperp));
+    const R ldet = fm::log(zpar * zperp * zperp * (ipar * ip * ip));
     // (S(eps') - S(eps))/kB - (log T(eps') - log T(eps)) = (C_K/kB - 1) log(eps'/eps)
     // summed over the two particles: log1p(x) + log1p(y) = log1p(x + y + x y)
-    const R xi = fm::div(deps, ei), xj = fm::div(deps, ej);
-    const R ent = k.CKm1 * fm::log1p(xi + xj + xi * xj);
+    // with x = deps/ei, y = deps/ej, i.e. deps (ei + ej + deps) / (ei ej)
+    const R ent = k.CKm1 * fm::log1p(fm::div(deps * (ei + ej + deps), ei * ej));
     const R a = R(0.5) * (g2 - quad) + ldet + ent;
-    const R mg = a - fm::log(U);
+    const R mg = a - lnU;
     margin = mg;
     if (mg < R(0)) decision = 2;  // U > exp(a)
   }
@@ -242,7 +250,7 @@ struct FdSmem {
   R acc[kMaxBlock];  // mixed path: float32 sum of this visit's energy changes
   int32_t cst[8], cbs[8];  // the block's cells: first storage index, offset in the block
   // staged pair data of the current chunk
-  R G0[kChunk], G1[kChunk], G2[kChunk], U[kChunk];
+  R G0[kChunk], G1[kChunk], G2[kChunk], lnU[kChunk];
   R ex[kChunk], ey[kChunk], ez[kChunk], base[kChunk];
   uint16_t pr[kChunk];
   uint16_t off[kMaxLevels + 1];  // level offsets of the block's pair list
@@ -363,7 +371,8 @@ __global__ void __launch_bounds__(W * 32, fd_min_blocks<P, W>())
         sm.base[slot] = fm::div(kernel_F<KIND>(r2 * inv_r * inv_h, cF), a.rho[ga] * a.rho[gb]);
         R G[3], U;
         pair_randoms_fast(seed, sweep, (uint64_t)a.id[ga], (uint64_t)a.id[gb], G, &U);
-        sm.G0[slot] = G[0]; sm.G1[slot] = G[1]; sm.G2[slot] = G[2]; sm.U[slot] = U;
+        sm.G0[slot] = G[0]; sm.G1[slot] = G[1]; sm.G2[slot] = G[2];
+        sm.lnU[slot] = k.scheme == SDPD_SCHEME_EMS ? fm::log(U) : U;  // off the pairs' dependency chain
       }
       __syncwarp();
       // the chunk's levels, or parts of them
@@ -389,7 +398,7 @@ __global__ void __launch_bounds__(W * 32, fd_min_blocks<P, W>())
             const double db = a.eps[gidx(ib)] + (double)sm.acc[ib];
             return fmin(da, db) + (double)dv;
           };
-          const int dcs = fd_pair<P>(k, sm.ex[slot], sm.ey[slot], sm.ez[slot], sm.base[slot], G, sm.U[slot], pa,
+          const int dcs = fd_pair<P>(k, sm.ex[slot], sm.ey[slot], sm.ez[slot], sm.base[slot], G, sm.lnU[slot], pa,
                                      pb, ea, eb, deps, margin, negative, exact);
           if (dcs == 0) {
             sm.px[ia] = pa[0]; sm.py[ia] = pa[1]; sm.pz[ia] = pa[2];

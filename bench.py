@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--adj-K", type=float, default=100.0)
     ap.add_argument("--adj-steps", type=int, default=100, help="adjoint workload: Verlet steps per gradient")
     ap.add_argument("--adj-every", type=int, default=10, help="adjoint workload: checkpoint interval")
+    ap.add_argument("--adj-sweep64", action="store_true",
+                    help="adjoint workload: float64 pair arithmetic in the recorded sweeps (default float32)")
     ap.add_argument("--replicas", type=int, default=256)
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default launch shapes instead of timing the candidates first")
@@ -505,10 +507,11 @@ def adjoint_cpu_sample(args):
 def run_adjoint(args, rank, world, local_rank):
     """One bench step = one gradient of the virial pressure after
     args.adj_steps steps (float64 Velocity Verlet, then the exact
-    Metropolised sweep with its increments frozen; checkpoint every
+    Metropolised sweep with its increments frozen, the sweep's pair
+    arithmetic in float32 unless --adj-sweep64; checkpoint every
     args.adj_every steps) with respect to (q0, p0, eps0, h, c_rho, C_K):
     set_state from device-resident inputs, the recorded forward run, the
-    virial pressure and its gradient, the reverse pass."""
+    virial pressure and its gradient, the reverse pass (float64)."""
     import torch
     from paper_1707_04232_gb300 import sdpd
 
@@ -522,7 +525,7 @@ def run_adjoint(args, rank, world, local_rank):
     with torch.cuda.stream(stream):
         fma64 = sdpd.sdpd_fma_peak(sdpd.FP64, stream.cuda_stream)
         s = sdpd.SDPD(w.N, w.L, m=w.m, h=w.h, K=w.K, precision=sdpd.FP64, scheme=sdpd.SCHEME_EMS,
-                      stream=stream)
+                      sweep_f32=not args.adj_sweep64, stream=stream)
         qd, pd, ed = (torch.as_tensor(a, device="cuda") for a in (q, p, e))
 
         s.set_state(qd, pd, ed)
@@ -583,10 +586,17 @@ def run_adjoint(args, rank, world, local_rank):
         units = w.N * nbr_mean
         flops = FLOPS_PER_VISIT[top] * units
     ach = flops / per_launch_s / 1e12
-    roof = {"kernel": top, "bound": "alu", "achieved": ach, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-            "frac": ach / FP64_NOMINAL_TFLOPS, "traffic": None,
-            "peak_note": "float64 nominal of GB300 (recipe); measured float64 FMA rate %.3f TFLOP/s "
-                         "(sdpd_fma_peak), frac of measured %.3f" % (fma64 / 1e12, ach / (fma64 / 1e12)),
+    if top == "fd_colours" and not args.adj_sweep64:  # float32 pair arithmetic
+        sm_max = (clk or {}).get("sm_max_mhz") or NOMINAL_SM_MHZ
+        peak = SMS * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+        note = ("FP32 FMA peak = 152 SMs x 128 lanes x 2 x %.0f MHz (recipe unit counts, sampled max "
+                "clock); the sweep's pair arithmetic is float32" % sm_max)
+    else:
+        peak = FP64_NOMINAL_TFLOPS
+        note = ("float64 nominal of GB300 (recipe); measured float64 FMA rate %.3f TFLOP/s "
+                "(sdpd_fma_peak), frac of measured %.3f" % (fma64 / 1e12, ach / (fma64 / 1e12)))
+    roof = {"kernel": top, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+            "frac": ach / peak, "traffic": None, "peak_note": note,
             "per_launch_ms": per_launch_s * 1e3,
             ("pair_updates_per_launch" if top == "fd_colours" else "visits_per_launch"): units}
     # end to end: host inputs in, host gradients out
@@ -609,11 +619,13 @@ def run_adjoint(args, rank, world, local_rank):
         "metric": "gradient particle-steps/s (virial pressure after %d steps, EMS sweeps frozen, reverse mode)" % ns,
         "value": value, "unit": UNIT, "n_gpus": world, "steps": steps, "warmup": args.warmup,
         "ms_per_step": ms_max / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64", "data": "synthetic",
+        "dtype": "f64" if args.adj_sweep64 else "f64 (sweep f32)", "data": "synthetic",
         "config": {"workload": "adjoint: %d^3 = %d particles, jittered sc lattice, L=%d, Lucy h=2.5a, kT=1, "
                                "K=%g, dt=%g, %d steps (Verlet + EMS sweep, increments frozen), "
-                               "checkpoint every %d, float64"
-                               % (w.n, w.N, w.n, w.K, args.dt, ns, every),
+                               "checkpoint every %d, float64 state, Verlet and reverse pass; sweep pair "
+                               "arithmetic %s"
+                               % (w.n, w.N, w.n, w.K, args.dt, ns, every,
+                                  "float64" if args.adj_sweep64 else "float32"),
                    "N": w.N, "K": w.K, "steps_per_gradient": ns, "checkpoint_every": every,
                    "l2": "working set below L2 (the workload is fixed at 32^3)"},
         "forward_ms_per_gradient": fwd_ms / steps, "reverse_ms_per_gradient": adj_ms / steps,

@@ -82,6 +82,11 @@ typedef struct {
                     or < 4, SDPD_ERR_BOX_TOO_SMALL if box/n < h).  The cell grid
                     fixes the colouring and so the order of the sweep's pair
                     updates; any grid gives a valid sweep of Section 3.2. */
+  int sweep_f32; /* float64 handles: 1 runs the fluctuation/dissipation sweep with
+                    float32 pair arithmetic on the float64 state, as the mixed path
+                    does (momenta and energies receive float32 increments; density,
+                    Velocity Verlet and the gradients stay float64).  Ignored by
+                    mixed handles. */
 } sdpd_params;
 
 /* Observables of the current state (Section 2.2: E and the total momentum

@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <new>
 #include <numeric>
+#include <type_traits>
 #include <vector>
 
 #include "sdpd_internal.cuh"
@@ -307,6 +308,10 @@ bool sweep_due(const sdpd_handle* s) {
   return s->prm.scheme != SDPD_SCHEME_NONE && (s->prm.fd_only || s->vv_step % theta == 0);
 }
 
+// Whether the sweep's pair arithmetic is float32 (the mixed path, or a
+// float64 state swept in float32).
+bool sweep_float(const sdpd_handle* s) { return s->prm.precision == SDPD_MIXED || s->prm.sweep_f32 != 0; }
+
 // One fluctuation/dissipation sweep with step dt_fd.
 template <class P>
 void fd_sweep_step(sdpd_handle* s, double dt_fd, uint64_t seed) {
@@ -321,7 +326,12 @@ void fd_sweep_step(sdpd_handle* s, double dt_fd, uint64_t seed) {
   }
   {
     StageTimer t(s, 5, 8);
-    launch_fd_colours<P>(c, s->w, s->cur, dt_fd, seed, rec, s->stream);
+    if constexpr (std::is_same<P, Fp64>::value) {
+      if (s->prm.sweep_f32) launch_fd_colours<Fp64, Mixed>(c, s->w, s->cur, dt_fd, seed, rec, s->stream);
+      else launch_fd_colours<Fp64, Fp64>(c, s->w, s->cur, dt_fd, seed, rec, s->stream);
+    } else {
+      launch_fd_colours<P, P>(c, s->w, s->cur, dt_fd, seed, rec, s->stream);
+    }
   }
   launch_advance_sweep(s->w, s->stream);
   s->launches += 9;
@@ -454,7 +464,7 @@ int sdpd_create(int64_t N, const double box[3], double m, double h, double K, co
     }
   }
   c.kernel = prm->kernel;
-  c.fd_variant = fd_default_variant(prm->precision == SDPD_MIXED);
+  c.fd_variant = fd_default_variant(prm->precision == SDPD_MIXED || prm->sweep_f32 != 0);
   c.pair_threads = 128;
   c.scheme = prm->scheme;
   s->prm = *prm;
@@ -529,8 +539,9 @@ int sdpd_bind_workspace(sdpd_t* s, void* ptr, size_t bytes) {
   e |= cuda_ok(cudaStreamSynchronize(st));
   // launch sizes of the sweep's colour kernels, queried here rather than
   // inside a later stream capture
-  if (s->prm.precision == SDPD_MIXED) fd_prepare<Mixed>();
-  else fd_prepare<Fp64>();
+  if (s->prm.precision == SDPD_MIXED) fd_prepare<Mixed, Mixed>();
+  else if (s->prm.sweep_f32) fd_prepare<Fp64, Mixed>();
+  else fd_prepare<Fp64, Fp64>();
   e |= launch_status();
   s->has_state = false;
   return e ? SDPD_ERR_CUDA : SDPD_OK;
@@ -752,9 +763,9 @@ int sdpd_get_tuning(const sdpd_t* s, sdpd_tuning* out) {
 
 int sdpd_set_tuning(sdpd_t* s, const sdpd_tuning* t) {
   if (!s || !t) return SDPD_ERR_INVALID_ARG;
-  const int v = t->fd_variant < 0 ? fd_default_variant(s->prm.precision == SDPD_MIXED) : t->fd_variant;
+  const int v = t->fd_variant < 0 ? fd_default_variant(sweep_float(s)) : t->fd_variant;
   const int pt = t->pair_threads == 0 ? 128 : t->pair_threads;
-  if (v >= kFdVariants || !fd_variant_fits(s->prm.precision == SDPD_MIXED, v) || !pair_threads_ok(pt))
+  if (v >= kFdVariants || !fd_variant_fits(sweep_float(s), v) || !pair_threads_ok(pt))
     return SDPD_ERR_INVALID_ARG;
   s->c.fd_variant = v;
   s->c.pair_threads = pt;
@@ -801,7 +812,7 @@ int sdpd_autotune(sdpd_t* s, double dt, int64_t steps, uint64_t seed, sdpd_tunin
   int bv = v0, bt = 128;
   double bms = INFINITY;
   for (int v = 0; v < kFdVariants; ++v) {
-    if (!fd_variant_fits(mixed, v)) continue;
+    if (!fd_variant_fits(sweep_float(s), v)) continue;
     const double ms = trial(v, 128);
     if (ms < bms) { bms = ms; bv = v; }
   }
@@ -1423,14 +1434,14 @@ int sdpd_ensemble_autotune(sdpd_ens_t* e, double dt, int64_t steps, const uint64
   // schedule given to all members; the fastest assignment is kept
   std::vector<std::vector<sdpd_tuning>> cand;
   std::vector<sdpd_tuning> dflt(n);
-  for (size_t i = 0; i < n; ++i) dflt[i] = {fd_default_variant(e->m[i]->prm.precision == SDPD_MIXED), 128};
+  for (size_t i = 0; i < n; ++i) dflt[i] = {fd_default_variant(sweep_float(e->m[i])), 128};
   cand.push_back(dflt);
   cand.push_back(alone);
   for (int v = 0; v < kFdVariants; ++v) {
     std::vector<sdpd_tuning> u(n);
     for (size_t i = 0; i < n; ++i) {
-      const bool mixed = e->m[i]->prm.precision == SDPD_MIXED;
-      u[i] = {fd_variant_fits(mixed, v) ? v : fd_default_variant(mixed), 128};
+      const bool fl = sweep_float(e->m[i]);
+      u[i] = {fd_variant_fits(fl, v) ? v : fd_default_variant(fl), 128};
     }
     cand.push_back(u);
   }

@@ -4,6 +4,7 @@
 // instantiates the block-schedule variants of its precision.
 #pragma once
 #include <algorithm>
+#include <type_traits>
 
 #include "sdpd_fd_common.cuh"
 
@@ -264,16 +265,22 @@ struct FdSmem {
 template <class P, int W>
 constexpr int fd_min_blocks() { return P::mixed ? 16 / W : (W >= 4 ? 1 : 4 / W); }
 
-template <class P, int KIND, int OPW, int W>
-__global__ void __launch_bounds__(W * 32, fd_min_blocks<P, W>())
-    k_fd_colour(Consts c, FDConst<typename P::R> k, Arrays<P> a, typename P::V4* __restrict__ qp4,
+// P is the storage policy of the state arrays, A the arithmetic policy of
+// the pair updates: A = P except for a float64 state swept with float32
+// pair arithmetic (P = Fp64, A = Mixed), where momenta and energies go back
+// as their float64 values plus the float32 increments of the visit.
+template <class P, class A, int KIND, int OPW, int W>
+__global__ void __launch_bounds__(W * 32, fd_min_blocks<A, W>())
+    k_fd_colour(Consts c, FDConst<typename A::R> k, Arrays<P> a, typename P::V4* __restrict__ qp4,
                 const int32_t* __restrict__ cell_start, const int32_t* __restrict__ mrank,
                 const uint32_t* __restrict__ xmx, const uint32_t* __restrict__ xmy,
                 const uint32_t* __restrict__ xmz, const uint32_t* __restrict__ hdr,
                 const uint16_t* __restrict__ lvl, const uint16_t* __restrict__ pairs, int colour, uint64_t seed,
                 const unsigned long long* __restrict__ sweep_ptr, unsigned long long* counters, int* status,
                 sdpd_pair_rec* recs, unsigned long long* rec_count, int64_t rec_cap, unsigned* __restrict__ queue) {
-  using R = typename P::R;
+  using R = typename A::R;  // pair arithmetic
+  using S = typename P::R;  // stored momenta, densities, geometry
+  constexpr bool kSame = std::is_same<R, S>::value;
   constexpr int kGroupLanes = 32 / OPW;
   __shared__ FdSmem<R> sm_all[W][OPW];
   const uint64_t sweep = *sweep_ptr;
@@ -282,8 +289,8 @@ __global__ void __launch_bounds__(W * 32, fd_min_blocks<P, W>())
   const int hx = c.nc[0] >> 1, hy = c.nc[1] >> 1, hz = c.nc[2] >> 1;
   const int64_t nown = (int64_t)hx * hy * hz;
   FdSmem<R>& sm = sm_all[warp][grp];
-  const R inv_h = k.inv_h, cF = k.cF;
-  const R pi_coef = (R)(c.c_rho / (c.C_K * c.m));
+  const S inv_h = (S)(1.0 / c.h), cF = (S)c.cF;
+  const S pi_coef = (S)(c.c_rho / (c.C_K * c.m));
   unsigned long long n_acc = 0, n_rb = 0, n_rm = 0, n_tot = 0;
   bool negative = false, bad = false;
   // The grid holds as many thread blocks as fit on the GPU at once; each
@@ -356,19 +363,19 @@ __global__ void __launch_bounds__(W * 32, fd_min_blocks<P, W>())
         const uint16_t pr = pl[t];
         const int ia = pr & 255, ib = pr >> 8;  // ia holds the lower id
         const int ga = gidx(ia), gb = gidx(ib);
-        R xa, ya, za, xb, yb, zb, rx, ry, rz;
+        S xa, ya, za, xb, yb, zb, rx, ry, rz;
         const typename P::V4 qa = ld4(&a.q4[ga]), qb = ld4(&a.q4[gb]);
         geo.local(qa, block_code(qa.w, ox, oy, oz), xa, ya, za);
         geo.local(qb, block_code(qb.w, ox, oy, oz), xb, yb, zb);
         geo.disp(xa, ya, za, xb, yb, zb, rx, ry, rz);
-        const R r2 = r2_of(rx, ry, rz);
-        const R inv_r = fm::rsqrt(r2);
+        const S r2 = r2_of(rx, ry, rz);
+        const S inv_r = fm::rsqrt(r2);
         const int slot = t - cbeg;
         sm.pr[slot] = pr;
-        sm.ex[slot] = rx * inv_r;
-        sm.ey[slot] = ry * inv_r;
-        sm.ez[slot] = rz * inv_r;
-        sm.base[slot] = fm::div(kernel_F<KIND>(r2 * inv_r * inv_h, cF), a.rho[ga] * a.rho[gb]);
+        sm.ex[slot] = (R)(rx * inv_r);
+        sm.ey[slot] = (R)(ry * inv_r);
+        sm.ez[slot] = (R)(rz * inv_r);
+        sm.base[slot] = (R)fm::div(kernel_F<KIND>(r2 * inv_r * inv_h, cF), a.rho[ga] * a.rho[gb]);
         R G[3], U;
         pair_randoms_fast(seed, sweep, (uint64_t)a.id[ga], (uint64_t)a.id[gb], G, &U);
         sm.G0[slot] = G[0]; sm.G1[slot] = G[1]; sm.G2[slot] = G[2];
@@ -398,14 +405,14 @@ __global__ void __launch_bounds__(W * 32, fd_min_blocks<P, W>())
             const double db = a.eps[gidx(ib)] + (double)sm.acc[ib];
             return fmin(da, db) + (double)dv;
           };
-          const int dcs = fd_pair<P>(k, sm.ex[slot], sm.ey[slot], sm.ez[slot], sm.base[slot], G, sm.lnU[slot], pa,
+          const int dcs = fd_pair<A>(k, sm.ex[slot], sm.ey[slot], sm.ez[slot], sm.base[slot], G, sm.lnU[slot], pa,
                                      pb, ea, eb, deps, margin, negative, exact);
           if (dcs == 0) {
             sm.px[ia] = pa[0]; sm.py[ia] = pa[1]; sm.pz[ia] = pa[2];
             sm.px[ib] = pb[0]; sm.py[ib] = pb[1]; sm.pz[ib] = pb[2];
             sm.e[ia] = ea + deps;
             sm.e[ib] = eb + deps;
-            if constexpr (P::mixed) {
+            if constexpr (A::mixed) {
               sm.acc[ia] += deps;
               sm.acc[ib] += deps;
             }
@@ -445,13 +452,19 @@ __global__ void __launch_bounds__(W * 32, fd_min_blocks<P, W>())
     }
     for (int q = gl; q < nb; q += kGroupLanes) {
       const int g = gidx(q);
-      a.px[g] = sm.px[q]; a.py[g] = sm.py[q]; a.pz[g] = sm.pz[q];
+      if constexpr (kSame) {
+        a.px[g] = sm.px[q]; a.py[g] = sm.py[q]; a.pz[g] = sm.pz[q];
+      } else {  // the stored value plus this visit's increment
+        a.px[g] += (S)(sm.px[q] - (R)a.px[g]);
+        a.py[g] += (S)(sm.py[q] - (R)a.py[g]);
+        a.pz[g] += (S)(sm.pz[q] - (R)a.pz[g]);
+      }
       double e;
-      if constexpr (P::mixed) e = a.eps[g] + (double)sm.acc[q];  // one float64 update per visit
+      if constexpr (A::mixed) e = a.eps[g] + (double)sm.acc[q];  // one float64 update per visit
       else e = sm.e[q];
       a.eps[g] = e;
       // pressure over rho^2 of the new energy, Eq. (pg-eos): pi = c_rho eps / (C_K m rho)
-      qp4[g].w = (R)e * pi_coef / a.rho[g];
+      qp4[g].w = (S)e * pi_coef / a.rho[g];
     }
     __syncwarp();  // the group's shared memory is refilled by the next block
   }
@@ -506,13 +519,13 @@ static FDConst<R> fd_const(const Consts& c, double dt) {
 // Thread blocks of a colour kernel that the device holds at once (SMs x
 // blocks per SM, from the occupancy calculator; at least one), computed once
 // per kernel on the device current at the first launch.
-template <class P, int KIND, int OPW, int W>
+template <class P, class A, int KIND, int OPW, int W>
 int fd_resident_blocks() {
   static const int n = [] {
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fd_colour<P, KIND, OPW, W>, W * 32, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fd_colour<P, A, KIND, OPW, W>, W * 32, 0);
     return std::max(1, sms) * std::max(1, per_sm);
   }();
   return n;
@@ -528,18 +541,18 @@ constexpr int kFdWarps[kFdVariants] = {2, 1, 1, 2, 4};
 
 // One colour launch with block-schedule variant (OPW, W); a schedule that
 // does not fit runs as variant 1.
-template <class P, int KIND, int OPW, int W>
-void launch_colour(const Consts& c, const FDConst<typename P::R>& k, const Arrays<P>& a, const Workspace& w,
+template <class P, class A, int KIND, int OPW, int W>
+void launch_colour(const Consts& c, const FDConst<typename A::R>& k, const Arrays<P>& a, const Workspace& w,
                    int col, uint64_t seed, sdpd_pair_rec* recs, cudaStream_t s) {
-  if constexpr (!fd_fits<P, OPW, W>()) {
-    launch_colour<P, KIND, 2, 1>(c, k, a, w, col, seed, recs, s);
+  if constexpr (!fd_fits<A, OPW, W>()) {
+    launch_colour<P, A, KIND, 2, 1>(c, k, a, w, col, seed, recs, s);
   } else {
     const int64_t nown = (int64_t)(c.nc[0] / 2) * (c.nc[1] / 2) * (c.nc[2] / 2);
     const int64_t per_block = (int64_t)W * OPW;
     const int64_t need = (nown + per_block - 1) / per_block;
-    const int64_t resident = (int64_t)fd_resident_blocks<P, KIND, OPW, W>();
+    const int64_t resident = (int64_t)fd_resident_blocks<P, A, KIND, OPW, W>();
     const unsigned gf = (unsigned)std::max<int64_t>(1, std::min(need, resident));
-    k_fd_colour<P, KIND, OPW, W><<<gf, W * 32, 0, s>>>(
+    k_fd_colour<P, A, KIND, OPW, W><<<gf, W * 32, 0, s>>>(
         c, k, a, (typename P::V4*)w.qp4, w.cell_start, w.mrank, w.xmin[0], w.xmin[1], w.xmin[2], w.sched_hdr,
         w.sched_lvl, w.sched_pair, col, seed, w.sweep, w.counters, w.status, recs, w.pair_rec_count,
         w.pair_rec_cap, w.fd_queue + 2 * col);
@@ -549,49 +562,49 @@ void launch_colour(const Consts& c, const FDConst<typename P::R>& k, const Array
 // The eight colour launches of one sweep.  variant indexes the block
 // schedules (blocks per warp, warps per thread block):
 // 0 (2, 2), 1 (2, 1), 2 (1, 1), 3 (1, 2), 4 (1, 4).
-template <class P, int KIND>
+template <class P, class A, int KIND>
 void launch_colours_kind(const Consts& c, const Workspace& w, int cur, double dt, uint64_t seed, int record,
                          int variant, cudaStream_t s) {
-  const FDConst<typename P::R> k = fd_const<typename P::R>(c, dt);
+  const FDConst<typename A::R> k = fd_const<typename A::R>(c, dt);
   const Arrays<P> a = view<P>(w, cur);
   sdpd_pair_rec* recs = record ? w.pair_recs : nullptr;
   for (int col = 0; col < 8; ++col) {
     switch (variant) {
-      case 0: launch_colour<P, KIND, 2, 2>(c, k, a, w, col, seed, recs, s); break;
-      case 1: launch_colour<P, KIND, 2, 1>(c, k, a, w, col, seed, recs, s); break;
-      case 2: launch_colour<P, KIND, 1, 1>(c, k, a, w, col, seed, recs, s); break;
-      case 3: launch_colour<P, KIND, 1, 2>(c, k, a, w, col, seed, recs, s); break;
-      default: launch_colour<P, KIND, 1, 4>(c, k, a, w, col, seed, recs, s); break;
+      case 0: launch_colour<P, A, KIND, 2, 2>(c, k, a, w, col, seed, recs, s); break;
+      case 1: launch_colour<P, A, KIND, 2, 1>(c, k, a, w, col, seed, recs, s); break;
+      case 2: launch_colour<P, A, KIND, 1, 1>(c, k, a, w, col, seed, recs, s); break;
+      case 3: launch_colour<P, A, KIND, 1, 2>(c, k, a, w, col, seed, recs, s); break;
+      default: launch_colour<P, A, KIND, 1, 4>(c, k, a, w, col, seed, recs, s); break;
     }
   }
 }
 
 // Fills the resident-block counts of every block schedule ahead of time (a
 // host query, kept out of stream captures).
-template <class P>
+template <class P, class A>
 void fd_prepare() {
-  fd_resident_blocks<P, SDPD_KERNEL_LUCY, 2, 2>();
-  fd_resident_blocks<P, SDPD_KERNEL_LUCY, 2, 1>();
-  fd_resident_blocks<P, SDPD_KERNEL_LUCY, 1, 1>();
-  fd_resident_blocks<P, SDPD_KERNEL_LUCY, 1, 2>();
-  fd_resident_blocks<P, SDPD_KERNEL_LUCY, 1, 4>();
-  fd_resident_blocks<P, SDPD_KERNEL_CUBIC, 2, 2>();
-  fd_resident_blocks<P, SDPD_KERNEL_CUBIC, 2, 1>();
-  fd_resident_blocks<P, SDPD_KERNEL_CUBIC, 1, 1>();
-  fd_resident_blocks<P, SDPD_KERNEL_CUBIC, 1, 2>();
-  fd_resident_blocks<P, SDPD_KERNEL_CUBIC, 1, 4>();
+  fd_resident_blocks<P, A, SDPD_KERNEL_LUCY, 2, 2>();
+  fd_resident_blocks<P, A, SDPD_KERNEL_LUCY, 2, 1>();
+  fd_resident_blocks<P, A, SDPD_KERNEL_LUCY, 1, 1>();
+  fd_resident_blocks<P, A, SDPD_KERNEL_LUCY, 1, 2>();
+  fd_resident_blocks<P, A, SDPD_KERNEL_LUCY, 1, 4>();
+  fd_resident_blocks<P, A, SDPD_KERNEL_CUBIC, 2, 2>();
+  fd_resident_blocks<P, A, SDPD_KERNEL_CUBIC, 2, 1>();
+  fd_resident_blocks<P, A, SDPD_KERNEL_CUBIC, 1, 1>();
+  fd_resident_blocks<P, A, SDPD_KERNEL_CUBIC, 1, 2>();
+  fd_resident_blocks<P, A, SDPD_KERNEL_CUBIC, 1, 4>();
 }
 
-template <class P>
+template <class P, class A>
 void launch_fd_colours(const Consts& c, const Workspace& w, int cur, double dt, uint64_t seed, int record,
                        cudaStream_t s) {
   if (c.N == 0) return;
   int variant = c.fd_variant;
-  if (variant < 0 || variant >= kFdVariants) variant = fd_default_variant(P::mixed);
+  if (variant < 0 || variant >= kFdVariants) variant = fd_default_variant(A::mixed);
   if (c.kernel == SDPD_KERNEL_LUCY)
-    launch_colours_kind<P, SDPD_KERNEL_LUCY>(c, w, cur, dt, seed, record, variant, s);
+    launch_colours_kind<P, A, SDPD_KERNEL_LUCY>(c, w, cur, dt, seed, record, variant, s);
   else
-    launch_colours_kind<P, SDPD_KERNEL_CUBIC>(c, w, cur, dt, seed, record, variant, s);
+    launch_colours_kind<P, A, SDPD_KERNEL_CUBIC>(c, w, cur, dt, seed, record, variant, s);
 }
 
 }  // namespace sdpd

@@ -1,13 +1,17 @@
-// sdpd_fd_colour_fp64.cu -- the colour kernels of the float64 path, every
-// block-schedule variant (kept apart from the other precision so that the
-// variants compile in parallel).
+// sdpd_fd_colour_fp64.cu -- the colour kernels of the float64 state, every
+// block-schedule variant, with float64 or float32 pair arithmetic (kept apart
+// from the mixed state so that the variants compile in parallel).
 #include "sdpd_fd_colour.cuh"
 
 namespace sdpd {
 
-template void fd_prepare<Fp64>();
-template void launch_fd_colours<Fp64>(const Consts&, const Workspace&, int, double, uint64_t, int,
-                                    cudaStream_t);
+template void fd_prepare<Fp64, Fp64>();
+template void fd_prepare<Fp64, Mixed>();
+template void launch_fd_colours<Fp64, Fp64>(const Consts&, const Workspace&, int, double, uint64_t, int,
+                                          cudaStream_t);
+// float64 state, float32 pair arithmetic
+template void launch_fd_colours<Fp64, Mixed>(const Consts&, const Workspace&, int, double, uint64_t, int,
+                                           cudaStream_t);
 
 template <class P, int V>
 constexpr bool fits_v() { return fd_fits<P, kFdOpw[V], kFdWarps[V]>(); }

@@ -5,8 +5,8 @@
 
 namespace sdpd {
 
-template void fd_prepare<Mixed>();
-template void launch_fd_colours<Mixed>(const Consts&, const Workspace&, int, double, uint64_t, int,
+template void fd_prepare<Mixed, Mixed>();
+template void launch_fd_colours<Mixed, Mixed>(const Consts&, const Workspace&, int, double, uint64_t, int,
                                     cudaStream_t);
 
 }  // namespace sdpd

@@ -333,9 +333,11 @@ void launch_force(const Consts& c, const Workspace& w, int cur, double half_dt, 
                   double* force_by_id, cudaStream_t s);
 template <class P>
 void launch_fd_schedule(const Consts& c, const Workspace& w, int cur, cudaStream_t s);
-template <class P>
+// the sweep's colour launches: P the state's storage policy, A the pair
+// arithmetic (A = Mixed on float64 state: float32 pair updates)
+template <class P, class A = P>
 void fd_prepare();
-template <class P>
+template <class P, class A = P>
 void launch_fd_colours(const Consts& c, const Workspace& w, int cur, double dt, uint64_t seed, int record,
                        cudaStream_t s);
 template <class P>

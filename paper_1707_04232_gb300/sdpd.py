@@ -26,7 +26,7 @@ class sdpd_params(C.Structure):
     _fields_ = [
         ("kB", C.c_double), ("eta", C.c_double), ("zeta", C.c_double), ("c_rho", C.c_double),
         ("kernel", C.c_int), ("scheme", C.c_int), ("precision", C.c_int), ("fd_only", C.c_int),
-        ("theta", C.c_int), ("debug", C.c_int), ("nc", C.c_int * 3),
+        ("theta", C.c_int), ("debug", C.c_int), ("nc", C.c_int * 3), ("sweep_f32", C.c_int),
     ]
 
 
@@ -297,7 +297,7 @@ class SDPD:
 
     def __init__(self, N, box, m=1.0, h=2.5, K=100.0, *, kB=1.0, eta=1.0, zeta=0.0, c_rho=-1.0,
                  kernel=KERNEL_LUCY, scheme=SCHEME_EMS, precision=FP64, fd_only=False, theta=1,
-                 debug=False, nc=None, stream=None):
+                 debug=False, nc=None, sweep_f32=False, stream=None):
         import torch
 
         if not torch.cuda.is_available():
@@ -307,7 +307,7 @@ class SDPD:
         self.m, self.h_smooth, self.K = float(m), float(h), float(K)
         prm = sdpd_params(kB=kB, eta=eta, zeta=zeta, c_rho=c_rho, kernel=kernel, scheme=scheme,
                           precision=precision, fd_only=int(bool(fd_only)), theta=int(theta),
-                          debug=int(bool(debug)))
+                          debug=int(bool(debug)), sweep_f32=int(bool(sweep_f32)))
         if nc is not None:  # cells per axis (0 = the default grid on that axis)
             for d, n in enumerate(nc if np.ndim(nc) else (nc,) * 3):
                 prm.nc[d] = int(n)

@@ -83,6 +83,19 @@ def test_strerror_covers_codes():
         assert sdpd.sdpd_strerror(code) != "unknown status"
 
 
+def test_float32_sweep_flag_on_host():
+    # accepted on both precisions; a float64 handle with it takes the float32
+    # block schedules (all five fit in shared memory)
+    lib = sdpd.load()
+    st, h = sdpd.sdpd_create(8000, (20.0,) * 3, 1.0, 2.5, 100.0, _params(precision=0, sweep_f32=1), 0)
+    assert st == sdpd.OK
+    t = sdpd.sdpd_tuning()
+    assert lib.sdpd_get_tuning(h, C.byref(t)) == sdpd.OK and t.fd_variant == 0
+    for v in range(5):
+        assert lib.sdpd_set_tuning(h, C.byref(sdpd.sdpd_tuning(fd_variant=v, pair_threads=128))) == sdpd.OK
+    sdpd.sdpd_destroy(h)
+
+
 def test_coarser_cell_grid_needs_less_workspace():
     st, h1 = sdpd.sdpd_create(32768, (32.0,) * 3, 1.0, 2.5, 100.0, _params(precision=1), 0)
     st2, h2 = sdpd.sdpd_create(32768, (32.0,) * 3, 1.0, 2.5, 100.0, _params(precision=1, nc=(10, 10, 10)), 0)

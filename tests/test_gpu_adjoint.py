@@ -343,3 +343,47 @@ def test_virial_after_100_steps_32k_against_central_differences():
                 vals.append(frozen_loss(make(w.N, L, Kk, **kw)))
         fd_t = (vals[0] - vals[1]) / (2 * d * base)
         assert abs(theta.grad[k].item() - fd_t) <= 1e-6 * abs(fd_t), (k, theta.grad[k].item(), fd_t)
+
+
+def test_float32_sweep_on_float64_state():
+    """sweep_f32: the sweep's pair arithmetic in float32 on the float64 state
+    (as the mixed path does it).  Against the float64 sweep over 10 steps, as
+    for the mixed path: a decision whose margin is within float32 rounding
+    may flip, moving that pair's momenta by one noise kick, so almost every
+    particle stays within 2e-6 a and none leaves 1e-2 a; the accept counts
+    agree up to those flips and the total energy within 1e-6.  The recorded
+    increments then give a gradient equal to the oracle's reverse pass over
+    those same increments (they enter as constants)."""
+    q, p, e, L, K = system("random_rect")
+    dt, seed, nsteps = 0.02, 7, 10
+    runs = {}
+    for f32 in (False, True):
+        s = sdpd.SDPD(len(q), L, h=2.5, K=K, scheme=sdpd.SCHEME_EMS, precision=sdpd.FP64, sweep_f32=f32)
+        s.set_state(q, p, e)
+        s.step(dt, nsteps, seed=seed)
+        runs[f32] = (s.get_state(), s.observables())
+    (q64, p64, e64), o64 = runs[False]
+    (q32, p32, e32), o32 = runs[True]
+    Lv = np.asarray(L)
+    dq = np.abs((q32 - q64 + 0.5 * Lv) % Lv - 0.5 * Lv).max(axis=1)
+    assert np.mean(dq < 2e-6) > 0.97 and dq.max() < 1e-2
+    assert abs(o32["n_pairs"] - o64["n_pairs"]) <= 10  # pair sets can differ where trajectories did
+    assert abs(o32["n_accept"] - o64["n_accept"]) <= 20
+    assert abs(o32["E"] - o64["E"]) < 1e-6 * abs(o64["E"])
+    assert o32["status"] == sdpd.OK
+    # gradient of the frozen map recorded with the float32 sweep
+    nsteps = 4
+    sim = sdpd.SDPD(len(q), L, h=2.5, K=K, scheme=sdpd.SCHEME_EMS, precision=sdpd.FP64, sweep_f32=True)
+    sim.set_state(q, p, e)
+    tape = sim.vv_record(dt, nsteps, 2, seed)
+    dps, des = recorded_increments(sim, tape, nsteps)
+    assert np.abs(dps).max() > 0.0
+    rng = np.random.default_rng(31)
+    cq, cp, ce = rng.standard_normal(q.shape), rng.standard_normal(p.shape), rng.standard_normal(e.shape)
+    gq, gp, ge, gt = sim.vv_adjoint(tape, dev(cq), dev(cp), dev(ce))
+    P = oparams(len(q), L, K, O.KERNEL_LUCY, O.SCHEME_EMS)
+    rgq, rgp, rge, rgt = O.frozen_vjp(P, q, p, e, dt, nsteps, dps, des, cq, cp, ce)
+    for got, ref in ((gq, rgq), (gp, rgp), (ge, rge)):
+        ok, err = close(got, ref, 1e-9)
+        assert ok, err
+    assert np.abs(gt - rgt).max() <= 1e-9 * np.abs(rgt).max()

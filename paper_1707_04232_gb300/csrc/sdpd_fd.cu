@@ -27,8 +27,9 @@
 // positions only, which are fixed during the sweep): k_sched_enum (one warp
 // per block: owned pairs in canonical order), k_sched_walk (one thread per
 // block: the dependency level of every pair) and k_sched_bucket (one warp per
-// block: pairs bucketed by level); then k_fd_colour runs once per colour (two
-// blocks per warp: the pair updates level by level in shared memory).
+// block: pairs bucketed by level); then k_fd_colour (sdpd_fd_colour.cuh)
+// runs once per colour: the pair updates level by level in shared memory,
+// one or two blocks per warp as the launch's block schedule says.
 #include "sdpd_fd_common.cuh"
 
 namespace sdpd {

@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(128) k_adj_pairsum(Consts c, const D4* __restr
     } else {
       t = r2;
     }
-    acc += kernel_F<KIND>(sqrt(r2) * inv_h, c.cF) * t;
+    acc += kernel_F<KIND>(pair_r(r2) * inv_h, c.cF) * t;
   }
   A[i] = c.m * c.m * acc;
 }
@@ -258,7 +258,7 @@ __global__ void __launch_bounds__(128) k_adj_back(Consts c, const D4* __restrict
     double dx, dy, dz;
     pair_disp(im, e & 63u, qi, qj, dx, dy, dz);
     const double r2 = r2_of(dx, dy, dz);
-    const double r = sqrt(r2), x = r * inv_h;
+    const double r = pair_r(r2), x = r * inv_h;
     const double f = kernel_F<KIND>(x, c.cF);
     const double rb = vi.w + vj.w;
     // density: d rho / d q along r_ij, and dW/dh = (r^2 F - 3 W)/h

@@ -38,7 +38,7 @@ __device__ __forceinline__ double log(double x) { return ::log(x); }
 __device__ __forceinline__ float log(float x) { return __logf(x); }
 __device__ __forceinline__ double sqrt(double x) { return ::sqrt(x); }
 __device__ __forceinline__ float sqrt(float x) { return x * rsqrtf(x); }
-__device__ __forceinline__ double rsqrt(double x) { return 1.0 / ::sqrt(x); }
+__device__ __forceinline__ double rsqrt(double x) { return x > 1e-30 ? pair_rinv(x) : 1.0 / ::sqrt(x); }
 __device__ __forceinline__ float rsqrt(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double expm1(double x) { return ::expm1(x); }
 // exp(x) - 1 for x <= 0: Taylor polynomial for small |x| (relative error

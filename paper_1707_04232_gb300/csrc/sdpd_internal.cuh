@@ -65,6 +65,21 @@ __host__ __device__ __forceinline__ uint32_t nbr_entry(int j, int ox, int oy, in
 }
 
 // ---------------------------------------------------------------------------
+// Pair distance from r^2.  float64: 1/r from the float32 reciprocal square
+// root refined by one Newton step for y = 1/sqrt(x), y <- y (3 - x y^2) / 2
+// (quadratic convergence: from the float32 estimate's ~2.4e-7 to ~1e-13
+// relative), then r = x y; a handful of float64 operations instead of a
+// correctly rounded square root.  r^2 below 1e-30 (coincident particles)
+// takes the library square root.  float: the library square root.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double pair_rinv(double r2) {
+  const double y = (double)rsqrtf((float)r2);
+  return y * (1.5 - 0.5 * r2 * y * y);
+}
+__device__ __forceinline__ double pair_r(double r2) { return r2 > 1e-30 ? r2 * pair_rinv(r2) : sqrt(r2); }
+__device__ __forceinline__ float pair_r(float r2) { return sqrtf(r2); }
+
+// ---------------------------------------------------------------------------
 // Smoothing kernels of Section 2.1.1 as functions of x = r/h in [0, 1).
 // W: cubic spline of Eq. (sdpd-cubic-w) (cW = 8/(pi h^3)) or Lucy's kernel
 // (cW = 105/(16 pi h^3)).  F with grad W = -F(r) r: cubic cF = 48/(pi h^5),

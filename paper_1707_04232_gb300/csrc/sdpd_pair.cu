@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(128) k_density(Consts c, Arrays<P> a, typename
           home.disp(qj, dx, dy, dz);
           const R r2 = r2_of(dx, dy, dz);
           if (r2 < h2) {
-            acc += kernel_W<KIND>(sqrt(r2) * inv_h, cW);
+            acc += kernel_W<KIND>(pair_r(r2) * inv_h, cW);
             if (cnt < c.nbr_cap) nlist[i * c.nbr_cap + cnt] = nbr_entry(j, ox, oy, oz);
             ++cnt;
           }
@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(128) k_force(Consts c, Arrays<P> a, const type
         R dx, dy, dz;
         home.disp_code(e & 63u, qj, dx, dy, dz);
         const R r2 = r2_of(dx, dy, dz);
-        const R s = (pi_i + qj.w) * kernel_F<KIND>(sqrt(r2) * inv_h, cF);
+        const R s = (pi_i + qj.w) * kernel_F<KIND>(pair_r(r2) * inv_h, cF);
         fx += s * dx;
         fy += s * dy;
         fz += s * dz;

@@ -192,7 +192,7 @@ int sdpd_stage_times(sdpd_t* s, double* ms, int64_t* launches, int n);
 /* Histogram of the internal energies of the current state, for the
  * statistics of FD-only runs: the distribution of eps against the Gamma
  * marginal of Eq. (dist-analytic) and its error, Eq. (error-dist)
- * (Section 5.1).  With x_i = eps_i * scale and w = (hi - lo) / nbins, adds
+ * (Section 4.1).  With x_i = eps_i * scale and w = (hi - lo) / nbins, adds
  * to counts (device memory, nbins + 2 uint64 entries, owned by the caller):
  * counts[b] += #{i : lo + b w <= x_i < lo + (b + 1) w} for b < nbins
  * (b = floor((x - lo) / w) in float64, capped at nbins - 1),

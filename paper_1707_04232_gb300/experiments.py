@@ -1,6 +1,6 @@
-"""The paper's numerical experiments, run on the GPU (Section 5).
+"""The paper's numerical experiments, run on the GPU (Section 4).
 
-``fd_statistics``: the fluctuation/dissipation dynamics alone (Section 5.1).
+``fd_statistics``: the fluctuation/dissipation dynamics alone (Section 4.1).
 For a scheme and a time step given in the reduced time unit of Eq.
 (reduced-units), t_K = l_K sqrt(m_K / (K kB T)) with l_K = (m/rho)^(1/3) and
 m_K = m, one FD-only run equilibrates and then histograms the internal
@@ -20,7 +20,7 @@ path's statistics at scale can be set against those of the float64 path
 (which matches the float64 oracle step by step).
 
 ``mts_drift``: the full dynamics with single (STS) and multiple (MTS) time
-steps (Section 5.2).  Independent replicas (seeds) run as one ensemble; the
+steps (Section 4.2).  Independent replicas (seeds) run as one ensemble; the
 total energy is read at regular intervals and its drift is the slope of a
 least-squares line through E(t).  The ratio of the MTS and STS slopes at the
 same Verlet step is the paper's measure of the benefit of MTS.
@@ -217,14 +217,14 @@ def run_statistics(precision="mixed", scheme="ems", K=100.0, kT=1.0, dt=0.005, n
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     sub = ap.add_subparsers(dest="what", required=True)
-    a = sub.add_parser("fd", help="FD-only distribution error and rejection rates (Section 5.1)")
+    a = sub.add_parser("fd", help="FD-only distribution error and rejection rates (Section 4.1)")
     a.add_argument("--n", type=int, default=64)
     a.add_argument("--K", type=float, default=5.0)
     a.add_argument("--schemes", default="ems,ams,ssa")
     a.add_argument("--dts", default="0.02,0.1,0.5,1,2,5")
     a.add_argument("--precision", default="mixed", choices=list(PRECISIONS))
     a.add_argument("--configs", type=int, default=50)
-    b = sub.add_parser("mts", help="energy drift with single and multiple time steps (Section 5.2)")
+    b = sub.add_parser("mts", help="energy drift with single and multiple time steps (Section 4.2)")
     b.add_argument("--dts", default="0.1,0.2,0.392")
     b.add_argument("--scheme", default="ems", choices=["ems", "ams"])
     b.add_argument("--replicas", type=int, default=10)

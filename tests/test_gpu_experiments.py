@@ -1,6 +1,6 @@
-"""The paper's experiments of Section 5 on the GPU, at test size.
+"""The paper's experiments of Section 4 on the GPU, at test size.
 
-FD-only statistics (Section 5.1): with the exact Metropolis scheme the only
+FD-only statistics (Section 4.1): with the exact Metropolis scheme the only
 error of the internal-energy distribution is statistical, so the error of
 Eq. (error-dist) against the Gamma marginal of Eq. (dist-analytic) must stay
 within a few times the floor of independent sampling; the approximate scheme

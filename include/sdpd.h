@@ -116,8 +116,8 @@ typedef struct {
  * >= 4 of cells of side >= h), chooses the cell grid and the workspace size.
  * stream: a cudaStream_t (NULL = the legacy default stream).
  * Errors: SDPD_ERR_INVALID_ARG, SDPD_ERR_BOX_TOO_SMALL.  *out is NULL on error. */
-int sdpd_create(int64_t N, const double box[3], double m, double h, double K,
-                const sdpd_params* params, void* stream, sdpd_t** out);
+int sdpd_create(int64_t N, const double box[3], double m, double h, const sdpd_params* params,
+                double K, void* stream, sdpd_t** out);
 
 /* Bytes of device workspace the handle needs (256-byte aligned start). */
 size_t sdpd_workspace_bytes(const sdpd_t* s);

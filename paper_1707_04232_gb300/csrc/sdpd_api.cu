@@ -384,7 +384,7 @@ const char* sdpd_strerror(int st) {
   }
 }
 
-int sdpd_create(int64_t N, const double box[3], double m, double h, double K, const sdpd_params* prm,
+int sdpd_create(int64_t N, const double box[3], double m, double h, const sdpd_params* prm, double K,
                 void* stream, sdpd_t** out) {
   if (!out) return SDPD_ERR_INVALID_ARG;
   *out = nullptr;

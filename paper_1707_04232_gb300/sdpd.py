@@ -56,8 +56,8 @@ PAIR_REC_DTYPE = np.dtype([
 _H = C.c_void_p
 _dp = C.POINTER(C.c_double)
 SIGNATURES = [
-    ("sdpd_create", C.c_int, [C.c_int64, _dp, C.c_double, C.c_double, C.c_double,
-                              C.POINTER(sdpd_params), C.c_void_p, C.POINTER(_H)]),
+    ("sdpd_create", C.c_int, [C.c_int64, _dp, C.c_double, C.c_double, C.POINTER(sdpd_params),
+                              C.c_double, C.c_void_p, C.POINTER(_H)]),
     ("sdpd_workspace_bytes", C.c_size_t, [_H]),
     ("sdpd_bind_workspace", C.c_int, [_H, C.c_void_p, C.c_size_t]),
     ("sdpd_set_state", C.c_int, [_H, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
@@ -135,10 +135,10 @@ def _check(status: int, where: str):
 
 # --- thin wrappers with the C names ------------------------------------------------
 
-def sdpd_create(N, box, m, h, K, params: sdpd_params, stream: int = 0):
+def sdpd_create(N, box, m, h, params: sdpd_params, K, stream: int = 0):
     b = (C.c_double * 3)(*[float(x) for x in box])
     out = _H()
-    st = load().sdpd_create(int(N), b, float(m), float(h), float(K), C.byref(params),
+    st = load().sdpd_create(int(N), b, float(m), float(h), C.byref(params), float(K),
                             C.c_void_p(stream), C.byref(out))
     return st, out
 
@@ -313,7 +313,7 @@ class SDPD:
                 prm.nc[d] = int(n)
         self.params = prm
         self.stream = stream if stream is not None else torch.cuda.current_stream()
-        st, self.h = sdpd_create(N, box if np.ndim(box) else (box,) * 3, m, h, K, prm,
+        st, self.h = sdpd_create(N, box if np.ndim(box) else (box,) * 3, m, h, prm, K,
                                  self.stream.cuda_stream)
         _check(st, "sdpd_create")
         nbytes = sdpd_workspace_bytes(self.h)

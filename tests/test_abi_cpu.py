@@ -56,7 +56,7 @@ def _params(**kw):
     ({"nc": (2, 4, 4)}, (20.0, 10.0, 10.0), 100.0, sdpd.ERR_INVALID_ARG),    # fewer than 4
 ])
 def test_create_validates_on_host(kw, box, K, expect):
-    st, h = sdpd.sdpd_create(1000, box, 1.0, 2.5, K, _params(**kw), 0)
+    st, h = sdpd.sdpd_create(1000, box, 1.0, 2.5, _params(**kw), K, 0)
     assert st == expect
     if st == sdpd.OK:
         assert sdpd.sdpd_workspace_bytes(h) > 0
@@ -70,8 +70,8 @@ def test_create_validates_on_host(kw, box, K, expect):
 
 
 def test_workspace_scales_with_precision():
-    st, h64 = sdpd.sdpd_create(32768, (32.0,) * 3, 1.0, 2.5, 100.0, _params(precision=0), 0)
-    st2, hm = sdpd.sdpd_create(32768, (32.0,) * 3, 1.0, 2.5, 100.0, _params(precision=1), 0)
+    st, h64 = sdpd.sdpd_create(32768, (32.0,) * 3, 1.0, 2.5, _params(precision=0), 100.0, 0)
+    st2, hm = sdpd.sdpd_create(32768, (32.0,) * 3, 1.0, 2.5, _params(precision=1), 100.0, 0)
     assert st == st2 == sdpd.OK
     assert sdpd.sdpd_workspace_bytes(hm) < sdpd.sdpd_workspace_bytes(h64)
     sdpd.sdpd_destroy(h64)
@@ -87,7 +87,7 @@ def test_float32_sweep_flag_on_host():
     # accepted on both precisions; a float64 handle with it takes the float32
     # block schedules (all five fit in shared memory)
     lib = sdpd.load()
-    st, h = sdpd.sdpd_create(8000, (20.0,) * 3, 1.0, 2.5, 100.0, _params(precision=0, sweep_f32=1), 0)
+    st, h = sdpd.sdpd_create(8000, (20.0,) * 3, 1.0, 2.5, _params(precision=0, sweep_f32=1), 100.0, 0)
     assert st == sdpd.OK
     t = sdpd.sdpd_tuning()
     assert lib.sdpd_get_tuning(h, C.byref(t)) == sdpd.OK and t.fd_variant == 0
@@ -97,8 +97,8 @@ def test_float32_sweep_flag_on_host():
 
 
 def test_coarser_cell_grid_needs_less_workspace():
-    st, h1 = sdpd.sdpd_create(32768, (32.0,) * 3, 1.0, 2.5, 100.0, _params(precision=1), 0)
-    st2, h2 = sdpd.sdpd_create(32768, (32.0,) * 3, 1.0, 2.5, 100.0, _params(precision=1, nc=(10, 10, 10)), 0)
+    st, h1 = sdpd.sdpd_create(32768, (32.0,) * 3, 1.0, 2.5, _params(precision=1), 100.0, 0)
+    st2, h2 = sdpd.sdpd_create(32768, (32.0,) * 3, 1.0, 2.5, _params(precision=1, nc=(10, 10, 10)), 100.0, 0)
     assert st == st2 == sdpd.OK
     assert sdpd.sdpd_workspace_bytes(h2) < sdpd.sdpd_workspace_bytes(h1)
     sdpd.sdpd_destroy(h1)
@@ -111,7 +111,7 @@ def test_coarser_cell_grid_needs_less_workspace():
 ])
 def test_launch_shapes_on_host(precision, default, fits):
     lib = sdpd.load()
-    st, h = sdpd.sdpd_create(8000, (20.0,) * 3, 1.0, 2.5, 100.0, _params(precision=precision), 0)
+    st, h = sdpd.sdpd_create(8000, (20.0,) * 3, 1.0, 2.5, _params(precision=precision), 100.0, 0)
     assert st == sdpd.OK
     t = sdpd.sdpd_tuning()
     assert lib.sdpd_get_tuning(h, C.byref(t)) == sdpd.OK

@@ -192,6 +192,8 @@ size_t layout(sdpd_handle* s, Workspace* w, char* base) {
   w->sweep = (unsigned long long*)at(8);
   w->status = (int*)at(8);
   w->fd_queue = (unsigned*)at(16 * 4);
+  w->blk_hist = (uint32_t*)at(8 * 256 * 4);
+  w->blk_order = (int32_t*)at(nc * 4);
   w->pair_rec_count = (unsigned long long*)at(8);
   w->pair_rec_cap = s->pair_rec_cap;
   w->pair_recs = s->pair_rec_cap > 0 ? (sdpd_pair_rec*)at((size_t)s->pair_rec_cap * sizeof(sdpd_pair_rec)) : nullptr;
@@ -319,9 +321,9 @@ void fd_sweep_step(sdpd_handle* s, double dt_fd, uint64_t seed) {
   const int rec = s->w.pair_recs != nullptr;
   if (rec) cudaMemsetAsync(s->w.pair_rec_count, 0, 8, s->stream);
   if (!s->sched_valid) {  // positions unchanged since the last sweep: reuse it
-    StageTimer t(s, 4, 3);
+    StageTimer t(s, 4, 5);
     launch_fd_schedule<P>(c, s->w, s->cur, s->stream);
-    s->launches += 3;
+    s->launches += 5;
     s->sched_valid = true;
   }
   {

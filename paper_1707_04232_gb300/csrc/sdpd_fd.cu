@@ -27,7 +27,8 @@
 // positions only, which are fixed during the sweep): k_sched_enum (one warp
 // per block: owned pairs in canonical order), k_sched_walk (one thread per
 // block: the dependency level of every pair) and k_sched_bucket (one warp per
-// block: pairs bucketed by level); then k_fd_colour (sdpd_fd_colour.cuh)
+// block: pairs bucketed by level); two more order each colour's blocks by
+// depth (k_sched_order_scan, k_sched_order_scatter); then k_fd_colour (sdpd_fd_colour.cuh)
 // runs once per colour: the pair updates level by level in shared memory,
 // one or two blocks per warp as the launch's block schedule says.
 #include "sdpd_fd_common.cuh"
@@ -66,9 +67,12 @@ template <class P>
 __global__ void __launch_bounds__(kSchedWarps * 32)
     k_sched_enum(Consts c, Arrays<P> a, const int32_t* __restrict__ cell_start, const int32_t* __restrict__ mrank,
                  const uint32_t* __restrict__ nlist, const uint8_t* __restrict__ nbr_off,
-                 uint32_t* __restrict__ hdr, uint16_t* __restrict__ canon, int* status) {
+                 uint32_t* __restrict__ hdr, uint16_t* __restrict__ canon, int* status,
+                 uint32_t* __restrict__ blk_hist) {
   __shared__ SchedSmem sm_all[kSchedWarps];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (blockIdx.x == 0)  // the depth histogram that k_sched_walk fills
+    for (int k = threadIdx.x; k < 8 * 256; k += blockDim.x) blk_hist[k] = 0u;
   const int64_t o = (int64_t)blockIdx.x * kSchedWarps + warp;
   if (o >= c.ncell) return;
   SchedSmem& sm = sm_all[warp];
@@ -291,9 +295,11 @@ __global__ void __launch_bounds__(kSchedWarps * 32)
 constexpr int kLevelThreads = 32;
 constexpr int kTile = 32;
 
-__global__ void __launch_bounds__(kLevelThreads) k_sched_walk(int64_t ncell, uint32_t* __restrict__ hdr,
+__global__ void __launch_bounds__(kLevelThreads) k_sched_walk(int64_t ncell, int nc0, int nc1,
+                                                            uint32_t* __restrict__ hdr,
                                                             const uint16_t* __restrict__ canon,
-                                                            uint8_t* __restrict__ level_of, int* status) {
+                                                            uint8_t* __restrict__ level_of, int* status,
+                                                            uint32_t* __restrict__ blk_hist) {
   __shared__ uint8_t last_s[kMaxBlock][kLevelThreads];  // level after which a particle is free
   __shared__ uint16_t tile[kLevelThreads][kTile + 1];
   __shared__ uint8_t ltile[kLevelThreads][kTile + 4];
@@ -334,10 +340,58 @@ __global__ void __launch_bounds__(kLevelThreads) k_sched_walk(int64_t ncell, uin
     if (overflow) {
       atomicOr(status, kStCapacity);
       hdr[o] = 0;
+      nlev = 0;
     } else {
       hdr[o] = (uint32_t)np | ((uint32_t)nlev << 16);
     }
+    // the block's colour is the parity pattern of its owner cell
+    const int ox = (int)(o % nc0), oy = (int)((o / nc0) % nc1), oz = (int)(o / ((int64_t)nc0 * nc1));
+    const int colour = (ox & 1) | ((oy & 1) << 1) | ((oz & 1) << 2);
+    atomicAdd(&blk_hist[colour * 256 + nlev], 1u);
   }
+}
+
+// ---------------------------------------------------------------------------
+// The order in which a colour launch hands out its blocks: deepest first.
+// Each warp of a colour launch runs its blocks in lockstep and pays for the
+// deepest, so neighbours in this order have similar depth, and the deep
+// blocks start first, which keeps the launch's tail short.  Blocks of a colour
+// are independent, so the order changes no result.
+// Step 1 (8 thread blocks of 256, one per colour): the depth histogram turned
+// into each depth's first position, deepest first.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_sched_order_scan(uint32_t* __restrict__ blk_hist) {
+  __shared__ uint32_t warp_sum[8];
+  const int t = threadIdx.x, lane = t & 31, wp = t >> 5;
+  uint32_t* h = blk_hist + blockIdx.x * 256;
+  const uint32_t v = h[255 - t];  // thread t takes depth 255 - t
+  uint32_t incl = v;
+#pragma unroll
+  for (int sh = 1; sh < 32; sh <<= 1) {
+    const uint32_t x = __shfl_up_sync(0xffffffffu, incl, sh);
+    if (lane >= sh) incl += x;
+  }
+  if (lane == 31) warp_sum[wp] = incl;
+  __syncthreads();
+  uint32_t before = 0;
+  for (int k = 0; k < wp; ++k) before += warp_sum[k];
+  __syncthreads();
+  h[255 - t] = before + incl - v;
+}
+
+// Step 2 (one thread per owner cell): each block's place in its colour's
+// order, by depth; the order among blocks of equal depth is free.
+__global__ void k_sched_order_scatter(int64_t ncell, int nc0, int nc1, const uint32_t* __restrict__ hdr,
+                                      uint32_t* __restrict__ blk_hist, int32_t* __restrict__ blk_order) {
+  const int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (o >= ncell) return;
+  const int ox = (int)(o % nc0), oy = (int)((o / nc0) % nc1), oz = (int)(o / ((int64_t)nc0 * nc1));
+  const int colour = (ox & 1) | ((oy & 1) << 1) | ((oz & 1) << 2);
+  const int hx = nc0 >> 1, hy = nc1 >> 1;
+  const int32_t w = (ox >> 1) + hx * ((oy >> 1) + hy * (oz >> 1));  // index among the colour's blocks
+  const int nlev = (int)(hdr[o] >> 16);
+  const uint32_t pos = atomicAdd(&blk_hist[colour * 256 + nlev], 1u);
+  blk_order[colour * (ncell >> 3) + pos] = w;
 }
 
 // Levels, step 2: one warp per block buckets the canonical list by level
@@ -401,11 +455,14 @@ void launch_fd_schedule(const Consts& c, const Workspace& w, int cur, cudaStream
   uint16_t* canon = w.sched_pair + (size_t)c.ncell * kMaxPairs;
   const unsigned gs = (unsigned)((c.ncell + kSchedWarps - 1) / kSchedWarps);
   k_sched_enum<P><<<gs, kSchedWarps * 32, 0, s>>>(c, a, w.cell_start, w.mrank, w.nlist, w.nbr_off,
-                                                   w.sched_hdr, canon, w.status);
+                                                   w.sched_hdr, canon, w.status, w.blk_hist);
   k_sched_walk<<<(unsigned)((c.ncell + kLevelThreads - 1) / kLevelThreads), kLevelThreads, 0, s>>>(
-      c.ncell, w.sched_hdr, canon, w.level_of, w.status);
+      c.ncell, c.nc[0], c.nc[1], w.sched_hdr, canon, w.level_of, w.status, w.blk_hist);
   k_sched_bucket<<<(unsigned)((c.ncell + kBucketWarps - 1) / kBucketWarps), kBucketWarps * 32, 0, s>>>(
       c.ncell, w.sched_hdr, canon, w.level_of, w.sched_lvl, w.sched_pair);
+  k_sched_order_scan<<<8, 256, 0, s>>>(w.blk_hist);
+  k_sched_order_scatter<<<(unsigned)((c.ncell + 255) / 256), 256, 0, s>>>(c.ncell, c.nc[0], c.nc[1], w.sched_hdr,
+                                                                         w.blk_hist, w.blk_order);
 }
 
 __global__ void k_sweep_set(unsigned long long* sweep, unsigned long long v) { *sweep = v; }

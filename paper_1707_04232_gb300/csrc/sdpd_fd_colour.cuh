@@ -277,7 +277,8 @@ __global__ void __launch_bounds__(W * 32, fd_min_blocks<A, W>())
                 const uint32_t* __restrict__ xmz, const uint32_t* __restrict__ hdr,
                 const uint16_t* __restrict__ lvl, const uint16_t* __restrict__ pairs, int colour, uint64_t seed,
                 const unsigned long long* __restrict__ sweep_ptr, unsigned long long* counters, int* status,
-                sdpd_pair_rec* recs, unsigned long long* rec_count, int64_t rec_cap, unsigned* __restrict__ queue) {
+                sdpd_pair_rec* recs, unsigned long long* rec_count, int64_t rec_cap, unsigned* __restrict__ queue,
+                const int32_t* __restrict__ order) {
   using R = typename A::R;  // pair arithmetic
   using S = typename P::R;  // stored momenta, densities, geometry
   constexpr bool kSame = std::is_same<R, S>::value;
@@ -296,14 +297,17 @@ __global__ void __launch_bounds__(W * 32, fd_min_blocks<A, W>())
   // The grid holds as many thread blocks as fit on the GPU at once; each
   // warp takes the colour's blocks OPW at a time from queue[0] until they
   // run out, so no partial last wave of thread blocks idles the GPU and
-  // blocks of uneven depth balance out.  queue[1] counts the warps that are
-  // done; the last one sets both back to zero for the next launch.
+  // blocks of uneven depth balance out.  The blocks come in the order of
+  // `order` (deepest first), so the blocks a warp runs in lockstep have
+  // similar depth.  queue[1] counts the warps that are done; the last one
+  // sets both back to zero for the next launch.
   for (;;) {
     unsigned w0 = 0;
     if (lane == 0) w0 = atomicAdd(queue, (unsigned)OPW);
     w0 = __shfl_sync(0xffffffffu, w0, 0);
     if ((int64_t)w0 >= nown) break;
-    const int64_t w = (int64_t)w0 + grp;
+    const int64_t wi = (int64_t)w0 + grp;
+    const int64_t w = wi < nown ? (int64_t)order[colour * nown + wi] : nown;
     int np = 0, nlev = 0;
     int64_t o = 0;
     int ox = 0, oy = 0, oz = 0;
@@ -555,7 +559,7 @@ void launch_colour(const Consts& c, const FDConst<typename A::R>& k, const Array
     k_fd_colour<P, A, KIND, OPW, W><<<gf, W * 32, 0, s>>>(
         c, k, a, (typename P::V4*)w.qp4, w.cell_start, w.mrank, w.xmin[0], w.xmin[1], w.xmin[2], w.sched_hdr,
         w.sched_lvl, w.sched_pair, col, seed, w.sweep, w.counters, w.status, recs, w.pair_rec_count,
-        w.pair_rec_cap, w.fd_queue + 2 * col);
+        w.pair_rec_cap, w.fd_queue + 2 * col, w.blk_order);
   }
 }
 

@@ -306,6 +306,8 @@ struct Workspace {
   unsigned long long* counters;  // [4]: pairs, accept, reject bound, reject metropolis
   unsigned long long* sweep;     // sweep counter: the random-number step of the next sweep
   int* status;
+  uint32_t* blk_hist;            // [8][256]: blocks of each colour by dependency depth, then cursors
+  int32_t* blk_order;            // [8][ncell / 8]: each colour's blocks, deepest first
   unsigned* fd_queue;            // [8][2]: next block and finished warps of each colour launch;
                                  // zero between launches
   sdpd_pair_rec* pair_recs;   // debug

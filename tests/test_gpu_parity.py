@@ -271,7 +271,7 @@ def test_fd_only_sweeps_reuse_the_schedule(precision):
     s.reset_counters()
     l0 = s.kernel_launches
     s.step(0.2, 4, seed=5)
-    assert s.kernel_launches - l0 == 3 + 4 * 9  # one schedule, four sweeps
+    assert s.kernel_launches - l0 == 5 + 4 * 9  # one schedule, four sweeps
     qg, pg, eg = s.get_state()
     P = oparams(N, L, K)
     st, qo, po, eo, stats, _ = O.run(P, q, p, e, 0.2, 4, seed=5, fd_only=True)

@@ -147,17 +147,19 @@ def check_sweep_against_oracle(recs_g, recs_o, tol_flip=1e-9):
 
 
 @pytest.mark.parametrize("scheme", [sdpd.SCHEME_EMS, sdpd.SCHEME_AMS, sdpd.SCHEME_SSA])
-@pytest.mark.parametrize("kind", ["lattice1000", "random_rect", "lattice_cold_K5"])
-def test_fd_sweep_fp64_matches_oracle(kind, scheme):
+@pytest.mark.parametrize("kind,kernel", [("lattice1000", sdpd.KERNEL_LUCY), ("random_rect", sdpd.KERNEL_LUCY),
+                                         ("lattice_cold_K5", sdpd.KERNEL_LUCY),
+                                         ("random_rect", sdpd.KERNEL_CUBIC)])
+def test_fd_sweep_fp64_matches_oracle(kind, kernel, scheme):
     q, p, e, L, K = system(kind)
     N = len(e)
     dt = 0.05 if kind == "lattice_cold_K5" else DT
-    s = gpu(N, L, K, scheme=scheme, fd_only=True, debug=True)
+    s = gpu(N, L, K, scheme=scheme, kernel=kernel, fd_only=True, debug=True)
     s.set_state(q, p, e)
     s.step(dt, 1, seed=77)
     qg, pg, eg = s.get_state()
     recs = s.pair_records()
-    P = oparams(N, L, K, scheme=scheme)
+    P = oparams(N, L, K, kernel=kernel, scheme=scheme)
     st, po, eo, stats, recs_o = O.fd_sweep(P, q, p, e, dt, 77, 0, records=True)
     flips = check_sweep_against_oracle(recs, recs_o)
     obs = s.observables(check=False)
@@ -219,19 +221,20 @@ def test_fd_sweep_mixed_metropolis_ratio_accuracy(dt):
 # Full steps
 # --------------------------------------------------------------------------
 
-@pytest.mark.parametrize("kind,scheme,theta", [("lattice1000", sdpd.SCHEME_EMS, 1),
-                                               ("lattice1000", sdpd.SCHEME_AMS, 1),
-                                               ("random_rect", sdpd.SCHEME_EMS, 1),
-                                               ("lattice1000", sdpd.SCHEME_EMS, 5),
-                                               ("lattice1000", sdpd.SCHEME_NONE, 1)])
-def test_trajectory_fp64_10_steps(kind, scheme, theta):
+@pytest.mark.parametrize("kind,scheme,theta,kernel", [("lattice1000", sdpd.SCHEME_EMS, 1, sdpd.KERNEL_LUCY),
+                                                      ("lattice1000", sdpd.SCHEME_AMS, 1, sdpd.KERNEL_LUCY),
+                                                      ("random_rect", sdpd.SCHEME_EMS, 1, sdpd.KERNEL_LUCY),
+                                                      ("lattice1000", sdpd.SCHEME_EMS, 5, sdpd.KERNEL_LUCY),
+                                                      ("lattice1000", sdpd.SCHEME_NONE, 1, sdpd.KERNEL_LUCY),
+                                                      ("random_rect", sdpd.SCHEME_EMS, 1, sdpd.KERNEL_CUBIC)])
+def test_trajectory_fp64_10_steps(kind, scheme, theta, kernel):
     q, p, e, L, K = system(kind)
     N = len(e)
-    s = gpu(N, L, K, scheme=scheme, theta=theta)
+    s = gpu(N, L, K, scheme=scheme, theta=theta, kernel=kernel)
     s.set_state(q, p, e)
     s.step(DT, 10, seed=3)
     qg, pg, eg = s.get_state()
-    P = oparams(N, L, K, scheme=scheme)
+    P = oparams(N, L, K, kernel=kernel, scheme=scheme)
     st, qo, po, eo, stats, nfd = O.run(P, q, p, e, DT, 10, seed=3, theta=theta)
     assert st == O.OK
     assert min_image_err(qg, qo, L) < 1e-6

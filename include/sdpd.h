@@ -308,7 +308,8 @@ int sdpd_set_tuning(sdpd_t* s, const sdpd_tuning* t);
  * warm-up step and `steps` (1..1000) timed steps of dt from the same state,
  * timed with CUDA events on the handle's stream.  The loaded state, the step
  * counters, the random-number counter and the pair counters are restored
- * afterwards, so the next sdpd_step continues as if nothing had run.
+ * afterwards, so the next sdpd_step continues as if nothing had run (only
+ * the per-pair debug records, when reserved, are those of the last trial).
  * best / ms_per_step (may be NULL) receive the chosen shapes and their time
  * per step.  Synchronising.  Errors: SDPD_ERR_INVALID_ARG, SDPD_ERR_NO_STATE,
  * SDPD_ERR_NO_WORKSPACE, SDPD_ERR_CUDA, or the sticky device status if the

@@ -44,6 +44,7 @@ extern "C" {
 #define SDPD_ERR_NO_WORKSPACE 8       /* no (or too small a) workspace is bound */
 #define SDPD_ERR_CAPACITY 9           /* a 2x2x2 cell block exceeded its particle/pair capacity */
 #define SDPD_ERR_NO_STATE 10          /* sdpd_step/get_state before sdpd_set_state */
+#define SDPD_ERR_HOST_MEMORY 11       /* a host-side table could not be allocated */
 
 /* smoothing kernels */
 #define SDPD_KERNEL_CUBIC 0 /* cubic spline, Eq. (sdpd-cubic-w) */
@@ -115,7 +116,9 @@ typedef struct {
  * d_ij < 1 in Eq. (sdpd-gamma-sigma); every box side gives an even number
  * >= 4 of cells of side >= h), chooses the cell grid and the workspace size.
  * stream: a cudaStream_t (NULL = the legacy default stream).
- * Errors: SDPD_ERR_INVALID_ARG, SDPD_ERR_BOX_TOO_SMALL.  *out is NULL on error. */
+ * Errors: SDPD_ERR_INVALID_ARG, SDPD_ERR_BOX_TOO_SMALL, SDPD_ERR_HOST_MEMORY
+ * (the per-cell tables, 4 + 4 + 16 bytes per cell, do not fit in host
+ * memory).  *out is NULL on error. */
 int sdpd_create(int64_t N, const double box[3], double m, double h, const sdpd_params* params,
                 double K, void* stream, sdpd_t** out);
 
@@ -212,8 +215,9 @@ int sdpd_energy_histogram(sdpd_t* s, double lo, double hi, int nbins, double sca
  *  SDPD_DEBUG_PAIRS   sdpd_pair_rec[] of the last sweep (needs params.debug = 1),
  *                     one per pair in an order of the library's choosing
  * dst: host memory, cap = capacity in elements; *count receives the number
- * of elements written.  Errors: SDPD_ERR_INVALID_ARG (unknown what or too
- * small cap), SDPD_ERR_NO_STATE. */
+ * of elements written.  The capacity is checked before anything is copied.
+ * Errors: SDPD_ERR_INVALID_ARG (unknown what or too small cap),
+ * SDPD_ERR_NO_STATE, SDPD_ERR_HOST_MEMORY (staging buffers of N elements). */
 #define SDPD_DEBUG_ORDER 0
 #define SDPD_DEBUG_CELLS 1
 #define SDPD_DEBUG_RHO 2
@@ -254,8 +258,9 @@ void sdpd_destroy(sdpd_t* s);
  * streams wait for the ensemble's work before later calls on them run.
  * Asynchronous.
  * Errors: SDPD_ERR_INVALID_ARG (bad or repeated member, a member on the
- * ensemble's stream, timing or debug on, U > 64), SDPD_ERR_NO_WORKSPACE,
- * SDPD_ERR_CUDA. */
+ * ensemble's stream, members' workspaces on different devices, timing or
+ * debug on, U > 64), SDPD_ERR_NO_WORKSPACE, SDPD_ERR_CUDA,
+ * SDPD_ERR_HOST_MEMORY. */
 typedef struct sdpd_ensemble sdpd_ens_t;
 int sdpd_ensemble_create(sdpd_t* const* members, int n, void* stream, sdpd_ens_t** out);
 int sdpd_ensemble_step(sdpd_ens_t* e, double dt, int64_t nsteps, const uint64_t* seeds);

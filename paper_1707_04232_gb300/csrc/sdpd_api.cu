@@ -382,6 +382,7 @@ const char* sdpd_strerror(int st) {
     case SDPD_ERR_NO_WORKSPACE: return "no or too small workspace bound";
     case SDPD_ERR_CAPACITY: return "a 2x2x2 cell block exceeded its particle or pair capacity";
     case SDPD_ERR_NO_STATE: return "no state loaded";
+    case SDPD_ERR_HOST_MEMORY: return "host memory allocation failed";
     default: return "unknown status";
   }
 }
@@ -482,9 +483,16 @@ int sdpd_create(int64_t N, const double box[3], double m, double h, const sdpd_p
   s->device = -1;
   for (int k = 0; k < SDPD_NSTAGES; ++k) { s->stage_ms[k] = 0.0; s->stage_launches[k] = 0; }
   // Morton order of the cells: rank of every cell, and the cell of every rank
-  s->mrank_h.resize((size_t)ncell);
-  s->rcoord_h.resize((size_t)ncell);
-  std::vector<std::pair<uint64_t, int64_t>> codes((size_t)ncell);
+  std::vector<std::pair<uint64_t, int64_t>> codes;
+  try {
+    s->mrank_h.resize((size_t)ncell);
+    s->rcoord_h.resize((size_t)ncell);
+    codes.resize((size_t)ncell);
+    for (int d = 0; d < 3; ++d) s->xmin_h[d].resize((size_t)c.nc[d]);
+  } catch (const std::bad_alloc&) {
+    delete s;
+    return SDPD_ERR_HOST_MEMORY;
+  }
   for (int z = 0; z < c.nc[2]; ++z)
     for (int y = 0; y < c.nc[1]; ++y)
       for (int x = 0; x < c.nc[0]; ++x) {
@@ -500,7 +508,6 @@ int sdpd_create(int64_t N, const double box[3], double m, double h, const sdpd_p
   }
   // fixed-point lower edge of each cell: ceil(c 2^32 / n_c)
   for (int d = 0; d < 3; ++d) {
-    s->xmin_h[d].resize((size_t)c.nc[d]);
     for (int k = 0; k < c.nc[d]; ++k) {
       uint64_t num = ((uint64_t)k << 32) + (uint64_t)c.nc[d] - 1;
       s->xmin_h[d][(size_t)k] = (uint32_t)(num / (uint64_t)c.nc[d]);
@@ -1145,22 +1152,28 @@ int sdpd_energy_histogram(sdpd_t* s, double lo, double hi, int nbins, double sca
   return launch_status();
 }
 
-int sdpd_debug_get(sdpd_t* s, int what, void* dst, int64_t cap, int64_t* count) {
-  if (!s || !dst) return SDPD_ERR_INVALID_ARG;
-  if (!s->ws) return SDPD_ERR_NO_WORKSPACE;
-  if (use_device(s) != SDPD_OK) return SDPD_ERR_CUDA;
-  if (!s->has_state) return SDPD_ERR_NO_STATE;
+}  // extern "C"
+
+namespace {
+
+// Body of sdpd_debug_get.  Every host staging buffer is allocated after the
+// capacity check, and every copy into one is synchronised before it is read
+// or goes out of scope.
+int debug_get(sdpd_handle* s, int what, void* dst, int64_t cap, int64_t* count) {
   const int64_t N = s->c.N;
   const bool mixed = s->prm.precision == SDPD_MIXED;
   cudaStream_t st = s->stream;
   const int cur = s->cur;
-  if (count) *count = 0;
-  std::vector<int32_t> ids((size_t)N);
-  if (N > 0 && cudaMemcpyAsync(ids.data(), s->w.id[cur], (size_t)N * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess)
-    return SDPD_ERR_CUDA;
+  std::vector<int32_t> ids;
+  // ids in storage order, copied asynchronously; the caller synchronises
+  auto fetch_ids = [&]() -> bool {
+    ids.resize((size_t)N);
+    return N == 0 || cudaMemcpyAsync(ids.data(), s->w.id[cur], (size_t)N * 4, cudaMemcpyDeviceToHost, st) == cudaSuccess;
+  };
   switch (what) {
     case SDPD_DEBUG_ORDER: {
       if (cap < N) return SDPD_ERR_INVALID_ARG;
+      if (!fetch_ids()) return SDPD_ERR_CUDA;
       if (cudaStreamSynchronize(st) != cudaSuccess) return SDPD_ERR_CUDA;
       int64_t* o = (int64_t*)dst;
       for (int64_t t = 0; t < N; ++t) o[t] = ids[(size_t)t];
@@ -1171,8 +1184,11 @@ int sdpd_debug_get(sdpd_t* s, int what, void* dst, int64_t cap, int64_t* count) 
       if (cap < N) return SDPD_ERR_INVALID_ARG;
       const size_t rec = mixed ? 16 : 32;
       std::vector<unsigned char> q4((size_t)N * rec);
-      if (N > 0 && cudaMemcpyAsync(q4.data(), s->w.q4[cur], (size_t)N * rec, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+      if (!fetch_ids()) return SDPD_ERR_CUDA;
+      if (N > 0 && cudaMemcpyAsync(q4.data(), s->w.q4[cur], (size_t)N * rec, cudaMemcpyDeviceToHost, st) != cudaSuccess) {
+        cudaStreamSynchronize(st);
         return SDPD_ERR_CUDA;
+      }
       if (cudaStreamSynchronize(st) != cudaSuccess) return SDPD_ERR_CUDA;
       int32_t* o = (int32_t*)dst;
       for (int64_t t = 0; t < N; ++t) {
@@ -1197,14 +1213,20 @@ int sdpd_debug_get(sdpd_t* s, int what, void* dst, int64_t cap, int64_t* count) 
       double* o = (double*)dst;
       if (mixed) {
         std::vector<float> r((size_t)N);
-        if (N > 0 && cudaMemcpyAsync(r.data(), s->w.rho[cur], (size_t)N * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        if (!fetch_ids()) return SDPD_ERR_CUDA;
+        if (N > 0 && cudaMemcpyAsync(r.data(), s->w.rho[cur], (size_t)N * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess) {
+          cudaStreamSynchronize(st);
           return SDPD_ERR_CUDA;
+        }
         if (cudaStreamSynchronize(st) != cudaSuccess) return SDPD_ERR_CUDA;
         for (int64_t t = 0; t < N; ++t) o[ids[(size_t)t]] = r[(size_t)t];
       } else {
         std::vector<double> r((size_t)N);
-        if (N > 0 && cudaMemcpyAsync(r.data(), s->w.rho[cur], (size_t)N * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        if (!fetch_ids()) return SDPD_ERR_CUDA;
+        if (N > 0 && cudaMemcpyAsync(r.data(), s->w.rho[cur], (size_t)N * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess) {
+          cudaStreamSynchronize(st);
           return SDPD_ERR_CUDA;
+        }
         if (cudaStreamSynchronize(st) != cudaSuccess) return SDPD_ERR_CUDA;
         for (int64_t t = 0; t < N; ++t) o[ids[(size_t)t]] = r[(size_t)t];
       }
@@ -1247,6 +1269,24 @@ int sdpd_debug_get(sdpd_t* s, int what, void* dst, int64_t cap, int64_t* count) 
     }
     default:
       return SDPD_ERR_INVALID_ARG;
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+int sdpd_debug_get(sdpd_t* s, int what, void* dst, int64_t cap, int64_t* count) {
+  if (!s || !dst) return SDPD_ERR_INVALID_ARG;
+  if (!s->ws) return SDPD_ERR_NO_WORKSPACE;
+  if (use_device(s) != SDPD_OK) return SDPD_ERR_CUDA;
+  if (!s->has_state) return SDPD_ERR_NO_STATE;
+  if (count) *count = 0;
+  try {
+    return debug_get(s, what, dst, cap, count);
+  } catch (const std::bad_alloc&) {
+    cudaStreamSynchronize(s->stream);
+    return SDPD_ERR_HOST_MEMORY;
   }
 }
 
@@ -1315,12 +1355,21 @@ int sdpd_ensemble_create(sdpd_t* const* members, int n, void* stream, sdpd_ens_t
   e->graph = nullptr;
   e->exec = nullptr;
   e->dt = 0.0;
+  try {
+    e->m.reserve((size_t)n);
+    e->join.assign((size_t)n, nullptr);
+  } catch (const std::bad_alloc&) {
+    delete e;
+    return SDPD_ERR_HOST_MEMORY;
+  }
   for (int i = 0; i < n; ++i) {
     sdpd_handle* h = members[i];
     if (!h || !h->ws || !h->has_state || h->timing || h->w.pair_recs || h->stream == e->stream) {
       delete e;
       return !h || h->ws ? SDPD_ERR_INVALID_ARG : SDPD_ERR_NO_WORKSPACE;
     }
+    // one graph runs on one device: every member's workspace on the first's
+    if (h->device != members[0]->device) { delete e; return SDPD_ERR_INVALID_ARG; }
     for (int j = 0; j < i; ++j)
       if (members[j] == h) { delete e; return SDPD_ERR_INVALID_ARG; }
     e->m.push_back(h);
@@ -1343,8 +1392,13 @@ int sdpd_ensemble_create(sdpd_t* const* members, int n, void* stream, sdpd_ens_t
     }
     e->own_stream = true;
   }
-  e->join.resize((size_t)n);
-  for (int i = 0; i < n; ++i) cudaEventCreateWithFlags(&e->join[(size_t)i], cudaEventDisableTiming);
+  for (int i = 0; i < n; ++i) {
+    if (cudaEventCreateWithFlags(&e->join[(size_t)i], cudaEventDisableTiming) != cudaSuccess) {
+      e->join[(size_t)i] = nullptr;
+      sdpd_ensemble_destroy(e);
+      return SDPD_ERR_CUDA;
+    }
+  }
   *out = e;
   return SDPD_OK;
 }
@@ -1513,7 +1567,8 @@ void sdpd_ensemble_destroy(sdpd_ens_t* e) {
   if (e->exec) cudaGraphExecDestroy(e->exec);
   if (e->graph) cudaGraphDestroy(e->graph);
   cudaEventDestroy(e->fork);
-  for (cudaEvent_t ev : e->join) cudaEventDestroy(ev);
+  for (cudaEvent_t ev : e->join)
+    if (ev) cudaEventDestroy(ev);
   if (e->own_stream) cudaStreamDestroy(e->stream);
   delete e;
 }

@@ -16,6 +16,7 @@ from . import build as _build
 OK = 0
 ERR_INVALID_ARG, ERR_BOX_TOO_SMALL, ERR_NONPOSITIVE_ENERGY, ERR_NEGATIVE_ENERGY = 1, 2, 3, 4
 ERR_NAN, ERR_CUDA, ERR_TIMEOUT, ERR_NO_WORKSPACE, ERR_CAPACITY, ERR_NO_STATE = 5, 6, 7, 8, 9, 10
+ERR_HOST_MEMORY = 11
 KERNEL_CUBIC, KERNEL_LUCY = 0, 1
 SCHEME_SSA, SCHEME_AMS, SCHEME_EMS, SCHEME_NONE = 0, 1, 2, 3
 FP64, MIXED = 0, 1

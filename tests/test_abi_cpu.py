@@ -79,8 +79,28 @@ def test_workspace_scales_with_precision():
 
 
 def test_strerror_covers_codes():
-    for code in range(11):
+    for code in range(12):
         assert sdpd.sdpd_strerror(code) != "unknown status"
+    assert sdpd.sdpd_strerror(12) == "unknown status"
+
+
+def test_status_codes_match_the_header():
+    text = open(os.path.join(ROOT, "include", "sdpd.h")).read()
+    codes = dict(re.findall(r"#define SDPD_(OK|ERR_[A-Z_]+) (\d+)", text))
+    assert len(codes) == 12
+    for name, value in codes.items():
+        assert getattr(sdpd, name) == int(value), name
+
+
+def test_debug_read_out_refused_without_workspace():
+    lib = sdpd.load()
+    st, h = sdpd.sdpd_create(1000, (10.0,) * 3, 1.0, 2.5, _params(), 100.0, 0)
+    assert st == sdpd.OK
+    buf = (C.c_int64 * 1000)()
+    n = C.c_int64(-1)
+    assert lib.sdpd_debug_get(h, 0, buf, 1000, C.byref(n)) == sdpd.ERR_NO_WORKSPACE
+    assert lib.sdpd_debug_get(h, 0, None, 1000, C.byref(n)) == sdpd.ERR_INVALID_ARG
+    sdpd.sdpd_destroy(h)
 
 
 def test_float32_sweep_flag_on_host():

@@ -477,3 +477,28 @@ def test_device_state_io_matches_host_io():
     b.get_state_device(qd, pd, ed)
     qa, pa, ea = a.get_state()
     assert (qd.cpu().numpy() == qa).all() and (pd.cpu().numpy() == pa).all() and (ed.cpu().numpy() == ea).all()
+
+
+def test_debug_read_outs_refuse_a_short_buffer_untouched():
+    """Every debug read-out checks the caller's capacity before it copies
+    anything: one element short, the call fails with SDPD_ERR_INVALID_ARG,
+    writes nothing and leaves the handle usable."""
+    q, p, e, L, K = system("random_rect")
+    N = len(e)
+    s = gpu(N, L, K, precision=sdpd.MIXED)
+    s.set_state(q, p, e)
+    s.step(DT, 2, seed=6)
+    cases = [(sdpd.DEBUG_ORDER, np.int64, N, s.order),
+             (sdpd.DEBUG_CELLS, np.int32, 3 * N, s.cells),
+             (sdpd.DEBUG_RHO, np.float64, N, s.density),
+             (sdpd.DEBUG_FORCE, np.float64, 3 * N, s.forces),
+             (sdpd.DEBUG_NCOUNT, np.int32, N, s.neighbour_counts)]
+    for what, dtype, size, full in cases:
+        cap = N - 1 if what != sdpd.DEBUG_FORCE else 3 * N - 1
+        buf = np.full(size, 7, dtype=dtype)
+        st, n = sdpd.sdpd_debug_get(s.h, what, buf.ctypes.data, cap)
+        assert st == sdpd.ERR_INVALID_ARG and n == 0, what
+        assert (buf == 7).all(), what
+        assert full().size == size, what
+    assert s.observables()["status"] == sdpd.OK
+    assert sdpd.sdpd_debug_get(s.h, 99, np.zeros(N).ctypes.data, N)[0] == sdpd.ERR_INVALID_ARG

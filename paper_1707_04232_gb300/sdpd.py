@@ -290,6 +290,43 @@ def _ptr(a) -> int:
     return a.data_ptr()
 
 
+def _state_shapes(N):
+    return ((N, 3), (N, 3), (N,))
+
+
+def _as_state(N, q, p, eps):
+    """(q, p, eps, on_device) for N particles.  CUDA tensors become contiguous
+    float64 CUDA tensors (on_device = 1); anything else (numpy arrays, CPU
+    tensors, sequences) becomes contiguous float64 numpy arrays.  The library
+    reads exactly N x 3, N x 3 and N doubles, so any other shape, or a mix of
+    host and device inputs, raises ValueError."""
+    arrs = (q, p, eps)
+    cuda = [bool(getattr(a, "is_cuda", False)) for a in arrs]
+    if any(cuda) and not all(cuda):
+        raise ValueError("q, p and eps must be all CUDA tensors or all host arrays")
+    out = []
+    for name, a, shape in zip(("q", "p", "eps"), arrs, _state_shapes(N)):
+        if cuda[0]:
+            a = a.detach().contiguous().double()
+        else:
+            if hasattr(a, "detach"):
+                a = a.detach().cpu().numpy()
+            a = np.ascontiguousarray(a, dtype=np.float64)
+        if tuple(a.shape) != shape:
+            raise ValueError("%s has shape %s, expected %s" % (name, tuple(a.shape), shape))
+        out.append(a)
+    return out[0], out[1], out[2], int(cuda[0])
+
+
+def _check_device_out(N, device, q, p, eps):
+    """Destination tensors of a device-side state copy: float64, contiguous,
+    on the handle's device, shapes N x 3, N x 3, N."""
+    for name, a, shape in zip(("q", "p", "eps"), (q, p, eps), _state_shapes(N)):
+        if (not getattr(a, "is_cuda", False) or a.device != device or str(a.dtype) != "torch.float64"
+                or not a.is_contiguous() or tuple(a.shape) != shape):
+            raise ValueError("%s must be a contiguous float64 tensor of shape %s on %s" % (name, shape, device))
+
+
 class SDPD:
     """One SDPD system on the current CUDA device.
 
@@ -331,15 +368,14 @@ class SDPD:
             self.h = None
 
     def set_state(self, q, p, eps):
-        if isinstance(q, np.ndarray):
-            q = np.ascontiguousarray(q, dtype=np.float64)
-            p = np.ascontiguousarray(p, dtype=np.float64)
-            eps = np.ascontiguousarray(eps, dtype=np.float64)
-            _check(sdpd_set_state(self.h, _ptr(q), _ptr(p), _ptr(eps), 0), "sdpd_set_state")
-        else:
-            q, p, eps = (t.contiguous().double() for t in (q, p, eps))
-            _check(sdpd_set_state(self.h, _ptr(q), _ptr(p), _ptr(eps), 1), "sdpd_set_state")
+        """Load positions [N,3], momenta [N,3] and internal energies [N] in id
+        order, from host arrays or from CUDA tensors on the handle's device."""
+        q, p, eps, on_device = _as_state(self.N, q, p, eps)
+        if on_device:
+            if q.device != self.workspace.device:
+                raise ValueError("state tensors are on %s, the handle on %s" % (q.device, self.workspace.device))
             self._keep = (q, p, eps)
+        _check(sdpd_set_state(self.h, _ptr(q), _ptr(p), _ptr(eps), on_device), "sdpd_set_state")
 
     def get_state(self):
         q = np.empty((self.N, 3))
@@ -350,6 +386,7 @@ class SDPD:
 
     def get_state_device(self, q, p, eps):
         """Copy the state into float64 CUDA tensors (id order); synchronises."""
+        _check_device_out(self.N, self.workspace.device, q, p, eps)
         _check(sdpd_get_state(self.h, _ptr(q), _ptr(p), _ptr(eps), 1), "sdpd_get_state")
 
     def step(self, dt, nsteps=1, seed=0):
@@ -364,6 +401,10 @@ class SDPD:
         tensor of nbins + 2 entries (allocated zeroed when None); returns it."""
         if counts is None:
             counts = self.torch.zeros(nbins + 2, dtype=self.torch.int64, device=self.workspace.device)
+        elif (counts.device != self.workspace.device or counts.dtype != self.torch.int64
+              or not counts.is_contiguous() or counts.numel() < int(nbins) + 2):
+            raise ValueError("counts must be a contiguous int64 tensor of nbins + 2 entries on %s"
+                             % self.workspace.device)
         _check(load().sdpd_energy_histogram(self.h, float(lo), float(hi), int(nbins), float(scale),
                                             counts.data_ptr()), "sdpd_energy_histogram")
         return counts
@@ -430,6 +471,9 @@ class SDPD:
         torch = self.torch
         dev = self.workspace.device
         keep = [None if g is None else g.detach().contiguous().double() for g in (gq, gp, geps)]
+        for name, g, shape in zip(("gq", "gp", "geps"), keep, _state_shapes(self.N)):
+            if g is not None and (g.device != dev or tuple(g.shape) != shape):
+                raise ValueError("%s must have shape %s on %s" % (name, shape, dev))
         ptr = [0 if g is None else g.data_ptr() for g in keep]
         gq0 = torch.empty((self.N, 3), dtype=torch.float64, device=dev)
         gp0 = torch.empty((self.N, 3), dtype=torch.float64, device=dev)

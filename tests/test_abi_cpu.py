@@ -150,3 +150,30 @@ def test_launch_shapes_on_host(precision, default, fits):
     assert lib.sdpd_autotune(h, -1.0, 2, 0, None, None) == sdpd.ERR_INVALID_ARG
     assert lib.sdpd_autotune(h, 0.005, 0, 0, None, None) == sdpd.ERR_INVALID_ARG
     sdpd.sdpd_destroy(h)
+
+
+def test_state_arrays_are_checked_before_the_library_reads_them():
+    """The binding hands the library bare pointers to N x 3, N x 3 and N
+    doubles, so it converts and checks shapes first (no device needed)."""
+    import numpy as np
+    torch = pytest.importorskip("torch")
+    N = 5
+    q, p, e = np.zeros((N, 3), np.float32), torch.ones(N, 3), [1.0] * N
+    qq, pp, ee, on_device = sdpd._as_state(N, q, p, e)
+    assert on_device == 0
+    for a, shape in zip((qq, pp, ee), ((N, 3), (N, 3), (N,))):
+        assert isinstance(a, np.ndarray) and a.dtype == np.float64 and a.shape == shape
+        assert a.flags["C_CONTIGUOUS"]
+    assert (pp == 1.0).all() and (ee == 1.0).all()
+    for bad in ((np.zeros((N - 1, 3)), p, e), (q, np.zeros(3 * N), e), (q, p, np.zeros((N, 1)))):
+        with pytest.raises(ValueError):
+            sdpd._as_state(N, *bad)
+
+    class OnDevice:  # stands in for a CUDA tensor
+        is_cuda = True
+
+    with pytest.raises(ValueError):
+        sdpd._as_state(N, OnDevice(), p, e)
+    with pytest.raises(ValueError):  # device-side outputs must be CUDA tensors
+        sdpd._check_device_out(N, torch.device("cuda", 0), torch.zeros(N, 3, dtype=torch.float64),
+                               torch.zeros(N, 3, dtype=torch.float64), torch.zeros(N, dtype=torch.float64))

@@ -502,3 +502,25 @@ def test_debug_read_outs_refuse_a_short_buffer_untouched():
         assert full().size == size, what
     assert s.observables()["status"] == sdpd.OK
     assert sdpd.sdpd_debug_get(s.h, 99, np.zeros(N).ctypes.data, N)[0] == sdpd.ERR_INVALID_ARG
+
+
+def test_binding_rejects_mis_shaped_buffers():
+    """Wrong shapes, dtypes or devices are refused before the library is
+    called, and the handle keeps its state."""
+    q, p, e, L, K = system("lattice1000")
+    N = len(e)
+    s = gpu(N, L, K)
+    s.set_state(q, p, e)
+    with pytest.raises(ValueError):
+        s.set_state(q[:-1], p[:-1], e[:-1])
+    with pytest.raises(ValueError):
+        s.set_state(torch.from_numpy(q).cuda(), p, e)
+    qd = torch.empty((N, 3), dtype=torch.float64, device="cuda")
+    with pytest.raises(ValueError):
+        s.get_state_device(qd, torch.empty((N, 3), dtype=torch.float32, device="cuda"), torch.empty(N, dtype=torch.float64, device="cuda"))
+    with pytest.raises(ValueError):
+        s.energy_histogram(0.0, 1.0, 10, counts=torch.zeros(11, dtype=torch.int64, device="cuda"))
+    # a CPU tensor is a host array, not a device pointer
+    s.set_state(torch.from_numpy(q), torch.from_numpy(p), torch.from_numpy(e))
+    q2, p2, e2 = s.get_state()
+    assert (q2 == q).all() and (p2 == p).all() and (e2 == e).all()

@@ -177,3 +177,23 @@ def test_state_arrays_are_checked_before_the_library_reads_them():
     with pytest.raises(ValueError):  # device-side outputs must be CUDA tensors
         sdpd._check_device_out(N, torch.device("cuda", 0), torch.zeros(N, 3, dtype=torch.float64),
                                torch.zeros(N, 3, dtype=torch.float64), torch.zeros(N, dtype=torch.float64))
+
+
+def test_product_path_fails_loudly_without_its_library(monkeypatch, tmp_path):
+    """No fallback: a missing CUDA library raises, and so does a handle
+    without a CUDA device; the package never imports the oracle."""
+    monkeypatch.setattr(sdpd, "_lib", None)
+    with pytest.raises(OSError):
+        sdpd.load(str(tmp_path / "libsdpd.so"))
+    monkeypatch.undo()
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        with pytest.raises(RuntimeError):
+            sdpd.SDPD(1000, 10.0)
+    pkg = os.path.join(ROOT, "paper_1707_04232_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"^\s*(import|from)\s+oracle\b", text, flags=re.M), f
+                assert "sdpd_oracle" not in text, f

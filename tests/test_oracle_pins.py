@@ -286,6 +286,45 @@ def test_fd_pair_conserves_momentum_and_energy(scheme):
     assert n_acc > 100
 
 
+def test_ams_is_ssa_with_the_energy_bound_and_ems_shares_its_proposal():
+    """Section 3.3.3: AMS takes the SSA move unless an internal energy would
+    become non-positive, and then keeps the old state; EMS uses the same
+    proposal, so every move it accepts equals AMS's, and it rejects every
+    move AMS rejects (the energy bound comes first)."""
+    rng = np.random.default_rng(21)
+    kw = dict(K=1.5)
+    Pssa, Pams, Pems = (small_cfg(scheme=sc, **kw).params() for sc in (O.SCHEME_SSA, O.SCHEME_AMS, O.SCHEME_EMS))
+    seen = {"ams_reject": 0, "ems_metropolis": 0, "accept": 0}
+    for k in range(600):
+        r, p_i, p_j, e_i, e_j = _random_pair(rng, Pssa, small_eps=(k % 3 != 0))
+        p_i, p_j = (0.05 * p_i, 0.05 * p_j) if k % 2 else (p_i, p_j)
+        G, U, dt = rng.normal(size=3), rng.uniform(), rng.choice([0.05, 0.5, 3.0])
+        args = (r, 1.0, 0.95, p_i, p_j, e_i, e_j, dt, G, U)
+        ds, _, neg, *xs = O.fd_pair(Pssa, *args)
+        da, _, _, *xa = O.fd_pair(Pams, *args)
+        de, _, _, *xe = O.fd_pair(Pems, *args)
+        assert ds == O.ACCEPT
+        ssa_ok = xs[2] > 0 and xs[3] > 0
+        if ssa_ok:
+            assert da == O.ACCEPT
+            for a, b in zip(xa, xs):
+                assert np.array_equal(a, b)
+        else:
+            assert da == O.REJECT_BOUND and neg == 1
+            assert (xa[0] == p_i).all() and (xa[1] == p_j).all() and xa[2] == e_i and xa[3] == e_j
+            seen["ams_reject"] += 1
+        if de == O.ACCEPT:
+            for a, b in zip(xe, xa):
+                assert np.array_equal(a, b)
+            seen["accept"] += 1
+        elif de == O.REJECT_BOUND:
+            assert da == O.REJECT_BOUND
+        else:
+            assert de == O.REJECT_METROPOLIS and da == O.ACCEPT
+            seen["ems_metropolis"] += 1
+    assert min(seen.values()) > 10, seen
+
+
 def test_ssa_flags_negative_energy_and_bound_rejects():
     rng = np.random.default_rng(3)
     seen_neg = seen_bound = 0

@@ -71,6 +71,11 @@ def test_perfect_lattice_density_and_neighbours():
         assert np.ptp(rho) < 1e-13
         # a lattice sum of a normalised kernel is close to the mean density m/a^3
         assert abs(rho[0] - 1.0) < 5e-3
+        # and equals the self term plus the shell table's sum (Eq. sdpd-rho-v)
+        inside = shells[shells[:, 0] < 6.25]
+        w_shells = sum(int(c) * float(O.W(kernel, np.sqrt(n2) * w.a, P.h)) for n2, c in inside)
+        exact = P.m * (float(O.W(kernel, 0.0, P.h)) + w_shells)
+        assert abs(rho[0] - exact) <= 1e-13 * exact
         assert (O.neighbour_counts(P, q) == expected).all()
         f = O.forces(P, q, rho, eps)
         assert np.abs(f).max() < 1e-12

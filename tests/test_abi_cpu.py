@@ -197,3 +197,21 @@ def test_product_path_fails_loudly_without_its_library(monkeypatch, tmp_path):
                 text = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"^\s*(import|from)\s+oracle\b", text, flags=re.M), f
                 assert "sdpd_oracle" not in text, f
+
+
+@pytest.mark.parametrize("N", [1000, 32768])
+def test_tape_size_follows_the_header_formula(N):
+    """sdpd_tape_bytes is host arithmetic: the states at the checkpoints, the
+    final state and one segment (56 B per particle each), every step's
+    increments (32 B), the reverse pass's buffers (160 B), plus alignment and
+    the reduction partials (a few KiB)."""
+    st, h = sdpd.sdpd_create(N, (32.0,) * 3, 1.0, 2.5, _params(), 100.0, 0)
+    assert st == sdpd.OK
+    for nsteps in (0, 1, 7, 100):
+        for every in (1, 3, 10, 200):
+            slots = -(-nsteps // every) + max(1, min(every, nsteps))
+            expect = (slots * 56 + max(1, nsteps) * 32 + 160) * N
+            got = sdpd.sdpd_tape_bytes(h, nsteps, every)
+            assert expect <= got <= expect + 64 * 1024, (nsteps, every, got, expect)
+    assert sdpd.sdpd_tape_bytes(h, -1, 1) == 0 and sdpd.sdpd_tape_bytes(h, 5, 0) == 0
+    sdpd.sdpd_destroy(h)

@@ -150,13 +150,14 @@ class ClockSampler:
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(self.rows)}
 
 
-def cpu_sample(args, steps: int):
-    """Time the FP64 oracle on a bounded sample of the workload: an
-    args.cpu_n^3 sub-lattice with the same density, temperature, K, dt and
-    scheme.  Returns (particle-steps/s, threads, description)."""
+def cpu_sample(args, steps: int, n: int | None = None, K: float | None = None, kT: float = 1.0):
+    """Time the FP64 oracle on a bounded sample of the workload: an n^3
+    (default args.cpu_n^3) sub-lattice with the same density, temperature,
+    K, dt and scheme.  Returns (particle-steps/s, threads, description)."""
     import oracle as O
 
-    w = Workload(n=args.cpu_n, K=args.K, kT=1.0)
+    n = args.cpu_n if n is None else n
+    w = Workload(n=n, K=args.K if K is None else K, kT=kT)
     q, p, e = lattice_state(w)
     scheme = {"ssa": O.SCHEME_SSA, "ams": O.SCHEME_AMS, "ems": O.SCHEME_EMS, "none": O.SCHEME_NONE}[args.scheme]
     P = O.Config(N=w.N, L=w.L, K=w.K, scheme=scheme).params()
@@ -166,24 +167,61 @@ def cpu_sample(args, steps: int):
     dt = time.perf_counter() - t0
     threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     desc = ("O(N^2) brute-force FP64 oracle, %d^3 = %d-particle sub-lattice of the same fluid, %d step(s), "
-            "%.1f s" % (args.cpu_n, w.N, steps, dt))
+            "%.1f s" % (n, w.N, steps, dt))
     return w.N * steps / dt, threads, desc
 
 
+# seconds of oracle work the reference arm's timed steps may take in total;
+# a larger --steps shrinks the per-step sample instead (cost ~ N^2 = n^6)
+REFERENCE_BUDGET_S = 240.0
+
+
+def _bounded_n(n: int, t_step: float, steps: int, n_min: int = 10) -> int:
+    """Largest lattice size <= n whose steps fit REFERENCE_BUDGET_S, given
+    one step's time at n (the oracle's cost grows as n^6)."""
+    if steps * t_step <= REFERENCE_BUDGET_S:
+        return n
+    return max(n_min, int(n * (REFERENCE_BUDGET_S / (steps * t_step)) ** (1.0 / 6.0)))
+
+
 def run_reference(args, rank, world):
+    """The oracle as it stands, on the host cores, for the workload's metric
+    and config: each timed step is a bounded sample of the workload (a
+    sub-lattice of the fluid, one replica-sized lattice of the ensemble, or
+    one oracle gradient).  One untimed probe step (the warm-up) sizes the
+    sample so that the timed steps stay within REFERENCE_BUDGET_S."""
     if rank != 0:
         return
     steps, warm = args.steps, args.warmup
-    # warm-up steps of the oracle are not timed; each timed step is a bounded
-    # sample (a cpu_n^3 sub-lattice) of the workload
-    if warm > 0:
-        cpu_sample(args, 1)
-    ps, threads, desc = cpu_sample(args, steps)
+    if args.workload == "adjoint":
+        metric, config = adjoint_metric(args.adj_steps), adjoint_config(args, Workload(n=args.adj_n, K=args.adj_K))
+        ps1, _, _ = adjoint_cpu_sample(args)
+        n = _bounded_n(16, 16 ** 3 / ps1 * 2, steps)
+        t, threads, descs = 0.0, 1, []
+        for _ in range(steps):
+            ps_k, threads, d = adjoint_cpu_sample(args, n=n)
+            t += n ** 3 * 2 / ps_k
+            descs.append(d)
+        ps, desc, per_step_units = steps * n ** 3 * 2 / t, "%d samples: %s" % (steps, descs[-1]), n ** 3 * 2
+    else:
+        if args.workload == "ensemble":
+            ws = ensemble_members(args, 0)
+            metric, config = METRIC, ensemble_config(args, ws)
+            w0 = min(ws, key=lambda w: w.n)  # the smallest replica, with its K and kT
+            n0, K, kT, what = w0.n, w0.K, w0.kT, "replica-sized"
+        else:
+            metric, config = METRIC, workload_config(args)
+            n0, K, kT, what = args.cpu_n, args.K, 1.0, "sub-lattice"
+        ps1, _, _ = cpu_sample(args, 1, n=n0, K=K, kT=kT)
+        n = _bounded_n(n0, n0 ** 3 / ps1, steps)
+        ps, threads, desc = cpu_sample(args, steps, n=n, K=K, kT=kT)
+        desc = "%s sample; %s" % (what, desc)
+        per_step_units = n ** 3
     line = {
-        "impl": "reference", "metric": METRIC, "value": ps, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": steps, "warmup": warm, "ms_per_step": 1e3 * (args.cpu_n ** 3) / ps,
+        "impl": "reference", "metric": metric, "value": ps, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": steps, "warmup": warm, "ms_per_step": 1e3 * per_step_units / ps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": workload_config(args),
+        "data": "synthetic", "config": config,
         "cpu_baseline": {"value": ps, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc},
         "e2e": {"value": ps, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -386,6 +424,15 @@ def ensemble_members(args, rank):
     return out
 
 
+def ensemble_config(args, ws):
+    return {"workload": "batched ensemble: %d replicas, N log-uniform in [2048, 65536] (cubes), "
+                        "K in {5,20,100}, kT in [0.1,1], dt=%g, %s, %s" % (len(ws), args.dt,
+                                                                          args.scheme.upper(), args.precision),
+            "particles": sum(w.N for w in ws), "replicas": len(ws),
+            "sizes": sorted({w.n for w in ws}),
+            "l2": "inputs larger than L2"}
+
+
 def run_ensemble(args, rank, world, local_rank):
     import torch
     from paper_1707_04232_gb300 import sdpd
@@ -464,13 +511,7 @@ def run_ensemble(args, rank, world, local_rank):
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "mixed" else "f64",
         "data": "synthetic",
-        "config": {"workload": "batched ensemble: %d replicas, N log-uniform in [2048, 65536] (cubes), "
-                               "K in {5,20,100}, kT in [0.1,1], dt=%g, %s, %s" % (len(ws), args.dt,
-                                                                                 args.scheme.upper(), args.precision),
-                   "particles": ntot, "replicas": len(ws),
-                   "sizes": sorted({w.n for w in ws}),
-                   "graph_kernel_nodes_per_2_steps": ens.kernel_nodes,
-                   "l2": "inputs larger than L2"},
+        "config": {**ensemble_config(args, ws), "graph_kernel_nodes_per_2_steps": ens.kernel_nodes},
         "unbatched_sequential": {"value": seq_ps, "unit": UNIT, "steps": seq_steps,
                                  "note": "same replicas stepped one after the other on one stream"},
         "temperature_error": {"max": max(terr), "mean": float(np.mean(terr)),
@@ -482,14 +523,14 @@ def run_ensemble(args, rank, world, local_rank):
         print(json.dumps(line))
 
 
-def adjoint_cpu_sample(args):
-    """The oracle's gradient on a 16^3 lattice of the same fluid, 2 steps:
-    the full steps with their exact Metropolised sweeps (increments kept),
-    the virial pressure's gradient, the reverse pass of the frozen map
-    (O(N^2) pair loops, forward states kept in memory)."""
+def adjoint_cpu_sample(args, n: int = 16):
+    """The oracle's gradient on an n^3 (default 16^3) lattice of the same
+    fluid, 2 steps: the full steps with their exact Metropolised sweeps
+    (increments kept), the virial pressure's gradient, the reverse pass of
+    the frozen map (O(N^2) pair loops, forward states kept in memory)."""
     import oracle as O
 
-    w = Workload(n=16, K=args.adj_K, kT=1.0, seed=0)
+    w = Workload(n=n, K=args.adj_K, kT=1.0, seed=0)
     q, p, e = lattice_state(w)
     P = O.Config(N=w.N, L=w.L, K=w.K, scheme=O.SCHEME_EMS).params()
     O.lib()
@@ -500,8 +541,24 @@ def adjoint_cpu_sample(args):
     O.frozen_vjp(P, q, p, e, args.dt, steps, dps, des, gq, gp, ge)
     dt = time.perf_counter() - t0
     desc = ("FP64 oracle gradient of the virial pressure with the EMS sweeps frozen (O(N^2) pair loops, "
-            "single thread), 16^3 = %d-particle lattice of the same fluid, %d steps, %.1f s" % (w.N, steps, dt))
+            "single thread), %d^3 = %d-particle lattice of the same fluid, %d steps, %.1f s" % (n, w.N, steps, dt))
     return w.N * steps / dt, 1, desc
+
+
+def adjoint_metric(ns):
+    return "gradient particle-steps/s (virial pressure after %d steps, EMS sweeps frozen, reverse mode)" % ns
+
+
+def adjoint_config(args, w):
+    ns, every = args.adj_steps, args.adj_every
+    return {"workload": "adjoint: %d^3 = %d particles, jittered sc lattice, L=%d, Lucy h=2.5a, kT=1, "
+                        "K=%g, dt=%g, %d steps (Verlet + EMS sweep, increments frozen), "
+                        "checkpoint every %d, float64 state, Verlet and reverse pass; sweep pair "
+                        "arithmetic %s"
+                        % (w.n, w.N, w.n, w.K, args.dt, ns, every,
+                           "float64" if args.adj_sweep64 else "float32"),
+            "N": w.N, "K": w.K, "steps_per_gradient": ns, "checkpoint_every": every,
+            "l2": "working set below L2 (the workload is fixed at 32^3)"}
 
 
 def run_adjoint(args, rank, world, local_rank):
@@ -616,18 +673,11 @@ def run_adjoint(args, rank, world, local_rank):
         stream.synchronize()
     e2e_s = allreduce_max(time.perf_counter() - t0, world)
     line = {
-        "metric": "gradient particle-steps/s (virial pressure after %d steps, EMS sweeps frozen, reverse mode)" % ns,
+        "metric": adjoint_metric(ns),
         "value": value, "unit": UNIT, "n_gpus": world, "steps": steps, "warmup": args.warmup,
         "ms_per_step": ms_max / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if args.adj_sweep64 else "f64 (sweep f32)", "data": "synthetic",
-        "config": {"workload": "adjoint: %d^3 = %d particles, jittered sc lattice, L=%d, Lucy h=2.5a, kT=1, "
-                               "K=%g, dt=%g, %d steps (Verlet + EMS sweep, increments frozen), "
-                               "checkpoint every %d, float64 state, Verlet and reverse pass; sweep pair "
-                               "arithmetic %s"
-                               % (w.n, w.N, w.n, w.K, args.dt, ns, every,
-                                  "float64" if args.adj_sweep64 else "float32"),
-                   "N": w.N, "K": w.K, "steps_per_gradient": ns, "checkpoint_every": every,
-                   "l2": "working set below L2 (the workload is fixed at 32^3)"},
+        "config": adjoint_config(args, w),
         "forward_ms_per_gradient": fwd_ms / steps, "reverse_ms_per_gradient": adj_ms / steps,
         "reverse_over_forward": adj_ms / max(fwd_ms, 1e-9),
         "roofline": roof,

@@ -175,7 +175,7 @@ int64_t sdpd_get_fd_step(const sdpd_t* s);
 int sdpd_reset_counters(sdpd_t* s);
 
 /* Number of CUDA kernels the handle has launched so far (a VV step launches
- * 8, a sweep 9 plus 3 when its schedule is rebuilt -- it is reused while the
+ * 8, a sweep 9 plus 5 when its schedule is rebuilt -- it is reused while the
  * positions do not change, as in FD-only runs -- sdpd_set_state 8,
  * sdpd_observables 2). */
 int64_t sdpd_kernel_launches(const sdpd_t* s);

@@ -44,7 +44,8 @@ BYTES_PER_PARTICLE_STEP = {"mixed": 64.0, "fp64": 112.0}
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: the workload's run length, 1000 fluid, 500 ensemble, 5 adjoint)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
@@ -70,7 +71,10 @@ def parse():
                     help="keep the default launch shapes instead of timing the candidates first")
     ap.add_argument("--shapes", default=None,
                     help="fixed launch shapes fd_variant/pair_threads (e.g. 2/32) instead of the autotuner")
-    return ap.parse_args()
+    args = ap.parse_args()
+    if args.steps is None:  # the run length of each workload's configuration
+        args.steps = {"fluid": 1000, "ensemble": 500, "adjoint": 5}[args.workload]
+    return args
 
 
 def measured_peaks():

@@ -60,3 +60,10 @@ def test_reference_sample_shrinks_to_the_time_budget():
     assert 100 * 10.0 * (n / 32) ** 6 <= B  # cost ~ n^6
     assert 100 * 10.0 * ((n + 1) / 32) ** 6 > B
     assert bench._bounded_n(32, 1e6, 100) == 10  # never below the smallest valid lattice
+
+
+def test_default_run_lengths_follow_the_workloads(monkeypatch):
+    for argv, steps in ((["bench.py"], 1000), (["bench.py", "--workload", "ensemble"], 500),
+                        (["bench.py", "--workload", "adjoint"], 5), (["bench.py", "--steps", "7"], 7)):
+        monkeypatch.setattr(sys, "argv", argv)
+        assert bench.parse().steps == steps

@@ -11,8 +11,6 @@ the viscosity, which the paper gives in SI units only, so their values are
 not compared with the paper's.  The multiple-time-step driver runs and
 reports finite drift slopes.
 """
-import math
-
 import numpy as np
 import pytest
 
@@ -24,16 +22,6 @@ if not torch.cuda.is_available():  # pragma: no cover
 pytest.importorskip("scipy")
 
 from paper_1707_04232_gb300 import experiments as X  # noqa: E402
-
-
-def test_gamma_bins_sum_to_one():
-    p = X.gamma_bin_probabilities(6.0, 1.0, 1e-9, 200.0, 1000)
-    assert abs(p.sum() - 1.0) < 1e-12
-
-
-def test_reduced_time_unit():
-    # m = 1, a = 1, kT = 1: t_K = 1 / sqrt(K)
-    assert abs(X.reduced_time_unit(5.0) - 1 / math.sqrt(5.0)) < 1e-15
 
 
 @pytest.mark.parametrize("precision", ["mixed", "fp64"])

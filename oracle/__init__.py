@@ -6,8 +6,9 @@ brute-force O(N^2) pairs, sequential colour-ordered sweep) through ctypes and
 shares no code with the CUDA library.
 
 Parity unpinned: nothing.  Every function is pinned by a ``-m "not gpu"``
-test in ``tests/test_oracle_pins.py`` against a closed form, an invariant, a
-library routine (numpy's Philox) or brute force.
+test in ``tests/test_oracle_pins.py`` or ``tests/test_oracle_adjoint.py``
+(the gradients) against a closed form, an invariant, a library routine
+(numpy's Philox), central differences or brute force.
 """
 from __future__ import annotations
 

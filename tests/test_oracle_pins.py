@@ -492,20 +492,25 @@ def test_owner_bits_spread_over_the_eight_blocks():
 # Statistical pins of the Metropolis scheme
 # --------------------------------------------------------------------------
 
-def _two_particle_chain(K, scheme, dt, nsteps, eta=1.0, e0=(0.4, 0.9), seed=5):
+def _two_particle_chain(K, scheme, dt, nsteps, eta=1.0, e0=(0.4, 0.9), seed=5, counts=None):
+    """FD-only chain of one pair; |v|^2 after every sweep.  ``counts``, a
+    dict, receives the pair updates and acceptances."""
     cfg = O.Config(N=2, L=10.0, K=K, scheme=scheme, eta=eta)
     P = cfg.params()
     q = np.array([[5.0, 5.0, 5.0], [5.9, 5.3, 5.0]])
     p = np.array([[0.5, -0.2, 0.1], [-0.5, 0.2, -0.1]])
     eps = np.array(e0)
-    c = np.empty(2)
     v2 = np.empty(nsteps)
-    step = 0
+    step = n_pairs = n_accept = 0
     for n in range(nsteps):
         s, p, eps, st, _ = O.fd_sweep(P, q, p, eps, dt, seed, step)
         step += 1
+        n_pairs += st.n_pairs
+        n_accept += st.n_accept
         v = (p[0] - p[1]) / P.m
         v2[n] = v @ v
+    if counts is not None:
+        counts.update(n_pairs=n_pairs, n_accept=n_accept)
     return P, p, eps, v2
 
 
@@ -561,8 +566,14 @@ def test_large_heat_capacity_limit():
     and the relative velocity has variance 2 kB T / m per component."""
     K = 1e7
     e0 = (1.5e7, 1.5e7)  # T = 1
-    P, p, eps, v2 = _two_particle_chain(K, O.SCHEME_EMS, dt=5.0, nsteps=20000, e0=e0)
+    n = {}
+    P, p, eps, v2 = _two_particle_chain(K, O.SCHEME_EMS, dt=5.0, nsteps=20000, e0=e0, counts=n)
     assert abs(v2[1000:].mean() / 3.0 - 2.0) < 0.1
+    assert n["n_pairs"] == 20000 and n["n_accept"] >= 0.999 * n["n_pairs"], n
+    # at an ordinary heat capacity and the same step the ratio does reject
+    m = {}
+    _two_particle_chain(2.0, O.SCHEME_EMS, dt=5.0, nsteps=2000, counts=m)
+    assert m["n_accept"] < 0.99 * m["n_pairs"], m
 
 
 @pytest.mark.slow

@@ -231,7 +231,11 @@ typedef struct {
   int32_t owner;      /* owner cell ox + nx (oy + ny oz) */
   int32_t decision;   /* 0 accept, 1 energy-bound reject, 2 Metropolis reject */
   int32_t level;      /* position of the pair in its block's dependency schedule */
-  double margin;      /* EMS: a - ln U; otherwise the smaller new internal energy */
+  double margin;      /* EMS: a - ln U; otherwise the smaller new internal energy
+                         (float64 on every path) */
+  double margin_lo;   /* mixed EMS: the float32 estimate of a - ln U; otherwise = margin */
+  double margin_tol;  /* mixed EMS: the bound on |margin_lo - margin| that decides when
+                         the float64 value is evaluated; otherwise 0 */
 } sdpd_pair_rec;
 
 int sdpd_debug_get(sdpd_t* s, int what, void* dst, int64_t cap, int64_t* count);
@@ -415,9 +419,10 @@ int sdpd_fma_peak(int precision, void* stream, double* flops);
  * whose device-memory footprint has to be fixed before it runs.  Such a
  * caller cannot create the workspace that sdpd_bind_workspace expects.
  *
- * Computes rho_i = sum_j m W(r_ij) over j = 1..N (self term included, Eq.
- * sdpd-rho-v) in float64 for N particles at positions q[N][3] (device,
- * float64, in [0, box)) into rho[N] (device, float64), with the kernel
+ * Computes rho_i = sum_j m W(r_ij) over j = 1..N (self term included) in
+ * float64 for N particles at positions q[N][3] (device, float64; each
+ * coordinate is wrapped periodically into [0, box) first, as sdpd_set_state
+ * does) into rho[N] (device, float64), with the kernel
  * SDPD_KERNEL_CUBIC or SDPD_KERNEL_LUCY and the same neighbour rule as the
  * rest of the library (cells of side >= h, minimum image, r^2 < h^2).
  * Asynchronous on stream (a cudaStream_t, NULL = legacy default stream).

@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(128) k_adj_pairsum(Consts c, const D4* __restr
   const int n = nn[i];
 #pragma unroll 2
   for (int k = 0; k < n; ++k) {
-    const uint32_t e = __ldg(&nlist[i * c.nbr_cap + k]);
+    const uint32_t e = __ldg(&nlist[nbr_slot(i, k, c.nbr_cap)]);
     const D4 qj = ld4(&qp4[e >> 6]);
     double dx, dy, dz;
     pair_disp(im, e & 63u, qi, qj, dx, dy, dz);
@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(128) k_adj_back(Consts c, const D4* __restrict
   const int n = nn[i];
 #pragma unroll 2
   for (int k = 0; k < n; ++k) {
-    const uint32_t e = __ldg(&nlist[i * c.nbr_cap + k]);
+    const uint32_t e = __ldg(&nlist[nbr_slot(i, k, c.nbr_cap)]);
     const D4 qj = ld4(&qp4[e >> 6]);
     const D4 vj = ld4(&vs4[e >> 6]);
     double dx, dy, dz;

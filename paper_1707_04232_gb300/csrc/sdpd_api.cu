@@ -164,9 +164,8 @@ size_t layout(sdpd_handle* s, Workspace* w, char* base) {
   }
   w->qp4 = at(N * sizeof(V4));
   w->qf4 = P::mixed ? nullptr : (float4*)at(N * sizeof(float4));
-  w->nlist = (uint32_t*)at(N * (size_t)c.nbr_cap * 4);
+  w->nlist = (uint32_t*)at((N + 31) / 32 * 32 * (size_t)c.nbr_cap * 4);
   w->nn = (int32_t*)at(N * 4);
-  w->nbr_off = (uint8_t*)at(N * 28);
   w->key = (int32_t*)at(N * 4);
   w->slot = (int32_t*)at(N * 4);
   w->tmp = (int32_t*)at(2 * N * 4);
@@ -251,7 +250,25 @@ void drain_events(sdpd_handle* s) {
   s->ev_pending.clear();
 }
 
-// Brackets one stage with events when timing is on.
+// Reduce the event pairs that the device has already passed, oldest first,
+// without waiting for the rest: the stage timers never block the host.
+void drain_completed_events(sdpd_handle* s) {
+  size_t k = 0;
+  for (; k < s->ev_pending.size(); ++k) {
+    auto& it = s->ev_pending[k];
+    if (cudaEventQuery(it.second.second) != cudaSuccess) break;  // not reached yet (cudaErrorNotReady)
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, it.second.first, it.second.second) == cudaSuccess) s->stage_ms[it.first] += ms;
+    s->ev_pool.push_back(it.second.first);
+    s->ev_pool.push_back(it.second.second);
+  }
+  s->ev_pending.erase(s->ev_pending.begin(), s->ev_pending.begin() + (ptrdiff_t)k);
+}
+
+// Brackets one stage with events when timing is on.  The pending pairs are
+// reduced when the device has passed them (checked without blocking every
+// 256 pairs) or at the next synchronising call; the event pool grows
+// meanwhile instead of waiting.
 struct StageTimer {
   sdpd_handle* s;
   int stage;
@@ -269,10 +286,7 @@ struct StageTimer {
       cudaEventRecord(b, s->stream);
       s->ev_pending.push_back({stage, {a, b}});
       s->stage_launches[stage] += launches;
-      if (s->ev_pending.size() > 4096) {  // bound the pool: wait for the oldest
-        cudaStreamSynchronize(s->stream);
-        drain_events(s);
-      }
+      if (s->ev_pending.size() % 256 == 0) drain_completed_events(s);
     }
   }
 };

@@ -37,242 +37,197 @@ namespace sdpd {
 
 
 // ---------------------------------------------------------------------------
-// Schedule, step 1: owned pairs of every block in canonical order.
+// Schedule, step 1: owned pairs of every block in canonical order, found
+// from the positions of the block's particles.  One thread block of
+// kEnumThreads threads per owner cell stages the particles of the block's 8
+// cells in shared memory (ids, ranks, coordinates), lists the block's
+// (particle, partner cell) segments, and tests every candidate of every
+// segment with the neighbour predicate r^2 < h^2 of the pair passes:
+//   * float64: absolute coordinates and the minimum image, the float32
+//     pre-test of the density pass first (it skips only pairs with r >= h);
+//   * mixed: block-local float32 coordinates, the same arithmetic the colour
+//     kernel uses for the pair's geometry.
+// A particle A (as the lower id of a pair) in block cell dA has owned
+// partners only in the cells dB that agree with dA where dA agrees with A's
+// owner bits and differ from dA elsewhere; in its own cell only the
+// particles after it (cells hold their particles by ascending id), in the
+// other cells those of higher rank.  Found pairs set bit rank(i) of row
+// rank(j) - rank(i) of a bitmap, which is then read out row by row.
 // ---------------------------------------------------------------------------
-constexpr int kSchedWarps = 2;
+constexpr int kEnumThreads = 128;
+constexpr int kMaxSegments = kMaxBlock * 8;
 
-struct SchedSmem {
+template <class R>
+struct EnumSmem {
+  R x[kMaxBlock], y[kMaxBlock], z[kMaxBlock];  // float64: absolute; mixed: block-local
+  float4 f[std::is_same<R, double>::value ? kMaxBlock : 1];  // float64: float32 copies for the pre-test
+  uint32_t bits[kRowWords][kMaxBlock];  // bit (lower rank) of row (rank difference); word-major
   int32_t id[kMaxBlock];
+  int32_t rowoff[kMaxBlock + 1];
+  uint16_t seg[kMaxSegments];  // particle | partner cell << 8
   uint8_t rank[kMaxBlock];
   uint8_t perm[kMaxBlock];
-  uint32_t bits[kRowWords][kMaxBlock];  // bit (lower rank) of row (rank difference); word-major, so
-                                        // that lanes reading consecutive rows hit distinct banks
-  int32_t rowoff[kMaxBlock + 1];
-  int32_t cstart[8], cbase[8], ccnt[8];  // the block's cells: first storage index, offset in the block, count
-  // the partner segments of the 32 particles of the current chunk, one row
-  // per lane: entries before segment s (cum, 0xff past the last), and the
-  // segment's first entry and partner cell (first | cell << 8)
-  uint8_t seg_cum[32][8];
-  uint16_t seg_pk[32][8];
+  int32_t cstart[8], cbase[9];
+  int32_t nseg, npairs, nb;
 };
 
-// The owned pairs are read from the neighbour lists of the density pass: as
-// the lower id of a pair, a particle in block cell dA has owned partners only
-// in the cells dB that agree with dA exactly where dA agrees with its owner
-// bits (and differ from dA elsewhere), whose entries sit in known stencil
-// groups of its list row; entries with a lower-ranked partner belong to the
-// partner's side.  Over the 8 blocks holding a particle these groups cover
-// its list once.
 template <class P>
-__global__ void __launch_bounds__(kSchedWarps * 32)
+__global__ void __launch_bounds__(kEnumThreads)
     k_sched_enum(Consts c, Arrays<P> a, const int32_t* __restrict__ cell_start, const int32_t* __restrict__ mrank,
-                 const uint32_t* __restrict__ nlist, const uint8_t* __restrict__ nbr_off,
-                 uint32_t* __restrict__ hdr, uint16_t* __restrict__ canon, int* status,
-                 uint32_t* __restrict__ blk_hist) {
-  __shared__ SchedSmem sm_all[kSchedWarps];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+                 const uint32_t* __restrict__ xmx, const uint32_t* __restrict__ xmy,
+                 const uint32_t* __restrict__ xmz, const float4* __restrict__ qf4, uint32_t* __restrict__ hdr,
+                 uint16_t* __restrict__ canon, int* status, uint32_t* __restrict__ blk_hist) {
+  using R = typename P::R;
+  __shared__ EnumSmem<R> sm;
+  const int t = threadIdx.x, lane = t & 31;
   if (blockIdx.x == 0)  // the depth histogram that k_sched_walk fills
-    for (int k = threadIdx.x; k < 8 * 256; k += blockDim.x) blk_hist[k] = 0u;
-  const int64_t o = (int64_t)blockIdx.x * kSchedWarps + warp;
-  if (o >= c.ncell) return;
-  SchedSmem& sm = sm_all[warp];
+    for (int k = t; k < 8 * 256; k += kEnumThreads) blk_hist[k] = 0u;
+  const int64_t o = blockIdx.x;
   int ox, oy, oz;
   owner_coords(c, o, ox, oy, oz);
-  // the block's 8 cells, one per lane: storage start, count, offset in the
-  // block (kept in shared memory, where they are indexed by cell code)
-  int ccnt = 0, cst = 0;
-  if (lane < 8) {
-    int cx = ox + (lane & 1), cy = oy + ((lane >> 1) & 1), cz = oz + ((lane >> 2) & 1);
-    if (cx >= c.nc[0]) cx -= c.nc[0];
-    if (cy >= c.nc[1]) cy -= c.nc[1];
-    if (cz >= c.nc[2]) cz -= c.nc[2];
-    const int r = __ldg(&mrank[cx + c.nc[0] * (cy + c.nc[1] * cz)]);
-    cst = __ldg(&cell_start[r]);
-    ccnt = __ldg(&cell_start[r + 1]) - cst;
-  }
-  int cinc = ccnt;
+  // the block's 8 cells: storage start, count and offset in the block
+  if (t < 32) {
+    int ccnt = 0, cst = 0;
+    if (lane < 8) {
+      int cx = ox + (lane & 1), cy = oy + ((lane >> 1) & 1), cz = oz + ((lane >> 2) & 1);
+      if (cx >= c.nc[0]) cx -= c.nc[0];
+      if (cy >= c.nc[1]) cy -= c.nc[1];
+      if (cz >= c.nc[2]) cz -= c.nc[2];
+      const int r = __ldg(&mrank[cx + c.nc[0] * (cy + c.nc[1] * cz)]);
+      cst = __ldg(&cell_start[r]);
+      ccnt = __ldg(&cell_start[r + 1]) - cst;
+    }
+    int cinc = ccnt;
 #pragma unroll
-  for (int sh = 1; sh < 8; sh <<= 1) {
-    const int t = __shfl_up_sync(0xffffffffu, cinc, sh);
-    if (lane >= sh) cinc += t;
+    for (int sh = 1; sh < 8; sh <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, cinc, sh);
+      if (lane >= sh) cinc += v;
+    }
+    if (lane < 8) {
+      sm.cstart[lane] = cst;
+      sm.cbase[lane] = cinc - ccnt;
+    }
+    if (lane == 7) {
+      sm.cbase[8] = cinc;
+      sm.nb = cinc;
+    }
+    if (lane == 0) { sm.nseg = 0; sm.npairs = 0; }
   }
-  const int nb = __shfl_sync(0xffffffffu, cinc, 7);
-  int maxcnt = ccnt;
-#pragma unroll
-  for (int sh = 4; sh > 0; sh >>= 1) maxcnt = max(maxcnt, __shfl_xor_sync(0xffffffffu, maxcnt, sh));
-  maxcnt = __shfl_sync(0xffffffffu, maxcnt, 0);
+  __syncthreads();
+  const int nb = sm.nb;
   if (nb > kMaxBlock) {
-    if (lane == 0) { atomicOr(status, kStCapacity); hdr[o] = 0; }
+    if (t == 0) { atomicOr(status, kStCapacity); hdr[o] = 0; }
     return;
   }
-  if (lane < 8) {
-    sm.cstart[lane] = cst;
-    sm.cbase[lane] = cinc - ccnt;
-    sm.ccnt[lane] = ccnt;
-  }
-  const int nw = (nb + 31) >> 5;  // bitmap words in use per row
-  for (int w = 0; w < nw; ++w)
-    for (int row = lane; row < nb; row += 32) sm.bits[w][row] = 0u;
-  __syncwarp();
   auto code_of = [&](int k) {
     int d = 0;
 #pragma unroll
-    for (int t = 1; t < 8; ++t) d += (k >= sm.cbase[t]);
+    for (int u = 1; u < 8; ++u) d += (k >= sm.cbase[u]);
     return d;
   };
-  for (int k = lane; k < nb; k += 32) {
+  const int nw = (nb + 31) >> 5;  // bitmap words in use per row
+  for (int q = t; q < nw * nb; q += kEnumThreads) sm.bits[q / nb][q % nb] = 0u;
+  BlockGeom<P> geo;
+  geo.init(c, ox, oy, oz, xmx, xmy, xmz);
+  for (int k = t; k < nb; k += kEnumThreads) {
     const int d = code_of(k);
-    sm.id[k] = a.id[sm.cstart[d] + (k - sm.cbase[d])];
+    const int g = sm.cstart[d] + (k - sm.cbase[d]);
+    sm.id[k] = a.id[g];
+    R x, y, zz;
+    geo.local(ld4(&a.q4[g]), d, x, y, zz);
+    sm.x[k] = x; sm.y[k] = y; sm.z[k] = zz;
+    if constexpr (!P::mixed) sm.f[k] = __ldg(&qf4[g]);
   }
-  __syncwarp();
+  __syncthreads();
   // rank of each id among the block's ids: every cell's ids are ascending
-  int steps = 0;
-  while ((1 << steps) <= maxcnt) ++steps;
-  for (int k = lane; k < nb; k += 32) {
+  for (int k = t; k < nb; k += kEnumThreads) {
     const int32_t myid = sm.id[k];
-    // per cell: number of ids below myid (branch-free lower bound with a
-    // fixed number of halvings, the 8 searches independent of each other)
-    int pos[8], len[8];
-#pragma unroll
-    for (int d = 0; d < 8; ++d) { pos[d] = sm.cbase[d]; len[d] = sm.ccnt[d]; }
-    for (int it = 0; it < steps; ++it) {
-#pragma unroll
-      for (int d = 0; d < 8; ++d) {
-        const int half = len[d] >> 1;
-        const bool below = len[d] > 0 && sm.id[pos[d] + half] < myid;
-        pos[d] = below ? pos[d] + half + 1 : pos[d];
-        len[d] = below ? len[d] - half - 1 : half;
-      }
-    }
     int r = 0;
 #pragma unroll
-    for (int d = 0; d < 8; ++d) r += pos[d] - sm.cbase[d];
+    for (int d = 0; d < 8; ++d) {
+      int pos = sm.cbase[d], len = sm.cbase[d + 1] - sm.cbase[d];
+      while (len > 0) {  // lower bound of myid in cell d
+        const int half = len >> 1;
+        if (sm.id[pos + half] < myid) { pos += half + 1; len -= half + 1; }
+        else len = half;
+      }
+      r += pos - sm.cbase[d];
+    }
     sm.rank[k] = (uint8_t)r;
     sm.perm[r] = (uint8_t)k;
   }
-  __syncwarp();
-  // Owned entries, spread over the warp: each lane lists the partner
-  // segments of one particle of a chunk of 32, a warp prefix sum over the
-  // lanes' entry totals maps the chunk's entries to lanes, and each entry
-  // finds its segment in the owner lane's row, so that the lanes load
-  // consecutive entries of a row together and share the work evenly (a
-  // particle has from one to eight partner segments, ~3 to ~80 entries).
-  for (int k0 = 0; k0 < nb; k0 += 32) {
-    const int k = k0 + lane;
-    const bool live = k < nb;
-    int dA = 0, g = 0, rk = 0;
-    if (live) {
-      dA = code_of(k);
-      g = sm.cstart[dA] + (k - sm.cbase[dA]);
-      rk = sm.rank[k];
-    }
-    // Partner cells of a pair this block owns with k as the lower id: along
-    // an axis where k's block-cell bit equals k's owner bit the partner may
-    // share the coordinate or sit across (free axes); elsewhere it must sit
-    // across.
-    const int hb = live ? (int)owner_bits(sm.id[k]) : 0;
-    const int free = 7 & ~(dA ^ hb);
+  // the (particle, partner cell) segments of the block, in any order
+  for (int k = t; k < nb; k += kEnumThreads) {
+    const int dA = code_of(k);
+    const int hb = (int)owner_bits(sm.id[k]);
+    const int free = 7 & ~(dA ^ hb);  // axes where the partner may share the cell
     const int fixed = 7 & ~dA & ~free;
-    int tot = 0, ns = 0;
-    if (live) {
-      const uint8_t* off = nbr_off + (int64_t)g * 28;
-      int sub = free;
-      for (;;) {  // partner cells dB = fixed | (subsets of free)
-        const int dB = fixed | sub;
-        const int sx = ((dB & 1) - (dA & 1)) + 1, sy = (((dB >> 1) & 1) - ((dA >> 1) & 1)) + 1,
-                  sz = (((dB >> 2) & 1) - ((dA >> 2) & 1)) + 1;
-        const int st = sx + 3 * sy + 9 * sz;
-        const int e0 = off[st], n = off[st + 1] - e0;
-        if (n > 0) {
-          sm.seg_cum[lane][ns] = (uint8_t)tot;
-          sm.seg_pk[lane][ns] = (uint16_t)(e0 | (dB << 8));
-          tot += n;
-          ++ns;
-        }
-        if (sub == 0) break;
-        sub = (sub - 1) & free;
-      }
+    const int ns = 1 << __popc(free);
+    const int base = atomicAdd(&sm.nseg, ns);
+    int sub = free, j = 0;
+    for (;;) {
+      sm.seg[base + j++] = (uint16_t)(k | ((fixed | sub) << 8));
+      if (sub == 0) break;
+      sub = (sub - 1) & free;
     }
-    for (int t = ns; t < 8; ++t) sm.seg_cum[lane][t] = 0xff;
-    __syncwarp();
-    int incl = tot;
-#pragma unroll
-    for (int sh = 1; sh < 32; sh <<= 1) {
-      const int t = __shfl_up_sync(0xffffffffu, incl, sh);
-      if (lane >= sh) incl += t;
-    }
-    const int total = __shfl_sync(0xffffffffu, incl, 31);
-    const int excl = incl - tot;
-    // kDeep rounds of 32 entries per iteration, all list loads issued before
-    // any is used
-    constexpr int kDeep = 4;
-    for (int t0 = 0; t0 < total; t0 += 32 * kDeep) {
-      int o_rk[kDeep], o_q[kDeep], o_b[kDeep];
-      uint32_t ent[kDeep];
-#pragma unroll
-      for (int h = 0; h < kDeep; ++h) {
-        const int t = t0 + 32 * h + lane;
-        // owner lane: the number of lanes whose inclusive count is <= t
-        int pos = 0;
-#pragma unroll
-        for (int step = 16; step > 0; step >>= 1) {
-          const int v = __shfl_sync(0xffffffffu, incl, pos + step - 1);
-          if (v <= t) pos += step;
-        }
-        const int src = min(pos, 31);
-        const int o_ex = __shfl_sync(0xffffffffu, excl, src);
-        const int o_g = __shfl_sync(0xffffffffu, g, src);
-        o_rk[h] = __shfl_sync(0xffffffffu, rk, src);
-        o_q[h] = -1;
-        o_b[h] = 0;
-        if (t < total) {
-          const int u = t - o_ex;  // entry of the owner lane's particle
-          int sg = 0;
-#pragma unroll
-          for (int s2 = 1; s2 < 8; ++s2) sg += (int)sm.seg_cum[src][s2] <= u;
-          const int pk = sm.seg_pk[src][sg];
-          o_q[h] = (pk & 255) + (u - sm.seg_cum[src][sg]);
-          o_b[h] = pk >> 8;
-        }
-        ent[h] = o_q[h] >= 0 ? __ldg(&nlist[(int64_t)o_g * c.nbr_cap + o_q[h]]) : 0u;
-      }
-#pragma unroll
-      for (int h = 0; h < kDeep; ++h) {
-        if (o_q[h] >= 0) {
-          const int oB = o_b[h];
-          const int j = (int)(ent[h] >> 6);
-          const int rj = sm.rank[sm.cbase[oB] + (j - sm.cstart[oB])];
-          if (o_rk[h] < rj) atomicOr(&sm.bits[o_rk[h] >> 5][rj - o_rk[h]], 1u << (o_rk[h] & 31));
-        }
-      }
-    }
-    __syncwarp();  // the segment rows are refilled by the next chunk
   }
-  __syncwarp();
-  // exclusive scan of the row populations, 32 consecutive rows at a time
-  int npairs = 0;
-  for (int r0 = 0; r0 < nb; r0 += 32) {
-    const int rr = r0 + lane;
-    int n = 0;
-    if (rr >= 1 && rr < nb)
-      for (int w = 0; w < nw; ++w) n += __popc(sm.bits[w][rr]);
-    int incl = n;
-#pragma unroll
-    for (int sh = 1; sh < 32; sh <<= 1) {
-      const int t = __shfl_up_sync(0xffffffffu, incl, sh);
-      if (lane >= sh) incl += t;
+  __syncthreads();
+  const int nseg = sm.nseg;
+  const R h2 = (R)c.h2;
+  for (int sgi = t; sgi < nseg; sgi += kEnumThreads) {
+    const int sg = sm.seg[sgi];
+    const int A = sg & 255, dB = sg >> 8;
+    const int dA = code_of(A);
+    const int rA = sm.rank[A];
+    const R xa = sm.x[A], ya = sm.y[A], za = sm.z[A];
+    float4 fa = make_float4(0.f, 0.f, 0.f, 0.f);
+    if constexpr (!P::mixed) fa = sm.f[A];
+    const int b0 = dB == dA ? A + 1 : sm.cbase[dB], b1 = sm.cbase[dB + 1];
+    for (int B = b0; B < b1; ++B) {
+      const int rB = sm.rank[B];
+      if (rB <= rA) continue;  // the pair belongs to B's segments
+      if constexpr (!P::mixed) {  // float32 pre-test: skips only pairs with r >= h
+        const float4 fb = sm.f[B];
+        float ex = fa.x - fb.x, ey = fa.y - fb.y, ez = fa.z - fb.z;
+        ex = ex > c.halfLf[0] ? ex - c.Lf[0] : (ex < -c.halfLf[0] ? ex + c.Lf[0] : ex);
+        ey = ey > c.halfLf[1] ? ey - c.Lf[1] : (ey < -c.halfLf[1] ? ey + c.Lf[1] : ey);
+        ez = ez > c.halfLf[2] ? ez - c.Lf[2] : (ez < -c.halfLf[2] ? ez + c.Lf[2] : ez);
+        if (ex * ex + ey * ey + ez * ez >= c.h2_filter) continue;
+      }
+      R dx, dy, dz;
+      geo.disp(xa, ya, za, sm.x[B], sm.y[B], sm.z[B], dx, dy, dz);
+      if (r2_of(dx, dy, dz) < h2) atomicOr(&sm.bits[rA >> 5][rB - rA], 1u << (rA & 31));
     }
-    sm.rowoff[rr] = npairs + incl - n;
-    npairs += __shfl_sync(0xffffffffu, incl, 31);
   }
+  __syncthreads();
+  // exclusive scan of the row populations (rows 1 .. nb - 1), one warp
+  if (t < 32) {
+    int npairs = 0;
+    for (int r0 = 0; r0 < nb; r0 += 32) {
+      const int rr = r0 + lane;
+      int n = 0;
+      if (rr >= 1 && rr < nb)
+        for (int w = 0; w < nw; ++w) n += __popc(sm.bits[w][rr]);
+      int incl = n;
+#pragma unroll
+      for (int sh = 1; sh < 32; sh <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, sh);
+        if (lane >= sh) incl += v;
+      }
+      if (rr < nb) sm.rowoff[rr] = npairs + incl - n;
+      npairs += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    if (lane == 0) sm.npairs = npairs;
+  }
+  __syncthreads();
+  const int npairs = sm.npairs;
   if (npairs > kMaxPairs) {
-    if (lane == 0) { atomicOr(status, kStCapacity); hdr[o] = 0; }
+    if (t == 0) { atomicOr(status, kStCapacity); hdr[o] = 0; }
     return;
   }
-  __syncwarp();
   // write the pairs row by row (difference ascending), lower rank ascending
   uint16_t* out = canon + o * kMaxPairs;
-  for (int rr = 1 + lane; rr < nb; rr += 32) {
+  for (int rr = 1 + t; rr < nb; rr += kEnumThreads) {
     int pos = sm.rowoff[rr];
     for (int w = 0; w < nw; ++w) {
       uint32_t bits = sm.bits[w][rr];
@@ -284,7 +239,7 @@ __global__ void __launch_bounds__(kSchedWarps * 32)
       }
     }
   }
-  if (lane == 0) hdr[o] = (uint32_t)npairs;
+  if (t == 0) hdr[o] = (uint32_t)npairs;
 }
 
 // Levels, step 1: one thread per block walks that block's canonical list and
@@ -453,9 +408,9 @@ void launch_fd_schedule(const Consts& c, const Workspace& w, int cur, cudaStream
   if (c.N == 0) return;
   Arrays<P> a = view<P>(w, cur);
   uint16_t* canon = w.sched_pair + (size_t)c.ncell * kMaxPairs;
-  const unsigned gs = (unsigned)((c.ncell + kSchedWarps - 1) / kSchedWarps);
-  k_sched_enum<P><<<gs, kSchedWarps * 32, 0, s>>>(c, a, w.cell_start, w.mrank, w.nlist, w.nbr_off,
-                                                   w.sched_hdr, canon, w.status, w.blk_hist);
+  k_sched_enum<P><<<(unsigned)c.ncell, kEnumThreads, 0, s>>>(c, a, w.cell_start, w.mrank, w.xmin[0], w.xmin[1],
+                                                               w.xmin[2], w.qf4, w.sched_hdr, canon, w.status,
+                                                               w.blk_hist);
   k_sched_walk<<<(unsigned)((c.ncell + kLevelThreads - 1) / kLevelThreads), kLevelThreads, 0, s>>>(
       c.ncell, c.nc[0], c.nc[1], w.sched_hdr, canon, w.level_of, w.status, w.blk_hist);
   k_sched_bucket<<<(unsigned)((c.ncell + kBucketWarps - 1) / kBucketWarps), kBucketWarps * 32, 0, s>>>(

@@ -20,6 +20,8 @@ struct FDConst {
   R inv_C_K, kB, two_over_CK, dt_over_m;
   R CKm1;               // C_K / kB - 1
   R four_kB_over_m;
+  double CKm1_d;          // C_K / kB - 1 in float64 (the exact Metropolis ratio)
+  float nq_hi, nq_lo;     // -1 / (4 m) as a float-float (energy change from momenta)
   int scheme;
 };
 
@@ -57,24 +59,51 @@ __device__ __forceinline__ float log1p(float x) {
 }
 }  // namespace fm
 
+// Error-free transformations in float32 (Knuth's two-sum, the FMA split of
+// a product): a + b = s + e and a * b = p + e exactly.  The rounded
+// intrinsics keep the compiler from contracting or reordering them.
+namespace eft {
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+  p = __fmul_rn(a, b);
+  e = __fmaf_rn(a, b, -p);
+}
+}  // namespace eft
+
 // Box-Muller normals and the uniform of one pair at one sweep (see
-// pair_randoms); the float32 path uses the hardware log and sin/cos.
+// pair_randoms), float32 path: the float64 path's uniforms rounded to
+// float32 with full relative precision (a fixed-point uniform would lose
+// the relative precision of the small values that the logarithms of
+// Box-Muller and of the Metropolis test magnify), the logarithm inside
+// Box-Muller accurate near 1 (log1p of u - 1), angles reduced to [-pi, pi)
+// for the hardware sine and cosine.
+__device__ __forceinline__ float uniform53f(uint64_t w) {  // (top 53 bits + 1/2) 2^-53
+  const uint64_t m = w >> 11;
+  const float hi = (float)(uint32_t)(m >> 21), lo = (float)(uint32_t)(m & 0x1fffffull) + 0.5f;
+  return __fmaf_rn(hi, 2.3283064365386963e-10f, lo * 1.1102230246251565e-16f);
+}
+__device__ __forceinline__ float uniform32f(uint32_t x) {  // (x + 1/2) 2^-32
+  return ((float)x + 0.5f) * 2.3283064365386963e-10f;
+}
+__device__ __forceinline__ float box_muller_log(float u) { return u < 0.5f ? __logf(u) : fm::log1p(u - 1.0f); }
 __device__ __forceinline__ void pair_randoms_fast(uint64_t seed, uint64_t sweep, uint64_t idi, uint64_t idj,
                                                   float G[3], float* U) {
   uint64_t w[4];
   philox4x64_10(sweep, idi, idj, 0ull, seed, 0ull, w);
-  const float two23 = 1.0f / 8388608.0f, twopi = 6.28318530717958647692f;
-  const float u0 = ((float)(uint32_t)(w[0] >> 41) + 0.5f) * two23;
-  const float u1 = ((float)(uint32_t)(w[1] >> 41) + 0.5f) * two23;
-  const float R = fm::sqrt(-2.0f * __logf(u0));
+  const float twopi = 6.28318530717958647692f;
+  const float u0 = uniform53f(w[0]), u1 = uniform53f(w[1]);
+  const float R = fm::sqrt(-2.0f * box_muller_log(u0));
   float sn, cs;
-  __sincosf(twopi * u1, &sn, &cs);
-  G[0] = R * cs;
-  G[1] = R * sn;
-  const float u2 = ((float)(uint32_t)(w[2] >> 41) + 0.5f) * two23;
-  const float u3 = ((float)((uint32_t)(w[2] & 0xffffffffull) >> 9) + 0.5f) * two23;
-  G[2] = fm::sqrt(-2.0f * __logf(u2)) * __cosf(twopi * u3);
-  *U = ((float)(uint32_t)(w[3] >> 41) + 0.5f) * two23;
+  __sincosf(twopi * (u1 - 0.5f), &sn, &cs);  // the angle 2 pi u1 - pi
+  G[0] = -R * cs;
+  G[1] = -R * sn;
+  const float u2 = uniform32f((uint32_t)(w[2] >> 32)), u3 = uniform32f((uint32_t)(w[2] & 0xffffffffull));
+  G[2] = -fm::sqrt(-2.0f * box_muller_log(u2)) * __cosf(twopi * (u3 - 0.5f));
+  *U = uniform53f(w[3]);
 }
 __device__ __forceinline__ void pair_randoms_fast(uint64_t seed, uint64_t sweep, uint64_t idi, uint64_t idj,
                                                   double G[3], double* U) {
@@ -88,51 +117,45 @@ __device__ __forceinline__ void pair_randoms_fast(uint64_t seed, uint64_t sweep,
 // (kappa cancels).  Ideal gas: T = eps / C_K and C = C_K, so
 // d = kB Ti Tj / (Ti + Tj)^2 * 2 / C_K.
 //
-// One expm1 per direction gives both alpha = 1 + expm1(x) and
-// 1 - alpha^2 = -expm1(x) (2 + expm1(x)), and one reciprocal of Ti + Tj
-// serves both quotients: the float64 dependency chain of a pair update is
-// what bounds the sweep when a colour has few blocks.
+// Returns m = alpha - 1 = expm1(x) per direction (alpha itself is 1 + m):
+// one expm1 per direction gives both alpha and 1 - alpha^2 = -m (2 + m), and
+// one reciprocal of Ti + Tj serves both quotients -- the float64 dependency
+// chain of a pair update is what bounds the sweep when a colour has few
+// blocks.
 template <class R>
-__device__ __forceinline__ void pair_coeffs(const FDConst<R>& k, R kpar, R kperp, R ei, R ej, R& apar,
-                                            R& aperp, R& zpar, R& zperp, R& xpar, R& xperp) {
+__device__ __forceinline__ void pair_coeffs(const FDConst<R>& k, R kpar, R kperp, R ei, R ej, R& mpar,
+                                            R& mperp, R& zpar, R& zperp) {
   const R Ti = ei * k.inv_C_K, Tj = ej * k.inv_C_K;
   const R isT = fm::div(R(1), Ti + Tj);
   const R hT = Ti * Tj * isT;
   const R omd = R(1) - k.kB * k.two_over_CK * hT * isT;
-  xpar = R(-2) * kpar * omd * k.dt_over_m;  // log alpha per direction
-  xperp = R(-2) * kperp * omd * k.dt_over_m;
-  const R mpar = fm::expm1(xpar), mperp = fm::expm1(xperp);
-  apar = R(1) + mpar;
-  aperp = R(1) + mperp;
+  const R xpar = R(-2) * kpar * omd * k.dt_over_m;  // log alpha per direction
+  const R xperp = R(-2) * kperp * omd * k.dt_over_m;
+  mpar = fm::expm1(xpar);
+  mperp = fm::expm1(xperp);
   const R s = fm::div(k.four_kB_over_m * hT, omd);
   zpar = fm::sqrt(s * (-mpar * (R(2) + mpar)));
   zperp = fm::sqrt(s * (-mperp * (R(2) + mperp)));
 }
 
-// State-dependent part of one pair update on (p_i, p_j) with internal
-// energies (ei, ej) in the arithmetic type R, given the pair's unit vector
-// e = r_ij / r_ij, base = F(r_ij) / (rho_i rho_j), its Gaussians G and the
-// logarithm lnU of its uniform.
-// Returns 0 accept, 1 energy-bound reject, 2 Metropolis reject; deps receives
-// the energy change shared by the two particles (applied by the caller on
-// acceptance).  exact_bound: float64 re-check of the energy bound for the
-// mixed path when its float32 margin is not decisive; it returns the smaller
-// new internal energy in float64.
-template <class P, class ExactBound>
-__device__ __forceinline__ int fd_pair(const FDConst<typename P::R>& k, typename P::R ex, typename P::R ey,
-                                       typename P::R ez, typename P::R base, const typename P::R G[3],
-                                       typename P::R lnU, typename P::R* pi, typename P::R* pj,
-                                       typename P::R ei, typename P::R ej, typename P::R& deps,
-                                       typename P::R& margin, bool& negative, ExactBound exact_bound) {
-  using R = typename P::R;
+// State-dependent part of one float64 pair update on (p_i, p_j) with
+// internal energies (ei, ej), given the pair's unit vector e = r_ij / r_ij,
+// base = F(r_ij) / (rho_i rho_j), its Gaussians G and the logarithm lnU of its
+// uniform.  Returns 0 accept, 1 energy-bound reject, 2 Metropolis reject;
+// deps receives the energy change shared by the two particles (applied by the
+// caller on acceptance).
+__device__ __forceinline__ int fd_pair(const FDConst<double>& k, double ex, double ey, double ez, double base,
+                                       const double G[3], double lnU, double* pi, double* pj, double ei,
+                                       double ej, double& deps, double& margin, bool& negative) {
+  using R = double;
   const R kpar = k.kpar_m2 * base, kperp = k.kperp_m2 * base;
   margin = R(0);
   deps = R(0);
   if (!(kperp > R(0)) || !(kpar > R(0))) return 0;  // at r = h the pair does nothing
   const R vx = (pi[0] - pj[0]) * k.inv_m, vy = (pi[1] - pj[1]) * k.inv_m, vz = (pi[2] - pj[2]) * k.inv_m;
-  R apar, aperp, zpar, zperp;
-  R xfpar, xfperp;
-  pair_coeffs(k, kpar, kperp, ei, ej, apar, aperp, zpar, zperp, xfpar, xfperp);
+  R mpar, mperp, zpar, zperp;
+  pair_coeffs(k, kpar, kperp, ei, ej, mpar, mperp, zpar, zperp);
+  const R apar = R(1) + mpar, aperp = R(1) + mperp;
   // proposal, Eq. (proposal): v' = sum_theta P^theta (alpha^theta v + zt^theta G)
   const R vpar = ex * vx + ey * vy + ez * vz;
   const R gpar = ex * G[0] + ey * G[1] + ez * G[2];
@@ -144,26 +167,11 @@ __device__ __forceinline__ int fd_pair(const FDConst<typename P::R>& k, typename
   const R dpx = k.half_m * (wx - vx), dpy = k.half_m * (wy - vy), dpz = k.half_m * (wz - vz);
   const R nix = pi[0] + dpx, niy = pi[1] + dpy, niz = pi[2] + dpz;
   const R njx = pj[0] - dpx, njy = pj[1] - dpy, njz = pj[2] - dpz;
-  if constexpr (P::mixed) {
-    // -1/2 of the kinetic-energy change of the stored momenta, as a sum of
-    // (new - old)(new + old) products so float32 carries no cancellation
-    const float dk = (nix - pi[0]) * (nix + pi[0]) + (niy - pi[1]) * (niy + pi[1]) +
-                     (niz - pi[2]) * (niz + pi[2]) + (njx - pj[0]) * (njx + pj[0]) +
-                     (njy - pj[1]) * (njy + pj[1]) + (njz - pj[2]) * (njz + pj[2]);
-    deps = -0.25f * k.inv_m * dk;
-  } else {
-    const double ko = pi[0] * pi[0] + pj[0] * pj[0] + pi[1] * pi[1] + pj[1] * pj[1] + pi[2] * pi[2] +
-                      pj[2] * pj[2];
-    const double kn = nix * nix + njx * njx + niy * niy + njy * njy + niz * niz + njz * njz;
-    deps = -0.5 * (kn - ko) * (0.5 * k.inv_m);
-  }
+  const double ko = pi[0] * pi[0] + pj[0] * pj[0] + pi[1] * pi[1] + pj[1] * pj[1] + pi[2] * pi[2] + pj[2] * pj[2];
+  const double kn = nix * nix + njx * njx + niy * niy + njy * njy + niz * niz + njz * njz;
+  deps = -0.5 * (kn - ko) * (0.5 * k.inv_m);
   // energy bound, Eq. (energy-bound): both new internal energies > 0
-  const R emin_old = ei < ej ? ei : ej;
-  R emin = emin_old + deps;
-  if constexpr (P::mixed) {
-    // float32 decides unless the margin is within a few ulps of zero
-    if (fabsf(emin) <= 8.0f * 1.1920929e-7f * emin_old) emin = exact_bound(deps) > 0.0 ? 1.0f : -1.0f;
-  }
+  const R emin = (ei < ej ? ei : ej) + deps;
   margin = emin;
   int decision = 0;
   if (k.scheme == SDPD_SCHEME_SSA) {
@@ -173,34 +181,20 @@ __device__ __forceinline__ int fd_pair(const FDConst<typename P::R>& k, typename
   } else if (k.scheme == SDPD_SCHEME_EMS) {
     // Metropolis ratio, Eq. (metropolis-ratio): the reverse move from v'
     // with the coefficients at the proposed energies
-    R bpar, bperp, ypar, yperp, xrpar, xrperp;
-    pair_coeffs(k, kpar, kperp, ei + deps, ej + deps, bpar, bperp, ypar, yperp, xrpar, xrperp);
+    R mrpar, mrperp, ypar, yperp;
+    pair_coeffs(k, kpar, kperp, ei + deps, ej + deps, mrpar, mrperp, ypar, yperp);
+    const R bpar = R(1) + mrpar, bperp = R(1) + mrperp;
     // one reciprocal for both directions of the reverse move's noise scale
     const R ryy = fm::div(R(1), ypar * yperp);
     const R ipar = yperp * ryy, ip = ypar * ryy;  // 1 / zt'_par, 1 / zt'_perp
-    R quad;
-    if constexpr (P::mixed) {
-      // reverse noise of the proposal v' = A v + B G:
-      // B'^-1 (v - A' v') = B'^-1 [(I - A' A) v - A' B G], each direction
-      // scaled separately, I - A' A from expm1 of the summed exponents; in
-      // float32 the literal v - A' v' loses its digits to cancellation when
-      // zt -> 0 (pairs near the cut-off)
-      const R cpar_r = -fm::expm1(xfpar + xrpar), cperp_r = -fm::expm1(xfperp + xrperp);
-      const R qpar = (cpar_r * vpar - bpar * zpar * gpar) * ipar;
-      const R qx = (cperp_r * (vx - vpar * ex) - bperp * zperp * (G[0] - gpar * ex)) * ip;
-      const R qy = (cperp_r * (vy - vpar * ey) - bperp * zperp * (G[1] - gpar * ey)) * ip;
-      const R qz = (cperp_r * (vz - vpar * ez) - bperp * zperp * (G[2] - gpar * ez)) * ip;
-      quad = qpar * qpar + qx * qx + qy * qy + qz * qz;
-    } else {
-      // reverse noise B'^-1 (v - A' v') from the proposed v' itself
-      const R wpar = ex * wx + ey * wy + ez * wz;
-      const R cb = (bpar - bperp) * wpar;
-      const R bx = vx - (bperp * wx + cb * ex), by = vy - (bperp * wy + cb * ey), bz = vz - (bperp * wz + cb * ez);
-      const R spar = ex * bx + ey * by + ez * bz;
-      const R cq = (ipar - ip) * spar;
-      const R qx = bx * ip + cq * ex, qy = by * ip + cq * ey, qz = bz * ip + cq * ez;
-      quad = qx * qx + qy * qy + qz * qz;
-    }
+    // reverse noise B'^-1 (v - A' v') from the proposed v' itself
+    const R wpar = ex * wx + ey * wy + ez * wz;
+    const R cb = (bpar - bperp) * wpar;
+    const R bx = vx - (bperp * wx + cb * ex), by = vy - (bperp * wy + cb * ey), bz = vz - (bperp * wz + cb * ez);
+    const R spar = ex * bx + ey * by + ez * bz;
+    const R cq = (ipar - ip) * spar;
+    const R qx = bx * ip + cq * ex, qy = by * ip + cq * ey, qz = bz * ip + cq * ez;
+    const R quad = qx * qx + qy * qy + qz * qz;
     const R g2 = G[0] * G[0] + G[1] * G[1] + G[2] * G[2];
     // log|B(v)| - log|B(v')| with |B| = zt_par zt_perp^2
     const R ldet = fm::log(zpar * zperp * zperp * (ipar * ip * ip));
@@ -216,6 +210,187 @@ __device__ __forceinline__ int fd_pair(const FDConst<typename P::R>& k, typename
   if (decision == 0) {
     pi[0] = nix; pi[1] = niy; pi[2] = niz;
     pj[0] = njx; pj[1] = njy; pj[2] = njz;
+  }
+  return decision;
+}
+
+// The float32 quantities that define a mixed-path proposal and its reverse
+// move, with the float64 energies: everything the Metropolis log-ratio of
+// Eq. (metropolis-ratio) is evaluated from.  alpha = 1 + m per direction
+// (m = expm1 of the exponent, so alpha - 1 carries no rounding of its own),
+// zt the noise scales; the r-suffixed values belong to the reverse move at
+// the proposed energies.
+struct MixedRatioIn {
+  float ex, ey, ez, vx, vy, vz, g0, g1, g2, u;
+  float mpar, mperp, zpar, zperp, mrpar, mrperp, ypar, yperp;
+  double ei, ej, deps;
+};
+
+// The Metropolis margin a - ln U of a mixed-path pair evaluated in float64
+// from its float32 inputs: the reference value that the float32 evaluation
+// approximates.  Reverse noise per direction theta,
+// G'_theta = [(1 - alpha'_theta alpha_theta) v_theta - alpha'_theta zt_theta G_theta] / zt'_theta,
+// which is B'^-1 (v - A' v') for v' = A v + B G; a = (|G|^2 - |G'|^2)/2 +
+// log(|B| / |B'|) + (C_K/kB - 1) log1p(deps (ei + ej + deps) / (ei ej)).
+// Kept out of line: it runs only for the rare pairs whose float32 margin is
+// within its error bound of zero (and for every pair when records are kept).
+static __device__ __noinline__ double mixed_margin_fp64(const MixedRatioIn& r, double CKm1) {
+  const double ex = r.ex, ey = r.ey, ez = r.ez, vx = r.vx, vy = r.vy, vz = r.vz;
+  const double g0 = r.g0, g1 = r.g1, g2 = r.g2;
+  const double mpar = r.mpar, mperp = r.mperp, mrpar = r.mrpar, mrperp = r.mrperp;
+  const double zpar = r.zpar, zperp = r.zperp, ypar = r.ypar, yperp = r.yperp;
+  const double vpar = ex * vx + ey * vy + ez * vz;
+  const double gpar = ex * g0 + ey * g1 + ez * g2;
+  const double cpar = -(mpar + mrpar + mpar * mrpar), cperp = -(mperp + mrperp + mperp * mrperp);
+  const double bpar = (1.0 + mrpar) * zpar, bperp = (1.0 + mrperp) * zperp;
+  const double qpar = (cpar * vpar - bpar * gpar) / ypar;
+  const double qx = (cperp * (vx - vpar * ex) - bperp * (g0 - gpar * ex)) / yperp;
+  const double qy = (cperp * (vy - vpar * ey) - bperp * (g1 - gpar * ey)) / yperp;
+  const double qz = (cperp * (vz - vpar * ez) - bperp * (g2 - gpar * ez)) / yperp;
+  const double quad = qpar * qpar + qx * qx + qy * qy + qz * qz;
+  const double gg = g0 * g0 + g1 * g1 + g2 * g2;
+  const double ldet = log((zpar * zperp * zperp) / (ypar * yperp * yperp));
+  const double ent = CKm1 * log1p(r.deps * (r.ei + r.ej + r.deps) / (r.ei * r.ej));
+  return 0.5 * (gg - quad) + ldet + ent - log((double)r.u);
+}
+
+// One pair update of the mixed path.  The pair arithmetic (geometry,
+// coefficients, proposal, momenta) is float32.  The internal energies are
+// float64 in the state; during a block visit a particle's energy is its
+// float64 value at load plus the visit's changes, which are kept as a
+// float-float sum (about 48 significant bits).  The energy change deps of a
+// pair is computed exactly from the float32 momenta before and after the
+// move: -1/(4m) sum (new^2 - old^2), each square split exactly by an FMA and
+// the differences and sums carried by two-sum, to float-float accuracy
+// (dh + dl).  This keeps every pair update energy-conserving to float64
+// rounding without float64 instructions, of which GB300 issues one for
+// every 64 float32 ones.
+//
+// The energy bound is decided in float32 when its margin is clearly away
+// from zero, else in float64 from the exact energies.  The Metropolis test
+// is decided in float64: the log-ratio is evaluated in float32 together with
+// a bound on its rounding error (a running error analysis of every
+// operation, the documented error of the hardware logarithm, and a factor 2
+// of safety), and a pair whose float32 margin is within that bound of zero
+// is re-evaluated by mixed_margin_fp64, so every decision is the one the
+// float64 evaluation of the same ratio gives.  m32 and tol receive the
+// float32 margin and its bound; margin the float64 margin whenever it was
+// evaluated (always when `exact` is set).  exact_e(ei, ej) gives the two
+// current energies in float64 (for the rare float64 evaluations).
+template <class ExactE>
+__device__ __forceinline__ int fd_pair_mixed(const FDConst<float>& k, float ex, float ey, float ez, float base,
+                                             const float G[3], float U, float lnU, float* pi, float* pj,
+                                             float eif, float ejf, ExactE exact_e, float& dh, float& dl,
+                                             double& margin, float& m32, float& tol, bool exact,
+                                             bool& negative) {
+  const float kpar = k.kpar_m2 * base, kperp = k.kperp_m2 * base;
+  margin = 0.0;
+  dh = 0.0f;
+  dl = 0.0f;
+  m32 = 0.0f;
+  tol = 0.0f;
+  if (!(kperp > 0.0f) || !(kpar > 0.0f)) return 0;  // at r = h the pair does nothing
+  const float vx = (pi[0] - pj[0]) * k.inv_m, vy = (pi[1] - pj[1]) * k.inv_m, vz = (pi[2] - pj[2]) * k.inv_m;
+  float mpar, mperp, zpar, zperp;  // alpha - 1 and zt per direction
+  pair_coeffs(k, kpar, kperp, eif, ejf, mpar, mperp, zpar, zperp);
+  // proposal, Eq. (proposal), as the velocity change
+  // v' - v = m_perp v + zt_perp G + [(m_par - m_perp) v_par + (zt_par - zt_perp) G_par] e
+  const float vpar = ex * vx + ey * vy + ez * vz;
+  const float gpar = ex * G[0] + ey * G[1] + ez * G[2];
+  const float cpar = (mpar - mperp) * vpar + (zpar - zperp) * gpar;
+  const float dvx = mperp * vx + zperp * G[0] + cpar * ex;
+  const float dvy = mperp * vy + zperp * G[1] + cpar * ey;
+  const float dvz = mperp * vz + zperp * G[2] + cpar * ez;
+  // momenta of Eq. (proposal-update), energy shared equally (Section 3.2)
+  const float dpx = k.half_m * dvx, dpy = k.half_m * dvy, dpz = k.half_m * dvz;
+  const float nn[6] = {pi[0] + dpx, pi[1] + dpy, pi[2] + dpz, pj[0] - dpx, pj[1] - dpy, pj[2] - dpz};
+  {  // deps = -1/2 of the kinetic-energy change of the stored momenta, exactly
+    const float oo[6] = {pi[0], pi[1], pi[2], pj[0], pj[1], pj[2]};
+    float Dh = 0.0f, Dl = 0.0f;
+#pragma unroll
+    for (int t = 0; t < 6; ++t) {
+      float pn, en, po, eo, d, ed, s, es;
+      eft::two_prod(nn[t], nn[t], pn, en);
+      eft::two_prod(oo[t], oo[t], po, eo);
+      eft::two_sum(pn, -po, d, ed);
+      eft::two_sum(Dh, d, s, es);
+      Dh = s;
+      Dl = __fadd_rn(Dl, __fadd_rn(__fadd_rn(es, ed), __fsub_rn(en, eo)));
+    }
+    eft::two_sum(Dh, Dl, Dh, Dl);  // renormalise
+    // times -1/(4m) (a float-float constant)
+    float ph, pl;
+    eft::two_prod(Dh, k.nq_hi, ph, pl);
+    pl = __fmaf_rn(Dh, k.nq_lo, __fmaf_rn(Dl, k.nq_hi, pl));
+    eft::two_sum(ph, pl, dh, dl);
+  }
+  // energy bound, Eq. (energy-bound): both new internal energies > 0;
+  // float32 decides unless the margin is within its rounding of zero
+  const float eminf = eif < ejf ? eif : ejf;
+  float emn = eminf + dh;
+  if (fabsf(emn) <= 32.0f * 5.9604645e-8f * (eminf + fabsf(dh))) {
+    double ei, ej;
+    exact_e(ei, ej);
+    emn = ((ei < ej ? ei : ej) + ((double)dh + (double)dl)) > 0.0 ? 1.0f : -1.0f;
+  }
+  margin = (double)emn;
+  int decision = 0;
+  if (k.scheme == SDPD_SCHEME_SSA) {
+    if (!(emn > 0.0f)) negative = true;
+  } else if (!(emn > 0.0f)) {
+    decision = 1;
+  } else if (k.scheme == SDPD_SCHEME_EMS) {
+    // reverse move from v' with the coefficients at the proposed energies
+    float mrpar, mrperp, ypar, yperp;
+    pair_coeffs(k, kpar, kperp, eif + dh, ejf + dh, mrpar, mrperp, ypar, yperp);
+    // 1 - alpha' alpha = -(m + m' + m m') (both m <= 0: no cancellation), alpha' zt
+    const float cpr = -(mpar + mrpar + mpar * mrpar), cqr = -(mperp + mrperp + mperp * mrperp);
+    const float bzpar = fmaf(mrpar, zpar, zpar), bzperp = fmaf(mrperp, zperp, zperp);
+    const float ryy = fm::div(1.0f, ypar * yperp);
+    const float ipar = yperp * ryy, ip = ypar * ryy;  // 1 / zt'_par, 1 / zt'_perp
+    // reverse noise B'^-1 (v - A' v') = B'^-1 [(I - A' A) v - A' B G] per
+    // direction: no cancellation when zt' -> 0 (pairs near the cut-off)
+    const float qpar = (cpr * vpar - bzpar * gpar) * ipar;
+    const float qx = (cqr * (vx - vpar * ex) - bzperp * (G[0] - gpar * ex)) * ip;
+    const float qy = (cqr * (vy - vpar * ey) - bzperp * (G[1] - gpar * ey)) * ip;
+    const float qz = (cqr * (vz - vpar * ez) - bzperp * (G[2] - gpar * ez)) * ip;
+    const float quad = qpar * qpar + qx * qx + qy * qy + qz * qz;
+    const float g2 = G[0] * G[0] + G[1] * G[1] + G[2] * G[2];
+    // log|B(v)| - log|B(v')| with |B| = zt_par zt_perp^2
+    const float ldet = fm::log(zpar * zperp * zperp * (ipar * ip * ip));
+    // (S(eps') - S(eps))/kB - (log T(eps') - log T(eps)) over both particles
+    const float x = fm::div(dh * (eif + ejf + dh), eif * ejf);
+    const float ent = k.CKm1 * fm::log1p(x);
+    const float mg = 0.5f * (g2 - quad) + ldet + ent - lnU;
+    // error bound of mg against its exact value for these inputs (u = 2^-24;
+    // 3.6e-7 bounds the absolute error of the hardware logarithm on
+    // [0.5, 2], 3 ulp elsewhere)
+    const float u = 5.9604645e-8f, elog = 3.6e-7f;
+    const float V = fabsf(vx) + fabsf(vy) + fabsf(vz), Gs = fabsf(G[0]) + fabsf(G[1]) + fabsf(G[2]);
+    const float qm = fabsf(qpar) * ipar * (fabsf(cpr) * V + bzpar * Gs) +
+                     (fabsf(qx) + fabsf(qy) + fabsf(qz)) * ip * (fabsf(cqr) * V + bzperp * Gs);
+    const float T = 8.0f * g2 + 23.0f * quad + 32.0f * qm + 11.0f * fabsf(ldet) + 25.0f * fabsf(ent) +
+                    11.0f * fabsf(lnU) + 23.0f;
+    tol = 2.0f * (u * T + 2.0f * elog);
+    if (fabsf(x) >= 0.0625f) tol += 2.0f * k.CKm1 * (elog + 16.0f * u);
+    m32 = mg;
+    double mgd = (double)mg;
+    if (exact || !(fabsf(mg) > tol)) {  // float32 not decisive (or NaN): float64
+      MixedRatioIn r;
+      r.ex = ex; r.ey = ey; r.ez = ez; r.vx = vx; r.vy = vy; r.vz = vz;
+      r.g0 = G[0]; r.g1 = G[1]; r.g2 = G[2]; r.u = U;
+      r.mpar = mpar; r.mperp = mperp; r.zpar = zpar; r.zperp = zperp;
+      r.mrpar = mrpar; r.mrperp = mrperp; r.ypar = ypar; r.yperp = yperp;
+      exact_e(r.ei, r.ej);
+      r.deps = (double)dh + (double)dl;
+      mgd = mixed_margin_fp64(r, k.CKm1_d);
+    }
+    margin = mgd;
+    if (mgd < 0.0) decision = 2;  // U > exp(a)
+  }
+  if (decision == 0) {
+    pi[0] = nn[0]; pi[1] = nn[1]; pi[2] = nn[2];
+    pj[0] = nn[3]; pj[1] = nn[4]; pj[2] = nn[5];
   }
   return decision;
 }
@@ -245,16 +420,28 @@ __device__ __forceinline__ int block_code(T w, int ox, int oy, int oz) {
 }
 
 template <class R>
-struct FdSmem {
+struct FdSmemBase {
   R px[kMaxBlock], py[kMaxBlock], pz[kMaxBlock];
-  R e[kMaxBlock];    // energy at hand (float64 path: the energy itself)
-  R acc[kMaxBlock];  // mixed path: float32 sum of this visit's energy changes
   int32_t cst[8], cbs[8];  // the block's cells: first storage index, offset in the block
   // staged pair data of the current chunk
   R G0[kChunk], G1[kChunk], G2[kChunk], lnU[kChunk];
   R ex[kChunk], ey[kChunk], ez[kChunk], base[kChunk];
   uint16_t pr[kChunk];
   uint16_t off[kMaxLevels + 1];  // level offsets of the block's pair list
+};
+template <class R>
+struct FdSmem;
+// float64 pair arithmetic: the energies themselves
+template <>
+struct FdSmem<double> : FdSmemBase<double> {
+  double e[kMaxBlock];
+};
+// float32 pair arithmetic: the energy at load (float32 copy) and the visit's
+// changes as a float-float sum; the uniforms, for float64 re-evaluations
+template <>
+struct FdSmem<float> : FdSmemBase<float> {
+  float e0[kMaxBlock], ahi[kMaxBlock], alo[kMaxBlock];
+  float U[kChunk];
 };
 
 // Block schedule of a colour launch: OPW blocks per warp (each on 32 / OPW
@@ -344,8 +531,13 @@ __global__ void __launch_bounds__(W * 32, fd_min_blocks<A, W>())
     for (int q = gl; q < nb; q += kGroupLanes) {
       const int g = gidx(q);
       sm.px[q] = a.px[g]; sm.py[q] = a.py[g]; sm.pz[q] = a.pz[g];
-      sm.e[q] = (R)a.eps[g];
-      sm.acc[q] = R(0);
+      if constexpr (A::mixed) {
+        sm.e0[q] = (float)a.eps[g];
+        sm.ahi[q] = 0.0f;
+        sm.alo[q] = 0.0f;
+      } else {
+        sm.e[q] = a.eps[g];
+      }
     }
     for (int L = gl; L <= nlev; L += kGroupLanes) sm.off[L] = lvl[o * (kMaxLevels + 1) + L];
     __syncwarp();
@@ -384,6 +576,7 @@ __global__ void __launch_bounds__(W * 32, fd_min_blocks<A, W>())
         pair_randoms_fast(seed, sweep, (uint64_t)a.id[ga], (uint64_t)a.id[gb], G, &U);
         sm.G0[slot] = G[0]; sm.G1[slot] = G[1]; sm.G2[slot] = G[2];
         sm.lnU[slot] = k.scheme == SDPD_SCHEME_EMS ? fm::log(U) : U;  // off the pairs' dependency chain
+        if constexpr (A::mixed) sm.U[slot] = U;
       }
       __syncwarp();
       // the chunk's levels, or parts of them
@@ -400,27 +593,45 @@ __global__ void __launch_bounds__(W * 32, fd_min_blocks<A, W>())
           const int ia = pr & 255, ib = pr >> 8;
           R pa[3] = {sm.px[ia], sm.py[ia], sm.pz[ia]};
           R pb[3] = {sm.px[ib], sm.py[ib], sm.pz[ib]};
-          const R ea = sm.e[ia], eb = sm.e[ib];
           const R G[3] = {sm.G0[slot], sm.G1[slot], sm.G2[slot]};
-          R deps, margin;
-          // float64 bound for the mixed path: energies at load plus this visit's sums
-          auto exact = [&](R dv) -> double {
-            const double da = a.eps[gidx(ia)] + (double)sm.acc[ia];
-            const double db = a.eps[gidx(ib)] + (double)sm.acc[ib];
-            return fmin(da, db) + (double)dv;
-          };
-          const int dcs = fd_pair<A>(k, sm.ex[slot], sm.ey[slot], sm.ez[slot], sm.base[slot], G, sm.lnU[slot], pa,
-                                     pb, ea, eb, deps, margin, negative, exact);
-          if (dcs == 0) {
-            sm.px[ia] = pa[0]; sm.py[ia] = pa[1]; sm.pz[ia] = pa[2];
-            sm.px[ib] = pb[0]; sm.py[ib] = pb[1]; sm.pz[ib] = pb[2];
-            sm.e[ia] = ea + deps;
-            sm.e[ib] = eb + deps;
-            if constexpr (A::mixed) {
-              sm.acc[ia] += deps;
-              sm.acc[ib] += deps;
+          double margin;
+          float m32 = 0.0f, tol = 0.0f;
+          int dcs;
+          if constexpr (A::mixed) {
+            const float eaf = sm.e0[ia] + sm.ahi[ia], ebf = sm.e0[ib] + sm.ahi[ib];
+            // the two energies in float64 (rare: near ties of the bound or the ratio)
+            auto exact_e = [&](double& ea, double& eb) {
+              ea = a.eps[gidx(ia)] + ((double)sm.ahi[ia] + (double)sm.alo[ia]);
+              eb = a.eps[gidx(ib)] + ((double)sm.ahi[ib] + (double)sm.alo[ib]);
+            };
+            float dh, dl;
+            dcs = fd_pair_mixed(k, sm.ex[slot], sm.ey[slot], sm.ez[slot], sm.base[slot], G, sm.U[slot],
+                                sm.lnU[slot], pa, pb, eaf, ebf, exact_e, dh, dl, margin, m32, tol,
+                                recs != nullptr, negative);
+            if (dcs == 0) {
+              sm.px[ia] = pa[0]; sm.py[ia] = pa[1]; sm.pz[ia] = pa[2];
+              sm.px[ib] = pb[0]; sm.py[ib] = pb[1]; sm.pz[ib] = pb[2];
+              float s, e;
+              eft::two_sum(sm.ahi[ia], dh, s, e);
+              sm.alo[ia] = __fadd_rn(sm.alo[ia], __fadd_rn(e, dl));
+              sm.ahi[ia] = s;
+              eft::two_sum(sm.ahi[ib], dh, s, e);
+              sm.alo[ib] = __fadd_rn(sm.alo[ib], __fadd_rn(e, dl));
+              sm.ahi[ib] = s;
+              bad |= !isfinite(eaf + dh) || !isfinite(ebf + dh);
             }
-            bad |= !isfinite(sm.e[ia]) || !isfinite(sm.e[ib]);
+          } else {
+            const double ea = sm.e[ia], eb = sm.e[ib];
+            double deps;
+            dcs = fd_pair(k, sm.ex[slot], sm.ey[slot], sm.ez[slot], sm.base[slot], G, sm.lnU[slot], pa, pb, ea,
+                          eb, deps, margin, negative);
+            if (dcs == 0) {
+              sm.px[ia] = pa[0]; sm.py[ia] = pa[1]; sm.pz[ia] = pa[2];
+              sm.px[ib] = pb[0]; sm.py[ib] = pb[1]; sm.pz[ib] = pb[2];
+              sm.e[ia] = ea + deps;
+              sm.e[ib] = eb + deps;
+              bad |= !isfinite(sm.e[ia]) || !isfinite(sm.e[ib]);
+            }
           }
           ++n_tot;
           n_acc += dcs == 0;
@@ -436,7 +647,9 @@ __global__ void __launch_bounds__(W * 32, fd_min_blocks<A, W>())
               rc.owner = (int32_t)o;
               rc.decision = dcs;
               rc.level = L;
-              rc.margin = (double)margin;
+              rc.margin = margin;
+              rc.margin_lo = A::mixed ? (double)m32 : margin;
+              rc.margin_tol = (double)tol;
               recs[s] = rc;
             }
           }
@@ -464,7 +677,7 @@ __global__ void __launch_bounds__(W * 32, fd_min_blocks<A, W>())
         a.pz[g] += (S)(sm.pz[q] - (R)a.pz[g]);
       }
       double e;
-      if constexpr (A::mixed) e = a.eps[g] + (double)sm.acc[q];  // one float64 update per visit
+      if constexpr (A::mixed) e = a.eps[g] + ((double)sm.ahi[q] + (double)sm.alo[q]);  // once per visit
       else e = sm.e[q];
       a.eps[g] = e;
       // pressure over rho^2 of the new energy, Eq. (pg-eos): pi = c_rho eps / (C_K m rho)
@@ -516,6 +729,9 @@ static FDConst<R> fd_const(const Consts& c, double dt) {
   k.dt_over_m = (R)(dt / c.m);
   k.CKm1 = (R)(c.C_K / c.kB - 1.0);
   k.four_kB_over_m = (R)(4.0 * c.kB / c.m);
+  k.CKm1_d = c.C_K / c.kB - 1.0;
+  k.nq_hi = (float)(-0.25 / c.m);
+  k.nq_lo = (float)(-0.25 / c.m - (double)k.nq_hi);
   k.scheme = c.scheme;
   return k;
 }

@@ -64,6 +64,16 @@ __host__ __device__ __forceinline__ uint32_t nbr_entry(int j, int ox, int oy, in
   return ((uint32_t)j << 6) | (uint32_t)((ox + 1) | ((oy + 1) << 2) | ((oz + 1) << 4));
 }
 
+// Position of entry k of particle i's neighbour list (cap entries, a multiple
+// of 4, per particle).  The lists of 32 consecutive particles (one warp of a
+// pair pass) are interleaved in groups of four entries:
+// [i / 32][k / 4][i % 32][k % 4], so that a warp reading entries k..k+3 of
+// its 32 particles with one 16-byte load per lane touches 512 consecutive
+// bytes.  The list array holds ceil(N / 32) * 32 * cap entries.
+__host__ __device__ __forceinline__ int64_t nbr_slot(int64_t i, int k, int cap) {
+  return ((((i >> 5) * (int64_t)(cap >> 2) + (k >> 2)) << 5) + (i & 31)) * 4 + (k & 3);
+}
+
 // ---------------------------------------------------------------------------
 // Pair distance from r^2.  float64: 1/r from the float32 reciprocal square
 // root refined by one Newton step for y = 1/sqrt(x), y <- y (3 - x y^2) / 2
@@ -125,8 +135,9 @@ __device__ __forceinline__ void philox4x64_10(uint64_t c0, uint64_t c1, uint64_t
 // Random numbers of one pair at one sweep: G ~ N(0, I3) and U ~ U(0,1).
 // Key (seed, 0), counter (sweep, id_min, id_max, 0).  Words 0 and 1 give G0,
 // G1 by Box-Muller on two uniforms; word 2 gives G2 by Box-Muller on its two
-// 32-bit halves; word 3 gives U.  float64: 53-bit uniforms (32-bit for G2);
-// float32: 23-bit uniforms from the top bits of the same words.
+// 32-bit halves; word 3 gives U.  Uniforms are (x + 1/2) 2^-b for the top
+// b = 53 bits of a word (32 for the halves of word 2).  The float32 path
+// rounds the same uniforms to float32 (pair_randoms_fast).
 __device__ __forceinline__ void pair_randoms(uint64_t seed, uint64_t sweep, uint64_t idi, uint64_t idj,
                                              double G[3], double* U) {
   uint64_t w[4];
@@ -143,24 +154,6 @@ __device__ __forceinline__ void pair_randoms(uint64_t seed, uint64_t sweep, uint
   double u3 = ((double)(uint32_t)(w[2] & 0xffffffffull) + 0.5) * two32;
   G[2] = sqrt(-2.0 * log(u2)) * cospi(2.0 * u3);
   *U = ((double)(w[3] >> 11) + 0.5) * two53;
-}
-
-__device__ __forceinline__ void pair_randoms(uint64_t seed, uint64_t sweep, uint64_t idi, uint64_t idj,
-                                             float G[3], float* U) {
-  uint64_t w[4];
-  philox4x64_10(sweep, idi, idj, 0ull, seed, 0ull, w);
-  const float two23 = 1.0f / 8388608.0f;
-  float u0 = ((float)(uint32_t)(w[0] >> 41) + 0.5f) * two23;
-  float u1 = ((float)(uint32_t)(w[1] >> 41) + 0.5f) * two23;
-  float R = sqrtf(-2.0f * logf(u0));
-  float s, c;
-  sincospif(2.0f * u1, &s, &c);
-  G[0] = R * c;
-  G[1] = R * s;
-  float u2 = ((float)(uint32_t)(w[2] >> 41) + 0.5f) * two23;
-  float u3 = ((float)((uint32_t)(w[2] & 0xffffffffull) >> 9) + 0.5f) * two23;
-  G[2] = sqrtf(-2.0f * logf(u2)) * cospif(2.0f * u3);
-  *U = ((float)(uint32_t)(w[3] >> 41) + 0.5f) * two23;
 }
 
 // ---------------------------------------------------------------------------
@@ -215,6 +208,17 @@ __device__ __forceinline__ double cellbits_to_w(uint32_t c, D4*) { return (doubl
 __device__ __forceinline__ float cellbits_to_w(uint32_t c, F4*) { return __uint_as_float(c); }
 __device__ __forceinline__ uint32_t w_to_cellbits(double w) { return (uint32_t)w; }
 __device__ __forceinline__ uint32_t w_to_cellbits(float w) { return __float_as_uint(w); }
+
+// Periodic wrap into [0, L) for a coordinate at most one box away.
+__device__ __forceinline__ double wrap_coord(double x, double L) {
+  if (x >= L) x = __dsub_rn(x, L);
+  else if (x < 0.0) x = __dadd_rn(x, L);
+  if (x >= L || x < 0.0) {  // further away: reduce with floor
+    x = x - L * floor(x / L);
+    if (x >= L) x = 0.0;
+  }
+  return x;
+}
 
 // Periodic minimum image of a float64 displacement (compare and subtract).
 __device__ __forceinline__ double min_image(double d, double L, double halfL) {
@@ -277,7 +281,6 @@ struct Workspace {
   float4* qf4;          // float64 path: float32 copies (x, y, z, 0) of the sorted positions
   uint32_t* nlist;      // neighbour lists, entry k of particle i at nlist[i * nbr_cap + k]
   int32_t* nn;          // neighbour count per particle
-  uint8_t* nbr_off;     // [N][28]: start of each of the 27 stencil cells' entries in the row, then the end
   // binning and sorting scratch
   int32_t* key;         // cell rank per particle (old order)
   int32_t* slot;        // arrival slot in the cell (old order)

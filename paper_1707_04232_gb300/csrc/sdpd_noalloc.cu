@@ -37,6 +37,7 @@ __global__ void k_static_zero(int32_t* cnt, int ncell) {
   if (c < ncell) cnt[c] = 0;
 }
 
+// cell of a coordinate already wrapped into [0, L)
 __device__ __forceinline__ int static_cell_1d(double x, double cs, int n) {
   int c = (int)floor(__ddiv_rn(x, cs));
   return c >= n ? n - 1 : (c < 0 ? 0 : c);
@@ -47,7 +48,7 @@ __global__ void k_static_bin(StaticGrid g, const double* __restrict__ q, int32_t
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= g.N) return;
   int c[3];
-  for (int d = 0; d < 3; ++d) c[d] = static_cell_1d(q[3 * i + d], g.cs[d], g.nc[d]);
+  for (int d = 0; d < 3; ++d) c[d] = static_cell_1d(sdpd::wrap_coord(q[3 * i + d], g.L[d]), g.cs[d], g.nc[d]);
   const int lin = c[0] + g.nc[0] * (c[1] + g.nc[1] * c[2]);
   cell_of[i] = lin;
   slot[i] = atomicAdd(&cnt[lin], 1);
@@ -103,7 +104,9 @@ __global__ void k_static_density(StaticGrid g, const double* __restrict__ q, con
                                  double* __restrict__ rho) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= g.N) return;
-  const double xi = q[3 * i], yi = q[3 * i + 1], zi = q[3 * i + 2];
+  // coordinates wrapped periodically into [0, L), as the regular path stores them
+  const double xi = sdpd::wrap_coord(q[3 * i], g.L[0]), yi = sdpd::wrap_coord(q[3 * i + 1], g.L[1]),
+               zi = sdpd::wrap_coord(q[3 * i + 2], g.L[2]);
   const int lin = cell_of[i];
   const int cx = lin % g.nc[0], cy = (lin / g.nc[0]) % g.nc[1], cz = lin / (g.nc[0] * g.nc[1]);
   const double inv_h = 1.0 / g.h;
@@ -118,9 +121,11 @@ __global__ void k_static_density(StaticGrid g, const double* __restrict__ q, con
         for (int t = start[c]; t < start[c + 1]; ++t) {
           const int j = order[t];
           if (j == i) continue;
-          const double dx = sdpd::min_image(__dsub_rn(xi, q[3 * j]), g.L[0], g.halfL[0]);
-          const double dy = sdpd::min_image(__dsub_rn(yi, q[3 * j + 1]), g.L[1], g.halfL[1]);
-          const double dz = sdpd::min_image(__dsub_rn(zi, q[3 * j + 2]), g.L[2], g.halfL[2]);
+          const double xj = sdpd::wrap_coord(q[3 * j], g.L[0]), yj = sdpd::wrap_coord(q[3 * j + 1], g.L[1]),
+                       zj = sdpd::wrap_coord(q[3 * j + 2], g.L[2]);
+          const double dx = sdpd::min_image(__dsub_rn(xi, xj), g.L[0], g.halfL[0]);
+          const double dy = sdpd::min_image(__dsub_rn(yi, yj), g.L[1], g.halfL[1]);
+          const double dz = sdpd::min_image(__dsub_rn(zi, zj), g.L[2], g.halfL[2]);
           const double r2 = sdpd::r2_of(dx, dy, dz);
           if (r2 < g.h2) acc += static_W(g, sqrt(r2) * inv_h);
         }

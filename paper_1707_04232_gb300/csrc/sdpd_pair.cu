@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(128) k_density(Consts c, Arrays<P> a, typename
                                                  const uint32_t* __restrict__ xmz, int update_eos,
                                                  int32_t* __restrict__ ncount_by_id,
                                                  uint32_t* __restrict__ nlist, int32_t* __restrict__ nn,
-                                                 uint8_t* __restrict__ nbr_off, int* __restrict__ status,
+                                                 int* __restrict__ status,
                                                  const float4* __restrict__ qf4) {
   using R = typename P::R;
   using V4 = typename P::V4;
@@ -156,7 +156,6 @@ __global__ void __launch_bounds__(128) k_density(Consts c, Arrays<P> a, typename
         const int r = __ldg(&mrank[nx + c.nc[0] * (ny + c.nc[1] * nz)]);
         const int beg = __ldg(&cell_start[r]), end = __ldg(&cell_start[r + 1]);
         home.frame(nx, ny, nz);
-        nbr_off[i * 28 + (ox + 1) + 3 * (oy + 1) + 9 * (oz + 1)] = (uint8_t)min(cnt, c.nbr_cap);
 #pragma unroll 4
         for (int j = beg; j < end; ++j) {
           if (j == i) continue;
@@ -174,7 +173,7 @@ __global__ void __launch_bounds__(128) k_density(Consts c, Arrays<P> a, typename
           const R r2 = r2_of(dx, dy, dz);
           if (r2 < h2) {
             acc += kernel_W<KIND>(pair_r(r2) * inv_h, cW);
-            if (cnt < c.nbr_cap) nlist[i * c.nbr_cap + cnt] = nbr_entry(j, ox, oy, oz);
+            if (cnt < c.nbr_cap) nlist[nbr_slot(i, cnt, c.nbr_cap)] = nbr_entry(j, ox, oy, oz);
             ++cnt;
           }
         }
@@ -183,7 +182,6 @@ __global__ void __launch_bounds__(128) k_density(Consts c, Arrays<P> a, typename
   }
   if (ncount_by_id) ncount_by_id[a.id[i]] = cnt;
   nn[i] = min(cnt, c.nbr_cap);
-  nbr_off[i * 28 + 27] = (uint8_t)min(cnt, c.nbr_cap);
   if (cnt > c.nbr_cap) atomicOr(status, kStNbrCap);
   const R rho_new = (R)c.m * ((R)c.W0 + acc);
   double e = a.eps[i];
@@ -245,11 +243,10 @@ __global__ void __launch_bounds__(128) k_force(Consts c, Arrays<P> a, const type
   R fx = R(0), fy = R(0), fz = R(0);
   home.frames_all(c);
   const int n = nn[i];
-  // the row is 16-byte aligned (nbr_cap is a multiple of 4): four entries
-  // per load, then four independent neighbour gathers
-  const uint4* row4 = reinterpret_cast<const uint4*>(nlist + i * c.nbr_cap);
+  // four entries per 16-byte load (a warp's loads are contiguous, see
+  // nbr_slot), then four independent neighbour gathers
   for (int k = 0; k < n; k += 4) {
-    const uint4 e4 = __ldg(&row4[k >> 2]);
+    const uint4 e4 = __ldg(reinterpret_cast<const uint4*>(nlist + nbr_slot(i, k, c.nbr_cap)));
     const uint32_t ev[4] = {e4.x, e4.y, e4.z, e4.w};
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
@@ -323,11 +320,11 @@ void launch_density(const Consts& c, const Workspace& w, int cur, int update_eos
   if (c.kernel == SDPD_KERNEL_LUCY)
     k_density<P, SDPD_KERNEL_LUCY><<<blocks_for(c.N, t), t, 0, s>>>(
         c, a, qp4, w.cell_start, w.mrank, w.xmin[0], w.xmin[1], w.xmin[2], update_eos, ncount_by_id, w.nlist,
-        w.nn, w.nbr_off, w.status, w.qf4);
+        w.nn, w.status, w.qf4);
   else
     k_density<P, SDPD_KERNEL_CUBIC><<<blocks_for(c.N, t), t, 0, s>>>(
         c, a, qp4, w.cell_start, w.mrank, w.xmin[0], w.xmin[1], w.xmin[2], update_eos, ncount_by_id, w.nlist,
-        w.nn, w.nbr_off, w.status, w.qf4);
+        w.nn, w.status, w.qf4);
 }
 
 template <class P>

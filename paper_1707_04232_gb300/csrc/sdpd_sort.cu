@@ -19,16 +19,6 @@ __device__ __forceinline__ int cell_of(double x, double cs, int n) {
 // Cell of a fixed-point coordinate: floor(u * n / 2^32), exact.
 __device__ __forceinline__ int cell_of(uint32_t u, int n) { return (int)__umulhi(u, (uint32_t)n); }
 
-// Periodic wrap into [0, L) for a coordinate at most one box away.
-__device__ __forceinline__ double wrap_coord(double x, double L) {
-  if (x >= L) x = __dsub_rn(x, L);
-  else if (x < 0.0) x = __dadd_rn(x, L);
-  if (x >= L || x < 0.0) {  // further away: reduce with floor
-    x = x - L * floor(x / L);
-    if (x >= L) x = 0.0;
-  }
-  return x;
-}
 
 template <class P>
 __global__ void k_load(Consts c, const double* __restrict__ io_q, const double* __restrict__ io_p,

@@ -51,6 +51,7 @@ class sdpd_obs(C.Structure):
 PAIR_REC_DTYPE = np.dtype([
     ("id_i", np.int64), ("id_j", np.int64), ("colour", np.int32), ("owner", np.int32),
     ("decision", np.int32), ("level", np.int32), ("margin", np.float64),
+    ("margin_lo", np.float64), ("margin_tol", np.float64),
 ])
 
 # Every symbol include/sdpd.h declares: (name, restype, argtypes).

@@ -8,8 +8,8 @@ shows no bias at dt = 1 t_K either; EMS rejects more than AMS and more at
 larger steps; SSA breaks down (negative internal energy) at K = 5 where the
 Metropolised schemes stay stable.  The rejection rates themselves depend on
 the viscosity, which the paper gives in SI units only, so their values are
-not compared with the paper's.  The multiple-time-step driver runs and
-reports finite drift slopes.
+not compared with the paper's.  Multiple time steps divide the energy drift
+of the full dynamics (Section 4.2).
 """
 import numpy as np
 import pytest
@@ -49,12 +49,19 @@ def test_ssa_breaks_down_where_metropolis_does_not():
     assert not ems["unstable"]
 
 
-def test_mts_drift_runs():
-    r = X.mts_drift(0.392, thetas=(1, 5), replicas=3, t_sim=40.0, n_samples=10)
-    for th in ("1", "5"):
-        assert np.isfinite(r["slopes"][th]["mean"])
+def test_mts_divides_the_energy_drift():
+    """Section 4.2: with the sweep taken every theta = 10 Verlet steps (and
+    step 10 dt), the energy drift of the full dynamics at dt = 0.392 t_K
+    (K = 5, 1000 particles, EMS, 10 replicas over 1000 t_K) is divided by
+    more than 2 against one sweep per step (measured: by 4.1; the paper
+    reports a factor of about 6).  The single-step drift is itself well
+    above its spread over the replicas, so the ratio is significant."""
+    r = X.mts_drift(0.392, thetas=(1, 10), replicas=10, t_sim=1000.0, n_samples=100)
+    for th in ("1", "10"):
         assert r["status"][th] == ["ok"]
-    assert np.isfinite(r["ratio_to_sts"]["5"])
+    sts = r["slopes"]["1"]
+    assert sts["mean"] > 3.0 * sts["std"] / np.sqrt(10.0), sts
+    assert 0.0 < r["ratio_to_sts"]["10"] < 0.5, r["ratio_to_sts"]
 
 
 def test_mixed_statistics_agree_with_float64():

@@ -5,11 +5,11 @@ Tolerances (from the accuracy targets of the library):
     bit-exact (float64 path; the predicate r^2 < h^2 is a fixed sequence of
     correctly rounded operations on both sides);
   * float64 path: rho within 1e-12 relative, F within 1e-12 of max|F|;
-    accept/reject decisions equal, a flip allowed only where the oracle's
-    margin |a - ln U| (or the energy bound margin) is below 1e-9;
-  * mixed path (float32 pair arithmetic): rho within 1e-5 of max rho, F within
-    1e-5 of max|F|;
-  * trajectories: positions within 1e-6 a after 10 steps.
+    accept/reject decisions equal (no flip);
+  * mixed path (float32 pair arithmetic, float64 energies, float64-decided
+    Metropolis tests): rho within 1e-5 of max rho, F within 1e-5 of max|F|;
+    sweep energy conserved to float64 rounding;
+  * trajectories: positions within 1e-6 a after 10 steps (both paths).
 """
 import numpy as np
 import pytest
@@ -120,7 +120,11 @@ def test_density_and_force_mixed(kind, kernel):
 # One fluctuation/dissipation sweep (Sections 3.2-3.3)
 # --------------------------------------------------------------------------
 
-def check_sweep_against_oracle(recs_g, recs_o, tol_flip=1e-9):
+def check_sweep_against_oracle(recs_g, recs_o, tol_flip=0.0):
+    """Pair set, colours, owners and per-particle order equal to the
+    oracle's; returns the decision flips as (pair, oracle margin, GPU
+    margin), each of which must have |oracle margin| < tol_flip (none at the
+    default 0: every decision equal)."""
     key = lambda r: (int(r["id_i"]), int(r["id_j"]))
     go = {key(r): r for r in recs_g}
     oo = {key(r): (k, r) for k, r in enumerate(recs_o)}
@@ -146,35 +150,84 @@ def check_sweep_against_oracle(recs_g, recs_o, tol_flip=1e-9):
     return flips
 
 
+_oracle_sweeps = {}
+
+
+def oracle_sweep(q, p, e, L, K, scheme, kernel, dt, seed):
+    """The oracle's sweep of a state, kept for the other launch shapes of
+    the same case."""
+    key = (q.tobytes(), p.tobytes(), e.tobytes(), tuple(L), K, scheme, kernel, dt, seed)
+    if key not in _oracle_sweeps:
+        P = oparams(len(e), L, K, kernel=kernel, scheme=scheme)
+        _oracle_sweeps.clear()
+        _oracle_sweeps[key] = O.fd_sweep(P, q, p, e, dt, seed, 0, records=True)
+    return _oracle_sweeps[key]
+
+
+def sweep_fp64_vs_oracle(q, p, e, L, K, scheme, kernel=sdpd.KERNEL_LUCY, dt=DT, seed=77, shapes=None):
+    """One float64 sweep on the GPU and in the oracle from the same state:
+    every decision equal, momenta and energies within 1e-10 (relative to
+    the largest).  Returns the GPU pair records."""
+    N = len(e)
+    s = gpu(N, L, K, scheme=scheme, kernel=kernel, fd_only=True, debug=True)
+    if shapes is not None:
+        s.set_tuning(*shapes)
+    s.set_state(q, p, e)
+    s.step(dt, 1, seed=seed)
+    qg, pg, eg = s.get_state()
+    recs = s.pair_records()
+    st, po, eo, stats, recs_o = oracle_sweep(q, p, e, L, K, scheme, kernel, dt, seed)
+    flips = check_sweep_against_oracle(recs, recs_o)
+    assert flips == []
+    obs = s.observables(check=False)
+    assert obs["n_pairs"] == stats.n_pairs
+    assert obs["n_accept"] == stats.n_accept
+    assert np.abs(pg - po).max() <= 1e-10 * max(1.0, np.abs(po).max())
+    assert np.abs(eg - eo).max() <= 1e-10 * eo.max()
+    assert (qg == q).all()  # the sweep never moves particles
+    return recs
+
+
 @pytest.mark.parametrize("scheme", [sdpd.SCHEME_EMS, sdpd.SCHEME_AMS, sdpd.SCHEME_SSA])
 @pytest.mark.parametrize("kind,kernel", [("lattice1000", sdpd.KERNEL_LUCY), ("random_rect", sdpd.KERNEL_LUCY),
                                          ("lattice_cold_K5", sdpd.KERNEL_LUCY),
                                          ("random_rect", sdpd.KERNEL_CUBIC)])
 def test_fd_sweep_fp64_matches_oracle(kind, kernel, scheme):
     q, p, e, L, K = system(kind)
-    N = len(e)
     dt = 0.05 if kind == "lattice_cold_K5" else DT
-    s = gpu(N, L, K, scheme=scheme, kernel=kernel, fd_only=True, debug=True)
-    s.set_state(q, p, e)
-    s.step(dt, 1, seed=77)
-    qg, pg, eg = s.get_state()
-    recs = s.pair_records()
-    P = oparams(N, L, K, kernel=kernel, scheme=scheme)
-    st, po, eo, stats, recs_o = O.fd_sweep(P, q, p, e, dt, 77, 0, records=True)
-    flips = check_sweep_against_oracle(recs, recs_o)
-    obs = s.observables(check=False)
-    assert obs["n_pairs"] == stats.n_pairs
-    if not flips:
-        assert obs["n_accept"] == stats.n_accept
-        assert np.abs(pg - po).max() <= 1e-10 * max(1.0, np.abs(po).max())
-        assert np.abs(eg - eo).max() <= 1e-10 * eo.max()
-    assert (qg == q).all()  # the sweep never moves particles
+    sweep_fp64_vs_oracle(q, p, e, L, K, scheme, kernel=kernel, dt=dt)
+
+
+@pytest.mark.parametrize("shapes", [(1, 128), (3, 32), (0, 128)])
+@pytest.mark.parametrize("scheme", [sdpd.SCHEME_EMS, sdpd.SCHEME_AMS, sdpd.SCHEME_SSA])
+def test_fd_sweep_fp64_matches_oracle_many_blocks(scheme, shapes):
+    """32^3 lattice: 12 cells per axis, 216 blocks per colour, several
+    blocks per warp or warp per block, taken from the atomic queue deepest
+    first -- the launch shapes of the large systems, against the oracle's
+    sequential sweep."""
+    q, p, e, L, K = system("lattice32k")
+    sweep_fp64_vs_oracle(q, p, e, L, K, scheme, shapes=shapes)
+
+
+def test_fd_sweep_fp64_matches_oracle_deep_blocks():
+    """A disordered fluid of 40^3 particles (uniform random positions, so
+    local density fluctuates): its deepest blocks run more than 100
+    dependency levels (101 in the oracle's order), against the oracle's
+    sequential sweep."""
+    L = (40.0,) * 3
+    N = 40 ** 3
+    q, p, e = random_box_state(N, 1.0, 1.0, 1.0, 1.5 * 99.0, seed=21)
+    q = q * 40.0
+    q = np.where(q >= 40.0, 0.0, q)
+    recs = sweep_fp64_vs_oracle(q, p, e, L, 100.0, sdpd.SCHEME_EMS, shapes=(1, 128))
+    assert recs["level"].max() >= 100
 
 
 def test_fd_sweep_mixed_statistics():
     """Mixed precision: same pair set and colouring, same decisions except
-    near ties, energy conserved by every sweep to float32 accuracy of the
-    kinetic-energy changes."""
+    near ties, energy conserved by every sweep to float64 rounding (the
+    energy changes are float64 sums of exact products of the float32
+    momenta)."""
     q, p, e, L, K = system("lattice_cold_K5")
     N = len(e)
     s = gpu(N, L, K, precision=sdpd.MIXED, fd_only=True, debug=True)
@@ -184,23 +237,38 @@ def test_fd_sweep_mixed_statistics():
     recs = s.pair_records()
     P = oparams(N, L, K)
     st, po, eo, stats, recs_o = O.fd_sweep(P, q, p, e, 0.05, 5, 0, records=True)
-    assert {(int(r["id_i"]), int(r["id_j"])) for r in recs} == {(int(r["id_i"]), int(r["id_j"])) for r in recs_o}
-    g = recs[np.lexsort((recs["id_j"], recs["id_i"]))]
-    o = recs_o[np.lexsort((recs_o["id_j"], recs_o["id_i"]))]
-    agree = np.mean(g["decision"] == o["decision"])
-    assert agree > 0.9999
+    flips = check_sweep_against_oracle(recs, recs_o, tol_flip=1e-4)
+    assert len(flips) <= 2
     E1 = s.observables()["E"]
-    assert abs(E1 - E0) < 1e-6 * abs(E0)
+    assert abs(E1 - E0) < 1e-12 * abs(E0)
 
 
-@pytest.mark.parametrize("dt", [0.001, 0.02])
-def test_fd_sweep_mixed_metropolis_ratio_accuracy(dt):
-    """Mixed EMS against the float64 path on the same state (20^3 lattice,
-    K = 100, kT = 1): at small steps most Metropolis margins a - ln U sit
-    just above zero, so float32 error in the log-ratio a would turn into
-    extra rejections.  The margins agree to 1e-4 near zero, and the decisions
-    of all but a few in 1e5 pairs are equal."""
+def test_mixed_records_do_not_change_the_sweep():
+    """Kept pair records make every Metropolis test evaluate its float64
+    ratio; without records only the near ties do.  Both runs must end in
+    the same state bit for bit (the float32 error bound is never wrong)."""
     w = Workload(n=20, K=100.0, kT=1.0, seed=2)
+    q, p, e = lattice_state(w)
+    out = []
+    for debug in (False, True):
+        s = gpu(w.N, (w.L,) * 3, w.K, precision=sdpd.MIXED, fd_only=True, debug=debug)
+        s.set_state(q, p, e)
+        s.step(0.005, 3, seed=8)
+        out.append(s.get_state())
+    for a, b in zip(*out):
+        assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("n", [20, 32])
+@pytest.mark.parametrize("dt", [0.001, 0.005, 0.02])
+def test_fd_sweep_mixed_metropolis_ratio_accuracy(dt, n):
+    """Mixed EMS against the float64 path on the same state (n^3 lattice,
+    K = 100, kT = 1).  The mixed path decides each Metropolis test in
+    float64: its float32 estimate of a - ln U stays within the error bound
+    that selects the float64 re-evaluation, and every decision follows the
+    float64 margin.  The two paths differ only through the float32 proposal
+    (coefficients and momenta), so decisions can differ only at near ties."""
+    w = Workload(n=n, K=100.0, kT=1.0, seed=2)
     q, p, e = lattice_state(w)
     out = {}
     for prec in (sdpd.FP64, sdpd.MIXED):
@@ -211,7 +279,14 @@ def test_fd_sweep_mixed_metropolis_ratio_accuracy(dt):
         out[prec] = r[np.lexsort((r["id_j"], r["id_i"]))]
     a, b = out[sdpd.FP64], out[sdpd.MIXED]
     assert np.array_equal(a["id_i"], b["id_i"]) and np.array_equal(a["id_j"], b["id_j"])
-    assert np.mean(a["decision"] != b["decision"]) < 3e-5
+    met = b["decision"] != 1
+    # the float32 estimate is within its bound, and the decision is the float64 one
+    assert (np.abs(b["margin_lo"] - b["margin"])[met] <= b["margin_tol"][met]).all()
+    assert np.array_equal(b["decision"][met] == 2, b["margin"][met] < 0.0)
+    assert b["margin_tol"][met].max() < 1e-3
+    flip = a["decision"] != b["decision"]
+    assert flip.mean() <= 1e-5
+    assert (np.abs(a["margin"][flip]) < 1e-4).all(), a["margin"][flip]
     near = (np.abs(a["margin"]) < 0.05) & (a["decision"] != 1)
     assert near.sum() > 1000
     assert np.abs(a["margin"][near] - b["margin"][near]).max() < 1e-4
@@ -319,7 +394,8 @@ def test_energy_histogram_is_exact(precision):
 @pytest.mark.parametrize("kind", ["lattice1000", "random_rect"])
 def test_trajectory_mixed_verlet_10_steps(kind):
     """Deterministic part (Velocity Verlet only): float32 pair arithmetic and
-    fixed-point positions stay within 2e-6 a of the float64 oracle."""
+    fixed-point positions stay within 1e-6 a of the float64 oracle after 10
+    steps (measured: 3e-8 a on the lattice, 5e-8 a in the random fluid)."""
     q, p, e, L, K = system(kind)
     N = len(e)
     s = gpu(N, L, K, precision=sdpd.MIXED, scheme=sdpd.SCHEME_NONE)
@@ -328,16 +404,19 @@ def test_trajectory_mixed_verlet_10_steps(kind):
     qg, pg, eg = s.get_state()
     P = oparams(N, L, K, scheme=O.SCHEME_NONE)
     st, qo, po, eo, stats, _ = O.run(P, q, p, e, DT, 10, seed=3)
-    assert min_image_err(qg, qo, L) < 2e-6
-    assert np.abs(eg - eo).max() < 1e-5 * eo.max()
+    assert min_image_err(qg, qo, L) < 1e-6
+    assert np.abs(pg - po).max() < 1e-5 * np.abs(po).max()
+    assert np.abs(eg - eo).max() < 1e-6 * eo.max()
 
 
 @pytest.mark.parametrize("kind", ["lattice1000", "random_rect"])
 def test_trajectory_mixed_ems_10_steps(kind):
-    """With the Metropolis sweep, float32 ratios flip the rare decisions whose
-    margin |a - ln U| is below their ~1e-6 error; those pairs' momenta then
-    differ by the noise of one pair update.  Per observable the run must
-    agree with the float64 oracle; per particle almost everywhere."""
+    """Full steps with the Metropolis sweep against the float64 oracle.  The
+    mixed path decides every Metropolis test in float64, for its float32
+    proposal; a decision can differ from the oracle's only where the two
+    proposals move the margin a - ln U across zero (margins within ~1e-4,
+    about 2e-7 of the decisions: ~0.1 expected over these 10 sweeps).  With
+    every decision equal, every particle stays within 1e-6 a."""
     q, p, e, L, K = system(kind)
     N = len(e)
     s = gpu(N, L, K, precision=sdpd.MIXED)
@@ -346,17 +425,16 @@ def test_trajectory_mixed_ems_10_steps(kind):
     qg, pg, eg = s.get_state()
     P = oparams(N, L, K)
     st, qo, po, eo, stats, _ = O.run(P, q, p, e, DT, 10, seed=3)
-    Lv = np.asarray(L)
-    dq = np.abs((qg - qo + 0.5 * Lv) % Lv - 0.5 * Lv).max(axis=1)
-    assert np.mean(dq < 2e-6) > 0.97
-    assert dq.max() < 1e-2
     o_g = s.observables()
+    assert o_g["n_pairs"] == stats.n_pairs
+    assert o_g["n_accept"] == stats.n_accept, "decisions differ from the oracle's"
+    assert min_image_err(qg, qo, L) < 1e-6
+    assert np.abs(pg - po).max() < 1e-5 * np.abs(po).max()
+    assert np.abs(eg - eo).max() < 1e-6 * eo.max()
     o_o = O.observables(P, po, eo)
-    assert abs(o_g["E"] - o_o["E"]) < 1e-6 * abs(o_o["E"])
-    assert abs(o_g["T_kin"] - o_o["T_kin"]) < 1e-3 * o_o["T_kin"]
-    # one flipped decision moves up to ~0.1 kT of internal energy of two
-    # particles: a few flips shift the mean internal temperature by ~1e-5
-    assert abs(o_g["T_int"] - o_o["T_int"]) < 1e-4 * o_o["T_int"]
+    assert abs(o_g["E"] - o_o["E"]) < 1e-7 * abs(o_o["E"])
+    assert abs(o_g["T_kin"] - o_o["T_kin"]) < 1e-5 * o_o["T_kin"]
+    assert abs(o_g["T_int"] - o_o["T_int"]) < 1e-7 * o_o["T_int"]
     # total momentum: every accepted pair update rounds two float32 sums per
     # component (p_i + dp, p_j - dp), an unbiased error of std <= 2^-24 |p| / sqrt(3)
     # each; the float64 oracle conserves it to rounding.  Five standard
@@ -379,7 +457,8 @@ def test_fd_only_conserves_energy_and_momentum(precision):
     o0 = s.observables()
     s.step(0.1, 20, seed=1)
     o1 = s.observables()
-    tol = 1e-12 if precision == sdpd.FP64 else 1e-6
+    # float64 energies and float64 energy changes on both paths
+    tol = 1e-12 if precision == sdpd.FP64 else 1e-10
     assert abs(o1["E"] - o0["E"]) < tol * abs(o0["E"])
     assert np.abs(o1["P"] - o0["P"]).max() < (1e-11 if precision == sdpd.FP64 else 1e-3)
     assert o1["eps_min"] > 0.0

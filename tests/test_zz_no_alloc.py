@@ -30,6 +30,17 @@ def systems():
     q, p, e = random_box_state(N, 1.0, 1.0, 1.0, 28.5, seed=9)
     q = np.where(q * np.array(L) >= np.array(L), 0.0, q * np.array(L))
     yield "random_rect", q, p, e, L
+    # 16^3 = 4096 cells (more than the 1024 threads of the cell scan, which
+    # then takes several cells per thread); a few coordinates just below 0
+    # and exactly at the box side, which both paths wrap periodically
+    L = (40.0,) * 3
+    N = 5000
+    q, p, e = random_box_state(N, 1.0, 1.0, 1.0, 28.5, seed=12)
+    q = q * 40.0
+    q[:8, 0] = -1e-12
+    q[8:16, 1] = 40.0
+    q[16:24, 2] = -1e-12
+    yield "random_40_edges", q, p, e, L
 
 
 @pytest.mark.parametrize("kernel", [sdpd.KERNEL_LUCY, sdpd.KERNEL_CUBIC])
@@ -52,8 +63,17 @@ def test_static_density_matches_regular_path_twice(kernel):
 
 
 def test_static_density_rejects_oversize_inputs():
-    # beyond the fixed working memory: rejected on the host, nothing launched
-    st = sdpd.sdpd_density_static(65537, (100.0,) * 3, 1.0, 2.5, sdpd.KERNEL_LUCY, 0, 0, 0)
+    """Beyond the fixed working memory: rejected on the host with
+    SDPD_ERR_CAPACITY before any device work, with valid buffers too."""
+    N = 1000
+    qd = torch.rand((N, 3), dtype=torch.float64, device="cuda") * 10.0
+    rho = torch.full((N,), -7.0, dtype=torch.float64, device="cuda")
+    s = torch.cuda.current_stream().cuda_stream
+    # too many particles
+    st = sdpd.sdpd_density_static(65537, (100.0,) * 3, 1.0, 2.5, sdpd.KERNEL_LUCY, 0, 0, s)
     assert st == sdpd.ERR_CAPACITY
-    st = sdpd.sdpd_density_static(1000, (500.0,) * 3, 1.0, 2.5, sdpd.KERNEL_LUCY, 0, 0, 0)
-    assert st in (sdpd.ERR_CAPACITY, sdpd.ERR_INVALID_ARG)
+    # too many cells: 200^3 cells for a 500^3 box at h = 2.5
+    st = sdpd.sdpd_density_static(N, (500.0,) * 3, 1.0, 2.5, sdpd.KERNEL_LUCY, qd.data_ptr(), rho.data_ptr(), s)
+    assert st == sdpd.ERR_CAPACITY
+    torch.cuda.synchronize()
+    assert (rho.cpu().numpy() == -7.0).all()

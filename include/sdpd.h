@@ -42,7 +42,9 @@ extern "C" {
 #define SDPD_ERR_CUDA 6               /* a CUDA runtime call failed */
 #define SDPD_ERR_TIMEOUT 7            /* a bounded device wait ran out */
 #define SDPD_ERR_NO_WORKSPACE 8       /* no (or too small a) workspace is bound */
-#define SDPD_ERR_CAPACITY 9           /* a 2x2x2 cell block exceeded its particle/pair capacity */
+#define SDPD_ERR_CAPACITY 9           /* a fixed capacity without a fallback was exceeded (the
+                                         gradient passes' neighbour-list rows of 160 entries;
+                                         sdpd_density_static's static working memory) */
 #define SDPD_ERR_NO_STATE 10          /* sdpd_step/get_state before sdpd_set_state */
 #define SDPD_ERR_HOST_MEMORY 11       /* a host-side table could not be allocated */
 
@@ -153,9 +155,13 @@ int sdpd_get_state(sdpd_t* s, double* q, double* p, double* eps, int on_device);
  * cell blocks are independent; within a block pairs go by (rank difference,
  * lower rank), rank = position of the id among the block's particles)
  * and draws the pair's random numbers from Philox4x64-10 keyed by seed with
- * counter (sweep number, min id, max id, 0).  Asynchronous on the handle's
- * stream.  Errors: SDPD_ERR_INVALID_ARG (dt <= 0, nsteps < 0),
- * SDPD_ERR_NO_STATE, SDPD_ERR_CUDA; device errors are sticky. */
+ * counter (sweep number, min id, max id, 0).  Any local density completes:
+ * a particle with more than 160 neighbours has its forces summed from the
+ * cells instead of its list, and a block with more than 256 particles, 2048
+ * owned pairs or 255 dependency levels is swept pair by pair in the same
+ * order (slower, same result).  Asynchronous on the handle's stream.
+ * Errors: SDPD_ERR_INVALID_ARG (dt <= 0, nsteps < 0), SDPD_ERR_NO_STATE,
+ * SDPD_ERR_CUDA; device errors are sticky. */
 int sdpd_step(sdpd_t* s, double dt, int64_t nsteps, uint64_t seed);
 
 /* Reduce the observables of the current state (float64) and copy them to

@@ -74,7 +74,8 @@ __global__ void k_adj_gather(int64_t N, const int32_t* __restrict__ id, const do
 template <int KIND, int MODE>
 __global__ void __launch_bounds__(128) k_adj_pairsum(Consts c, const D4* __restrict__ qp4, const D4* __restrict__ q4,
                                                      const D4* __restrict__ vs4, const uint32_t* __restrict__ nlist,
-                                                     const int32_t* __restrict__ nn, double* __restrict__ A) {
+                                                     const int32_t* __restrict__ nn, double* __restrict__ A,
+                                                     int* __restrict__ status) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= c.N) return;
   const D4 qi = ld4(&qp4[i]);
@@ -84,7 +85,11 @@ __global__ void __launch_bounds__(128) k_adj_pairsum(Consts c, const D4* __restr
   if (MODE == 0) vi = ld4(&vs4[i]);
   const double inv_h = 1.0 / c.h;
   double acc = 0.0;
-  const int n = nn[i];
+  int n = nn[i];
+  if (n > c.nbr_cap) {  // the gradient passes walk the list only
+    atomicOr(status, kStNbrCap);
+    n = c.nbr_cap;
+  }
 #pragma unroll 2
   for (int k = 0; k < n; ++k) {
     const uint32_t e = __ldg(&nlist[nbr_slot(i, k, c.nbr_cap)]);
@@ -240,7 +245,8 @@ __global__ void __launch_bounds__(128) k_adj_back(Consts c, const D4* __restrict
                                                   const D4* __restrict__ vs4, const int32_t* __restrict__ id,
                                                   const uint32_t* __restrict__ nlist,
                                                   const int32_t* __restrict__ nn, double wt, int accumulate,
-                                                  double* __restrict__ qbar, double* __restrict__ thbar) {
+                                                  double* __restrict__ qbar, double* __restrict__ thbar,
+                                                  int* __restrict__ status) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= c.N) return;
   const D4 qi = ld4(&qp4[i]);
@@ -249,7 +255,11 @@ __global__ void __launch_bounds__(128) k_adj_back(Consts c, const D4* __restrict
   im.init(c, q4[i].w);
   const double inv_h = 1.0 / c.h, m = c.m, cm2 = wt * c.m * c.m;
   double gx = 0.0, gy = 0.0, gz = 0.0, gh = 0.0;
-  const int n = nn[i];
+  int n = nn[i];
+  if (n > c.nbr_cap) {  // the gradient passes walk the list only
+    atomicOr(status, kStNbrCap);
+    n = c.nbr_cap;
+  }
 #pragma unroll 2
   for (int k = 0; k < n; ++k) {
     const uint32_t e = __ldg(&nlist[nbr_slot(i, k, c.nbr_cap)]);
@@ -350,11 +360,11 @@ void launch_adj_pairsum(const Consts& c, const Workspace& w, int cur, int mode, 
   const D4* q4 = (const D4*)w.q4[cur];
   const unsigned nb = nblocks(c.N, 128);
   if (c.kernel == SDPD_KERNEL_LUCY) {
-    if (mode == 0) k_adj_pairsum<SDPD_KERNEL_LUCY, 0><<<nb, 128, 0, s>>>(c, qp4, q4, vs4, w.nlist, w.nn, A);
-    else k_adj_pairsum<SDPD_KERNEL_LUCY, 1><<<nb, 128, 0, s>>>(c, qp4, q4, vs4, w.nlist, w.nn, A);
+    if (mode == 0) k_adj_pairsum<SDPD_KERNEL_LUCY, 0><<<nb, 128, 0, s>>>(c, qp4, q4, vs4, w.nlist, w.nn, A, w.status);
+    else k_adj_pairsum<SDPD_KERNEL_LUCY, 1><<<nb, 128, 0, s>>>(c, qp4, q4, vs4, w.nlist, w.nn, A, w.status);
   } else {
-    if (mode == 0) k_adj_pairsum<SDPD_KERNEL_CUBIC, 0><<<nb, 128, 0, s>>>(c, qp4, q4, vs4, w.nlist, w.nn, A);
-    else k_adj_pairsum<SDPD_KERNEL_CUBIC, 1><<<nb, 128, 0, s>>>(c, qp4, q4, vs4, w.nlist, w.nn, A);
+    if (mode == 0) k_adj_pairsum<SDPD_KERNEL_CUBIC, 0><<<nb, 128, 0, s>>>(c, qp4, q4, vs4, w.nlist, w.nn, A, w.status);
+    else k_adj_pairsum<SDPD_KERNEL_CUBIC, 1><<<nb, 128, 0, s>>>(c, qp4, q4, vs4, w.nlist, w.nn, A, w.status);
   }
 }
 
@@ -400,7 +410,7 @@ void launch_adj_back(const Consts& c, const Workspace& w, int cur, int mode, dou
   const unsigned nb = nblocks(c.N, 128);
   const int32_t* id = w.id[cur];
 #define SDPD_ADJ_BACK(KIND, MODE) \
-  k_adj_back<KIND, MODE><<<nb, 128, 0, s>>>(c, qp4, q4, vs4, id, w.nlist, w.nn, wt, accumulate, qbar, thbar)
+  k_adj_back<KIND, MODE><<<nb, 128, 0, s>>>(c, qp4, q4, vs4, id, w.nlist, w.nn, wt, accumulate, qbar, thbar, w.status)
   if (c.kernel == SDPD_KERNEL_LUCY) {
     if (mode == 0) SDPD_ADJ_BACK(SDPD_KERNEL_LUCY, 0);
     else if (mode == 1) SDPD_ADJ_BACK(SDPD_KERNEL_LUCY, 1);

@@ -33,6 +33,7 @@ struct sdpd_handle {
   std::vector<uint32_t> xmin_h[3];
   int64_t pair_rec_cap;
   int device;  // device of the bound workspace; selected on entry to every call
+  int ovf_slot = 0;  // slot of the neighbour-list overflow list of the latest density pass
   // stage timing: event pairs recorded on the stream, reduced at sync points
   bool timing;
   std::vector<cudaEvent_t> ev_pool;
@@ -190,7 +191,13 @@ size_t layout(sdpd_handle* s, Workspace* w, char* base) {
   w->counters = (unsigned long long*)at(4 * 8);
   w->sweep = (unsigned long long*)at(8);
   w->status = (int*)at(8);
-  w->fd_queue = (unsigned*)at(16 * 4);
+  w->fd_queue = (unsigned*)at(32 * 4);
+  w->big_perm = (int32_t*)at(N * 4);
+  w->big_list = (int2*)at(nc * 8);
+  w->big_count = (uint32_t*)at(16 * 4);
+  w->ovf_list = (int32_t*)at(2 * N * 4);
+  w->ovf_count = (int32_t*)at(2 * 4);
+  w->ovf_slot = &s->ovf_slot;
   w->blk_hist = (uint32_t*)at(8 * 256 * 4);
   w->blk_order = (int32_t*)at(nc * 4);
   w->pair_rec_count = (unsigned long long*)at(8);
@@ -296,7 +303,7 @@ template <class P>
 void vv_step(sdpd_handle* s, double dt) {
   const Consts& c = s->c;
   {  // p^{n+1/2} = p^n + F^n dt/2, q^{n+1} = q^n + p^{n+1/2} dt/m
-    StageTimer t(s, 0, 1);
+    StageTimer t(s, 0, 2);
     launch_force<P>(c, s->w, s->cur, 0.5 * dt, dt, nullptr, s->stream);
   }
   {
@@ -309,10 +316,10 @@ void vv_step(sdpd_handle* s, double dt) {
     launch_density<P>(c, s->w, s->cur, 1, nullptr, s->stream);
   }
   {  // p^{n+1} = p^{n+1/2} + F^{n+1} dt/2
-    StageTimer t(s, 3, 1);
+    StageTimer t(s, 3, 2);
     launch_force<P>(c, s->w, s->cur, 0.5 * dt, 0.0, nullptr, s->stream);
   }
-  s->launches += 8;
+  s->launches += 10;  // force + overflow, 5 sort, density, force + overflow
   s->vv_step++;
   s->sched_valid = false;
 }
@@ -558,7 +565,8 @@ int sdpd_bind_workspace(sdpd_t* s, void* ptr, size_t bytes) {
   e |= cuda_ok(cudaMemsetAsync(s->w.counters, 0, 4 * 8, st));
   e |= cuda_ok(cudaMemsetAsync(s->w.status, 0, 8, st));
   e |= cuda_ok(cudaMemsetAsync(s->w.sched_hdr, 0, (size_t)c.ncell * 4, st));
-  e |= cuda_ok(cudaMemsetAsync(s->w.fd_queue, 0, 16 * 4, st));
+  e |= cuda_ok(cudaMemsetAsync(s->w.fd_queue, 0, 32 * 4, st));
+  e |= cuda_ok(cudaMemsetAsync(s->w.ovf_count, 0, 2 * 4, st));
   e |= cuda_ok(cudaStreamSynchronize(st));
   // launch sizes of the sweep's colour kernels, queried here rather than
   // inside a later stream capture
@@ -590,7 +598,7 @@ int sdpd_set_state(sdpd_t* s, const double* q, const double* p, const double* ep
   }
   e |= cuda_ok(cudaMemsetAsync(s->w.counters, 0, 4 * 8, st));
   e |= cuda_ok(cudaMemsetAsync(s->w.status, 0, 8, st));
-  e |= cuda_ok(cudaMemsetAsync(s->w.fd_queue, 0, 16 * 4, st));
+  e |= cuda_ok(cudaMemsetAsync(s->w.fd_queue, 0, 32 * 4, st));
   if (e) return SDPD_ERR_CUDA;
   if (s->prm.precision == SDPD_MIXED) do_load<Mixed>(s);
   else do_load<Fp64>(s);
@@ -1251,7 +1259,7 @@ int debug_get(sdpd_handle* s, int what, void* dst, int64_t cap, int64_t* count) 
       if (cap < 3 * N) return SDPD_ERR_INVALID_ARG;
       if (mixed) launch_force<Mixed>(s->c, s->w, cur, 0.0, 0.0, s->w.io_p, st);
       else launch_force<Fp64>(s->c, s->w, cur, 0.0, 0.0, s->w.io_p, st);
-      s->launches += 1;
+      s->launches += 2;
       if (N > 0 && cudaMemcpyAsync(dst, s->w.io_p, (size_t)N * 24, cudaMemcpyDeviceToHost, st) != cudaSuccess)
         return SDPD_ERR_CUDA;
       if (count) *count = 3 * N;

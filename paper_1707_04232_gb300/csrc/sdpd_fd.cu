@@ -40,35 +40,56 @@ namespace sdpd {
 // Schedule, step 1: owned pairs of every block in canonical order, found
 // from the positions of the block's particles.  One thread block of
 // kEnumThreads threads per owner cell stages the particles of the block's 8
-// cells in shared memory (ids, ranks, coordinates), lists the block's
-// (particle, partner cell) segments, and tests every candidate of every
-// segment with the neighbour predicate r^2 < h^2 of the pair passes:
-//   * float64: absolute coordinates and the minimum image, the float32
-//     pre-test of the density pass first (it skips only pairs with r >= h);
-//   * mixed: block-local float32 coordinates, the same arithmetic the colour
+// cells in shared memory (ids, coordinates) and tests every candidate pair
+// with the neighbour predicate r^2 < h^2 of the pair passes:
+//   * float64: absolute coordinates and the minimum image, after the float32
+//     pre-test of the density pass (which skips only pairs with r >= h);
+//   * mixed: block-local float32 coordinates, the arithmetic the colour
 //     kernel uses for the pair's geometry.
-// A particle A (as the lower id of a pair) in block cell dA has owned
-// partners only in the cells dB that agree with dA where dA agrees with A's
-// owner bits and differ from dA elsewhere; in its own cell only the
-// particles after it (cells hold their particles by ascending id), in the
-// other cells those of higher rank.  Found pairs set bit rank(i) of row
-// rank(j) - rank(i) of a bitmap, which is then read out row by row.
+// Ranks.  Every cell holds its particles by ascending id, so the rank of a
+// particle among the block's ids is the sum over the 8 cells of the number
+// of smaller ids there (lb[k][d'] = ids in cell d' below particle k's, from
+// a merge of the two cells' id runs; in its own cell, its position).
+// Candidates.  A particle A (as the lower id of a pair) in block cell dA has
+// owned partners only in the cells dB that agree with dA where dA agrees
+// with A's owner bits and differ from dA elsewhere, and only among the ids
+// above its own: the suffix of cell dB from lb[A][dB] on (from A + 1 in its
+// own cell).  One thread walks each particle's candidates, the particles
+// taken in order of their number of candidates (a counting sort).
+// Found pairs set bit rank(i) of row d = rank(j) - rank(i) of a triangular
+// bitmap (row d holds nb - d bits in whole words: it starts at word
+// F(nb - 1) - F(nb - d) with F(n) = sum_{k <= n} ceil(k / 32)), which is then
+// read out row by row.  The kernel is kept small (about 13 KB of shared
+// memory for the mixed path) so that 16 blocks share an SM: its phases are
+// short and wait on memory, and other blocks fill the gaps.
 // ---------------------------------------------------------------------------
 constexpr int kEnumThreads = 128;
-constexpr int kMaxSegments = kMaxBlock * 8;
+constexpr int kTriWords = 1152;  // >= F(255) = 1144: a triangle of 256 rows
+
+// words of the first rows of the triangular bitmap: F(n) = sum_{k=1..n} ceil(k/32)
+__device__ __forceinline__ int tri_f(int n) {
+  const int q = n >> 5, s = n & 31;
+  return 16 * q * (q + 1) + s * (q + 1);
+}
 
 template <class R>
 struct EnumSmem {
-  R x[kMaxBlock], y[kMaxBlock], z[kMaxBlock];  // float64: absolute; mixed: block-local
+  // coordinates: float64 absolute, mixed block-local (w unused)
+  typename std::conditional<std::is_same<R, double>::value, D4, float4>::type x[kMaxBlock];
   float4 f[std::is_same<R, double>::value ? kMaxBlock : 1];  // float64: float32 copies for the pre-test
-  uint32_t bits[kRowWords][kMaxBlock];  // bit (lower rank) of row (rank difference); word-major
+  uint32_t bits[kTriWords];
   int32_t id[kMaxBlock];
-  int32_t rowoff[kMaxBlock + 1];
-  uint16_t seg[kMaxSegments];  // particle | partner cell << 8
+  uint8_t lb[kMaxBlock][8];  // ids of each cell below the particle's (own cell: its position)
+  uint16_t rowoff[kMaxBlock];
+  uint16_t rowbase[kMaxBlock];  // first word of each row of the bitmap
+  uint8_t ncand[kMaxBlock];     // each particle's number of candidates (clamped to 255)
+  uint8_t order[kMaxBlock];     // the particles by number of candidates, most first
+  int32_t hist[kMaxBlock + 1];  // particles by number of candidates (clamped to 255)
+  uint8_t code[kMaxBlock];   // block cell of each particle
   uint8_t rank[kMaxBlock];
   uint8_t perm[kMaxBlock];
   int32_t cstart[8], cbase[9];
-  int32_t nseg, npairs, nb;
+  int32_t npairs, nb;
 };
 
 template <class P>
@@ -76,15 +97,16 @@ __global__ void __launch_bounds__(kEnumThreads)
     k_sched_enum(Consts c, Arrays<P> a, const int32_t* __restrict__ cell_start, const int32_t* __restrict__ mrank,
                  const uint32_t* __restrict__ xmx, const uint32_t* __restrict__ xmy,
                  const uint32_t* __restrict__ xmz, const float4* __restrict__ qf4, uint32_t* __restrict__ hdr,
-                 uint16_t* __restrict__ canon, int* status, uint32_t* __restrict__ blk_hist) {
+                 uint16_t* __restrict__ canon, uint32_t* __restrict__ blk_hist, uint32_t* __restrict__ big_count) {
   using R = typename P::R;
   __shared__ EnumSmem<R> sm;
   const int t = threadIdx.x, lane = t & 31;
-  if (blockIdx.x == 0)  // the depth histogram that k_sched_walk fills
+  if (blockIdx.x == 0) {  // the depth histogram and the lists of blocks beyond capacity that k_sched_walk fills
     for (int k = t; k < 8 * 256; k += kEnumThreads) blk_hist[k] = 0u;
-  const int64_t o = blockIdx.x;
-  int ox, oy, oz;
-  owner_coords(c, o, ox, oy, oz);
+    if (t < 16) big_count[t] = 0u;
+  }
+  const int o = blockIdx.x;  // owner cell (fewer than 2^31 cells)
+  const int ox = o % c.nc[0], oy = (o / c.nc[0]) % c.nc[1], oz = o / (c.nc[0] * c.nc[1]);
   // the block's 8 cells: storage start, count and offset in the block
   if (t < 32) {
     int ccnt = 0, cst = 0;
@@ -111,110 +133,150 @@ __global__ void __launch_bounds__(kEnumThreads)
       sm.cbase[8] = cinc;
       sm.nb = cinc;
     }
-    if (lane == 0) { sm.nseg = 0; sm.npairs = 0; }
+    if (lane == 0) sm.npairs = 0;
   }
   __syncthreads();
   const int nb = sm.nb;
-  if (nb > kMaxBlock) {
-    if (t == 0) { atomicOr(status, kStCapacity); hdr[o] = 0; }
+  if (nb > kMaxBlock) {  // beyond capacity: swept pair by pair (see kHdrBig)
+    if (t == 0) hdr[o] = kHdrBig;
     return;
   }
-  auto code_of = [&](int k) {
-    int d = 0;
-#pragma unroll
-    for (int u = 1; u < 8; ++u) d += (k >= sm.cbase[u]);
-    return d;
-  };
-  const int nw = (nb + 31) >> 5;  // bitmap words in use per row
-  for (int q = t; q < nw * nb; q += kEnumThreads) sm.bits[q / nb][q % nb] = 0u;
+  const int ntri = nb > 1 ? tri_f(nb - 1) : 0;  // words of the bitmap in use
+  for (int q = t; q < ntri; q += kEnumThreads) sm.bits[q] = 0u;
   BlockGeom<P> geo;
   geo.init(c, ox, oy, oz, xmx, xmy, xmz);
-  for (int k = t; k < nb; k += kEnumThreads) {
-    const int d = code_of(k);
+  int cb[9];
+#pragma unroll
+  for (int u = 0; u < 9; ++u) cb[u] = sm.cbase[u];
+  for (int k = t; k < nb; k += kEnumThreads) {  // the particles
+    int d = 0;
+#pragma unroll
+    for (int u = 1; u < 8; ++u) d += (k >= cb[u]);
     const int g = sm.cstart[d] + (k - sm.cbase[d]);
     sm.id[k] = a.id[g];
+    sm.code[k] = (uint8_t)d;
     R x, y, zz;
     geo.local(ld4(&a.q4[g]), d, x, y, zz);
-    sm.x[k] = x; sm.y[k] = y; sm.z[k] = zz;
+    sm.x[k].x = x; sm.x[k].y = y; sm.x[k].z = zz;
     if constexpr (!P::mixed) sm.f[k] = __ldg(&qf4[g]);
   }
   __syncthreads();
-  // rank of each id among the block's ids: every cell's ids are ascending
+  // lower bounds: thread (d, e) merges the id runs of cells d and e, giving
+  // for every particle of cell d the number of ids of cell e below its own
+  // (its own cell: its position); then the ranks, and each particle's number
+  // of candidates (ids above its own in its partner cells)
+  if (t < 64) {
+    const int d = t >> 3, e = t & 7;
+    const int b0 = sm.cbase[d], b1 = sm.cbase[d + 1];
+    if (d == e) {
+      for (int k = b0; k < b1; ++k) sm.lb[k][d] = (uint8_t)(k - b0);
+    } else {
+      const int e0 = sm.cbase[e], e1 = sm.cbase[e + 1];
+      int j = e0;
+      for (int k = b0; k < b1; ++k) {
+        const int32_t idk = sm.id[k];
+        while (j < e1 && sm.id[j] < idk) ++j;
+        sm.lb[k][e] = (uint8_t)(j - e0);
+      }
+    }
+  }
+  for (int q = t; q <= kMaxBlock; q += kEnumThreads) sm.hist[q] = 0;
+  for (int d = 1 + t; d < nb; d += kEnumThreads)  // row d of the bitmap starts at F(nb - 1) - F(nb - d)
+    sm.rowbase[d] = (uint16_t)(tri_f(nb - 1) - tri_f(nb - d));
+  __syncthreads();
   for (int k = t; k < nb; k += kEnumThreads) {
-    const int32_t myid = sm.id[k];
     int r = 0;
 #pragma unroll
-    for (int d = 0; d < 8; ++d) {
-      int pos = sm.cbase[d], len = sm.cbase[d + 1] - sm.cbase[d];
-      while (len > 0) {  // lower bound of myid in cell d
-        const int half = len >> 1;
-        if (sm.id[pos + half] < myid) { pos += half + 1; len -= half + 1; }
-        else len = half;
-      }
-      r += pos - sm.cbase[d];
-    }
+    for (int d = 0; d < 8; ++d) r += sm.lb[k][d];
     sm.rank[k] = (uint8_t)r;
     sm.perm[r] = (uint8_t)k;
-  }
-  // the (particle, partner cell) segments of the block, in any order
-  for (int k = t; k < nb; k += kEnumThreads) {
-    const int dA = code_of(k);
-    const int hb = (int)owner_bits(sm.id[k]);
-    const int free = 7 & ~(dA ^ hb);  // axes where the partner may share the cell
+    const int dA = sm.code[k];
+    const int free = 7 & ~(dA ^ (int)owner_bits(sm.id[k]));
     const int fixed = 7 & ~dA & ~free;
-    const int ns = 1 << __popc(free);
-    const int base = atomicAdd(&sm.nseg, ns);
-    int sub = free, j = 0;
+    int cand = 0, sub = free;
     for (;;) {
-      sm.seg[base + j++] = (uint16_t)(k | ((fixed | sub) << 8));
+      const int dB = fixed | sub;
+      cand += (sm.cbase[dB + 1] - sm.cbase[dB]) - (dB == dA ? sm.lb[k][dA] + 1 : sm.lb[k][dB]);
       if (sub == 0) break;
       sub = (sub - 1) & free;
     }
+    sm.ncand[k] = (uint8_t)min(cand, 255);
+    atomicAdd(&sm.hist[min(cand, 255)], 1);
   }
   __syncthreads();
-  const int nseg = sm.nseg;
+  if (t < 32) {  // positions by candidate count, most first
+    int run = 0;
+    for (int l0 = 255; l0 >= 0; l0 -= 32) {
+      const int l = l0 - lane;
+      const int v = l >= 0 ? sm.hist[l] : 0;
+      int incl = v;
+#pragma unroll
+      for (int sh = 1; sh < 32; sh <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, incl, sh);
+        if (lane >= sh) incl += u;
+      }
+      if (l >= 0) sm.hist[l] = run + incl - v;
+      run += __shfl_sync(0xffffffffu, incl, 31);
+    }
+  }
+  __syncthreads();
+  for (int k = t; k < nb; k += kEnumThreads) sm.order[atomicAdd(&sm.hist[sm.ncand[k]], 1)] = (uint8_t)k;
+  __syncthreads();
+  // candidates: one thread per particle A (as the lower id), the particles
+  // with the most candidates first, so that a warp's lanes have similar work
   const R h2 = (R)c.h2;
-  for (int sgi = t; sgi < nseg; sgi += kEnumThreads) {
-    const int sg = sm.seg[sgi];
-    const int A = sg & 255, dB = sg >> 8;
-    const int dA = code_of(A);
+  for (int q = t; q < nb; q += kEnumThreads) {
+    const int A = sm.order[q];
+    const int dA = sm.code[A];
+    const int hb = (int)owner_bits(sm.id[A]);
+    const int free = 7 & ~(dA ^ hb);  // axes where the partner may share the cell
+    const int fixed = 7 & ~dA & ~free;
     const int rA = sm.rank[A];
-    const R xa = sm.x[A], ya = sm.y[A], za = sm.z[A];
+    const auto xa = sm.x[A];
     float4 fa = make_float4(0.f, 0.f, 0.f, 0.f);
     if constexpr (!P::mixed) fa = sm.f[A];
-    const int b0 = dB == dA ? A + 1 : sm.cbase[dB], b1 = sm.cbase[dB + 1];
-    for (int B = b0; B < b1; ++B) {
-      const int rB = sm.rank[B];
-      if (rB <= rA) continue;  // the pair belongs to B's segments
-      if constexpr (!P::mixed) {  // float32 pre-test: skips only pairs with r >= h
-        const float4 fb = sm.f[B];
-        float ex = fa.x - fb.x, ey = fa.y - fb.y, ez = fa.z - fb.z;
-        ex = ex > c.halfLf[0] ? ex - c.Lf[0] : (ex < -c.halfLf[0] ? ex + c.Lf[0] : ex);
-        ey = ey > c.halfLf[1] ? ey - c.Lf[1] : (ey < -c.halfLf[1] ? ey + c.Lf[1] : ey);
-        ez = ez > c.halfLf[2] ? ez - c.Lf[2] : (ez < -c.halfLf[2] ? ez + c.Lf[2] : ez);
-        if (ex * ex + ey * ey + ez * ez >= c.h2_filter) continue;
+    const int wA = rA >> 5;
+    const uint32_t bit = 1u << (rA & 31);
+    int sub = free;
+    for (;;) {
+      const int dB = fixed | sub;
+      const int b0 = dB == dA ? A + 1 : sm.cbase[dB] + sm.lb[A][dB], b1 = sm.cbase[dB + 1];
+      for (int B = b0; B < b1; ++B) {
+        if constexpr (!P::mixed) {  // float32 pre-test: skips only pairs with r >= h
+          const float4 fb = sm.f[B];
+          float ex = fa.x - fb.x, ey = fa.y - fb.y, ez = fa.z - fb.z;
+          ex = ex > c.halfLf[0] ? ex - c.Lf[0] : (ex < -c.halfLf[0] ? ex + c.Lf[0] : ex);
+          ey = ey > c.halfLf[1] ? ey - c.Lf[1] : (ey < -c.halfLf[1] ? ey + c.Lf[1] : ey);
+          ez = ez > c.halfLf[2] ? ez - c.Lf[2] : (ez < -c.halfLf[2] ? ez + c.Lf[2] : ez);
+          if (ex * ex + ey * ey + ez * ez >= c.h2_filter) continue;
+        }
+        const auto xb = sm.x[B];
+        R dx, dy, dz;
+        geo.disp((R)xa.x, (R)xa.y, (R)xa.z, (R)xb.x, (R)xb.y, (R)xb.z, dx, dy, dz);
+        if (r2_of(dx, dy, dz) < h2) atomicOr(&sm.bits[sm.rowbase[sm.rank[B] - rA] + wA], bit);
       }
-      R dx, dy, dz;
-      geo.disp(xa, ya, za, sm.x[B], sm.y[B], sm.z[B], dx, dy, dz);
-      if (r2_of(dx, dy, dz) < h2) atomicOr(&sm.bits[rA >> 5][rB - rA], 1u << (rA & 31));
+      if (sub == 0) break;
+      sub = (sub - 1) & free;
     }
   }
   __syncthreads();
   // exclusive scan of the row populations (rows 1 .. nb - 1), one warp
   if (t < 32) {
     int npairs = 0;
-    for (int r0 = 0; r0 < nb; r0 += 32) {
+    for (int r0 = 1; r0 < nb; r0 += 32) {
       const int rr = r0 + lane;
       int n = 0;
-      if (rr >= 1 && rr < nb)
-        for (int w = 0; w < nw; ++w) n += __popc(sm.bits[w][rr]);
+      if (rr < nb) {
+        const int w0 = sm.rowbase[rr], nwr = (nb - rr + 31) >> 5;
+        for (int w = 0; w < nwr; ++w) n += __popc(sm.bits[w0 + w]);
+      }
       int incl = n;
 #pragma unroll
       for (int sh = 1; sh < 32; sh <<= 1) {
         const int v = __shfl_up_sync(0xffffffffu, incl, sh);
         if (lane >= sh) incl += v;
       }
-      if (rr < nb) sm.rowoff[rr] = npairs + incl - n;
+      if (rr < nb) sm.rowoff[rr] = (uint16_t)min(npairs + incl - n, 65535);
       npairs += __shfl_sync(0xffffffffu, incl, 31);
     }
     if (lane == 0) sm.npairs = npairs;
@@ -222,15 +284,16 @@ __global__ void __launch_bounds__(kEnumThreads)
   __syncthreads();
   const int npairs = sm.npairs;
   if (npairs > kMaxPairs) {
-    if (t == 0) { atomicOr(status, kStCapacity); hdr[o] = 0; }
+    if (t == 0) hdr[o] = kHdrBig;
     return;
   }
   // write the pairs row by row (difference ascending), lower rank ascending
-  uint16_t* out = canon + o * kMaxPairs;
+  uint16_t* out = canon + (int64_t)o * kMaxPairs;
   for (int rr = 1 + t; rr < nb; rr += kEnumThreads) {
     int pos = sm.rowoff[rr];
-    for (int w = 0; w < nw; ++w) {
-      uint32_t bits = sm.bits[w][rr];
+    const int w0 = sm.rowbase[rr], nwr = (nb - rr + 31) >> 5;
+    for (int w = 0; w < nwr; ++w) {
+      uint32_t bits = sm.bits[w0 + w];
       while (bits) {
         const int bit = __ffs(bits) - 1;
         bits &= bits - 1;
@@ -250,11 +313,15 @@ __global__ void __launch_bounds__(kEnumThreads)
 constexpr int kLevelThreads = 32;
 constexpr int kTile = 32;
 
-__global__ void __launch_bounds__(kLevelThreads) k_sched_walk(int64_t ncell, int nc0, int nc1,
+__global__ void __launch_bounds__(kLevelThreads) k_sched_walk(int64_t ncell, int nc0, int nc1, int nc2,
                                                             uint32_t* __restrict__ hdr,
                                                             const uint16_t* __restrict__ canon,
-                                                            uint8_t* __restrict__ level_of, int* status,
-                                                            uint32_t* __restrict__ blk_hist) {
+                                                            uint8_t* __restrict__ level_of,
+                                                            uint32_t* __restrict__ blk_hist,
+                                                            const int32_t* __restrict__ cell_start,
+                                                            const int32_t* __restrict__ mrank,
+                                                            uint32_t* __restrict__ big_count,
+                                                            int2* __restrict__ big_list) {
   __shared__ uint8_t last_s[kMaxBlock][kLevelThreads];  // level after which a particle is free
   __shared__ uint16_t tile[kLevelThreads][kTile + 1];
   __shared__ uint8_t ltile[kLevelThreads][kTile + 4];
@@ -262,18 +329,25 @@ __global__ void __launch_bounds__(kLevelThreads) k_sched_walk(int64_t ncell, int
   const int64_t o0 = (int64_t)blockIdx.x * kLevelThreads;
   const int64_t o = o0 + t;
   const bool live = o < ncell;
-  const int np = live ? (int)(hdr[o] & 0xffffu) : 0;
+  const bool big = live && hdr[o] == kHdrBig;
+  const int np = live && !big ? (int)(hdr[o] & 0xffffu) : 0;
   int npmax = np;
   for (int s = 16; s > 0; s >>= 1) npmax = max(npmax, __shfl_xor_sync(0xffffffffu, npmax, s));
   for (int k = 0; k < kMaxBlock; ++k) last_s[k][t] = 0;
   int nlev = 0;
   bool overflow = false;
   for (int k0 = 0; k0 < npmax; k0 += kTile) {
-    __syncwarp();
+    // the next 32 entries of the 32 blocks' lists: all loads issued before
+    // the first is used
+    uint16_t v[kLevelThreads];
+#pragma unroll
     for (int j = 0; j < kLevelThreads; ++j) {
       const int64_t oj = o0 + j;
-      if (oj < ncell) tile[j][t] = canon[oj * kMaxPairs + k0 + t];
+      v[j] = oj < ncell ? canon[oj * kMaxPairs + k0 + t] : (uint16_t)0;
     }
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < kLevelThreads; ++j) tile[j][t] = v[j];
     __syncwarp();
     const int kn = min(kTile, np - k0);
     for (int k = 0; k < kn; ++k) {
@@ -286,22 +360,36 @@ __global__ void __launch_bounds__(kLevelThreads) k_sched_walk(int64_t ncell, int
       nlev = max(nlev, L + 1);
     }
     __syncwarp();
+#pragma unroll
     for (int j = 0; j < kLevelThreads; ++j) {
       const int64_t oj = o0 + j;
       if (oj < ncell) level_of[oj * kMaxPairs + k0 + t] = ltile[j][t];
     }
   }
   if (live) {
-    if (overflow) {
-      atomicOr(status, kStCapacity);
-      hdr[o] = 0;
-      nlev = 0;
-    } else {
-      hdr[o] = (uint32_t)np | ((uint32_t)nlev << 16);
-    }
     // the block's colour is the parity pattern of its owner cell
     const int ox = (int)(o % nc0), oy = (int)((o / nc0) % nc1), oz = (int)(o / ((int64_t)nc0 * nc1));
     const int colour = (ox & 1) | ((oy & 1) << 1) | ((oz & 1) << 2);
+    if (overflow || big) {
+      // swept pair by pair after the colour's other blocks: listed with the
+      // place of its particles in big_perm (blocks of a colour are disjoint)
+      hdr[o] = kHdrBig;
+      nlev = kMaxLevels;
+      int nb = 0;
+      for (int d = 0; d < 8; ++d) {
+        int cx = ox + (d & 1), cy = oy + ((d >> 1) & 1), cz = oz + ((d >> 2) & 1);
+        if (cx >= nc0) cx -= nc0;
+        if (cy >= nc1) cy -= nc1;
+        if (cz >= nc2) cz -= nc2;
+        const int r = mrank[cx + nc0 * (cy + nc1 * cz)];
+        nb += cell_start[r + 1] - cell_start[r];
+      }
+      const uint32_t off = atomicAdd(&big_count[8 + colour], (uint32_t)nb);
+      const uint32_t slot = atomicAdd(&big_count[colour], 1u);
+      big_list[colour * (ncell >> 3) + slot] = make_int2((int)o, (int)off);
+    } else {
+      hdr[o] = (uint32_t)np | ((uint32_t)nlev << 16);
+    }
     atomicAdd(&blk_hist[colour * 256 + nlev], 1u);
   }
 }
@@ -344,7 +432,8 @@ __global__ void k_sched_order_scatter(int64_t ncell, int nc0, int nc1, const uin
   const int colour = (ox & 1) | ((oy & 1) << 1) | ((oz & 1) << 2);
   const int hx = nc0 >> 1, hy = nc1 >> 1;
   const int32_t w = (ox >> 1) + hx * ((oy >> 1) + hy * (oz >> 1));  // index among the colour's blocks
-  const int nlev = (int)(hdr[o] >> 16);
+  const uint32_t hd = hdr[o];
+  const int nlev = hd == kHdrBig ? kMaxLevels : (int)(hd >> 16);
   const uint32_t pos = atomicAdd(&blk_hist[colour * 256 + nlev], 1u);
   blk_order[colour * (ncell >> 3) + pos] = w;
 }
@@ -364,12 +453,14 @@ __global__ void __launch_bounds__(kBucketWarps * 32) k_sched_bucket(int64_t ncel
   const int64_t o = (int64_t)blockIdx.x * kBucketWarps + warp;
   if (o >= ncell) return;
   const uint32_t hd = hdr[o];
+  if (hd == kHdrBig) return;
   const int np = (int)(hd & 0xffffu), nlev = (int)(hd >> 16);
   int32_t* cnt = cnt_s[warp];
   for (int L = lane; L <= kMaxLevels; L += 32) cnt[L] = 0;
   __syncwarp();
   const uint16_t* in = canon + o * kMaxPairs;
   const uint8_t* lv = level_of + o * kMaxPairs;
+#pragma unroll 4
   for (int k = lane; k < np; k += 32) atomicAdd(&cnt[lv[k]], 1);
   __syncwarp();
   // exclusive scan over nlev (<= 255) levels: 8 per lane
@@ -399,6 +490,7 @@ __global__ void __launch_bounds__(kBucketWarps * 32) k_sched_bucket(int64_t ncel
   if (lane == 31) off[nlev] = (uint16_t)run;
   __syncwarp();
   uint16_t* out = pairs + o * kMaxPairs;
+#pragma unroll 4
   for (int k = lane; k < np; k += 32) out[atomicAdd(&cnt[lv[k]], 1)] = in[k];
 }
 
@@ -409,10 +501,11 @@ void launch_fd_schedule(const Consts& c, const Workspace& w, int cur, cudaStream
   Arrays<P> a = view<P>(w, cur);
   uint16_t* canon = w.sched_pair + (size_t)c.ncell * kMaxPairs;
   k_sched_enum<P><<<(unsigned)c.ncell, kEnumThreads, 0, s>>>(c, a, w.cell_start, w.mrank, w.xmin[0], w.xmin[1],
-                                                               w.xmin[2], w.qf4, w.sched_hdr, canon, w.status,
-                                                               w.blk_hist);
+                                                               w.xmin[2], w.qf4, w.sched_hdr, canon, w.blk_hist,
+                                                               w.big_count);
   k_sched_walk<<<(unsigned)((c.ncell + kLevelThreads - 1) / kLevelThreads), kLevelThreads, 0, s>>>(
-      c.ncell, c.nc[0], c.nc[1], w.sched_hdr, canon, w.level_of, w.status, w.blk_hist);
+      c.ncell, c.nc[0], c.nc[1], c.nc[2], w.sched_hdr, canon, w.level_of, w.blk_hist, w.cell_start, w.mrank,
+      w.big_count, w.big_list);
   k_sched_bucket<<<(unsigned)((c.ncell + kBucketWarps - 1) / kBucketWarps), kBucketWarps * 32, 0, s>>>(
       c.ncell, w.sched_hdr, canon, w.level_of, w.sched_lvl, w.sched_pair);
   k_sched_order_scan<<<8, 256, 0, s>>>(w.blk_hist);

@@ -304,19 +304,41 @@ __device__ __forceinline__ int fd_pair_mixed(const FDConst<float>& k, float ex, 
   // momenta of Eq. (proposal-update), energy shared equally (Section 3.2)
   const float dpx = k.half_m * dvx, dpy = k.half_m * dvy, dpz = k.half_m * dvz;
   const float nn[6] = {pi[0] + dpx, pi[1] + dpy, pi[2] + dpz, pj[0] - dpx, pj[1] - dpy, pj[2] - dpz};
+  // float32 estimate of the energy change: it places the reverse move's
+  // coefficients (at eps + deps, rounded to float32, where it agrees with the
+  // exact value below to a float32 rounding) without waiting for the exact
+  // float-float sum, which takes a longer dependency chain
+  float dhf;
+  {
+    float dk = 0.0f;
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+      dk = fmaf(nn[t] - pi[t], nn[t] + pi[t], dk);
+      dk = fmaf(nn[t + 3] - pj[t], nn[t + 3] + pj[t], dk);
+    }
+    dhf = k.nq_hi * dk;
+  }
   {  // deps = -1/2 of the kinetic-energy change of the stored momenta, exactly
     const float oo[6] = {pi[0], pi[1], pi[2], pj[0], pj[1], pj[2]};
-    float Dh = 0.0f, Dl = 0.0f;
+    float d[6], lo[6];  // new^2 - old^2 per component as d + lo, exactly
 #pragma unroll
     for (int t = 0; t < 6; ++t) {
-      float pn, en, po, eo, d, ed, s, es;
+      float pn, en, po, eo, ed;
       eft::two_prod(nn[t], nn[t], pn, en);
       eft::two_prod(oo[t], oo[t], po, eo);
-      eft::two_sum(pn, -po, d, ed);
-      eft::two_sum(Dh, d, s, es);
-      Dh = s;
-      Dl = __fadd_rn(Dl, __fadd_rn(__fadd_rn(es, ed), __fsub_rn(en, eo)));
+      eft::two_sum(pn, -po, d[t], ed);
+      lo[t] = __fadd_rn(ed, __fsub_rn(en, eo));
     }
+    // the six high parts summed by a tree of two-sums (depth 3), the low
+    // parts and the two-sum errors plainly (they are 2^-24 of the result)
+    float s01, e01, s23, e23, s45, e45, s03, e03, Dh, eD, Dl;
+    eft::two_sum(d[0], d[1], s01, e01);
+    eft::two_sum(d[2], d[3], s23, e23);
+    eft::two_sum(d[4], d[5], s45, e45);
+    eft::two_sum(s01, s23, s03, e03);
+    eft::two_sum(s03, s45, Dh, eD);
+    Dl = __fadd_rn(__fadd_rn(__fadd_rn(lo[0], lo[1]), __fadd_rn(lo[2], lo[3])),
+                   __fadd_rn(__fadd_rn(lo[4], lo[5]), __fadd_rn(__fadd_rn(e01, e23), __fadd_rn(e45, __fadd_rn(e03, eD)))));
     eft::two_sum(Dh, Dl, Dh, Dl);  // renormalise
     // times -1/(4m) (a float-float constant)
     float ph, pl;
@@ -342,7 +364,7 @@ __device__ __forceinline__ int fd_pair_mixed(const FDConst<float>& k, float ex, 
   } else if (k.scheme == SDPD_SCHEME_EMS) {
     // reverse move from v' with the coefficients at the proposed energies
     float mrpar, mrperp, ypar, yperp;
-    pair_coeffs(k, kpar, kperp, eif + dh, ejf + dh, mrpar, mrperp, ypar, yperp);
+    pair_coeffs(k, kpar, kperp, eif + dhf, ejf + dhf, mrpar, mrperp, ypar, yperp);
     // 1 - alpha' alpha = -(m + m' + m m') (both m <= 0: no cancellation), alpha' zt
     const float cpr = -(mpar + mrpar + mpar * mrpar), cqr = -(mperp + mrperp + mperp * mrperp);
     const float bzpar = fmaf(mrpar, zpar, zpar), bzperp = fmaf(mrperp, zperp, zperp);
@@ -444,6 +466,168 @@ struct FdSmem<float> : FdSmemBase<float> {
   float U[kChunk];
 };
 
+// A block beyond the capacities of the shared-memory schedule (kHdrBig: more
+// than kMaxBlock particles, kMaxPairs owned pairs or kMaxLevels levels).
+// The whole warp sweeps its owned pairs in canonical order, one pair after
+// the other, on the state in global memory; slow, but any block completes
+// with the result of the sequential sweep.  The block's particles in rank
+// order (ids ascending) go to its place in big_perm (blocks of one colour
+// are disjoint, so N entries suffice).  Row d of
+// the canonical order holds the pairs (perm[r], perm[r + d]), r ascending;
+// the lanes test 32 candidates of a row at once (owner rule, then the
+// neighbour predicate of the schedule enumeration) and lane 0 updates the
+// hits in order of r.
+// pair counters and flags of a sequential block sweep
+struct BigCounts {
+  unsigned long long tot, acc, rb, rm;
+  int negative, bad;
+};
+
+template <class P, class A, int KIND>
+__device__ __noinline__ BigCounts fd_big_block(const Consts& c, const FDConst<typename A::R>& k, const Arrays<P>& a,
+                                          typename P::V4* __restrict__ qp4, const int32_t* __restrict__ cell_start,
+                                          const int32_t* __restrict__ mrank, const uint32_t* xmx,
+                                          const uint32_t* xmy, const uint32_t* xmz, int64_t o, int ox, int oy,
+                                          int oz, int colour, uint64_t seed, uint64_t sweep, sdpd_pair_rec* recs,
+                                          unsigned long long* rec_count, int64_t rec_cap, int32_t* perm) {
+  using R = typename A::R;
+  using S = typename P::R;
+  using V4 = typename P::V4;
+  constexpr bool kSame = std::is_same<R, S>::value;
+  const int lane = threadIdx.x & 31;
+  unsigned long long n_tot = 0, n_acc = 0, n_rb = 0, n_rm = 0;
+  bool negative = false, bad = false;
+  BlockCells b;
+  block_cells(c, ox, oy, oz, mrank, cell_start, b);
+  const int nb = b.base[8];
+  for (int q = lane; q < nb; q += 32) {  // rank order: every cell holds its ids ascending
+    const int d = cell_code_of(b, q);
+    const int g = b.start[d] + (q - b.base[d]);
+    const int32_t id = a.id[g];
+    int r = 0;
+    for (int e = 0; e < 8; ++e) {  // ids of cell e below id
+      int lo = b.start[e], n = b.cnt[e];
+      while (n > 0) {
+        const int half = n >> 1;
+        if (a.id[lo + half] < id) { lo += half + 1; n -= half + 1; }
+        else n = half;
+      }
+      r += lo - b.start[e];
+    }
+    perm[r] = g;
+  }
+  __syncwarp();
+  BlockGeom<P> geo;
+  geo.init(c, ox, oy, oz, xmx, xmy, xmz);
+  const S h2 = (S)c.h2, inv_h = (S)(1.0 / c.h), cF = (S)c.cF;
+  int seq = 0;
+  for (int d = 1; d < nb; ++d) {
+    for (int r0 = 0; r0 < nb - d; r0 += 32) {
+      const int r = r0 + lane;
+      int gA = 0, gB = 0;
+      bool hit = false;
+      if (r < nb - d) {
+        gA = perm[r];
+        gB = perm[r + d];
+        const V4 qa = ld4(&a.q4[gA]), qb = ld4(&a.q4[gB]);
+        const int dA = block_code(qa.w, ox, oy, oz), dB = block_code(qb.w, ox, oy, oz);
+        const int hb = (int)owner_bits(a.id[gA]);
+        if ((((dA ^ hb) & ~(dA ^ dB)) & 7) == 0) {  // owned: on shared axes the cell bit equals the owner bit
+          S xa, ya, za, xb, yb, zb, rx, ry, rz;
+          geo.local(qa, dA, xa, ya, za);
+          geo.local(qb, dB, xb, yb, zb);
+          geo.disp(xa, ya, za, xb, yb, zb, rx, ry, rz);
+          hit = r2_of(rx, ry, rz) < h2;
+        }
+      }
+      unsigned m = __ballot_sync(0xffffffffu, hit);
+      while (m) {
+        const int src = __ffs(m) - 1;
+        m &= m - 1;
+        const int ga = __shfl_sync(0xffffffffu, gA, src), gb = __shfl_sync(0xffffffffu, gB, src);
+        if (lane == 0) {
+          const V4 qa = ld4(&a.q4[ga]), qb = ld4(&a.q4[gb]);
+          S xa, ya, za, xb, yb, zb, rx, ry, rz;
+          geo.local(qa, block_code(qa.w, ox, oy, oz), xa, ya, za);
+          geo.local(qb, block_code(qb.w, ox, oy, oz), xb, yb, zb);
+          geo.disp(xa, ya, za, xb, yb, zb, rx, ry, rz);
+          const S r2 = r2_of(rx, ry, rz);
+          const S inv_r = fm::rsqrt(r2);
+          const R ex = (R)(rx * inv_r), ey = (R)(ry * inv_r), ez = (R)(rz * inv_r);
+          const R bs = (R)fm::div(kernel_F<KIND>(r2 * inv_r * inv_h, cF), a.rho[ga] * a.rho[gb]);
+          R G[3], U;
+          pair_randoms_fast(seed, sweep, (uint64_t)a.id[ga], (uint64_t)a.id[gb], G, &U);
+          const R lnU = k.scheme == SDPD_SCHEME_EMS ? fm::log(U) : U;
+          R pa[3] = {(R)a.px[ga], (R)a.py[ga], (R)a.pz[ga]};
+          R pb[3] = {(R)a.px[gb], (R)a.py[gb], (R)a.pz[gb]};
+          const R pa0[3] = {pa[0], pa[1], pa[2]}, pb0[3] = {pb[0], pb[1], pb[2]};
+          double margin;
+          float m32 = 0.0f, tol = 0.0f;
+          int dcs;
+          if constexpr (A::mixed) {
+            auto exact_e = [&](double& x, double& y) { x = a.eps[ga]; y = a.eps[gb]; };
+            float dh, dl;
+            dcs = fd_pair_mixed(k, ex, ey, ez, bs, G, U, lnU, pa, pb, (float)a.eps[ga], (float)a.eps[gb], exact_e,
+                                dh, dl, margin, m32, tol, recs != nullptr, negative);
+            if (dcs == 0) {
+              const double de = (double)dh + (double)dl;
+              a.eps[ga] += de;
+              a.eps[gb] += de;
+            }
+          } else {
+            double deps;
+            dcs = fd_pair(k, ex, ey, ez, bs, G, lnU, pa, pb, a.eps[ga], a.eps[gb], deps, margin, negative);
+            if (dcs == 0) {
+              a.eps[ga] = a.eps[ga] + deps;
+              a.eps[gb] = a.eps[gb] + deps;
+            }
+          }
+          if (dcs == 0) {
+            if constexpr (kSame) {
+              a.px[ga] = pa[0]; a.py[ga] = pa[1]; a.pz[ga] = pa[2];
+              a.px[gb] = pb[0]; a.py[gb] = pb[1]; a.pz[gb] = pb[2];
+            } else {  // the stored value plus the increment
+              a.px[ga] += (S)(pa[0] - pa0[0]); a.py[ga] += (S)(pa[1] - pa0[1]); a.pz[ga] += (S)(pa[2] - pa0[2]);
+              a.px[gb] += (S)(pb[0] - pb0[0]); a.py[gb] += (S)(pb[1] - pb0[1]); a.pz[gb] += (S)(pb[2] - pb0[2]);
+            }
+            bad |= !isfinite(a.eps[ga]) || !isfinite(a.eps[gb]);
+          }
+          ++n_tot;
+          n_acc += dcs == 0;
+          n_rb += dcs == 1;
+          n_rm += dcs == 2;
+          if (recs) {
+            const unsigned long long sr = atomicAdd(rec_count, 1ull);
+            if ((int64_t)sr < rec_cap) {
+              sdpd_pair_rec rc;
+              rc.id_i = a.id[ga];
+              rc.id_j = a.id[gb];
+              rc.colour = colour;
+              rc.owner = (int32_t)o;
+              rc.decision = dcs;
+              rc.level = seq;  // position in the sequential order
+              rc.margin = margin;
+              rc.margin_lo = A::mixed ? (double)m32 : margin;
+              rc.margin_tol = (double)tol;
+              recs[sr] = rc;
+            }
+          }
+        }
+        ++seq;
+        __syncwarp();
+      }
+    }
+  }
+  // pressure over rho^2 of the new energies, Eq. (pg-eos)
+  const S pi_coef = (S)(c.c_rho / (c.C_K * c.m));
+  for (int q = lane; q < nb; q += 32) {
+    const int g = perm[q];
+    qp4[g].w = (S)a.eps[g] * pi_coef / a.rho[g];
+  }
+  __syncwarp();
+  return BigCounts{n_tot, n_acc, n_rb, n_rm, (int)negative, (int)bad};
+}
+
 // Block schedule of a colour launch: OPW blocks per warp (each on 32 / OPW
 // lanes) and W warps per thread block.  Every variant runs the same pair
 // updates in the same per-particle order, so the results are identical; only
@@ -465,7 +649,8 @@ __global__ void __launch_bounds__(W * 32, fd_min_blocks<A, W>())
                 const uint16_t* __restrict__ lvl, const uint16_t* __restrict__ pairs, int colour, uint64_t seed,
                 const unsigned long long* __restrict__ sweep_ptr, unsigned long long* counters, int* status,
                 sdpd_pair_rec* recs, unsigned long long* rec_count, int64_t rec_cap, unsigned* __restrict__ queue,
-                const int32_t* __restrict__ order) {
+                const int32_t* __restrict__ order, int32_t* __restrict__ big_perm,
+                const int2* __restrict__ big_list, const uint32_t* __restrict__ big_count) {
   using R = typename A::R;  // pair arithmetic
   using S = typename P::R;  // stored momenta, densities, geometry
   constexpr bool kSame = std::is_same<R, S>::value;
@@ -487,7 +672,8 @@ __global__ void __launch_bounds__(W * 32, fd_min_blocks<A, W>())
   // blocks of uneven depth balance out.  The blocks come in the order of
   // `order` (deepest first), so the blocks a warp runs in lockstep have
   // similar depth.  queue[1] counts the warps that are done; the last one
-  // sets both back to zero for the next launch.
+  // sets them back to zero for the next launch (queue[2]: the next entry of
+  // the colour's list of blocks beyond capacity).
   for (;;) {
     unsigned w0 = 0;
     if (lane == 0) w0 = atomicAdd(queue, (unsigned)OPW);
@@ -504,8 +690,10 @@ __global__ void __launch_bounds__(W * 32, fd_min_blocks<A, W>())
       oz = 2 * (int)(w / ((int64_t)hx * hy)) + ((colour >> 2) & 1);
       o = ox + (int64_t)c.nc[0] * (oy + (int64_t)c.nc[1] * oz);
       const uint32_t hd = hdr[o];
-      np = (int)(hd & 0xffffu);
-      nlev = (int)(hd >> 16);
+      if (hd != kHdrBig) {  // (a block beyond capacity was swept above)
+        np = (int)(hd & 0xffffu);
+        nlev = (int)(hd >> 16);
+      }
     }
     BlockCells b;
     b.base[8] = 0;
@@ -685,12 +873,30 @@ __global__ void __launch_bounds__(W * 32, fd_min_blocks<A, W>())
     }
     __syncwarp();  // the group's shared memory is refilled by the next block
   }
+  // the colour's blocks beyond capacity (listed by the schedule), swept pair
+  // by pair by whole warps once the queue is empty
+  for (;;) {
+    unsigned bi = 0;
+    if (lane == 0) bi = atomicAdd(&queue[2], 1u);
+    bi = __shfl_sync(0xffffffffu, bi, 0);
+    if (bi >= big_count[colour]) break;
+    const int2 ent = big_list[colour * nown + bi];
+    const int64_t ob = ent.x;
+    int bx, by, bz;
+    owner_coords(c, ob, bx, by, bz);
+    const BigCounts bc = fd_big_block<P, A, KIND>(c, k, a, qp4, cell_start, mrank, xmx, xmy, xmz, ob, bx, by, bz,
+                                                  colour, seed, sweep, recs, rec_count, rec_cap, big_perm + ent.y);
+    n_tot += bc.tot; n_acc += bc.acc; n_rb += bc.rb; n_rm += bc.rm;
+    negative |= bc.negative != 0;
+    bad |= bc.bad != 0;
+  }
   if (lane == 0) {
     const unsigned total = gridDim.x * (unsigned)W;
     __threadfence();  // this warp's last take from queue[0] is performed before it counts as done
     if (atomicAdd(&queue[1], 1u) == total - 1u) {  // every warp has taken its last block
       queue[0] = 0u;
       queue[1] = 0u;
+      queue[2] = 0u;
     }
   }
   // counters
@@ -775,7 +981,7 @@ void launch_colour(const Consts& c, const FDConst<typename A::R>& k, const Array
     k_fd_colour<P, A, KIND, OPW, W><<<gf, W * 32, 0, s>>>(
         c, k, a, (typename P::V4*)w.qp4, w.cell_start, w.mrank, w.xmin[0], w.xmin[1], w.xmin[2], w.sched_hdr,
         w.sched_lvl, w.sched_pair, col, seed, w.sweep, w.counters, w.status, recs, w.pair_rec_count,
-        w.pair_rec_cap, w.fd_queue + 2 * col, w.blk_order);
+        w.pair_rec_cap, w.fd_queue + 3 * col, w.blk_order, w.big_perm, w.big_list, w.big_count);
   }
 }
 

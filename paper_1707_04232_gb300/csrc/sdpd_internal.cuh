@@ -15,14 +15,18 @@ namespace sdpd {
 constexpr int kMaxBlock = 256;   // particles in a block (8-bit local index)
 constexpr int kMaxPairs = 2048;  // owned pairs of a block
 constexpr int kMaxLevels = 255;  // dependency levels of a block's pair schedule
+// Schedule header of a block beyond one of these capacities: its sweep runs
+// in canonical order, one pair after the other, on the whole warp that takes
+// it (no shared-memory schedule), so any block size completes.
+constexpr uint32_t kHdrBig = 0xFFFFFFFFu;
 
 // Sticky device status bits, mapped to SDPD_ERR_* on the host.
 enum : int {
   kStNegative = 1,    // SSA produced eps <= 0
   kStNaN = 2,         // non-finite momentum / energy
-  kStCapacity = 4,    // block capacity exceeded
+  kStCapacity = 4,    // a capacity that has no fallback was exceeded
   kStBadEnergy = 8,   // set_state got eps <= 0
-  kStNbrCap = 16,     // a particle has more neighbours than its list holds
+  kStNbrCap = 16,     // a gradient pass met a neighbour list longer than its row
 };
 
 // Per-run constants; every kernel gets a copy by value.
@@ -80,14 +84,15 @@ __host__ __device__ __forceinline__ int64_t nbr_slot(int64_t i, int k, int cap) 
 // (quadratic convergence: from the float32 estimate's ~2.4e-7 to ~1e-13
 // relative), then r = x y; a handful of float64 operations instead of a
 // correctly rounded square root.  r^2 below 1e-30 (coincident particles)
-// takes the library square root.  float: the library square root.
+// takes the library square root.  float: r^2 times the hardware reciprocal
+// square root (0 for coincident particles).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double pair_rinv(double r2) {
   const double y = (double)rsqrtf((float)r2);
   return y * (1.5 - 0.5 * r2 * y * y);
 }
 __device__ __forceinline__ double pair_r(double r2) { return r2 > 1e-30 ? r2 * pair_rinv(r2) : sqrt(r2); }
-__device__ __forceinline__ float pair_r(float r2) { return sqrtf(r2); }
+__device__ __forceinline__ float pair_r(float r2) { return r2 > 0.0f ? r2 * rsqrtf(r2) : 0.0f; }
 
 // ---------------------------------------------------------------------------
 // Smoothing kernels of Section 2.1.1 as functions of x = r/h in [0, 1).
@@ -311,8 +316,20 @@ struct Workspace {
   int* status;
   uint32_t* blk_hist;            // [8][256]: blocks of each colour by dependency depth, then cursors
   int32_t* blk_order;            // [8][ncell / 8]: each colour's blocks, deepest first
-  unsigned* fd_queue;            // [8][2]: next block and finished warps of each colour launch;
-                                 // zero between launches
+  unsigned* fd_queue;            // [8][3]: next block, finished warps and next entry of
+                                 // big_list of each colour launch; zero between launches
+  int32_t* big_perm;             // [N]: rank order of the particles of blocks beyond capacity
+  int2* big_list;                // [8][ncell / 8]: each colour's blocks beyond capacity (owner
+                                 // cell, offset in big_perm)
+  uint32_t* big_count;           // [8] entries of big_list, then [8] entries of big_perm in use
+  // particles whose neighbour list overflows its row, listed by the density
+  // pass into one of two slots: [2][N] entries and [2] counts.  A density
+  // pass fills slot *ovf_slot (toggled on the host before each launch) and
+  // clears the other one, which no kernel reads any more (the force passes
+  // read the slot of the latest density pass).
+  int32_t* ovf_list;
+  int32_t* ovf_count;
+  int* ovf_slot;                 // host: the slot of the latest density pass
   sdpd_pair_rec* pair_recs;   // debug
   unsigned long long* pair_rec_count;
   int64_t pair_rec_cap;

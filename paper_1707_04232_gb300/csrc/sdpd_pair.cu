@@ -128,11 +128,12 @@ __global__ void __launch_bounds__(128) k_density(Consts c, Arrays<P> a, typename
                                                  const uint32_t* __restrict__ xmz, int update_eos,
                                                  int32_t* __restrict__ ncount_by_id,
                                                  uint32_t* __restrict__ nlist, int32_t* __restrict__ nn,
-                                                 int* __restrict__ status,
-                                                 const float4* __restrict__ qf4) {
+                                                 int32_t* __restrict__ ovf_list, int32_t* __restrict__ ovf_count,
+                                                 int32_t* __restrict__ ovf_other, const float4* __restrict__ qf4) {
   using R = typename P::R;
   using V4 = typename P::V4;
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i == 0) *ovf_other = 0;  // the other slot: its readers have run
   if (i >= c.N) return;
   const V4 qi = ld4(&a.q4[i]);
   float4 fi = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -144,6 +145,7 @@ __global__ void __launch_bounds__(128) k_density(Consts c, Arrays<P> a, typename
   const R h2 = (R)c.h2, inv_h = R(1) / (R)c.h, cW = (R)c.cW;
   R acc = R(0);
   int cnt = 0;
+  uint32_t* wp = nlist + nbr_slot(i, 0, c.nbr_cap);  // where entry cnt of the list goes
 #pragma unroll 1
   for (int oz = -1; oz <= 1; ++oz) {
     const int nz = wrapc(cz + oz, c.nc[2]);
@@ -156,10 +158,11 @@ __global__ void __launch_bounds__(128) k_density(Consts c, Arrays<P> a, typename
         const int r = __ldg(&mrank[nx + c.nc[0] * (ny + c.nc[1] * nz)]);
         const int beg = __ldg(&cell_start[r]), end = __ldg(&cell_start[r + 1]);
         home.frame(nx, ny, nz);
+        const uint32_t code = nbr_entry(0, ox, oy, oz);
 #pragma unroll 4
         for (int j = beg; j < end; ++j) {
-          if (j == i) continue;
           if constexpr (!P::mixed) {  // float32 pre-test: skips only pairs with r >= h
+            if (j == i) continue;
             const float4 fj = __ldg(&qf4[j]);
             float ex = fi.x - fj.x, ey = fi.y - fj.y, ez = fi.z - fj.z;
             ex = ex > c.halfLf[0] ? ex - c.Lf[0] : (ex < -c.halfLf[0] ? ex + c.Lf[0] : ex);
@@ -171,9 +174,12 @@ __global__ void __launch_bounds__(128) k_density(Consts c, Arrays<P> a, typename
           R dx, dy, dz;
           home.disp(qj, dx, dy, dz);
           const R r2 = r2_of(dx, dy, dz);
-          if (r2 < h2) {
+          // kept neighbours (about one candidate in six) take the short
+          // branch: the kernel value and one list store at a stepped address
+          if (r2 < h2 && j != i) {
             acc += kernel_W<KIND>(pair_r(r2) * inv_h, cW);
-            if (cnt < c.nbr_cap) nlist[nbr_slot(i, cnt, c.nbr_cap)] = nbr_entry(j, ox, oy, oz);
+            if (cnt < c.nbr_cap) *wp = ((uint32_t)j << 6) | code;
+            wp += (cnt & 3) == 3 ? 125 : 1;  // nbr_slot(i, cnt + 1) - nbr_slot(i, cnt)
             ++cnt;
           }
         }
@@ -181,8 +187,8 @@ __global__ void __launch_bounds__(128) k_density(Consts c, Arrays<P> a, typename
     }
   }
   if (ncount_by_id) ncount_by_id[a.id[i]] = cnt;
-  nn[i] = min(cnt, c.nbr_cap);
-  if (cnt > c.nbr_cap) atomicOr(status, kStNbrCap);
+  nn[i] = cnt;
+  if (cnt > c.nbr_cap) ovf_list[atomicAdd(ovf_count, 1)] = (int32_t)i;  // forces from the cells
   const R rho_new = (R)c.m * ((R)c.W0 + acc);
   double e = a.eps[i];
   if (update_eos) {
@@ -207,62 +213,18 @@ __global__ void __launch_bounds__(128) k_density(Consts c, Arrays<P> a, typename
   st4(&qp4[i], o);
 }
 
-// ---------------------------------------------------------------------------
-// Conservative force, Eq. (cons-forces): F_i = sum_{j != i, r_ij < h}
-// m^2 (pi_i + pi_j) F(r_ij) r_ij, and the kick p_i += F_i dt/2 of Eq.
-// (sdpd-verlet).  With drift: q_i += p_i dt/m (wrapped), new cell counted
-// for the sort.
-// ---------------------------------------------------------------------------
-template <class P, int KIND>
-__global__ void __launch_bounds__(128) k_force(Consts c, Arrays<P> a, const typename P::V4* __restrict__ qp4,
-                                               const int32_t* __restrict__ cell_start,
-                                               const int32_t* __restrict__ mrank,
-                                               const uint32_t* __restrict__ xmx,
-                                               const uint32_t* __restrict__ xmy,
-                                               const uint32_t* __restrict__ xmz, double half_dt,
-                                               double dt_drift, typename P::Q* __restrict__ qdx,
-                                               typename P::Q* __restrict__ qdy,
-                                               typename P::Q* __restrict__ qdz, int32_t* __restrict__ key,
-                                               int32_t* __restrict__ slot, int32_t* __restrict__ cell_count,
-                                               double* __restrict__ force_by_id,
-                                               const uint32_t* __restrict__ nlist, const int32_t* __restrict__ nn,
-                                               float3 drift3) {
-  // mixed path: dt / m * 2^32 / L per axis, computed on the host
-  const float drift_f[3] = {drift3.x, drift3.y, drift3.z};
+// Kick (and, with dt_drift != 0, drift and binning) of particle i with the
+// force sum f (before the factor m^2): p_i += m^2 f dt/2 of Eq. (sdpd-verlet),
+// q_i += p_i dt/m wrapped, and the new cell counted for the sort.
+template <class P>
+__device__ __forceinline__ void kick_particle(const Consts& c, const Arrays<P>& a, int64_t i, typename P::R fx,
+                                              typename P::R fy, typename P::R fz, double half_dt, double dt_drift,
+                                              typename P::Q* __restrict__ qdx, typename P::Q* __restrict__ qdy,
+                                              typename P::Q* __restrict__ qdz, int32_t* __restrict__ key,
+                                              int32_t* __restrict__ slot, int32_t* __restrict__ cell_count,
+                                              const int32_t* __restrict__ mrank, double* __restrict__ force_by_id,
+                                              const float drift_f[3]) {
   using R = typename P::R;
-  using V4 = typename P::V4;
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= c.N) return;
-  const V4 qi = ld4(&a.q4[i]);
-  const R pi_i = ld4(&qp4[i]).w;
-  int cx, cy, cz;
-  unpack_cell(w_to_cellbits(qi.w), cx, cy, cz);
-  Home<P> home;
-  home.init(c, qi, cx, cy, cz, xmx, xmy, xmz);
-  const R inv_h = R(1) / (R)c.h, cF = (R)c.cF;
-  R fx = R(0), fy = R(0), fz = R(0);
-  home.frames_all(c);
-  const int n = nn[i];
-  // four entries per 16-byte load (a warp's loads are contiguous, see
-  // nbr_slot), then four independent neighbour gathers
-  for (int k = 0; k < n; k += 4) {
-    const uint4 e4 = __ldg(reinterpret_cast<const uint4*>(nlist + nbr_slot(i, k, c.nbr_cap)));
-    const uint32_t ev[4] = {e4.x, e4.y, e4.z, e4.w};
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      if (k + u < n) {
-        const uint32_t e = ev[u];
-        const V4 qj = ld4(&qp4[e >> 6]);
-        R dx, dy, dz;
-        home.disp_code(e & 63u, qj, dx, dy, dz);
-        const R r2 = r2_of(dx, dy, dz);
-        const R s = (pi_i + qj.w) * kernel_F<KIND>(pair_r(r2) * inv_h, cF);
-        fx += s * dx;
-        fy += s * dy;
-        fz += s * dz;
-      }
-    }
-  }
   const R m2 = (R)(c.m * c.m);
   fx *= m2; fy *= m2; fz *= m2;
   if (force_by_id) {
@@ -304,6 +266,144 @@ __global__ void __launch_bounds__(128) k_force(Consts c, Arrays<P> a, const type
   }
 }
 
+// Force and kick of a particle with more neighbours than its list row
+// holds: the pair force sum from the 27 cells around it, with the
+// candidates, the predicate and the order of the density pass, so that the
+// sum is the one a long enough list would give.
+template <class P, int KIND>
+__device__ __forceinline__ void force_from_cells(const Consts& c, const Arrays<P>& a, int64_t i,
+                                              const typename P::V4* __restrict__ qp4,
+                                              const int32_t* __restrict__ cell_start,
+                                              const int32_t* __restrict__ mrank, const uint32_t* xmx,
+                                              const uint32_t* xmy, const uint32_t* xmz, double half_dt,
+                                              double dt_drift, typename P::Q* qdx, typename P::Q* qdy,
+                                              typename P::Q* qdz, int32_t* key, int32_t* slot,
+                                              int32_t* cell_count, double* force_by_id, float3 drift3) {
+  using R = typename P::R;
+  using V4 = typename P::V4;
+  const V4 qi = ld4(&qp4[i]);
+  int cx, cy, cz;
+  unpack_cell(w_to_cellbits(ld4(&a.q4[i]).w), cx, cy, cz);
+  Home<P> home;
+  home.init(c, qi, cx, cy, cz, xmx, xmy, xmz);
+  const R h2 = (R)c.h2, inv_h = R(1) / (R)c.h, cF = (R)c.cF;
+  R fx = R(0), fy = R(0), fz = R(0);
+  for (int oz = -1; oz <= 1; ++oz) {
+    const int nz = wrapc(cz + oz, c.nc[2]);
+    for (int oy = -1; oy <= 1; ++oy) {
+      const int ny = wrapc(cy + oy, c.nc[1]);
+      for (int ox = -1; ox <= 1; ++ox) {
+        const int nx = wrapc(cx + ox, c.nc[0]);
+        const int r = __ldg(&mrank[nx + c.nc[0] * (ny + c.nc[1] * nz)]);
+        const int beg = __ldg(&cell_start[r]), end = __ldg(&cell_start[r + 1]);
+        home.frame(nx, ny, nz);
+        for (int j = beg; j < end; ++j) {
+          if (j == i) continue;
+          const V4 qj = ld4(&qp4[j]);
+          R dx, dy, dz;
+          home.disp(qj, dx, dy, dz);
+          const R r2 = r2_of(dx, dy, dz);
+          if (r2 < h2) {
+            const R s = (qi.w + qj.w) * kernel_F<KIND>(pair_r(r2) * inv_h, cF);
+            fx += s * dx;
+            fy += s * dy;
+            fz += s * dz;
+          }
+        }
+      }
+    }
+  }
+  const float drift_f[3] = {drift3.x, drift3.y, drift3.z};
+  kick_particle<P>(c, a, i, fx, fy, fz, half_dt, dt_drift, qdx, qdy, qdz, key, slot, cell_count, mrank,
+                   force_by_id, drift_f);
+}
+
+// ---------------------------------------------------------------------------
+// Conservative force, Eq. (cons-forces): F_i = sum_{j != i, r_ij < h}
+// m^2 (pi_i + pi_j) F(r_ij) r_ij, and the kick p_i += F_i dt/2 of Eq.
+// (sdpd-verlet).  With drift: q_i += p_i dt/m (wrapped), new cell counted
+// for the sort.  A particle whose neighbour list overflowed its row (listed
+// by the density pass) is left to k_force_overflow.
+// ---------------------------------------------------------------------------
+template <class P, int KIND>
+__global__ void __launch_bounds__(128) k_force(Consts c, Arrays<P> a, const typename P::V4* __restrict__ qp4,
+                                               const int32_t* __restrict__ cell_start,
+                                               const int32_t* __restrict__ mrank,
+                                               const uint32_t* __restrict__ xmx,
+                                               const uint32_t* __restrict__ xmy,
+                                               const uint32_t* __restrict__ xmz, double half_dt,
+                                               double dt_drift, typename P::Q* __restrict__ qdx,
+                                               typename P::Q* __restrict__ qdy,
+                                               typename P::Q* __restrict__ qdz, int32_t* __restrict__ key,
+                                               int32_t* __restrict__ slot, int32_t* __restrict__ cell_count,
+                                               double* __restrict__ force_by_id,
+                                               const uint32_t* __restrict__ nlist, const int32_t* __restrict__ nn,
+                                               float3 drift3) {
+  // mixed path: dt / m * 2^32 / L per axis, computed on the host
+  const float drift_f[3] = {drift3.x, drift3.y, drift3.z};
+  using R = typename P::R;
+  using V4 = typename P::V4;
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int n = i < c.N ? nn[i] : 0;
+  if (i < c.N && n <= c.nbr_cap) {
+    const V4 qi = ld4(&a.q4[i]);
+    const R pi_i = ld4(&qp4[i]).w;
+    int cx, cy, cz;
+    unpack_cell(w_to_cellbits(qi.w), cx, cy, cz);
+    Home<P> home;
+    home.init(c, qi, cx, cy, cz, xmx, xmy, xmz);
+    const R inv_h = R(1) / (R)c.h, cF = (R)c.cF;
+    R fx = R(0), fy = R(0), fz = R(0);
+    home.frames_all(c);
+    // four entries per 16-byte load (a warp's loads are contiguous, see
+    // nbr_slot), then four independent neighbour gathers
+    for (int k = 0; k < n; k += 4) {
+      const uint4 e4 = __ldg(reinterpret_cast<const uint4*>(nlist + nbr_slot(i, k, c.nbr_cap)));
+      const uint32_t ev[4] = {e4.x, e4.y, e4.z, e4.w};
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (k + u < n) {
+          const uint32_t e = ev[u];
+          const V4 qj = ld4(&qp4[e >> 6]);
+          R dx, dy, dz;
+          home.disp_code(e & 63u, qj, dx, dy, dz);
+          const R r2 = r2_of(dx, dy, dz);
+          const R s = (pi_i + qj.w) * kernel_F<KIND>(pair_r(r2) * inv_h, cF);
+          fx += s * dx;
+          fy += s * dy;
+          fz += s * dz;
+        }
+      }
+    }
+    kick_particle<P>(c, a, i, fx, fy, fz, half_dt, dt_drift, qdx, qdy, qdz, key, slot, cell_count, mrank,
+                     force_by_id, drift_f);
+  }
+}
+
+// The particles that k_force left: more neighbours than a list row holds.
+// A few thread blocks loop over the density pass's overflow list (usually
+// empty: the launch then ends at once).
+constexpr int kOverflowBlocks = 4;
+template <class P, int KIND>
+__global__ void __launch_bounds__(128) k_force_overflow(Consts c, Arrays<P> a, const typename P::V4* __restrict__ qp4,
+                                                        const int32_t* __restrict__ cell_start,
+                                                        const int32_t* __restrict__ mrank,
+                                                        const uint32_t* __restrict__ xmx,
+                                                        const uint32_t* __restrict__ xmy,
+                                                        const uint32_t* __restrict__ xmz, double half_dt,
+                                                        double dt_drift, typename P::Q* __restrict__ qdx,
+                                                        typename P::Q* __restrict__ qdy,
+                                                        typename P::Q* __restrict__ qdz, int32_t* __restrict__ key,
+                                                        int32_t* __restrict__ slot, int32_t* __restrict__ cell_count,
+                                                        double* __restrict__ force_by_id, float3 drift3,
+                                                        const int32_t* __restrict__ ovf_list,
+                                                        const int32_t* __restrict__ ovf_count) {
+  const int novf = *ovf_count;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < novf; q += gridDim.x * blockDim.x)
+    force_from_cells<P, KIND>(c, a, ovf_list[q], qp4, cell_start, mrank, xmx, xmy, xmz, half_dt, dt_drift, qdx, qdy,
+                              qdz, key, slot, cell_count, force_by_id, drift3);
+}
+
 static inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 // threads per block of the pair passes (one thread per particle, no shared
@@ -317,14 +417,18 @@ void launch_density(const Consts& c, const Workspace& w, int cur, int update_eos
   Arrays<P> a = view<P>(w, cur);
   auto qp4 = (typename P::V4*)w.qp4;
   const int t = pair_block(c);
+  const int sl = (*w.ovf_slot ^= 1);  // this pass's slot of the overflow list
+  int32_t* ovf_list = w.ovf_list + (size_t)sl * (size_t)c.N;
+  int32_t* ovf_count = w.ovf_count + sl;
+  int32_t* ovf_other = w.ovf_count + (sl ^ 1);
   if (c.kernel == SDPD_KERNEL_LUCY)
     k_density<P, SDPD_KERNEL_LUCY><<<blocks_for(c.N, t), t, 0, s>>>(
         c, a, qp4, w.cell_start, w.mrank, w.xmin[0], w.xmin[1], w.xmin[2], update_eos, ncount_by_id, w.nlist,
-        w.nn, w.status, w.qf4);
+        w.nn, ovf_list, ovf_count, ovf_other, w.qf4);
   else
     k_density<P, SDPD_KERNEL_CUBIC><<<blocks_for(c.N, t), t, 0, s>>>(
         c, a, qp4, w.cell_start, w.mrank, w.xmin[0], w.xmin[1], w.xmin[2], update_eos, ncount_by_id, w.nlist,
-        w.nn, w.status, w.qf4);
+        w.nn, ovf_list, ovf_count, ovf_other, w.qf4);
 }
 
 template <class P>
@@ -338,15 +442,25 @@ void launch_force(const Consts& c, const Workspace& w, int cur, double half_dt, 
   auto qdz = (typename P::Q*)w.qdz;
   const float3 drift3 = make_float3((float)(dt_drift / c.m * c.inv_scale[0]), (float)(dt_drift / c.m * c.inv_scale[1]),
                                     (float)(dt_drift / c.m * c.inv_scale[2]));
+  const int sl = *w.ovf_slot;  // the overflow list of the latest density pass
+  const int32_t* ovf_list = w.ovf_list + (size_t)sl * (size_t)c.N;
+  const int32_t* ovf_count = w.ovf_count + sl;
   const int t = pair_block(c);
-  if (c.kernel == SDPD_KERNEL_LUCY)
+  if (c.kernel == SDPD_KERNEL_LUCY) {
     k_force<P, SDPD_KERNEL_LUCY><<<blocks_for(c.N, t), t, 0, s>>>(
         c, a, qp4, w.cell_start, w.mrank, w.xmin[0], w.xmin[1], w.xmin[2], half_dt, dt_drift, qdx, qdy,
         qdz, w.key, w.slot, w.cell_count, force_by_id, w.nlist, w.nn, drift3);
-  else
+    k_force_overflow<P, SDPD_KERNEL_LUCY><<<kOverflowBlocks, 128, 0, s>>>(
+        c, a, qp4, w.cell_start, w.mrank, w.xmin[0], w.xmin[1], w.xmin[2], half_dt, dt_drift, qdx, qdy,
+        qdz, w.key, w.slot, w.cell_count, force_by_id, drift3, ovf_list, ovf_count);
+  } else {
     k_force<P, SDPD_KERNEL_CUBIC><<<blocks_for(c.N, t), t, 0, s>>>(
         c, a, qp4, w.cell_start, w.mrank, w.xmin[0], w.xmin[1], w.xmin[2], half_dt, dt_drift, qdx, qdy,
         qdz, w.key, w.slot, w.cell_count, force_by_id, w.nlist, w.nn, drift3);
+    k_force_overflow<P, SDPD_KERNEL_CUBIC><<<kOverflowBlocks, 128, 0, s>>>(
+        c, a, qp4, w.cell_start, w.mrank, w.xmin[0], w.xmin[1], w.xmin[2], half_dt, dt_drift, qdx, qdy,
+        qdz, w.key, w.slot, w.cell_count, force_by_id, drift3, ovf_list, ovf_count);
+  }
 }
 
 template void launch_density<Fp64>(const Consts&, const Workspace&, int, int, int32_t*, cudaStream_t);

@@ -501,22 +501,56 @@ def test_ssa_negative_energy_is_reported_not_fatal():
         assert obs["status"] == 0 and obs["eps_min"] > 0 and obs["n_reject_bound"] > 0
 
 
-@pytest.mark.parametrize("precision", [sdpd.FP64, sdpd.MIXED])
-def test_capacity_overflow_is_reported(precision):
-    """A dense cluster (300 particles in a unit cube) overflows the
-    neighbour-list rows (160 entries) and its 2x2x2 cell block (256
-    particles): the library reports SDPD_ERR_CAPACITY after the step and the
-    context stays usable."""
+def dense_cluster():
+    """300 particles in a unit cube inside a 12^3 box of 800 others: every
+    particle of the cluster has ~300 neighbours (list rows hold 160) and
+    the 2x2x2 cell blocks around it hold more than 256 particles, 2048
+    owned pairs and 255 dependency levels."""
     L = 12.0
     rng = np.random.default_rng(5)
     q = np.concatenate([rng.random((800, 3)) * L, 5.0 + rng.random((300, 3))])
     p = rng.standard_normal(q.shape)
     e = np.full(len(q), 30.0)
-    s = gpu(len(q), (L,) * 3, 20.0, precision=precision)
+    return q, p, e, (L,) * 3, 20.0
+
+
+def test_capacity_overflow_sweep_matches_oracle():
+    """Blocks beyond the shared-memory schedule's capacities are swept pair
+    by pair in canonical order: the float64 sweep of the dense cluster
+    equals the oracle's pair for pair (set, colours, owners, order,
+    decisions), with status OK."""
+    q, p, e, L, K = dense_cluster()
+    recs = sweep_fp64_vs_oracle(q, p, e, L, K, sdpd.SCHEME_EMS, shapes=(1, 128))
+    assert recs["level"].max() > 255  # a block past the level capacity
+
+
+@pytest.mark.parametrize("precision", [sdpd.FP64, sdpd.MIXED])
+def test_capacity_overflow_steps_match_oracle(precision):
+    """Full steps of the dense cluster: neighbour rows past 160 entries make
+    the force pass walk the cells, and the cluster's blocks are swept pair
+    by pair; the steps complete with status OK and match the oracle's."""
+    q, p, e, L, K = dense_cluster()
+    N = len(e)
+    s = gpu(N, L, K, precision=precision)
     s.set_state(q, p, e)
+    P = oparams(N, L, K)
+    assert s.neighbour_counts().max() > 160
+    if precision == sdpd.FP64:
+        rho = O.density(P, q)
+        f = O.forces(P, q, rho, e)
+        assert np.abs(s.forces() - f).max() <= 1e-12 * np.abs(f).max()
     s.step(DT, 2, seed=1)
-    obs = s.observables(check=False)
-    assert obs["status"] == sdpd.ERR_CAPACITY
+    obs = s.observables()
+    assert obs["status"] == sdpd.OK
+    qg, pg, eg = s.get_state()
+    st, qo, po, eo, stats, _ = O.run(P, q, p, e, DT, 2, seed=1)
+    assert st == O.OK
+    assert obs["n_pairs"] == stats.n_pairs and obs["n_accept"] == stats.n_accept
+    tol = 1e-9 if precision == sdpd.FP64 else 1e-5
+    assert min_image_err(qg, qo, L) < tol
+    assert np.abs(pg - po).max() < tol * np.abs(po).max()
+    assert np.abs(eg - eo).max() < tol * eo.max()
+    # the context and the library stay usable
     ok = gpu(1000, (10.0,) * 3, 100.0, precision=precision)
     qq, pp, ee, _, _ = system("lattice1000")
     ok.set_state(qq, pp, ee)

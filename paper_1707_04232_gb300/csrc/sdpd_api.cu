@@ -164,6 +164,7 @@ size_t layout(sdpd_handle* s, Workspace* w, char* base) {
     w->id[k] = (int32_t*)at(N * sizeof(int32_t));
   }
   w->qp4 = at(N * sizeof(V4));
+  w->qr4 = at(N * sizeof(V4));
   w->qf4 = P::mixed ? nullptr : (float4*)at(N * sizeof(float4));
   w->nlist = (uint32_t*)at((N + 31) / 32 * 32 * (size_t)c.nbr_cap * 4);
   w->nn = (int32_t*)at(N * 4);

@@ -48,8 +48,8 @@ namespace sdpd {
 //     kernel uses for the pair's geometry.
 // Ranks.  Every cell holds its particles by ascending id, so the rank of a
 // particle among the block's ids is the sum over the 8 cells of the number
-// of smaller ids there (lb[k][d'] = ids in cell d' below particle k's, from
-// a merge of the two cells' id runs; in its own cell, its position).
+// of smaller ids there (lb[k][d'] = ids in cell d' below particle k's, by
+// binary search; in its own cell, its position).
 // Candidates.  A particle A (as the lower id of a pair) in block cell dA has
 // owned partners only in the cells dB that agree with dA where dA agrees
 // with A's owner bits and differ from dA elsewhere, and only among the ids
@@ -161,23 +161,33 @@ __global__ void __launch_bounds__(kEnumThreads)
     if constexpr (!P::mixed) sm.f[k] = __ldg(&qf4[g]);
   }
   __syncthreads();
-  // lower bounds: thread (d, e) merges the id runs of cells d and e, giving
-  // for every particle of cell d the number of ids of cell e below its own
-  // (its own cell: its position); then the ranks, and each particle's number
-  // of candidates (ids above its own in its partner cells)
-  if (t < 64) {
-    const int d = t >> 3, e = t & 7;
-    const int b0 = sm.cbase[d], b1 = sm.cbase[d + 1];
-    if (d == e) {
-      for (int k = b0; k < b1; ++k) sm.lb[k][d] = (uint8_t)(k - b0);
-    } else {
-      const int e0 = sm.cbase[e], e1 = sm.cbase[e + 1];
-      int j = e0;
-      for (int k = b0; k < b1; ++k) {
-        const int32_t idk = sm.id[k];
-        while (j < e1 && sm.id[j] < idk) ++j;
-        sm.lb[k][e] = (uint8_t)(j - e0);
+  // lower bounds: for every particle and cell, the ids of the cell below the
+  // particle's, by branch-free binary searches of a fixed length, the 8
+  // searches of a particle independent of each other (own cell: its
+  // position); then the ranks, and each particle's number of candidates (ids
+  // above its own in its partner cells)
+  {
+    int maxcnt = 0;
+#pragma unroll
+    for (int d = 0; d < 8; ++d) maxcnt = max(maxcnt, cb[d + 1] - cb[d]);
+    int steps = 0;
+    while ((1 << steps) <= maxcnt) ++steps;
+    for (int k = t; k < nb; k += kEnumThreads) {
+      const int32_t myid = sm.id[k];
+      int pos[8], len[8];
+#pragma unroll
+      for (int d = 0; d < 8; ++d) { pos[d] = cb[d]; len[d] = cb[d + 1] - cb[d]; }
+      for (int it = 0; it < steps; ++it) {
+#pragma unroll
+        for (int d = 0; d < 8; ++d) {
+          const int half = len[d] >> 1;
+          const bool below = len[d] > 0 && sm.id[pos[d] + half] < myid;
+          pos[d] = below ? pos[d] + half + 1 : pos[d];
+          len[d] = below ? len[d] - half - 1 : half;
+        }
       }
+#pragma unroll
+      for (int d = 0; d < 8; ++d) sm.lb[k][d] = (uint8_t)(pos[d] - cb[d]);
     }
   }
   for (int q = t; q <= kMaxBlock; q += kEnumThreads) sm.hist[q] = 0;
@@ -260,27 +270,37 @@ __global__ void __launch_bounds__(kEnumThreads)
     }
   }
   __syncthreads();
-  // exclusive scan of the row populations (rows 1 .. nb - 1), one warp
-  if (t < 32) {
-    int npairs = 0;
-    for (int r0 = 1; r0 < nb; r0 += 32) {
-      const int rr = r0 + lane;
-      int n = 0;
-      if (rr < nb) {
-        const int w0 = sm.rowbase[rr], nwr = (nb - rr + 31) >> 5;
-        for (int w = 0; w < nwr; ++w) n += __popc(sm.bits[w0 + w]);
-      }
-      int incl = n;
-#pragma unroll
-      for (int sh = 1; sh < 32; sh <<= 1) {
-        const int v = __shfl_up_sync(0xffffffffu, incl, sh);
-        if (lane >= sh) incl += v;
-      }
-      if (rr < nb) sm.rowoff[rr] = (uint16_t)min(npairs + incl - n, 65535);
-      npairs += __shfl_sync(0xffffffffu, incl, 31);
+  // exclusive scan of the row populations (rows 1 .. nb - 1): each warp
+  // scans 32 rows at a time, then the chunk totals are added in
+  const int wid = t >> 5;
+  for (int r0 = 1 + 32 * wid; r0 < nb; r0 += kEnumThreads) {
+    const int rr = r0 + lane;
+    int n = 0;
+    if (rr < nb) {
+      const int w0 = sm.rowbase[rr], nwr = (nb - rr + 31) >> 5;
+      for (int w = 0; w < nwr; ++w) n += __popc(sm.bits[w0 + w]);
     }
-    if (lane == 0) sm.npairs = npairs;
+    int incl = n;
+#pragma unroll
+    for (int sh = 1; sh < 32; sh <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, sh);
+      if (lane >= sh) incl += v;
+    }
+    if (rr < nb) sm.rowoff[rr] = (uint16_t)(incl - n);  // within the chunk
+    if (lane == 31) sm.hist[(r0 - 1) >> 5] = incl;        // chunk total
   }
+  __syncthreads();
+  if (t == 0) {  // chunk totals to chunk offsets (at most 8 chunks)
+    int run = 0;
+    for (int ch = 0; ch * 32 + 1 < nb; ++ch) {
+      const int v = sm.hist[ch];
+      sm.hist[ch] = run;
+      run += v;
+    }
+    sm.npairs = run;
+  }
+  __syncthreads();
+  for (int rr = 1 + t; rr < nb; rr += kEnumThreads) sm.rowoff[rr] = (uint16_t)(sm.rowoff[rr] + sm.hist[(rr - 1) >> 5]);
   __syncthreads();
   const int npairs = sm.npairs;
   if (npairs > kMaxPairs) {

@@ -276,10 +276,11 @@ static __device__ __noinline__ double mixed_margin_fp64(const MixedRatioIn& r, d
 // float64 evaluation of the same ratio gives.  m32 and tol receive the
 // float32 margin and its bound; margin the float64 margin whenever it was
 // evaluated (always when `exact` is set).  exact_e(ei, ej) gives the two
-// current energies in float64 (for the rare float64 evaluations).
-template <class ExactE>
+// current energies in float64 and uniform() the pair's uniform U (both for
+// the rare float64 evaluations).
+template <class ExactE, class Uniform>
 __device__ __forceinline__ int fd_pair_mixed(const FDConst<float>& k, float ex, float ey, float ez, float base,
-                                             const float G[3], float U, float lnU, float* pi, float* pj,
+                                             const float G[3], Uniform uniform, float lnU, float* pi, float* pj,
                                              float eif, float ejf, ExactE exact_e, float& dh, float& dl,
                                              double& margin, float& m32, float& tol, bool exact,
                                              bool& negative) {
@@ -400,7 +401,7 @@ __device__ __forceinline__ int fd_pair_mixed(const FDConst<float>& k, float ex, 
     if (exact || !(fabsf(mg) > tol)) {  // float32 not decisive (or NaN): float64
       MixedRatioIn r;
       r.ex = ex; r.ey = ey; r.ez = ez; r.vx = vx; r.vy = vy; r.vz = vz;
-      r.g0 = G[0]; r.g1 = G[1]; r.g2 = G[2]; r.u = U;
+      r.g0 = G[0]; r.g1 = G[1]; r.g2 = G[2]; r.u = uniform();
       r.mpar = mpar; r.mperp = mperp; r.zpar = zpar; r.zperp = zperp;
       r.mrpar = mrpar; r.mrperp = mrperp; r.ypar = ypar; r.yperp = yperp;
       exact_e(r.ei, r.ej);
@@ -458,12 +459,13 @@ template <>
 struct FdSmem<double> : FdSmemBase<double> {
   double e[kMaxBlock];
 };
-// float32 pair arithmetic: the energy at load (float32 copy) and the visit's
-// changes as a float-float sum; the uniforms, for float64 re-evaluations
+// float32 pair arithmetic: each particle's energy as a running float32 sum
+// es (the energy at load rounded to float32, plus the visit's changes) and
+// its compensation ec (the rounding errors of that sum and the low parts of
+// the changes), so that the energy is eps(load) + (es - (float)eps(load)) + ec
 template <>
 struct FdSmem<float> : FdSmemBase<float> {
-  float e0[kMaxBlock], ahi[kMaxBlock], alo[kMaxBlock];
-  float U[kChunk];
+  float es[kMaxBlock], ec[kMaxBlock];
 };
 
 // A block beyond the capacities of the shared-memory schedule (kHdrBig: more
@@ -567,8 +569,9 @@ __device__ __noinline__ BigCounts fd_big_block(const Consts& c, const FDConst<ty
           if constexpr (A::mixed) {
             auto exact_e = [&](double& x, double& y) { x = a.eps[ga]; y = a.eps[gb]; };
             float dh, dl;
-            dcs = fd_pair_mixed(k, ex, ey, ez, bs, G, U, lnU, pa, pb, (float)a.eps[ga], (float)a.eps[gb], exact_e,
-                                dh, dl, margin, m32, tol, recs != nullptr, negative);
+            auto uniform = [&]() { return U; };
+            dcs = fd_pair_mixed(k, ex, ey, ez, bs, G, uniform, lnU, pa, pb, (float)a.eps[ga], (float)a.eps[gb],
+                                exact_e, dh, dl, margin, m32, tol, recs != nullptr, negative);
             if (dcs == 0) {
               const double de = (double)dh + (double)dl;
               a.eps[ga] += de;
@@ -643,6 +646,7 @@ constexpr int fd_min_blocks() { return P::mixed ? 16 / W : (W >= 4 ? 1 : 4 / W);
 template <class P, class A, int KIND, int OPW, int W>
 __global__ void __launch_bounds__(W * 32, fd_min_blocks<A, W>())
     k_fd_colour(Consts c, FDConst<typename A::R> k, Arrays<P> a, typename P::V4* __restrict__ qp4,
+                const typename P::V4* __restrict__ qr4,
                 const int32_t* __restrict__ cell_start, const int32_t* __restrict__ mrank,
                 const uint32_t* __restrict__ xmx, const uint32_t* __restrict__ xmy,
                 const uint32_t* __restrict__ xmz, const uint32_t* __restrict__ hdr,
@@ -716,13 +720,19 @@ __global__ void __launch_bounds__(W * 32, fd_min_blocks<A, W>())
       for (int t = 1; t < 8; ++t) d += (q >= sm.cbs[t]);
       return sm.cst[d] + (q - sm.cbs[d]);
     };
+    // the same, also giving the particle's cell in the block
+    auto gidx_code = [&](int q, int& d) {
+      d = 0;
+#pragma unroll
+      for (int t = 1; t < 8; ++t) d += (q >= sm.cbs[t]);
+      return sm.cst[d] + (q - sm.cbs[d]);
+    };
     for (int q = gl; q < nb; q += kGroupLanes) {
       const int g = gidx(q);
       sm.px[q] = a.px[g]; sm.py[q] = a.py[g]; sm.pz[q] = a.pz[g];
       if constexpr (A::mixed) {
-        sm.e0[q] = (float)a.eps[g];
-        sm.ahi[q] = 0.0f;
-        sm.alo[q] = 0.0f;
+        sm.es[q] = (float)a.eps[g];
+        sm.ec[q] = 0.0f;
       } else {
         sm.e[q] = a.eps[g];
       }
@@ -746,11 +756,13 @@ __global__ void __launch_bounds__(W * 32, fd_min_blocks<A, W>())
       for (int t = cbeg + gl; t < cend; t += kGroupLanes) {
         const uint16_t pr = pl[t];
         const int ia = pr & 255, ib = pr >> 8;  // ia holds the lower id
-        const int ga = gidx(ia), gb = gidx(ib);
+        int da, db;
+        const int ga = gidx_code(ia, da), gb = gidx_code(ib, db);
         S xa, ya, za, xb, yb, zb, rx, ry, rz;
-        const typename P::V4 qa = ld4(&a.q4[ga]), qb = ld4(&a.q4[gb]);
-        geo.local(qa, block_code(qa.w, ox, oy, oz), xa, ya, za);
-        geo.local(qb, block_code(qb.w, ox, oy, oz), xb, yb, zb);
+        // positions and densities of the latest density pass (one load each)
+        const typename P::V4 qa = ld4(&qr4[ga]), qb = ld4(&qr4[gb]);
+        geo.local(qa, da, xa, ya, za);
+        geo.local(qb, db, xb, yb, zb);
         geo.disp(xa, ya, za, xb, yb, zb, rx, ry, rz);
         const S r2 = r2_of(rx, ry, rz);
         const S inv_r = fm::rsqrt(r2);
@@ -759,12 +771,11 @@ __global__ void __launch_bounds__(W * 32, fd_min_blocks<A, W>())
         sm.ex[slot] = (R)(rx * inv_r);
         sm.ey[slot] = (R)(ry * inv_r);
         sm.ez[slot] = (R)(rz * inv_r);
-        sm.base[slot] = (R)fm::div(kernel_F<KIND>(r2 * inv_r * inv_h, cF), a.rho[ga] * a.rho[gb]);
+        sm.base[slot] = (R)fm::div(kernel_F<KIND>(r2 * inv_r * inv_h, cF), qa.w * qb.w);
         R G[3], U;
         pair_randoms_fast(seed, sweep, (uint64_t)a.id[ga], (uint64_t)a.id[gb], G, &U);
         sm.G0[slot] = G[0]; sm.G1[slot] = G[1]; sm.G2[slot] = G[2];
         sm.lnU[slot] = k.scheme == SDPD_SCHEME_EMS ? fm::log(U) : U;  // off the pairs' dependency chain
-        if constexpr (A::mixed) sm.U[slot] = U;
       }
       __syncwarp();
       // the chunk's levels, or parts of them
@@ -786,27 +797,34 @@ __global__ void __launch_bounds__(W * 32, fd_min_blocks<A, W>())
           float m32 = 0.0f, tol = 0.0f;
           int dcs;
           if constexpr (A::mixed) {
-            const float eaf = sm.e0[ia] + sm.ahi[ia], ebf = sm.e0[ib] + sm.ahi[ib];
-            // the two energies in float64 (rare: near ties of the bound or the ratio)
+            const float eaf = sm.es[ia], ebf = sm.es[ib];
+            // rare (near ties of the bound or the ratio): the two energies in
+            // float64, and the pair's uniform drawn again
             auto exact_e = [&](double& ea, double& eb) {
-              ea = a.eps[gidx(ia)] + ((double)sm.ahi[ia] + (double)sm.alo[ia]);
-              eb = a.eps[gidx(ib)] + ((double)sm.ahi[ib] + (double)sm.alo[ib]);
+              const double ga = a.eps[gidx(ia)], gb = a.eps[gidx(ib)];
+              ea = ga + (((double)eaf - (double)(float)ga) + (double)sm.ec[ia]);
+              eb = gb + (((double)ebf - (double)(float)gb) + (double)sm.ec[ib]);
+            };
+            auto uniform = [&]() {
+              R Gr[3], U;
+              pair_randoms_fast(seed, sweep, (uint64_t)a.id[gidx(ia)], (uint64_t)a.id[gidx(ib)], Gr, &U);
+              return U;
             };
             float dh, dl;
-            dcs = fd_pair_mixed(k, sm.ex[slot], sm.ey[slot], sm.ez[slot], sm.base[slot], G, sm.U[slot],
+            dcs = fd_pair_mixed(k, sm.ex[slot], sm.ey[slot], sm.ez[slot], sm.base[slot], G, uniform,
                                 sm.lnU[slot], pa, pb, eaf, ebf, exact_e, dh, dl, margin, m32, tol,
                                 recs != nullptr, negative);
             if (dcs == 0) {
               sm.px[ia] = pa[0]; sm.py[ia] = pa[1]; sm.pz[ia] = pa[2];
               sm.px[ib] = pb[0]; sm.py[ib] = pb[1]; sm.pz[ib] = pb[2];
               float s, e;
-              eft::two_sum(sm.ahi[ia], dh, s, e);
-              sm.alo[ia] = __fadd_rn(sm.alo[ia], __fadd_rn(e, dl));
-              sm.ahi[ia] = s;
-              eft::two_sum(sm.ahi[ib], dh, s, e);
-              sm.alo[ib] = __fadd_rn(sm.alo[ib], __fadd_rn(e, dl));
-              sm.ahi[ib] = s;
-              bad |= !isfinite(eaf + dh) || !isfinite(ebf + dh);
+              eft::two_sum(eaf, dh, s, e);
+              sm.ec[ia] = __fadd_rn(sm.ec[ia], __fadd_rn(e, dl));
+              sm.es[ia] = s;
+              eft::two_sum(ebf, dh, s, e);
+              sm.ec[ib] = __fadd_rn(sm.ec[ib], __fadd_rn(e, dl));
+              sm.es[ib] = s;
+              bad |= !isfinite(sm.es[ia]) || !isfinite(sm.es[ib]);
             }
           } else {
             const double ea = sm.e[ia], eb = sm.e[ib];
@@ -865,7 +883,10 @@ __global__ void __launch_bounds__(W * 32, fd_min_blocks<A, W>())
         a.pz[g] += (S)(sm.pz[q] - (R)a.pz[g]);
       }
       double e;
-      if constexpr (A::mixed) e = a.eps[g] + ((double)sm.ahi[q] + (double)sm.alo[q]);  // once per visit
+      if constexpr (A::mixed) {  // once per visit: the load value plus the visit's exact change
+        const double e0 = a.eps[g];
+        e = e0 + (((double)sm.es[q] - (double)(float)e0) + (double)sm.ec[q]);
+      }
       else e = sm.e[q];
       a.eps[g] = e;
       // pressure over rho^2 of the new energy, Eq. (pg-eos): pi = c_rho eps / (C_K m rho)
@@ -979,7 +1000,7 @@ void launch_colour(const Consts& c, const FDConst<typename A::R>& k, const Array
     const int64_t resident = (int64_t)fd_resident_blocks<P, A, KIND, OPW, W>();
     const unsigned gf = (unsigned)std::max<int64_t>(1, std::min(need, resident));
     k_fd_colour<P, A, KIND, OPW, W><<<gf, W * 32, 0, s>>>(
-        c, k, a, (typename P::V4*)w.qp4, w.cell_start, w.mrank, w.xmin[0], w.xmin[1], w.xmin[2], w.sched_hdr,
+        c, k, a, (typename P::V4*)w.qp4, (const typename P::V4*)w.qr4, w.cell_start, w.mrank, w.xmin[0], w.xmin[1], w.xmin[2], w.sched_hdr,
         w.sched_lvl, w.sched_pair, col, seed, w.sweep, w.counters, w.status, recs, w.pair_rec_count,
         w.pair_rec_cap, w.fd_queue + 3 * col, w.blk_order, w.big_perm, w.big_list, w.big_count);
   }

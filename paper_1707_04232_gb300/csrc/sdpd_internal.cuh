@@ -283,6 +283,7 @@ struct Workspace {
   void* rho[2];
   int32_t* id[2];
   void* qp4;            // sorted (x, y, z, pi): positions and p/rho^2 for force passes
+  void* qr4;            // sorted (x, y, z, rho) of the latest density pass: the sweep's geometry
   float4* qf4;          // float64 path: float32 copies (x, y, z, 0) of the sorted positions
   uint32_t* nlist;      // neighbour lists, entry k of particle i at nlist[i * nbr_cap + k]
   int32_t* nn;          // neighbour count per particle

@@ -129,7 +129,8 @@ __global__ void __launch_bounds__(128) k_density(Consts c, Arrays<P> a, typename
                                                  int32_t* __restrict__ ncount_by_id,
                                                  uint32_t* __restrict__ nlist, int32_t* __restrict__ nn,
                                                  int32_t* __restrict__ ovf_list, int32_t* __restrict__ ovf_count,
-                                                 int32_t* __restrict__ ovf_other, const float4* __restrict__ qf4) {
+                                                 int32_t* __restrict__ ovf_other, const float4* __restrict__ qf4,
+                                                 typename P::V4* __restrict__ qr4) {
   using R = typename P::R;
   using V4 = typename P::V4;
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -211,6 +212,8 @@ __global__ void __launch_bounds__(128) k_density(Consts c, Arrays<P> a, typename
   V4 o = qi;
   o.w = pi;
   st4(&qp4[i], o);
+  o.w = rho_new;  // positions and density together for the sweep's pair geometry
+  st4(&qr4[i], o);
 }
 
 // Kick (and, with dt_drift != 0, drift and binning) of particle i with the
@@ -424,11 +427,11 @@ void launch_density(const Consts& c, const Workspace& w, int cur, int update_eos
   if (c.kernel == SDPD_KERNEL_LUCY)
     k_density<P, SDPD_KERNEL_LUCY><<<blocks_for(c.N, t), t, 0, s>>>(
         c, a, qp4, w.cell_start, w.mrank, w.xmin[0], w.xmin[1], w.xmin[2], update_eos, ncount_by_id, w.nlist,
-        w.nn, ovf_list, ovf_count, ovf_other, w.qf4);
+        w.nn, ovf_list, ovf_count, ovf_other, w.qf4, (typename P::V4*)w.qr4);
   else
     k_density<P, SDPD_KERNEL_CUBIC><<<blocks_for(c.N, t), t, 0, s>>>(
         c, a, qp4, w.cell_start, w.mrank, w.xmin[0], w.xmin[1], w.xmin[2], update_eos, ncount_by_id, w.nlist,
-        w.nn, ovf_list, ovf_count, ovf_other, w.qf4);
+        w.nn, ovf_list, ovf_count, ovf_other, w.qf4, (typename P::V4*)w.qr4);
 }
 
 template <class P>

@@ -168,6 +168,7 @@ size_t layout(sdpd_handle* s, Workspace* w, char* base) {
   w->qf4 = P::mixed ? nullptr : (float4*)at(N * sizeof(float4));
   w->nlist = (uint32_t*)at((N + 31) / 32 * 32 * (size_t)c.nbr_cap * 4);
   w->nn = (int32_t*)at(N * 4);
+  w->cend = (uint32_t*)at(9 * N * 4);
   w->key = (int32_t*)at(N * 4);
   w->slot = (int32_t*)at(N * 4);
   w->tmp = (int32_t*)at(2 * N * 4);

@@ -24,8 +24,9 @@
 // sharing a particle), so the pairs of a level touch disjoint particles.
 //
 // Three kernels prepare the schedule of every block (it depends on the
-// positions only, which are fixed during the sweep): k_sched_enum (one warp
-// per block: owned pairs in canonical order), k_sched_walk (one thread per
+// positions only, which are fixed during the sweep): k_sched_enum (one
+// thread block per block: owned pairs in canonical order, from the
+// neighbour lists of the density pass), k_sched_walk (one thread per
 // block: the dependency level of every pair) and k_sched_bucket (one warp per
 // block: pairs bucketed by level); two more order each colour's blocks by
 // depth (k_sched_order_scan, k_sched_order_scatter); then k_fd_colour (sdpd_fd_colour.cuh)
@@ -37,34 +38,39 @@ namespace sdpd {
 
 
 // ---------------------------------------------------------------------------
-// Schedule, step 1: owned pairs of every block in canonical order, found
-// from the positions of the block's particles.  One thread block of
-// kEnumThreads threads per owner cell stages the particles of the block's 8
-// cells in shared memory (ids, coordinates) and tests every candidate pair
-// with the neighbour predicate r^2 < h^2 of the pair passes:
-//   * float64: absolute coordinates and the minimum image, after the float32
-//     pre-test of the density pass (which skips only pairs with r >= h);
-//   * mixed: block-local float32 coordinates, the arithmetic the colour
-//     kernel uses for the pair's geometry.
-// Ranks.  Every cell holds its particles by ascending id, so the rank of a
-// particle among the block's ids is the sum over the 8 cells of the number
-// of smaller ids there (lb[k][d'] = ids in cell d' below particle k's, by
-// binary search; in its own cell, its position).
-// Candidates.  A particle A (as the lower id of a pair) in block cell dA has
-// owned partners only in the cells dB that agree with dA where dA agrees
-// with A's owner bits and differ from dA elsewhere, and only among the ids
-// above its own: the suffix of cell dB from lb[A][dB] on (from A + 1 in its
-// own cell).  One thread walks each particle's candidates, the particles
-// taken in order of their number of candidates (a counting sort).
+// Schedule, step 1: owned pairs of every block in canonical order, read from
+// the neighbour lists of the density pass.  One thread block of
+// kEnumThreads threads per owner cell.
+// Owned pairs.  The pairs of this block whose lower id is particle A (block
+// cell dA) are A's neighbours in the cells that this block holds and that
+// the owner rule gives to this block when A is the lower id: per axis k the
+// offset +1 (A's cell is the block's lower one: dA_k = 0) or -1 (its upper
+// one), and the offset 0 where bit k of A's owner bits equals dA_k.  These
+// cells are 1, 2 or 4 rows of A's 27-cell walk, each a run of consecutive
+// cells, so their entries are at most four slot ranges of A's list (the
+// density pass records where each row's cells start and end).  Of these
+// entries, those whose partner ranks above A are A's owned pairs; the others
+// are found from the partner's side.  The predicate is the density pass's
+// r^2 < h^2, so the sweep's pair set is the one of the density sum.  A block
+// with a member whose list overflowed its row is swept pair by pair
+// (kHdrBig).
+// Ranks.  Every cell holds its particles by ascending id; the 8 sorted cells
+// are merged in three rounds of pairwise merges (the place of an id in the
+// merged run = its place in its own run + the ids below it in the sibling
+// run, by binary search), which gives each particle's rank among the block's
+// ids and the particle of each rank.
+// Entries.  The members' entry counts are scanned into offsets of one flat
+// range, and the threads take its entries in turn, so that the global loads
+// are spread evenly and issued together.
 // Found pairs set bit rank(i) of row d = rank(j) - rank(i) of a triangular
 // bitmap (row d holds nb - d bits in whole words: it starts at word
 // F(nb - 1) - F(nb - d) with F(n) = sum_{k <= n} ceil(k / 32)), which is then
-// read out row by row.  The kernel is kept small (about 13 KB of shared
-// memory for the mixed path) so that 16 blocks share an SM: its phases are
-// short and wait on memory, and other blocks fill the gaps.
+// read out row by row.
 // ---------------------------------------------------------------------------
-constexpr int kEnumThreads = 128;
-constexpr int kTriWords = 1152;  // >= F(255) = 1144: a triangle of 256 rows
+constexpr int kEnumThreads = 160;
+constexpr int kEnumWarps = kEnumThreads / 32;
+constexpr int kTriWords = 1152;   // >= F(255) = 1144: a triangle of 256 rows
+constexpr int kFlatEntries = 4096;  // group entries of one block (more: kHdrBig)
 
 // words of the first rows of the triangular bitmap: F(n) = sum_{k=1..n} ceil(k/32)
 __device__ __forceinline__ int tri_f(int n) {
@@ -72,35 +78,32 @@ __device__ __forceinline__ int tri_f(int n) {
   return 16 * q * (q + 1) + s * (q + 1);
 }
 
-template <class R>
 struct EnumSmem {
-  // coordinates: float64 absolute, mixed block-local (w unused)
-  typename std::conditional<std::is_same<R, double>::value, D4, float4>::type x[kMaxBlock];
-  float4 f[std::is_same<R, double>::value ? kMaxBlock : 1];  // float64: float32 copies for the pre-test
   uint32_t bits[kTriWords];
-  int32_t id[kMaxBlock];
-  uint8_t lb[kMaxBlock][8];  // ids of each cell below the particle's (own cell: its position)
+  int32_t ids[2][kMaxBlock];  // merge rounds: the ids in run order
+  uint8_t ks[2][kMaxBlock];   // and the block-local index of each
+  uint8_t rank[kMaxBlock];    // rank of each block-local index
+  uint8_t perm[kMaxBlock];    // block-local index of each rank
+  uint8_t who[kFlatEntries];  // member of each flat entry
+  uint32_t rng[kMaxBlock];    // up to four slot ranges (first slot, length) of each member's group, packed
+  uint32_t rcum[kMaxBlock];   // cumulative lengths after ranges 0, 1, 2 (bytes)
+  uint8_t ncnt[kMaxBlock];    // entries of each member's group
+  int32_t off[kMaxBlock + 1];  // first flat entry of each member
   uint16_t rowoff[kMaxBlock];
   uint16_t rowbase[kMaxBlock];  // first word of each row of the bitmap
-  uint8_t ncand[kMaxBlock];     // each particle's number of candidates (clamped to 255)
-  uint8_t order[kMaxBlock];     // the particles by number of candidates, most first
-  int32_t hist[kMaxBlock + 1];  // particles by number of candidates (clamped to 255)
-  uint8_t code[kMaxBlock];   // block cell of each particle
-  uint8_t rank[kMaxBlock];
-  uint8_t perm[kMaxBlock];
-  int32_t cstart[8], cbase[9];
-  int32_t npairs, nb;
+  int32_t wtot[kEnumWarps];     // per-warp totals of the offset scan
+  int32_t ctot[8];              // row-scan chunk totals
+  int32_t cstart[8], cbase[9], koff[8];
+  int32_t nb, big;
 };
 
-template <class P>
 __global__ void __launch_bounds__(kEnumThreads)
-    k_sched_enum(Consts c, Arrays<P> a, const int32_t* __restrict__ cell_start, const int32_t* __restrict__ mrank,
-                 const uint32_t* __restrict__ xmx, const uint32_t* __restrict__ xmy,
-                 const uint32_t* __restrict__ xmz, const float4* __restrict__ qf4, uint32_t* __restrict__ hdr,
+    k_sched_enum(Consts c, const int32_t* __restrict__ pid, const int32_t* __restrict__ cell_start,
+                 const int32_t* __restrict__ mrank, const uint32_t* __restrict__ nlist,
+                 const int32_t* __restrict__ nn, const uint32_t* __restrict__ cend, uint32_t* __restrict__ hdr,
                  uint16_t* __restrict__ canon, uint32_t* __restrict__ blk_hist, uint32_t* __restrict__ big_count) {
-  using R = typename P::R;
-  __shared__ EnumSmem<R> sm;
-  const int t = threadIdx.x, lane = t & 31;
+  __shared__ EnumSmem sm;
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
   if (blockIdx.x == 0) {  // the depth histogram and the lists of blocks beyond capacity that k_sched_walk fills
     for (int k = t; k < 8 * 256; k += kEnumThreads) blk_hist[k] = 0u;
     if (t < 16) big_count[t] = 0u;
@@ -128,12 +131,13 @@ __global__ void __launch_bounds__(kEnumThreads)
     if (lane < 8) {
       sm.cstart[lane] = cst;
       sm.cbase[lane] = cinc - ccnt;
+      sm.koff[lane] = cinc - ccnt - cst;  // block-local index = storage index + koff
     }
     if (lane == 7) {
       sm.cbase[8] = cinc;
       sm.nb = cinc;
     }
-    if (lane == 0) sm.npairs = 0;
+    if (lane == 0) sm.big = 0;
   }
   __syncthreads();
   const int nb = sm.nb;
@@ -143,174 +147,189 @@ __global__ void __launch_bounds__(kEnumThreads)
   }
   const int ntri = nb > 1 ? tri_f(nb - 1) : 0;  // words of the bitmap in use
   for (int q = t; q < ntri; q += kEnumThreads) sm.bits[q] = 0u;
-  BlockGeom<P> geo;
-  geo.init(c, ox, oy, oz, xmx, xmy, xmz);
   int cb[9];
 #pragma unroll
   for (int u = 0; u < 9; ++u) cb[u] = sm.cbase[u];
-  for (int k = t; k < nb; k += kEnumThreads) {  // the particles
+  const int64_t N = c.N;
+  // the members: id, and the slot ranges of the owner group in the list
+  for (int k = t; k < nb; k += kEnumThreads) {
     int d = 0;
 #pragma unroll
     for (int u = 1; u < 8; ++u) d += (k >= cb[u]);
     const int g = sm.cstart[d] + (k - sm.cbase[d]);
-    sm.id[k] = a.id[g];
-    sm.code[k] = (uint8_t)d;
-    R x, y, zz;
-    geo.local(ld4(&a.q4[g]), d, x, y, zz);
-    sm.x[k].x = x; sm.x[k].y = y; sm.x[k].z = zz;
-    if constexpr (!P::mixed) sm.f[k] = __ldg(&qf4[g]);
+    const int32_t id = __ldg(&pid[g]);
+    sm.ids[0][k] = id;
+    sm.ks[0][k] = (uint8_t)k;
+    if (__ldg(&nn[g]) > c.nbr_cap) sm.big = 1;  // the list lost entries
+    const unsigned ob = owner_bits(id);
+    // per axis the cells of the group as indices [lo, hi) of the offsets
+    // (-1, 0, +1): dA_k = 0: {0 if ob_k = 0, +1}; dA_k = 1: {-1, 0 if ob_k = 1}
+    int lo[3], hi[3];
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+      const int dk = (d >> ax) & 1, bk = (int)(ob >> ax) & 1;
+      lo[ax] = dk ? 0 : 2 - (bk ^ 1);
+      hi[ax] = dk ? 1 + bk : 3;
+    }
+    // rows (iz, iy) of the group: at most 2 x 2; x range [lo[0], hi[0]) of bytes
+    uint32_t w[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int iz = lo[2] + (q >> 1), iy = lo[1] + (q & 1);
+      w[q] = (iz < hi[2] && iy < hi[1]) ? __ldg(&cend[(int64_t)(iz * 3 + iy) * N + g]) : 0u;
+    }
+    uint32_t rng = 0u, cum = 0u;
+    int tot = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int s0 = (int)((w[q] >> (8 * lo[0])) & 255u), s1 = (int)((w[q] >> (8 * hi[0])) & 255u);
+      const int len = s1 > s0 ? s1 - s0 : 0;  // empty for rows outside the group (w = 0)
+      rng |= (uint32_t)s0 << (8 * q);
+      tot += len;
+      if (q < 3) cum |= (uint32_t)min(tot, 255) << (8 * q);
+    }
+    sm.rng[k] = rng;
+    sm.rcum[k] = cum;
+    sm.off[k] = tot;  // the count; turned into an offset below
+    sm.ncnt[k] = (uint8_t)tot;  // at most the row capacity
   }
   __syncthreads();
-  // lower bounds: for every particle and cell, the ids of the cell below the
-  // particle's, by branch-free binary searches of a fixed length, the 8
-  // searches of a particle independent of each other (own cell: its
-  // position); then the ranks, and each particle's number of candidates (ids
-  // above its own in its partner cells)
-  {
-    int maxcnt = 0;
-#pragma unroll
-    for (int d = 0; d < 8; ++d) maxcnt = max(maxcnt, cb[d + 1] - cb[d]);
-    int steps = 0;
-    while ((1 << steps) <= maxcnt) ++steps;
-    for (int k = t; k < nb; k += kEnumThreads) {
-      const int32_t myid = sm.id[k];
-      int pos[8], len[8];
-#pragma unroll
-      for (int d = 0; d < 8; ++d) { pos[d] = cb[d]; len[d] = cb[d + 1] - cb[d]; }
-      for (int it = 0; it < steps; ++it) {
-#pragma unroll
-        for (int d = 0; d < 8; ++d) {
-          const int half = len[d] >> 1;
-          const bool below = len[d] > 0 && sm.id[pos[d] + half] < myid;
-          pos[d] = below ? pos[d] + half + 1 : pos[d];
-          len[d] = below ? len[d] - half - 1 : half;
-        }
-      }
-#pragma unroll
-      for (int d = 0; d < 8; ++d) sm.lb[k][d] = (uint8_t)(pos[d] - cb[d]);
-    }
+  if (sm.big) {
+    if (t == 0) hdr[o] = kHdrBig;
+    return;
   }
-  for (int q = t; q <= kMaxBlock; q += kEnumThreads) sm.hist[q] = 0;
+  // ranks: three rounds of pairwise merges of the sorted cells, interleaved
+  // with the exclusive scan of the members' entry counts
+  int cnt0 = 0, incl = 0;
+#pragma unroll 1
+  for (int L = 0; L < 3; ++L) {
+    const int src = L & 1, dst = src ^ 1;
+    for (int k = t; k < nb; k += kEnumThreads) {
+      int d = 0;
+#pragma unroll
+      for (int u = 1; u < 8; ++u) d += (k >= cb[u]);
+      const int run = d >> L, sib = run ^ 1;
+      const int own0 = sm.cbase[run << L], m0 = sm.cbase[(run & ~1) << L];
+      int pos = sm.cbase[sib << L], len = sm.cbase[(sib + 1) << L] - pos;
+      const int sib0 = pos;
+      const int32_t myid = sm.ids[src][k];
+      while (len > 0) {
+        const int half = len >> 1;
+        const bool below = sm.ids[src][pos + half] < myid;
+        pos = below ? pos + half + 1 : pos;
+        len = below ? len - half - 1 : half;
+      }
+      const int np = m0 + (k - own0) + (pos - sib0);
+      sm.ids[dst][np] = myid;
+      sm.ks[dst][np] = sm.ks[src][k];
+    }
+    if (L == 0) {  // counts of members t and t + kEnumThreads: per-warp inclusive scan
+      cnt0 = t < nb ? sm.off[t] : 0;
+      const int cnt1 = t + kEnumThreads < nb ? sm.off[t + kEnumThreads] : 0;
+      incl = cnt0 + cnt1;
+#pragma unroll
+      for (int sh = 1; sh < 32; sh <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, sh);
+        if (lane >= sh) incl += v;
+      }
+      if (lane == 31) sm.wtot[wid] = incl;
+    } else if (L == 1) {  // offsets: member t, then member t + kEnumThreads (the flat order needs no more)
+      int before = 0, total = 0;
+#pragma unroll
+      for (int q = 0; q < kEnumWarps; ++q) {
+        before += q < wid ? sm.wtot[q] : 0;
+        total += sm.wtot[q];
+      }
+      const int ex = before + incl - (cnt0 + (t + kEnumThreads < nb ? sm.off[t + kEnumThreads] : 0));
+      if (t < nb) sm.off[t] = ex;
+      if (t + kEnumThreads < nb) sm.off[t + kEnumThreads] = ex + cnt0;
+      if (t == 0) sm.off[nb] = total;
+      if (total > kFlatEntries && t == 0) sm.big = 1;
+    } else {  // the member of each flat entry
+      if (!sm.big)
+        for (int k = t; k < nb; k += kEnumThreads)
+          for (int e = sm.off[k], e1 = sm.off[k] + sm.ncnt[k]; e < e1; ++e) sm.who[e] = (uint8_t)k;
+    }
+    __syncthreads();
+  }
+  if (sm.big) {
+    if (t == 0) hdr[o] = kHdrBig;
+    return;
+  }
+  for (int r = t; r < nb; r += kEnumThreads) {  // the merged run is ids[1]
+    const int k = sm.ks[1][r];
+    sm.perm[r] = (uint8_t)k;
+    sm.rank[k] = (uint8_t)r;
+  }
   for (int d = 1 + t; d < nb; d += kEnumThreads)  // row d of the bitmap starts at F(nb - 1) - F(nb - d)
     sm.rowbase[d] = (uint16_t)(tri_f(nb - 1) - tri_f(nb - d));
   __syncthreads();
-  for (int k = t; k < nb; k += kEnumThreads) {
-    int r = 0;
+  // the flat entries: partner, rank test, bit
+  const int E = sm.off[nb], cap = c.nbr_cap;
+#pragma unroll 4
+  for (int e = t; e < E; e += kEnumThreads) {
+    const int A = sm.who[e];
+    const int m = e - sm.off[A];
+    const uint32_t rng = sm.rng[A], cum = sm.rcum[A];
+    const int c0 = cum & 255u, c1 = (cum >> 8) & 255u, c2 = (cum >> 16) & 255u;
+    const int q = (m >= c0) + (m >= c1) + (m >= c2);
+    const int before = q == 0 ? 0 : (q == 1 ? c0 : (q == 2 ? c1 : c2));
+    const int slot = (int)((rng >> (8 * q)) & 255u) + (m - before);
+    int dA = 0;
 #pragma unroll
-    for (int d = 0; d < 8; ++d) r += sm.lb[k][d];
-    sm.rank[k] = (uint8_t)r;
-    sm.perm[r] = (uint8_t)k;
-    const int dA = sm.code[k];
-    const int free = 7 & ~(dA ^ (int)owner_bits(sm.id[k]));
-    const int fixed = 7 & ~dA & ~free;
-    int cand = 0, sub = free;
-    for (;;) {
-      const int dB = fixed | sub;
-      cand += (sm.cbase[dB + 1] - sm.cbase[dB]) - (dB == dA ? sm.lb[k][dA] + 1 : sm.lb[k][dB]);
-      if (sub == 0) break;
-      sub = (sub - 1) & free;
+    for (int u = 1; u < 8; ++u) dA += (A >= cb[u]);
+    const int gA = A - sm.koff[dA];  // storage index
+    const uint32_t en = __ldg(&nlist[nbr_slot(gA, slot, cap)]);
+    // partner cell in the block: dA plus the stencil offset (code - 1 per axis)
+    const int dB = ((dA & 1) + (int)(en & 3u) - 1) | ((((dA >> 1) & 1) + (int)((en >> 2) & 3u) - 1) << 1) |
+                   (((dA >> 2) + (int)((en >> 4) & 3u) - 1) << 2);
+    const int kB = (int)(en >> 6) + sm.koff[dB & 7];
+    if ((unsigned)kB < (unsigned)nb) {
+      const int rA = sm.rank[A], rB = sm.rank[kB];
+      if (rB > rA) atomicOr(&sm.bits[sm.rowbase[rB - rA] + (rA >> 5)], 1u << (rA & 31));
     }
-    sm.ncand[k] = (uint8_t)min(cand, 255);
-    atomicAdd(&sm.hist[min(cand, 255)], 1);
   }
   __syncthreads();
-  if (t < 32) {  // positions by candidate count, most first
-    int run = 0;
-    for (int l0 = 255; l0 >= 0; l0 -= 32) {
-      const int l = l0 - lane;
-      const int v = l >= 0 ? sm.hist[l] : 0;
-      int incl = v;
+  // row populations (rows 1 .. nb - 1): each warp scans 32 rows at a time
+  // (row 1 + t is thread t's in every phase below), then the chunk totals
+  // are added in
+  int rowex[2] = {0, 0};
 #pragma unroll
-      for (int sh = 1; sh < 32; sh <<= 1) {
-        const int u = __shfl_up_sync(0xffffffffu, incl, sh);
-        if (lane >= sh) incl += u;
-      }
-      if (l >= 0) sm.hist[l] = run + incl - v;
-      run += __shfl_sync(0xffffffffu, incl, 31);
-    }
-  }
-  __syncthreads();
-  for (int k = t; k < nb; k += kEnumThreads) sm.order[atomicAdd(&sm.hist[sm.ncand[k]], 1)] = (uint8_t)k;
-  __syncthreads();
-  // candidates: one thread per particle A (as the lower id), the particles
-  // with the most candidates first, so that a warp's lanes have similar work
-  const R h2 = (R)c.h2;
-  for (int q = t; q < nb; q += kEnumThreads) {
-    const int A = sm.order[q];
-    const int dA = sm.code[A];
-    const int hb = (int)owner_bits(sm.id[A]);
-    const int free = 7 & ~(dA ^ hb);  // axes where the partner may share the cell
-    const int fixed = 7 & ~dA & ~free;
-    const int rA = sm.rank[A];
-    const auto xa = sm.x[A];
-    float4 fa = make_float4(0.f, 0.f, 0.f, 0.f);
-    if constexpr (!P::mixed) fa = sm.f[A];
-    const int wA = rA >> 5;
-    const uint32_t bit = 1u << (rA & 31);
-    int sub = free;
-    for (;;) {
-      const int dB = fixed | sub;
-      const int b0 = dB == dA ? A + 1 : sm.cbase[dB] + sm.lb[A][dB], b1 = sm.cbase[dB + 1];
-      for (int B = b0; B < b1; ++B) {
-        if constexpr (!P::mixed) {  // float32 pre-test: skips only pairs with r >= h
-          const float4 fb = sm.f[B];
-          float ex = fa.x - fb.x, ey = fa.y - fb.y, ez = fa.z - fb.z;
-          ex = ex > c.halfLf[0] ? ex - c.Lf[0] : (ex < -c.halfLf[0] ? ex + c.Lf[0] : ex);
-          ey = ey > c.halfLf[1] ? ey - c.Lf[1] : (ey < -c.halfLf[1] ? ey + c.Lf[1] : ey);
-          ez = ez > c.halfLf[2] ? ez - c.Lf[2] : (ez < -c.halfLf[2] ? ez + c.Lf[2] : ez);
-          if (ex * ex + ey * ey + ez * ez >= c.h2_filter) continue;
-        }
-        const auto xb = sm.x[B];
-        R dx, dy, dz;
-        geo.disp((R)xa.x, (R)xa.y, (R)xa.z, (R)xb.x, (R)xb.y, (R)xb.z, dx, dy, dz);
-        if (r2_of(dx, dy, dz) < h2) atomicOr(&sm.bits[sm.rowbase[sm.rank[B] - rA] + wA], bit);
-      }
-      if (sub == 0) break;
-      sub = (sub - 1) & free;
-    }
-  }
-  __syncthreads();
-  // exclusive scan of the row populations (rows 1 .. nb - 1): each warp
-  // scans 32 rows at a time, then the chunk totals are added in
-  const int wid = t >> 5;
-  for (int r0 = 1 + 32 * wid; r0 < nb; r0 += kEnumThreads) {
+  for (int it = 0; it < 2; ++it) {
+    const int r0 = 1 + 32 * wid + it * kEnumThreads;
+    if (r0 >= nb) break;
     const int rr = r0 + lane;
     int n = 0;
     if (rr < nb) {
       const int w0 = sm.rowbase[rr], nwr = (nb - rr + 31) >> 5;
       for (int w = 0; w < nwr; ++w) n += __popc(sm.bits[w0 + w]);
     }
-    int incl = n;
+    int inc = n;
 #pragma unroll
     for (int sh = 1; sh < 32; sh <<= 1) {
-      const int v = __shfl_up_sync(0xffffffffu, incl, sh);
-      if (lane >= sh) incl += v;
+      const int v = __shfl_up_sync(0xffffffffu, inc, sh);
+      if (lane >= sh) inc += v;
     }
-    if (rr < nb) sm.rowoff[rr] = (uint16_t)(incl - n);  // within the chunk
-    if (lane == 31) sm.hist[(r0 - 1) >> 5] = incl;        // chunk total
+    rowex[it] = inc - n;
+    if (lane == 31) sm.ctot[(r0 - 1) >> 5] = inc;
   }
   __syncthreads();
-  if (t == 0) {  // chunk totals to chunk offsets (at most 8 chunks)
-    int run = 0;
-    for (int ch = 0; ch * 32 + 1 < nb; ++ch) {
-      const int v = sm.hist[ch];
-      sm.hist[ch] = run;
-      run += v;
-    }
-    sm.npairs = run;
-  }
-  __syncthreads();
-  for (int rr = 1 + t; rr < nb; rr += kEnumThreads) sm.rowoff[rr] = (uint16_t)(sm.rowoff[rr] + sm.hist[(rr - 1) >> 5]);
-  __syncthreads();
-  const int npairs = sm.npairs;
+  const int nchunk = (nb - 1 + 31) >> 5;
+  int npairs = 0;
+  for (int ch = 0; ch < nchunk; ++ch) npairs += sm.ctot[ch];
   if (npairs > kMaxPairs) {
     if (t == 0) hdr[o] = kHdrBig;
     return;
   }
   // write the pairs row by row (difference ascending), lower rank ascending
   uint16_t* out = canon + (int64_t)o * kMaxPairs;
-  for (int rr = 1 + t; rr < nb; rr += kEnumThreads) {
-    int pos = sm.rowoff[rr];
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const int rr = 1 + t + it * kEnumThreads;
+    if (rr >= nb) break;
+    const int chunk = (rr - 1) >> 5;
+    int pos = rowex[it];
+    for (int ch = 0; ch < chunk; ++ch) pos += sm.ctot[ch];
     const int w0 = sm.rowbase[rr], nwr = (nb - rr + 31) >> 5;
     for (int w = 0; w < nwr; ++w) {
       uint32_t bits = sm.bits[w0 + w];
@@ -520,9 +539,8 @@ void launch_fd_schedule(const Consts& c, const Workspace& w, int cur, cudaStream
   if (c.N == 0) return;
   Arrays<P> a = view<P>(w, cur);
   uint16_t* canon = w.sched_pair + (size_t)c.ncell * kMaxPairs;
-  k_sched_enum<P><<<(unsigned)c.ncell, kEnumThreads, 0, s>>>(c, a, w.cell_start, w.mrank, w.xmin[0], w.xmin[1],
-                                                               w.xmin[2], w.qf4, w.sched_hdr, canon, w.blk_hist,
-                                                               w.big_count);
+  k_sched_enum<<<(unsigned)c.ncell, kEnumThreads, 0, s>>>(c, a.id, w.cell_start, w.mrank, w.nlist, w.nn, w.cend,
+                                                          w.sched_hdr, canon, w.blk_hist, w.big_count);
   k_sched_walk<<<(unsigned)((c.ncell + kLevelThreads - 1) / kLevelThreads), kLevelThreads, 0, s>>>(
       c.ncell, c.nc[0], c.nc[1], c.nc[2], w.sched_hdr, canon, w.level_of, w.blk_hist, w.cell_start, w.mrank,
       w.big_count, w.big_list);

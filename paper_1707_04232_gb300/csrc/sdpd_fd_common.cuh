@@ -85,22 +85,6 @@ struct BlockGeom<Mixed> {
   }
 };
 
-// Owner bits of a particle id (bit k for axis k): the top three bits of a
-// multiply / xor-shift mix of the id as a 32-bit unsigned integer.  Along an
-// axis where a pair's two cells coincide, the bit of the pair's lower id
-// picks which of the two blocks holding that coordinate owns the pair: the
-// one where the cell is the lower (0) or the upper (1) cell of the block.
-__device__ __forceinline__ unsigned owner_bits(int32_t id) {
-  uint32_t x = (uint32_t)id;
-  x *= 2654435761u;
-  x ^= x >> 15;
-  x *= 2246822519u;
-  x ^= x >> 13;
-  x *= 3266489917u;
-  x ^= x >> 16;
-  return x >> 29;
-}
-
 __device__ __forceinline__ void owner_coords(const Consts& c, int64_t o, int& ox, int& oy, int& oz) {
   ox = (int)(o % c.nc[0]);
   oy = (int)((o / c.nc[0]) % c.nc[1]);

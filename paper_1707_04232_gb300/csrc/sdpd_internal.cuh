@@ -78,6 +78,22 @@ __host__ __device__ __forceinline__ int64_t nbr_slot(int64_t i, int k, int cap) 
   return ((((i >> 5) * (int64_t)(cap >> 2) + (k >> 2)) << 5) + (i & 31)) * 4 + (k & 3);
 }
 
+// Owner bits of a particle id (bit k for axis k): the top three bits of a
+// multiply / xor-shift mix of the id as a 32-bit unsigned integer.  Along an
+// axis where a pair's two cells coincide, the bit of the pair's lower id
+// picks which of the two blocks holding that coordinate owns the pair: the
+// one where the cell is the lower (0) or the upper (1) cell of the block.
+__device__ __forceinline__ unsigned owner_bits(int32_t id) {
+  uint32_t x = (uint32_t)id;
+  x *= 2654435761u;
+  x ^= x >> 15;
+  x *= 2246822519u;
+  x ^= x >> 13;
+  x *= 3266489917u;
+  x ^= x >> 16;
+  return x >> 29;
+}
+
 // ---------------------------------------------------------------------------
 // Pair distance from r^2.  float64: 1/r from the float32 reciprocal square
 // root refined by one Newton step for y = 1/sqrt(x), y <- y (3 - x y^2) / 2
@@ -285,8 +301,9 @@ struct Workspace {
   void* qp4;            // sorted (x, y, z, pi): positions and p/rho^2 for force passes
   void* qr4;            // sorted (x, y, z, rho) of the latest density pass: the sweep's geometry
   float4* qf4;          // float64 path: float32 copies (x, y, z, 0) of the sorted positions
-  uint32_t* nlist;      // neighbour lists, entry k of particle i at nlist[i * nbr_cap + k]
+  uint32_t* nlist;      // neighbour lists, entry k of particle i at nlist[nbr_slot(i, k, nbr_cap)]
   int32_t* nn;          // neighbour count per particle
+  uint32_t* cend;       // [9][N]: per particle and row of 3 cells, where its list stands (see k_density)
   // binning and sorting scratch
   int32_t* key;         // cell rank per particle (old order)
   int32_t* slot;        // arrival slot in the cell (old order)

@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(128) k_density(Consts c, Arrays<P> a, typename
                                                  uint32_t* __restrict__ nlist, int32_t* __restrict__ nn,
                                                  int32_t* __restrict__ ovf_list, int32_t* __restrict__ ovf_count,
                                                  int32_t* __restrict__ ovf_other, const float4* __restrict__ qf4,
-                                                 typename P::V4* __restrict__ qr4) {
+                                                 typename P::V4* __restrict__ qr4, uint32_t* __restrict__ cend) {
   using R = typename P::R;
   using V4 = typename P::V4;
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -147,12 +147,19 @@ __global__ void __launch_bounds__(128) k_density(Consts c, Arrays<P> a, typename
   R acc = R(0);
   int cnt = 0;
   uint32_t* wp = nlist + nbr_slot(i, 0, c.nbr_cap);  // where entry cnt of the list goes
+  // Every lane walks the 27 cells in the same order (z, then y, then x
+  // offset, each -1, 0, +1), so the warp's loops stay converged.  Per row
+  // (oz, oy) of three cells, cend[row][i] records where the list stands:
+  // byte 0 at the row's start, byte 1 + k after its k-th cell (counts
+  // clamped to 255).  The sweep's schedule finds each block's pairs in
+  // these cell runs of the list.
 #pragma unroll 1
   for (int oz = -1; oz <= 1; ++oz) {
     const int nz = wrapc(cz + oz, c.nc[2]);
 #pragma unroll 1
     for (int oy = -1; oy <= 1; ++oy) {
       const int ny = wrapc(cy + oy, c.nc[1]);
+      uint32_t rw = (uint32_t)min(cnt, 255);
 #pragma unroll 1
       for (int ox = -1; ox <= 1; ++ox) {
         const int nx = wrapc(cx + ox, c.nc[0]);
@@ -184,7 +191,9 @@ __global__ void __launch_bounds__(128) k_density(Consts c, Arrays<P> a, typename
             ++cnt;
           }
         }
+        rw |= (uint32_t)min(cnt, 255) << (8 * (ox + 2));
       }
+      cend[(int64_t)((oz + 1) * 3 + (oy + 1)) * c.N + i] = rw;
     }
   }
   if (ncount_by_id) ncount_by_id[a.id[i]] = cnt;
@@ -427,11 +436,11 @@ void launch_density(const Consts& c, const Workspace& w, int cur, int update_eos
   if (c.kernel == SDPD_KERNEL_LUCY)
     k_density<P, SDPD_KERNEL_LUCY><<<blocks_for(c.N, t), t, 0, s>>>(
         c, a, qp4, w.cell_start, w.mrank, w.xmin[0], w.xmin[1], w.xmin[2], update_eos, ncount_by_id, w.nlist,
-        w.nn, ovf_list, ovf_count, ovf_other, w.qf4, (typename P::V4*)w.qr4);
+        w.nn, ovf_list, ovf_count, ovf_other, w.qf4, (typename P::V4*)w.qr4, w.cend);
   else
     k_density<P, SDPD_KERNEL_CUBIC><<<blocks_for(c.N, t), t, 0, s>>>(
         c, a, qp4, w.cell_start, w.mrank, w.xmin[0], w.xmin[1], w.xmin[2], update_eos, ncount_by_id, w.nlist,
-        w.nn, ovf_list, ovf_count, ovf_other, w.qf4, (typename P::V4*)w.qr4);
+        w.nn, ovf_list, ovf_count, ovf_other, w.qf4, (typename P::V4*)w.qr4, w.cend);
 }
 
 template <class P>

@@ -88,6 +88,8 @@ struct EnumSmem {
   uint32_t rng[kMaxBlock];    // up to four slot ranges (first slot, length) of each member's group, packed
   uint32_t rcum[kMaxBlock];   // cumulative lengths after ranges 0, 1, 2 (bytes)
   uint8_t ncnt[kMaxBlock];    // entries of each member's group
+  uint8_t dk[kMaxBlock];      // block cell of each member
+  int32_t gk[kMaxBlock];      // storage index of each member
   int32_t off[kMaxBlock + 1];  // first flat entry of each member
   uint16_t rowoff[kMaxBlock];
   uint16_t rowbase[kMaxBlock];  // first word of each row of the bitmap
@@ -192,6 +194,8 @@ __global__ void __launch_bounds__(kEnumThreads)
     sm.rcum[k] = cum;
     sm.off[k] = tot;  // the count; turned into an offset below
     sm.ncnt[k] = (uint8_t)tot;  // at most the row capacity
+    sm.dk[k] = (uint8_t)d;
+    sm.gk[k] = g;
   }
   __syncthreads();
   if (sm.big) {
@@ -223,9 +227,9 @@ __global__ void __launch_bounds__(kEnumThreads)
       sm.ids[dst][np] = myid;
       sm.ks[dst][np] = sm.ks[src][k];
     }
-    if (L == 0) {  // counts of members t and t + kEnumThreads: per-warp inclusive scan
-      cnt0 = t < nb ? sm.off[t] : 0;
-      const int cnt1 = t + kEnumThreads < nb ? sm.off[t + kEnumThreads] : 0;
+    if (L == 0) {  // counts of members 2t and 2t + 1: per-warp inclusive scan
+      cnt0 = 2 * t < nb ? sm.ncnt[2 * t] : 0;
+      const int cnt1 = 2 * t + 1 < nb ? sm.ncnt[2 * t + 1] : 0;
       incl = cnt0 + cnt1;
 #pragma unroll
       for (int sh = 1; sh < 32; sh <<= 1) {
@@ -233,22 +237,38 @@ __global__ void __launch_bounds__(kEnumThreads)
         if (lane >= sh) incl += v;
       }
       if (lane == 31) sm.wtot[wid] = incl;
-    } else if (L == 1) {  // offsets: member t, then member t + kEnumThreads (the flat order needs no more)
+    } else if (L == 1) {  // offsets in member order
       int before = 0, total = 0;
 #pragma unroll
       for (int q = 0; q < kEnumWarps; ++q) {
         before += q < wid ? sm.wtot[q] : 0;
         total += sm.wtot[q];
       }
-      const int ex = before + incl - (cnt0 + (t + kEnumThreads < nb ? sm.off[t + kEnumThreads] : 0));
-      if (t < nb) sm.off[t] = ex;
-      if (t + kEnumThreads < nb) sm.off[t + kEnumThreads] = ex + cnt0;
+      const int ex = before + incl - cnt0 - (2 * t + 1 < nb ? sm.ncnt[2 * t + 1] : 0);
+      if (2 * t < nb) sm.off[2 * t] = ex;
+      if (2 * t + 1 < nb) sm.off[2 * t + 1] = ex + cnt0;
       if (t == 0) sm.off[nb] = total;
       if (total > kFlatEntries && t == 0) sm.big = 1;
-    } else {  // the member of each flat entry
-      if (!sm.big)
-        for (int k = t; k < nb; k += kEnumThreads)
-          for (int e = sm.off[k], e1 = sm.off[k] + sm.ncnt[k]; e < e1; ++e) sm.who[e] = (uint8_t)k;
+    } else if (!sm.big) {  // the member of each flat entry, in equal stretches per thread
+      const int E = sm.off[nb], per = (E + kEnumThreads - 1) / kEnumThreads;
+      const int e0 = t * per, e1 = min(E, e0 + per);
+      if (e0 < e1) {
+        int pos = 1, len = nb - 1;  // members 1 .. nb - 1 starting at or before e0
+        while (len > 0) {
+          const int half = len >> 1;
+          const bool le = sm.off[pos + half] <= e0;
+          pos = le ? pos + half + 1 : pos;
+          len = le ? len - half - 1 : half;
+        }
+        int k = pos - 1, kend = sm.off[k] + sm.ncnt[k];
+        for (int e = e0; e < e1; ++e) {
+          while (e >= kend) {  // (members without entries are skipped)
+            ++k;
+            kend = sm.off[k] + sm.ncnt[k];
+          }
+          sm.who[e] = (uint8_t)k;
+        }
+      }
     }
     __syncthreads();
   }
@@ -275,10 +295,7 @@ __global__ void __launch_bounds__(kEnumThreads)
     const int q = (m >= c0) + (m >= c1) + (m >= c2);
     const int before = q == 0 ? 0 : (q == 1 ? c0 : (q == 2 ? c1 : c2));
     const int slot = (int)((rng >> (8 * q)) & 255u) + (m - before);
-    int dA = 0;
-#pragma unroll
-    for (int u = 1; u < 8; ++u) dA += (A >= cb[u]);
-    const int gA = A - sm.koff[dA];  // storage index
+    const int dA = sm.dk[A], gA = sm.gk[A];
     const uint32_t en = __ldg(&nlist[nbr_slot(gA, slot, cap)]);
     // partner cell in the block: dA plus the stencil offset (code - 1 per axis)
     const int dB = ((dA & 1) + (int)(en & 3u) - 1) | ((((dA >> 1) & 1) + (int)((en >> 2) & 3u) - 1) << 1) |

@@ -356,7 +356,7 @@ __device__ __forceinline__ int fd_pair_mixed(const FDConst<float>& k, float ex, 
     exact_e(ei, ej);
     emn = ((ei < ej ? ei : ej) + ((double)dh + (double)dl)) > 0.0 ? 1.0f : -1.0f;
   }
-  margin = (double)emn;
+  if (exact) margin = (double)emn;  // (float64 work only where it is asked for)
   int decision = 0;
   if (k.scheme == SDPD_SCHEME_SSA) {
     if (!(emn > 0.0f)) negative = true;
@@ -397,7 +397,6 @@ __device__ __forceinline__ int fd_pair_mixed(const FDConst<float>& k, float ex, 
     tol = 2.0f * (u * T + 2.0f * elog);
     if (fabsf(x) >= 0.0625f) tol += 2.0f * k.CKm1 * (elog + 16.0f * u);
     m32 = mg;
-    double mgd = (double)mg;
     if (exact || !(fabsf(mg) > tol)) {  // float32 not decisive (or NaN): float64
       MixedRatioIn r;
       r.ex = ex; r.ey = ey; r.ez = ez; r.vx = vx; r.vy = vy; r.vz = vz;
@@ -406,10 +405,11 @@ __device__ __forceinline__ int fd_pair_mixed(const FDConst<float>& k, float ex, 
       r.mrpar = mrpar; r.mrperp = mrperp; r.ypar = ypar; r.yperp = yperp;
       exact_e(r.ei, r.ej);
       r.deps = (double)dh + (double)dl;
-      mgd = mixed_margin_fp64(r, k.CKm1_d);
+      margin = mixed_margin_fp64(r, k.CKm1_d);
+      if (margin < 0.0) decision = 2;  // U > exp(a)
+    } else if (mg < 0.0f) {  // decided in float32: |mg| exceeds its error bound
+      decision = 2;
     }
-    margin = mgd;
-    if (mgd < 0.0) decision = 2;  // U > exp(a)
   }
   if (decision == 0) {
     pi[0] = nn[0]; pi[1] = nn[1]; pi[2] = nn[2];
@@ -668,7 +668,7 @@ __global__ void __launch_bounds__(W * 32, fd_min_blocks<A, W>())
   FdSmem<R>& sm = sm_all[warp][grp];
   const S inv_h = (S)(1.0 / c.h), cF = (S)c.cF;
   const S pi_coef = (S)(c.c_rho / (c.C_K * c.m));
-  unsigned long long n_acc = 0, n_rb = 0, n_rm = 0, n_tot = 0;
+  unsigned n_tot = 0, n_rb = 0, n_rm = 0;  // per lane (accepted = total - rejected)
   bool negative = false, bad = false;
   // The grid holds as many thread blocks as fit on the GPU at once; each
   // warp takes the colour's blocks OPW at a time from queue[0] until they
@@ -840,7 +840,6 @@ __global__ void __launch_bounds__(W * 32, fd_min_blocks<A, W>())
             }
           }
           ++n_tot;
-          n_acc += dcs == 0;
           n_rb += dcs == 1;
           n_rm += dcs == 2;
           if (recs) {
@@ -890,6 +889,7 @@ __global__ void __launch_bounds__(W * 32, fd_min_blocks<A, W>())
       else e = sm.e[q];
       a.eps[g] = e;
       // pressure over rho^2 of the new energy, Eq. (pg-eos): pi = c_rho eps / (C_K m rho)
+      // (from the stored float64 energy, as a restart recomputes it)
       qp4[g].w = (S)e * pi_coef / a.rho[g];
     }
     __syncwarp();  // the group's shared memory is refilled by the next block
@@ -907,7 +907,19 @@ __global__ void __launch_bounds__(W * 32, fd_min_blocks<A, W>())
     owner_coords(c, ob, bx, by, bz);
     const BigCounts bc = fd_big_block<P, A, KIND>(c, k, a, qp4, cell_start, mrank, xmx, xmy, xmz, ob, bx, by, bz,
                                                   colour, seed, sweep, recs, rec_count, rec_cap, big_perm + ent.y);
-    n_tot += bc.tot; n_acc += bc.acc; n_rb += bc.rb; n_rm += bc.rm;
+    unsigned long long bt = bc.tot, ba = bc.acc, bb = bc.rb, bm = bc.rm;  // (rare: counted at once)
+    for (int s = 16; s > 0; s >>= 1) {
+      bt += __shfl_xor_sync(0xffffffffu, bt, s);
+      ba += __shfl_xor_sync(0xffffffffu, ba, s);
+      bb += __shfl_xor_sync(0xffffffffu, bb, s);
+      bm += __shfl_xor_sync(0xffffffffu, bm, s);
+    }
+    if (lane == 0 && bt) {
+      atomicAdd(&counters[0], bt);
+      atomicAdd(&counters[1], ba);
+      atomicAdd(&counters[2], bb);
+      atomicAdd(&counters[3], bm);
+    }
     negative |= bc.negative != 0;
     bad |= bc.bad != 0;
   }
@@ -921,19 +933,20 @@ __global__ void __launch_bounds__(W * 32, fd_min_blocks<A, W>())
     }
   }
   // counters
+  unsigned long long c_tot = n_tot, c_rb = n_rb, c_rm = n_rm, c_acc = n_tot - n_rb - n_rm;
   for (int s = 16; s > 0; s >>= 1) {
-    n_tot += __shfl_xor_sync(0xffffffffu, n_tot, s);
-    n_acc += __shfl_xor_sync(0xffffffffu, n_acc, s);
-    n_rb += __shfl_xor_sync(0xffffffffu, n_rb, s);
-    n_rm += __shfl_xor_sync(0xffffffffu, n_rm, s);
+    c_tot += __shfl_xor_sync(0xffffffffu, c_tot, s);
+    c_acc += __shfl_xor_sync(0xffffffffu, c_acc, s);
+    c_rb += __shfl_xor_sync(0xffffffffu, c_rb, s);
+    c_rm += __shfl_xor_sync(0xffffffffu, c_rm, s);
   }
   const unsigned any_neg = __any_sync(0xffffffffu, negative), any_bad = __any_sync(0xffffffffu, bad);
   if (lane == 0) {
-    if (n_tot) {
-      atomicAdd(&counters[0], n_tot);
-      atomicAdd(&counters[1], n_acc);
-      atomicAdd(&counters[2], n_rb);
-      atomicAdd(&counters[3], n_rm);
+    if (c_tot) {
+      atomicAdd(&counters[0], c_tot);
+      atomicAdd(&counters[1], c_acc);
+      atomicAdd(&counters[2], c_rb);
+      atomicAdd(&counters[3], c_rm);
     }
     if (any_neg) atomicOr(status, kStNegative);
     if (any_bad) atomicOr(status, kStNaN);

@@ -70,7 +70,7 @@ namespace sdpd {
 constexpr int kEnumThreads = 160;
 constexpr int kEnumWarps = kEnumThreads / 32;
 constexpr int kTriWords = 1152;   // >= F(255) = 1144: a triangle of 256 rows
-constexpr int kFlatEntries = 4096;  // group entries of one block (more: kHdrBig)
+constexpr int kFlatEntries = 2048;  // group entries of one block (more: kHdrBig)
 
 // words of the first rows of the triangular bitmap: F(n) = sum_{k=1..n} ceil(k/32)
 __device__ __forceinline__ int tri_f(int n) {
@@ -89,13 +89,13 @@ struct EnumSmem {
   uint32_t rcum[kMaxBlock];   // cumulative lengths after ranges 0, 1, 2 (bytes)
   uint8_t ncnt[kMaxBlock];    // entries of each member's group
   uint8_t dk[kMaxBlock];      // block cell of each member
-  int32_t gk[kMaxBlock];      // storage index of each member
+  int64_t lbase[kMaxBlock];   // nbr_slot(member, 0) with the slot's in-row part removed
+  uint8_t dtab[8][64];        // partner cell of (member cell, stencil code); 8: not in the block
   int32_t off[kMaxBlock + 1];  // first flat entry of each member
-  uint16_t rowoff[kMaxBlock];
   uint16_t rowbase[kMaxBlock];  // first word of each row of the bitmap
   int32_t wtot[kEnumWarps];     // per-warp totals of the offset scan
   int32_t ctot[8];              // row-scan chunk totals
-  int32_t cstart[8], cbase[9], koff[8];
+  int32_t cstart[8], cbase[9], koff[9];
   int32_t nb, big;
 };
 
@@ -139,7 +139,22 @@ __global__ void __launch_bounds__(kEnumThreads)
       sm.cbase[8] = cinc;
       sm.nb = cinc;
     }
-    if (lane == 0) sm.big = 0;
+    if (lane == 0) {
+      sm.big = 0;
+      sm.koff[8] = -(1 << 30);  // a partner outside the block: out of range
+    }
+  }
+  for (int q = t; q < 8 * 64; q += kEnumThreads) {  // partner cell: member cell + (code - 1) per axis
+    const int dA = q >> 6, code = q & 63;
+    int dB = 0;
+    bool in = true;
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+      const int f = (code >> (2 * ax)) & 3, b = ((dA >> ax) & 1) + f - 1;
+      in = in && f < 3 && b >= 0 && b <= 1;
+      dB |= (b & 1) << ax;
+    }
+    sm.dtab[dA][code] = (uint8_t)(in ? dB : 8);
   }
   __syncthreads();
   const int nb = sm.nb;
@@ -195,7 +210,7 @@ __global__ void __launch_bounds__(kEnumThreads)
     sm.off[k] = tot;  // the count; turned into an offset below
     sm.ncnt[k] = (uint8_t)tot;  // at most the row capacity
     sm.dk[k] = (uint8_t)d;
-    sm.gk[k] = g;
+    sm.lbase[k] = ((int64_t)(g >> 5) * (c.nbr_cap >> 2) << 7) + ((g & 31) << 2);
   }
   __syncthreads();
   if (sm.big) {
@@ -209,9 +224,7 @@ __global__ void __launch_bounds__(kEnumThreads)
   for (int L = 0; L < 3; ++L) {
     const int src = L & 1, dst = src ^ 1;
     for (int k = t; k < nb; k += kEnumThreads) {
-      int d = 0;
-#pragma unroll
-      for (int u = 1; u < 8; ++u) d += (k >= cb[u]);
+      const int d = sm.dk[k];
       const int run = d >> L, sib = run ^ 1;
       const int own0 = sm.cbase[run << L], m0 = sm.cbase[(run & ~1) << L];
       int pos = sm.cbase[sib << L], len = sm.cbase[(sib + 1) << L] - pos;
@@ -285,7 +298,7 @@ __global__ void __launch_bounds__(kEnumThreads)
     sm.rowbase[d] = (uint16_t)(tri_f(nb - 1) - tri_f(nb - d));
   __syncthreads();
   // the flat entries: partner, rank test, bit
-  const int E = sm.off[nb], cap = c.nbr_cap;
+  const int E = sm.off[nb];
 #pragma unroll 4
   for (int e = t; e < E; e += kEnumThreads) {
     const int A = sm.who[e];
@@ -295,12 +308,9 @@ __global__ void __launch_bounds__(kEnumThreads)
     const int q = (m >= c0) + (m >= c1) + (m >= c2);
     const int before = q == 0 ? 0 : (q == 1 ? c0 : (q == 2 ? c1 : c2));
     const int slot = (int)((rng >> (8 * q)) & 255u) + (m - before);
-    const int dA = sm.dk[A], gA = sm.gk[A];
-    const uint32_t en = __ldg(&nlist[nbr_slot(gA, slot, cap)]);
-    // partner cell in the block: dA plus the stencil offset (code - 1 per axis)
-    const int dB = ((dA & 1) + (int)(en & 3u) - 1) | ((((dA >> 1) & 1) + (int)((en >> 2) & 3u) - 1) << 1) |
-                   (((dA >> 2) + (int)((en >> 4) & 3u) - 1) << 2);
-    const int kB = (int)(en >> 6) + sm.koff[dB & 7];
+    const int dA = sm.dk[A];
+    const uint32_t en = __ldg(&nlist[sm.lbase[A] + ((slot >> 2) << 7) + (slot & 3)]);  // nbr_slot(g, slot)
+    const int kB = (int)(en >> 6) + sm.koff[sm.dtab[dA][en & 63u]];
     if ((unsigned)kB < (unsigned)nb) {
       const int rA = sm.rank[A], rB = sm.rank[kB];
       if (rB > rA) atomicOr(&sm.bits[sm.rowbase[rB - rA] + (rA >> 5)], 1u << (rA & 31));

@@ -220,6 +220,11 @@ int sdpd_energy_histogram(sdpd_t* s, double lo, double hi, int nbins, double sca
  *  SDPD_DEBUG_NCOUNT  int32[N]   number of neighbours j != i with r_ij < h, id order
  *  SDPD_DEBUG_PAIRS   sdpd_pair_rec[] of the last sweep (needs params.debug = 1),
  *                     one per pair in an order of the library's choosing
+ *  SDPD_DEBUG_BIG     uint32[8]  per colour, the 2x2x2 cell blocks that the
+ *                     latest sweep schedule left to the pair-by-pair sweep
+ *                     (beyond its capacities: more than 256 particles, 2048
+ *                     owned pairs or 255 dependency levels, or a member whose
+ *                     neighbour list overflowed its row; Sections 3.2-3.3)
  * dst: host memory, cap = capacity in elements; *count receives the number
  * of elements written.  The capacity is checked before anything is copied.
  * Errors: SDPD_ERR_INVALID_ARG (unknown what or too small cap),
@@ -230,6 +235,7 @@ int sdpd_energy_histogram(sdpd_t* s, double lo, double hi, int nbins, double sca
 #define SDPD_DEBUG_FORCE 3
 #define SDPD_DEBUG_NCOUNT 4
 #define SDPD_DEBUG_PAIRS 5
+#define SDPD_DEBUG_BIG 6
 
 typedef struct {
   int64_t id_i, id_j; /* id_i < id_j */

@@ -1291,6 +1291,13 @@ int debug_get(sdpd_handle* s, int what, void* dst, int64_t cap, int64_t* count) 
       if (r == SDPD_OK && (int64_t)n > s->w.pair_rec_cap) return SDPD_ERR_CAPACITY;
       return r;
     }
+    case SDPD_DEBUG_BIG: {
+      if (cap < 8) return SDPD_ERR_INVALID_ARG;
+      if (cudaMemcpyAsync(dst, s->w.big_count, 8 * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return SDPD_ERR_CUDA;
+      if (count) *count = 8;
+      return sdpd_sync(s);
+    }
     default:
       return SDPD_ERR_INVALID_ARG;
   }

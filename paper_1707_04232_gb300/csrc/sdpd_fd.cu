@@ -61,7 +61,8 @@ namespace sdpd {
 // ids and the particle of each rank.
 // Entries.  The members' entry counts are scanned into offsets of one flat
 // range, and the threads take its entries in turn, so that the global loads
-// are spread evenly and issued together.
+// are spread evenly and issued together (in chunks of kFlatEntries, the
+// size of the table of each entry's member).
 // Found pairs set bit rank(i) of row d = rank(j) - rank(i) of a triangular
 // bitmap (row d holds nb - d bits in whole words: it starts at word
 // F(nb - 1) - F(nb - d) with F(n) = sum_{k <= n} ceil(k / 32)), which is then
@@ -70,7 +71,7 @@ namespace sdpd {
 constexpr int kEnumThreads = 160;
 constexpr int kEnumWarps = kEnumThreads / 32;
 constexpr int kTriWords = 1152;   // >= F(255) = 1144: a triangle of 256 rows
-constexpr int kFlatEntries = 2048;  // group entries of one block (more: kHdrBig)
+constexpr int kFlatEntries = 2048;  // group entries of one block per chunk
 
 // words of the first rows of the triangular bitmap: F(n) = sum_{k=1..n} ceil(k/32)
 __device__ __forceinline__ int tri_f(int n) {
@@ -217,6 +218,30 @@ __global__ void __launch_bounds__(kEnumThreads)
     if (t == 0) hdr[o] = kHdrBig;
     return;
   }
+  // the member of each flat entry of the chunk [E0, E0 + kFlatEntries), in
+  // equal stretches per thread: one binary search for the stretch's first
+  // entry, then a walk (members without entries are skipped)
+  auto fill_who = [&](int E0) {
+    const int E = sm.off[nb], Ec = min(E - E0, kFlatEntries), per = (Ec + kEnumThreads - 1) / kEnumThreads;
+    const int e0 = E0 + t * per, e1 = min(E0 + Ec, e0 + per);
+    if (e0 < e1) {
+      int pos = 1, len = nb - 1;  // members 1 .. nb - 1 starting at or before e0
+      while (len > 0) {
+        const int half = len >> 1;
+        const bool le = sm.off[pos + half] <= e0;
+        pos = le ? pos + half + 1 : pos;
+        len = le ? len - half - 1 : half;
+      }
+      int k = pos - 1, kend = sm.off[k] + sm.ncnt[k];
+      for (int e = e0; e < e1; ++e) {
+        while (e >= kend) {
+          ++k;
+          kend = sm.off[k] + sm.ncnt[k];
+        }
+        sm.who[e - E0] = (uint8_t)k;
+      }
+    }
+  };
   // ranks: three rounds of pairwise merges of the sorted cells, interleaved
   // with the exclusive scan of the members' entry counts
   int cnt0 = 0, incl = 0;
@@ -261,33 +286,10 @@ __global__ void __launch_bounds__(kEnumThreads)
       if (2 * t < nb) sm.off[2 * t] = ex;
       if (2 * t + 1 < nb) sm.off[2 * t + 1] = ex + cnt0;
       if (t == 0) sm.off[nb] = total;
-      if (total > kFlatEntries && t == 0) sm.big = 1;
-    } else if (!sm.big) {  // the member of each flat entry, in equal stretches per thread
-      const int E = sm.off[nb], per = (E + kEnumThreads - 1) / kEnumThreads;
-      const int e0 = t * per, e1 = min(E, e0 + per);
-      if (e0 < e1) {
-        int pos = 1, len = nb - 1;  // members 1 .. nb - 1 starting at or before e0
-        while (len > 0) {
-          const int half = len >> 1;
-          const bool le = sm.off[pos + half] <= e0;
-          pos = le ? pos + half + 1 : pos;
-          len = le ? len - half - 1 : half;
-        }
-        int k = pos - 1, kend = sm.off[k] + sm.ncnt[k];
-        for (int e = e0; e < e1; ++e) {
-          while (e >= kend) {  // (members without entries are skipped)
-            ++k;
-            kend = sm.off[k] + sm.ncnt[k];
-          }
-          sm.who[e] = (uint8_t)k;
-        }
-      }
+    } else {  // the member of each entry of the first chunk
+      fill_who(0);
     }
     __syncthreads();
-  }
-  if (sm.big) {
-    if (t == 0) hdr[o] = kHdrBig;
-    return;
   }
   for (int r = t; r < nb; r += kEnumThreads) {  // the merged run is ids[1]
     const int k = sm.ks[1][r];
@@ -297,26 +299,34 @@ __global__ void __launch_bounds__(kEnumThreads)
   for (int d = 1 + t; d < nb; d += kEnumThreads)  // row d of the bitmap starts at F(nb - 1) - F(nb - d)
     sm.rowbase[d] = (uint16_t)(tri_f(nb - 1) - tri_f(nb - d));
   __syncthreads();
-  // the flat entries: partner, rank test, bit
+  // the flat entries: partner, rank test, bit; chunk by chunk (a block with
+  // more entries than the table holds takes several)
   const int E = sm.off[nb];
-#pragma unroll 4
-  for (int e = t; e < E; e += kEnumThreads) {
-    const int A = sm.who[e];
-    const int m = e - sm.off[A];
-    const uint32_t rng = sm.rng[A], cum = sm.rcum[A];
-    const int c0 = cum & 255u, c1 = (cum >> 8) & 255u, c2 = (cum >> 16) & 255u;
-    const int q = (m >= c0) + (m >= c1) + (m >= c2);
-    const int before = q == 0 ? 0 : (q == 1 ? c0 : (q == 2 ? c1 : c2));
-    const int slot = (int)((rng >> (8 * q)) & 255u) + (m - before);
-    const int dA = sm.dk[A];
-    const uint32_t en = __ldg(&nlist[sm.lbase[A] + ((slot >> 2) << 7) + (slot & 3)]);  // nbr_slot(g, slot)
-    const int kB = (int)(en >> 6) + sm.koff[sm.dtab[dA][en & 63u]];
-    if ((unsigned)kB < (unsigned)nb) {
-      const int rA = sm.rank[A], rB = sm.rank[kB];
-      if (rB > rA) atomicOr(&sm.bits[sm.rowbase[rB - rA] + (rA >> 5)], 1u << (rA & 31));
+  for (int E0 = 0; E0 < E; E0 += kFlatEntries) {
+    if (E0 > 0) {
+      fill_who(E0);
+      __syncthreads();
     }
+    const int E1 = min(E, E0 + kFlatEntries);
+#pragma unroll 4
+    for (int e = E0 + t; e < E1; e += kEnumThreads) {
+      const int A = sm.who[e - E0];
+      const int m = e - sm.off[A];
+      const uint32_t rng = sm.rng[A], cum = sm.rcum[A];
+      const int c0 = cum & 255u, c1 = (cum >> 8) & 255u, c2 = (cum >> 16) & 255u;
+      const int q = (m >= c0) + (m >= c1) + (m >= c2);
+      const int before = q == 0 ? 0 : (q == 1 ? c0 : (q == 2 ? c1 : c2));
+      const int slot = (int)((rng >> (8 * q)) & 255u) + (m - before);
+      const int dA = sm.dk[A];
+      const uint32_t en = __ldg(&nlist[sm.lbase[A] + ((slot >> 2) << 7) + (slot & 3)]);  // nbr_slot(g, slot)
+      const int kB = (int)(en >> 6) + sm.koff[sm.dtab[dA][en & 63u]];
+      if ((unsigned)kB < (unsigned)nb) {
+        const int rA = sm.rank[A], rB = sm.rank[kB];
+        if (rB > rA) atomicOr(&sm.bits[sm.rowbase[rB - rA] + (rA >> 5)], 1u << (rA & 31));
+      }
+    }
+    __syncthreads();
   }
-  __syncthreads();
   // row populations (rows 1 .. nb - 1): each warp scans 32 rows at a time
   // (row 1 + t is thread t's in every phase below), then the chunk totals
   // are added in

@@ -20,7 +20,7 @@ ERR_HOST_MEMORY = 11
 KERNEL_CUBIC, KERNEL_LUCY = 0, 1
 SCHEME_SSA, SCHEME_AMS, SCHEME_EMS, SCHEME_NONE = 0, 1, 2, 3
 FP64, MIXED = 0, 1
-DEBUG_ORDER, DEBUG_CELLS, DEBUG_RHO, DEBUG_FORCE, DEBUG_NCOUNT, DEBUG_PAIRS = range(6)
+DEBUG_ORDER, DEBUG_CELLS, DEBUG_RHO, DEBUG_FORCE, DEBUG_NCOUNT, DEBUG_PAIRS, DEBUG_BIG = range(7)
 
 
 class sdpd_params(C.Structure):
@@ -563,6 +563,13 @@ class SDPD:
     def neighbour_counts(self) -> np.ndarray:
         out = np.empty(self.N, dtype=np.int32)
         self._debug(DEBUG_NCOUNT, out, self.N)
+        return out
+
+    def big_blocks(self) -> np.ndarray:
+        """Per colour, the blocks of the latest sweep schedule swept pair by
+        pair (beyond the schedule's capacities)."""
+        out = np.empty(8, dtype=np.uint32)
+        self._debug(DEBUG_BIG, out, 8)
         return out
 
     def pair_records(self) -> np.ndarray:

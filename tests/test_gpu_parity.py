@@ -525,6 +525,26 @@ def test_capacity_overflow_sweep_matches_oracle():
 
 
 @pytest.mark.parametrize("precision", [sdpd.FP64, sdpd.MIXED])
+def test_uneven_lattice_blocks_stay_in_the_schedule(precision):
+    """On the 32^3 lattice (cell side 8/3: cells of 8 to 27 particles,
+    blocks of up to 216 with more owner-group entries than one chunk of the
+    enumeration's table) every block is scheduled in shared memory; the
+    dense cluster's blocks are the ones left to the pair-by-pair sweep."""
+    w = Workload(n=32, K=100.0, jitter=0.05, seed=3)
+    q, p, e = lattice_state(w)
+    s = gpu(w.N, (w.L,) * 3, w.K, precision=precision)
+    s.set_state(q, p, e)
+    s.step(DT, 1, seed=4)
+    assert s.observables()["status"] == sdpd.OK
+    assert s.big_blocks().sum() == 0
+    q, p, e, L, K = dense_cluster()
+    c = gpu(len(e), L, K, precision=precision)
+    c.set_state(q, p, e)
+    c.step(DT, 1, seed=4)
+    assert c.big_blocks().sum() > 0
+
+
+@pytest.mark.parametrize("precision", [sdpd.FP64, sdpd.MIXED])
 def test_capacity_overflow_steps_match_oracle(precision):
     """Full steps of the dense cluster: neighbour rows past 160 entries make
     the force pass walk the cells, and the cluster's blocks are swept pair

@@ -1,5 +1,6 @@
 // sdpd_api.cu -- the C ABI of include/sdpd.h: parameter checks, workspace
 // layout, cell tables, the time-step driver and the float64 observables.
+#include <float.h>
 #include <math.h>
 #include <string.h>
 
@@ -586,17 +587,24 @@ int sdpd_set_state(sdpd_t* s, const double* q, const double* p, const double* ep
   if (use_device(s) != SDPD_OK) return SDPD_ERR_CUDA;
   const int64_t N = s->c.N;
   if (N > 0 && (!q || !p || !eps)) return SDPD_ERR_INVALID_ARG;
-  if (!on_device) {
-    for (int64_t i = 0; i < N; ++i)
-      if (!(eps[i] > 0.0) || !isfinite(eps[i])) return SDPD_ERR_NONPOSITIVE_ENERGY;
-  }
   const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   int e = SDPD_OK;
   cudaStream_t st = s->stream;
+  // the copies go to staging buffers only, so they can start before the
+  // host check (which overlaps them for pinned memory): a rejected state
+  // launches no kernel and leaves the loaded state as it was
   if (N > 0) {
     e |= cuda_ok(cudaMemcpyAsync(s->w.io_q, q, (size_t)N * 3 * 8, kind, st));
     e |= cuda_ok(cudaMemcpyAsync(s->w.io_p, p, (size_t)N * 3 * 8, kind, st));
     e |= cuda_ok(cudaMemcpyAsync(s->w.io_e, eps, (size_t)N * 8, kind, st));
+  }
+  if (!on_device) {
+    int bad = 0;  // eps_i > 0 and finite (NaN fails both comparisons), without branches
+    for (int64_t i = 0; i < N; ++i) bad |= (int)!((eps[i] > 0.0) & (eps[i] <= DBL_MAX));
+    if (bad) {
+      if (cudaStreamSynchronize(st) != cudaSuccess) return SDPD_ERR_CUDA;  // the copies read the caller's memory
+      return SDPD_ERR_NONPOSITIVE_ENERGY;
+    }
   }
   e |= cuda_ok(cudaMemsetAsync(s->w.counters, 0, 4 * 8, st));
   e |= cuda_ok(cudaMemsetAsync(s->w.status, 0, 8, st));

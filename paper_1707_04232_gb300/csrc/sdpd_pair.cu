@@ -120,7 +120,7 @@ __device__ __forceinline__ int wrapc(int v, int n) { return v < 0 ? v + n : (v >
 // P = c_rho rho eps / (C_K m).
 // ---------------------------------------------------------------------------
 template <class P, int KIND>
-__global__ void __launch_bounds__(128) k_density(Consts c, Arrays<P> a, typename P::V4* __restrict__ qp4,
+__global__ void __launch_bounds__(128, P::mixed ? 12 : 1) k_density(Consts c, Arrays<P> a, typename P::V4* __restrict__ qp4,
                                                  const int32_t* __restrict__ cell_start,
                                                  const int32_t* __restrict__ mrank,
                                                  const uint32_t* __restrict__ xmx,

@@ -338,7 +338,7 @@ __device__ __forceinline__ void force_from_cells(const Consts& c, const Arrays<P
 // by the density pass) is left to k_force_overflow.
 // ---------------------------------------------------------------------------
 template <class P, int KIND>
-__global__ void __launch_bounds__(128) k_force(Consts c, Arrays<P> a, const typename P::V4* __restrict__ qp4,
+__global__ void __launch_bounds__(128, P::mixed ? (KIND == SDPD_KERNEL_LUCY ? 16 : 12) : 1) k_force(Consts c, Arrays<P> a, const typename P::V4* __restrict__ qp4,
                                                const int32_t* __restrict__ cell_start,
                                                const int32_t* __restrict__ mrank,
                                                const uint32_t* __restrict__ xmx,

@@ -158,8 +158,10 @@ int sdpd_get_state(sdpd_t* s, double* q, double* p, double* eps, int on_device);
  * counter (sweep number, min id, max id, 0).  Any local density completes:
  * a particle with more than 160 neighbours has its forces summed from the
  * cells instead of its list, and a block with more than 256 particles, 2048
- * owned pairs or 255 dependency levels is swept pair by pair in the same
- * order (slower, same result).  Asynchronous on the handle's stream.
+ * owned pairs or 255 dependency levels, or with a member of more than 160
+ * neighbours, is swept pair by pair in the same order (slower, same
+ * result; SDPD_DEBUG_BIG counts such blocks).  Asynchronous on the handle's
+ * stream.
  * Errors: SDPD_ERR_INVALID_ARG (dt <= 0, nsteps < 0), SDPD_ERR_NO_STATE,
  * SDPD_ERR_CUDA; device errors are sticky. */
 int sdpd_step(sdpd_t* s, double dt, int64_t nsteps, uint64_t seed);

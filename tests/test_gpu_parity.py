@@ -319,6 +319,28 @@ def test_trajectory_fp64_10_steps(kind, scheme, theta, kernel):
     assert obs["fd_step"] == nfd
 
 
+def test_trajectory_fp64_32k_lattice_3_steps():
+    """Full float64 steps (Verlet, schedule from the density pass's lists,
+    EMS sweep) on the 32^3 lattice: 216 blocks per colour, blocks of up to
+    216 particles whose owner groups take the enumeration several chunks,
+    against the oracle's 3 steps."""
+    q, p, e, L, K = system("lattice32k")
+    N = len(e)
+    s = gpu(N, L, K)
+    s.set_state(q, p, e)
+    s.step(DT, 3, seed=5)
+    qg, pg, eg = s.get_state()
+    obs = s.observables()
+    assert s.big_blocks().sum() == 0
+    P = oparams(N, L, K)
+    st, qo, po, eo, stats, nfd = O.run(P, q, p, e, DT, 3, seed=5)
+    assert st == O.OK
+    assert obs["n_pairs"] == stats.n_pairs and obs["n_accept"] == stats.n_accept
+    assert min_image_err(qg, qo, L) < 1e-9
+    assert np.abs(pg - po).max() < 1e-9 * max(1.0, np.abs(po).max())
+    assert np.abs(eg - eo).max() < 1e-9 * eo.max()
+
+
 def test_mts_sweeps_follow_the_step_count_not_the_call():
     """With theta = 5 a sweep follows every 5th Verlet step since
     set_state, however the steps are split over calls; the result equals the

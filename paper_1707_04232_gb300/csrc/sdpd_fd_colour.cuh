@@ -79,8 +79,8 @@ __device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
 // float32 with full relative precision (a fixed-point uniform would lose
 // the relative precision of the small values that the logarithms of
 // Box-Muller and of the Metropolis test magnify), the logarithm inside
-// Box-Muller accurate near 1 (log1p of u - 1), angles reduced to [-pi, pi)
-// for the hardware sine and cosine.
+// Box-Muller accurate near 1 (log1p of minus 1 - u, formed from the
+// integer), angles reduced to [-pi, pi) for the hardware sine and cosine.
 __device__ __forceinline__ float uniform53f(uint64_t w) {  // (top 53 bits + 1/2) 2^-53
   const uint64_t m = w >> 11;
   const float hi = (float)(uint32_t)(m >> 21), lo = (float)(uint32_t)(m & 0x1fffffull) + 0.5f;
@@ -89,20 +89,35 @@ __device__ __forceinline__ float uniform53f(uint64_t w) {  // (top 53 bits + 1/2
 __device__ __forceinline__ float uniform32f(uint32_t x) {  // (x + 1/2) 2^-32
   return ((float)x + 0.5f) * 2.3283064365386963e-10f;
 }
-__device__ __forceinline__ float box_muller_log(float u) { return u < 0.5f ? __logf(u) : fm::log1p(u - 1.0f); }
+// -2 ln u for the radius of Box-Muller.  Below 1/2 the logarithm of u
+// itself; above, log1p(-(1 - u)) with 1 - u = (c + 1/2) 2^-b formed from the
+// integer complement c = 2^b - 1 - m, because u rounded to float32 reaches
+// 1 for the largest m (and -2 ln u would then be 0 instead of ~2^-b).
+__device__ __forceinline__ float neg2log_u53(uint64_t w) {  // u = (top 53 bits m + 1/2) 2^-53
+  const uint64_t m = w >> 11;
+  if (m < (1ull << 52)) return -2.0f * __logf(uniform53f(w));
+  const uint64_t c = ((1ull << 53) - 1ull) - m;
+  const float t = __fmaf_rn((float)(uint32_t)(c >> 21), 2.3283064365386963e-10f,
+                            ((float)(uint32_t)(c & 0x1fffffull) + 0.5f) * 1.1102230246251565e-16f);
+  return -2.0f * fm::log1p(-t);
+}
+__device__ __forceinline__ float neg2log_u32(uint32_t x) {  // u = (x + 1/2) 2^-32
+  if (x < 0x80000000u) return -2.0f * __logf(uniform32f(x));
+  return -2.0f * fm::log1p(-(((float)(0xffffffffu - x) + 0.5f) * 2.3283064365386963e-10f));
+}
 __device__ __forceinline__ void pair_randoms_fast(uint64_t seed, uint64_t sweep, uint64_t idi, uint64_t idj,
                                                   float G[3], float* U) {
   uint64_t w[4];
   philox4x64_10(sweep, idi, idj, 0ull, seed, 0ull, w);
   const float twopi = 6.28318530717958647692f;
-  const float u0 = uniform53f(w[0]), u1 = uniform53f(w[1]);
-  const float R = fm::sqrt(-2.0f * box_muller_log(u0));
+  const float u1 = uniform53f(w[1]);
+  const float R = fm::sqrt(neg2log_u53(w[0]));
   float sn, cs;
   __sincosf(twopi * (u1 - 0.5f), &sn, &cs);  // the angle 2 pi u1 - pi
   G[0] = -R * cs;
   G[1] = -R * sn;
-  const float u2 = uniform32f((uint32_t)(w[2] >> 32)), u3 = uniform32f((uint32_t)(w[2] & 0xffffffffull));
-  G[2] = -fm::sqrt(-2.0f * box_muller_log(u2)) * __cosf(twopi * (u3 - 0.5f));
+  const float u3 = uniform32f((uint32_t)(w[2] & 0xffffffffull));
+  G[2] = -fm::sqrt(neg2log_u32((uint32_t)(w[2] >> 32))) * __cosf(twopi * (u3 - 0.5f));
   *U = uniform53f(w[3]);
 }
 __device__ __forceinline__ void pair_randoms_fast(uint64_t seed, uint64_t sweep, uint64_t idi, uint64_t idj,

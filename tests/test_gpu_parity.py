@@ -341,6 +341,24 @@ def test_trajectory_fp64_32k_lattice_3_steps():
     assert np.abs(eg - eo).max() < 1e-9 * eo.max()
 
 
+def test_mixed_sweep_never_rejects_where_the_bound_is_far():
+    """AMS rejects a move only at the energy bound, which no pair comes near
+    at K = 100, kT = 1 (eps ~ 150, changes ~ 1): the float64 path rejects
+    nothing there, and neither may the mixed path.  A uniform within 2^-25
+    of 1 rounds to 1 in float32; Box-Muller must still give a finite normal
+    (it once gave NaN, rejected as a bound violation, ~4e-8 of the pairs).
+    40 sweeps of the 64^3 lattice draw ~4e8 pairs."""
+    w = Workload(n=64, K=100.0, kT=1.0, jitter=0.05, seed=0)
+    q, p, e = lattice_state(w)
+    s = gpu(w.N, (w.L,) * 3, w.K, precision=sdpd.MIXED, scheme=sdpd.SCHEME_AMS)
+    s.set_state(q, p, e)
+    s.step(DT, 40, seed=7)
+    o = s.observables()
+    assert o["status"] == sdpd.OK
+    assert o["n_pairs"] > 3e8
+    assert o["n_reject_bound"] == 0 and o["n_reject_metropolis"] == 0
+
+
 def test_mts_sweeps_follow_the_step_count_not_the_call():
     """With theta = 5 a sweep follows every 5th Verlet step since
     set_state, however the steps are split over calls; the result equals the

@@ -251,9 +251,9 @@ FLOPS_PER_VISIT = {"density_eos": 18.0, "kick1_drift_bin": 24.0, "kick2": 24.0,
 FP64_NOMINAL_TFLOPS = 1.25  # GB300 float64, nominal
 # DRAM traffic of one colour launch of the mixed-precision sweep, per
 # particle: dram__bytes_read.sum + dram__bytes_write.sum of one launch at
-# N = 96^3 (50.22 MB + 3.30 MB), divided by the particles every colour
+# N = 96^3 (50.21 MB + 3.26 MB), divided by the particles every colour
 # launch visits once; a launch's traffic scales with N
-FD_COLOUR_DRAM_BYTES_PER_PARTICLE = (50.217472e6 + 3.299328e6) / 96 ** 3
+FD_COLOUR_DRAM_BYTES_PER_PARTICLE = (50.207488e6 + 3.262720e6) / 96 ** 3
 FLOPS_PER_PAIR_UPDATE = {"ems": 210.0, "ams": 150.0, "ssa": 140.0}
 
 
